@@ -1,0 +1,323 @@
+"""Seeded synthetic power grids and evaluation points.
+
+This module only draws data: network topology, line and bus parameters,
+generator costs, and random primal/dual/barrier points at which the NLP
+callbacks are evaluated.  It holds none of the method's arithmetic (no power
+flow, no derivatives, no assembly), so both the CUDA library and the CPU
+oracle may take their inputs from it.
+
+The recipe stands in for the pglib-opf ``goc``/``pegase`` cases the paper
+benchmarks (Section V.A), which are not available here:
+
+* topology: a uniformly random recursive spanning tree over a random bus
+  permutation, then unique random extra edges (no self-loops, no parallel
+  lines) up to the requested branch count;
+* branches: r ~ U(0.001, 0.05), x ~ U(0.01, 0.3), total charging b ~ U(0, 0.1),
+  tap 1 except U(0.95, 1.05) on 10 % of branches, shift 0,
+  rate_a ~ U(1, 5) p.u., angle-difference limits +-30 degrees;
+* buses: Pd ~ U(0, 1), Qd = 0.3 Pd, Gs = Bs = 0, Vm in [0.9, 1.1];
+* generators at distinct random buses: c2 ~ U(0, 0.1), c1 ~ U(10, 40), c0 = 0,
+  Pg in [0, Pmax] with Pmax ~ U(1, 5), Qg in [-Pmax/2, Pmax/2];
+  the bus of generator 0 is the (single) reference bus;
+* points: x uniform within its bounds (voltage angles, which are unbounded,
+  uniform in +-30 degrees; flows of unrated lines uniform in +-1), multipliers
+  y ~ N(0, 1), and the barrier diagonals Sigma_x, Sigma_s log-uniform in
+  [1e-8, 1e8].
+
+All draws use numpy's PCG64 through ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+REF_BUS_TYPE = 3
+
+
+@dataclasses.dataclass
+class Grid:
+    """Raw network data in per-unit, structure-of-arrays form.
+
+    Buses, branches and generators are numbered from 0.  A branch connects
+    its from-bus ``f`` to its to-bus ``t``; the tap ratio (0 read as 1) and
+    phase shift sit on the from side.
+    """
+
+    bus_type: np.ndarray
+    Pd: np.ndarray
+    Qd: np.ndarray
+    Gs: np.ndarray
+    Bs: np.ndarray
+    Vmin: np.ndarray
+    Vmax: np.ndarray
+    f: np.ndarray
+    t: np.ndarray
+    r: np.ndarray
+    x: np.ndarray
+    b: np.ndarray
+    tap: np.ndarray
+    shift: np.ndarray
+    rate_a: np.ndarray
+    angmin: np.ndarray
+    angmax: np.ndarray
+    gen_bus: np.ndarray
+    Pmin: np.ndarray
+    Pmax: np.ndarray
+    Qmin: np.ndarray
+    Qmax: np.ndarray
+    c2: np.ndarray
+    c1: np.ndarray
+    c0: np.ndarray
+    name: str = "grid"
+
+    @property
+    def n_bus(self) -> int:
+        return int(self.Pd.shape[0])
+
+    @property
+    def n_branch(self) -> int:
+        return int(self.f.shape[0])
+
+    @property
+    def n_gen(self) -> int:
+        return int(self.gen_bus.shape[0])
+
+    @property
+    def n_ref(self) -> int:
+        return int(np.count_nonzero(self.bus_type == REF_BUS_TYPE))
+
+    @property
+    def n_var(self) -> int:
+        """Length of x: va, vm per bus; pg, qg per generator; p, q per arc."""
+        return 2 * self.n_bus + 2 * self.n_gen + 4 * self.n_branch
+
+    @property
+    def n_con(self) -> int:
+        """Length of g: reference rows, 7 rows per branch, 2 balance rows per bus."""
+        return self.n_ref + 7 * self.n_branch + 2 * self.n_bus
+
+    def copy(self) -> "Grid":
+        return dataclasses.replace(
+            self, **{fl.name: np.array(getattr(self, fl.name), copy=True)
+                     for fl in dataclasses.fields(self) if fl.name != "name"})
+
+    def nbytes(self) -> int:
+        return sum(getattr(self, fl.name).nbytes
+                   for fl in dataclasses.fields(self) if fl.name != "name")
+
+
+@dataclasses.dataclass
+class Point:
+    """One evaluation point: primal x, multipliers y, barrier diagonals."""
+
+    x: np.ndarray
+    y: np.ndarray
+    sigma_x: np.ndarray
+    sigma_s: np.ndarray
+    obj_weight: float = 1.0
+    delta_w: float = 0.0
+    delta_c: float = 0.0
+
+
+def _random_topology(rng: np.random.Generator, n_bus: int, n_branch: int):
+    if n_bus < 2:
+        raise ValueError("need at least 2 buses")
+    if n_branch < n_bus - 1:
+        raise ValueError("need at least n_bus - 1 branches for a spanning tree")
+    max_edges = n_bus * (n_bus - 1) // 2
+    if n_branch > max_edges:
+        raise ValueError("more branches than distinct bus pairs")
+    perm = rng.permutation(n_bus)
+    k = np.arange(1, n_bus, dtype=np.float64)
+    parent_pos = np.minimum(np.floor(rng.random(n_bus - 1) * k).astype(np.int64),
+                            np.arange(0, n_bus - 1))
+    a = perm[1:].astype(np.int64)
+    b = perm[parent_pos].astype(np.int64)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keys = lo * n_bus + hi
+    need = n_branch - (n_bus - 1)
+    while need > 0:
+        cand_a = rng.integers(0, n_bus, size=2 * need + 16)
+        cand_b = rng.integers(0, n_bus, size=2 * need + 16)
+        ok = cand_a != cand_b
+        clo = np.minimum(cand_a, cand_b)[ok]
+        chi = np.maximum(cand_a, cand_b)[ok]
+        ck = clo * n_bus + chi
+        _, first = np.unique(ck, return_index=True)
+        ck = ck[np.sort(first)]
+        ck = ck[~np.isin(ck, keys)][:need]
+        keys = np.concatenate([keys, ck])
+        need -= ck.shape[0]
+    lo = keys // n_bus
+    hi = keys % n_bus
+    swap = rng.random(keys.shape[0]) < 0.5
+    f = np.where(swap, hi, lo)
+    t = np.where(swap, lo, hi)
+    order = rng.permutation(keys.shape[0])
+    return f[order].astype(np.int32), t[order].astype(np.int32)
+
+
+def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
+              name: str | None = None) -> Grid:
+    """Synthetic grid with the recipe of the module docstring."""
+    if not 1 <= n_gen <= n_bus:
+        raise ValueError("need 1 <= n_gen <= n_bus")
+    rng = np.random.default_rng(seed)
+    f, t = _random_topology(rng, n_bus, n_branch)
+    nl = f.shape[0]
+    r = rng.uniform(0.001, 0.05, nl)
+    x = rng.uniform(0.01, 0.3, nl)
+    b = rng.uniform(0.0, 0.1, nl)
+    tap = np.ones(nl)
+    tapped = rng.random(nl) < 0.1
+    tap[tapped] = rng.uniform(0.95, 1.05, int(tapped.sum()))
+    shift = np.zeros(nl)
+    rate_a = rng.uniform(1.0, 5.0, nl)
+    ang = math.pi / 6.0
+    angmin = np.full(nl, -ang)
+    angmax = np.full(nl, ang)
+
+    Pd = rng.uniform(0.0, 1.0, n_bus)
+    Qd = 0.3 * Pd
+    Gs = np.zeros(n_bus)
+    Bs = np.zeros(n_bus)
+    Vmin = np.full(n_bus, 0.9)
+    Vmax = np.full(n_bus, 1.1)
+
+    gen_bus = rng.choice(n_bus, size=n_gen, replace=False).astype(np.int32)
+    Pmax = rng.uniform(1.0, 5.0, n_gen)
+    Pmin = np.zeros(n_gen)
+    Qmax = 0.5 * Pmax
+    Qmin = -0.5 * Pmax
+    c2 = rng.uniform(0.0, 0.1, n_gen)
+    c1 = rng.uniform(10.0, 40.0, n_gen)
+    c0 = np.zeros(n_gen)
+
+    bus_type = np.ones(n_bus, dtype=np.int32)
+    bus_type[gen_bus] = 2
+    bus_type[gen_bus[0]] = REF_BUS_TYPE
+    return Grid(bus_type=bus_type, Pd=Pd, Qd=Qd, Gs=Gs, Bs=Bs, Vmin=Vmin, Vmax=Vmax,
+                f=f, t=t, r=r, x=x, b=b, tap=tap, shift=shift, rate_a=rate_a,
+                angmin=angmin, angmax=angmax, gen_bus=gen_bus, Pmin=Pmin, Pmax=Pmax,
+                Qmin=Qmin, Qmax=Qmax, c2=c2, c1=c1, c0=c0,
+                name=name or f"synthetic-{n_bus}bus-seed{seed}")
+
+
+def make_edge_case_grid(seed: int = 7) -> Grid:
+    """Small grid carrying every structural corner the formulation has.
+
+    Starting from a 24-bus synthetic grid it adds: parallel branches (two and
+    three lines between the same buses, in both orientations), a bus with
+    three generators, an isolated bus (no branches, one generator), a second
+    reference bus, nonzero phase shifts, a tap given as 0 (meaning 1),
+    unrated lines (rate_a = 0), and nonzero bus shunts Gs, Bs.
+    """
+    rng = np.random.default_rng(seed)
+    g = make_grid(24, 34, 5, seed)
+    nb = g.n_bus + 1                      # bus 24 is isolated
+    iso = nb - 1
+
+    def ext(a, v):
+        return np.concatenate([a, np.asarray(v, dtype=a.dtype)])
+
+    bus_type = ext(g.bus_type, [1])
+    other_ref = int(np.flatnonzero(bus_type != REF_BUS_TYPE)[3])
+    bus_type[other_ref] = REF_BUS_TYPE
+    Pd = ext(g.Pd, [0.4])
+    Qd = ext(g.Qd, [0.1])
+    Gs = rng.uniform(-0.05, 0.05, nb)
+    Bs = rng.uniform(-0.2, 0.2, nb)
+    Vmin = ext(g.Vmin, [0.9])
+    Vmax = ext(g.Vmax, [1.1])
+
+    # parallel lines: duplicate branches 0, 1 (reversed) and 2 (twice)
+    dup = [0, 1, 2, 2]
+    f = ext(g.f, [g.f[0], g.t[1], g.f[2], g.t[2]])
+    t = ext(g.t, [g.t[0], g.f[1], g.t[2], g.f[2]])
+    nl = f.shape[0]
+    r = ext(g.r, rng.uniform(0.001, 0.05, len(dup)))
+    x = ext(g.x, rng.uniform(0.01, 0.3, len(dup)))
+    b = ext(g.b, rng.uniform(0.0, 0.1, len(dup)))
+    tap = ext(g.tap, [1.02, 0.97, 1.0, 0.0])
+    tap[5] = 0.0
+    tap[6] = 1.04
+    shift = np.zeros(nl)
+    shift[[3, 6, nl - 2]] = [0.05, -0.08, 0.03]
+    rate_a = ext(g.rate_a, rng.uniform(1.0, 5.0, len(dup)))
+    rate_a[[4, 9]] = 0.0
+    angmin = ext(g.angmin, [-math.pi / 6] * len(dup))
+    angmax = ext(g.angmax, [math.pi / 6] * len(dup))
+
+    bus3 = int(g.gen_bus[1])
+    gen_bus = ext(g.gen_bus, [bus3, bus3, iso])
+    ng = gen_bus.shape[0]
+    Pmax = ext(g.Pmax, rng.uniform(1.0, 5.0, 3))
+    Pmin = np.zeros(ng)
+    Qmax = 0.5 * Pmax
+    Qmin = -0.5 * Pmax
+    c2 = ext(g.c2, rng.uniform(0.0, 0.1, 3))
+    c1 = ext(g.c1, rng.uniform(10.0, 40.0, 3))
+    c0 = ext(g.c0, rng.uniform(0.0, 5.0, 3))
+    return Grid(bus_type=bus_type, Pd=Pd, Qd=Qd, Gs=Gs, Bs=Bs, Vmin=Vmin, Vmax=Vmax,
+                f=f, t=t, r=r, x=x, b=b, tap=tap, shift=shift, rate_a=rate_a,
+                angmin=angmin, angmax=angmax, gen_bus=gen_bus, Pmin=Pmin, Pmax=Pmax,
+                Qmin=Qmin, Qmax=Qmax, c2=c2, c1=c1, c0=c0,
+                name=f"edge-cases-seed{seed}")
+
+
+def scale_loads(grid: Grid, seed: int, lo: float = 0.9, hi: float = 1.1) -> Grid:
+    """Load scenario: every bus's Pd (and Qd) scaled by its own U(lo, hi) draw."""
+    rng = np.random.default_rng(seed)
+    out = grid.copy()
+    s = rng.uniform(lo, hi, grid.n_bus)
+    out.Pd = grid.Pd * s
+    out.Qd = grid.Qd * s
+    out.name = f"{grid.name}-load{seed}"
+    return out
+
+
+def make_point(grid: Grid, seed: int, *, obj_weight: float = 1.0,
+               delta_w: float = 0.0, delta_c: float = 0.0) -> Point:
+    """Random evaluation point.
+
+    x is laid out as [va (n_bus), vm (n_bus), pg (n_gen), qg (n_gen),
+    p (2 n_branch), q (2 n_branch)], arcs 0..n_branch-1 being the from ends
+    and n_branch..2 n_branch-1 the to ends of the branches.
+    """
+    rng = np.random.default_rng(seed)
+    nb, ng, nl = grid.n_bus, grid.n_gen, grid.n_branch
+    ang = math.pi / 6.0
+    va = rng.uniform(-ang, ang, nb)
+    vm = rng.uniform(grid.Vmin, grid.Vmax)
+    pg = rng.uniform(grid.Pmin, grid.Pmax)
+    qg = rng.uniform(grid.Qmin, grid.Qmax)
+    rate = np.where(grid.rate_a > 0, grid.rate_a, 1.0)
+    rate2 = np.concatenate([rate, rate])
+    p = rng.uniform(-rate2, rate2)
+    q = rng.uniform(-rate2, rate2)
+    x = np.concatenate([va, vm, pg, qg, p, q])
+    y = rng.standard_normal(grid.n_con)
+    sigma_x = 10.0 ** rng.uniform(-8.0, 8.0, grid.n_var)
+    sigma_s = 10.0 ** rng.uniform(-8.0, 8.0, grid.n_con)
+    return Point(x=x, y=y, sigma_x=sigma_x, sigma_s=sigma_s,
+                 obj_weight=obj_weight, delta_w=delta_w, delta_c=delta_c)
+
+
+# The workloads used by the tests and the benchmark, by size.
+WORKLOADS = {
+    "30bus": dict(n_bus=30, n_branch=41, n_gen=6, seed=1000),
+    "10kbus": dict(n_bus=10_000, n_branch=13_500, n_gen=2_000, seed=1001),
+    "80kbus": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1002),
+}
+
+
+def workload_grid(name: str) -> Grid:
+    spec = WORKLOADS[name]
+    return make_grid(spec["n_bus"], spec["n_branch"], spec["n_gen"], spec["seed"],
+                     name=f"synthetic-{name}")
+
+
+def point_seed(grid_seed: int, call_index: int) -> int:
+    return grid_seed * 7919 + call_index
