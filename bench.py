@@ -1,0 +1,426 @@
+"""Benchmark: ACOPF evaluate-and-assemble calls per second on GB300.
+
+One step is one call of the fused unit of work of an IPM iteration (objective,
+gradient, constraints, sparse Jacobian, Lagrangian Hessian and the condensed
+KKT matrix W + Sigma_x + A'DA) on the 80,000-bus / 110,000-branch / 12,000-
+generator synthetic grid, at a fresh random point, inputs resident in HBM.
+Input and output buffers rotate over 4 sets (about 110 MB each, 4 x 110 MB >
+the 129 MB L2), so no call finds its data in L2 from the previous one.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(instances shard with no collective): the barrier and max-over-ranks timing
+bracket the timed steps and `value` counts the calls of all ranks.
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2307_16830_gb300 import synth  # noqa: E402
+
+METRIC = "eval+KKT-assembly calls/s and % HBM roofline; served p50/p99 vs plain launches"
+UNIT = "calls/s"
+ROTATE = 4
+
+# DRAM traffic (read + write bytes) per launch of the fused phase-1 kernel on
+# the 80k-bus workload, from `ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum` (see profiles/), valid for the kernels.cu whose hash
+# is recorded with it; reported as null once the kernel source changes.
+NCU_TRAFFIC = {"kernels_sha": None, "phase1_bytes": None, "phase2_bytes": None}
+
+
+def kernels_sha() -> str:
+    p = os.path.join(ROOT, "paper_2307_16830_gb300", "csrc", "kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                parts = [p.strip() for p in out.stdout.strip().split(",")]
+                if len(parts) >= 8:
+                    self.samples.append((time.time(), parts))
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def start(self):
+        self._t.start()
+        return self
+
+    def stop(self):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(p[0]) for _, p in self.samples if p[0].replace(".", "").isdigit()]
+        mx = [float(p[1]) for _, p in self.samples if p[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in self.samples:
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes and FP64 flops
+# ---------------------------------------------------------------------------
+def workload_sizes(model, grid):
+    nb, nl, ng = grid.n_bus, grid.n_branch, grid.n_gen
+    return dict(nb=nb, nl=nl, ng=ng, n=model.n, m=model.m, nnzj=model.nnz_jac,
+                nnzh=model.nnz_hess, nnzk=model.nnz_kkt)
+
+
+def algorithmic_bytes(s):
+    """Compulsory bytes of one call: inputs read once, model data read once,
+    outputs written once (index metadata excluded)."""
+    inputs = 8 * (2 * s["n"] + 2 * s["m"])
+    model = 72 * s["nl"] + 32 * s["nb"] + 28 * s["ng"]
+    outputs = 8 * (1 + s["n"] + s["m"] + s["nnzj"] + s["nnzh"] + s["nnzk"])
+    return inputs + model + outputs
+
+
+def phase1_bytes(s, kkt_arc_gen):
+    """Compulsory bytes of the phase-1 kernel (branch and generator threads):
+    branch and generator model data; x of the buses' va/vm (read once), of
+    the generators and arcs; y and Sigma_s of the branch rows; Sigma_x of the
+    arc and generator variables; outputs it writes (branch constraint rows,
+    all Jacobian and Hessian entries but the bus terms, gradient of arc and
+    generator variables, and the arc and generator rows of M_cond)."""
+    nb, nl, ng = s["nb"], s["nl"], s["ng"]
+    reads = 72 * nl + 28 * ng + 8 * (2 * nb + 2 * ng + 4 * nl) + 8 * (6 * nl + 7 * nl) \
+        + 8 * (2 * nb) + 8 * (4 * nl + 2 * ng)
+    writes = 8 * (7 * nl + (30 * nl + 2 * ng) + (14 * nl + ng) + (4 * nl + 2 * ng) + kkt_arc_gen)
+    return reads + writes
+
+
+# FP64 flops per unit of the phase-1 kernel (FMA = 2), counted from the
+# kernel's arithmetic on the fused path without regularisation; the sincos
+# pair is counted as the 2 x 11 FMA of a degree-11 polynomial pair after a
+# 3-FMA argument reduction.
+FLOPS_PER_BRANCH = 2 * 3 + 2 * 2 * 11 + 262
+FLOPS_PER_GEN = 11
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    grid = synth.workload_grid(args.workload)
+    seed = synth.WORKLOADS[args.workload]["seed"]
+    model = acopf.model_create(grid, local)
+    s = workload_sizes(model, grid)
+    stream = torch.cuda.Stream(device=dev)
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sets = []
+    for r in range(ROTATE):
+        pt = synth.make_point(grid, synth.point_seed(seed, 1000 * rank + r))
+        sets.append(dict(
+            x=t(pt.x), y=t(pt.y), sx=t(pt.sigma_x), ss=t(pt.sigma_s),
+            f=torch.empty(1, dtype=torch.float64, device=dev),
+            grad=torch.empty(model.n, dtype=torch.float64, device=dev),
+            cons=torch.empty(model.m, dtype=torch.float64, device=dev),
+            jac=torch.empty(model.nnz_jac, dtype=torch.float64, device=dev),
+            hess=torch.empty(model.nnz_hess, dtype=torch.float64, device=dev),
+            kkt=torch.empty(model.nnz_kkt, dtype=torch.float64, device=dev)))
+
+    def step(k):
+        b = sets[k % ROTATE]
+        acopf.eval_assemble(model, b["x"], b["y"], 1.0, b["sx"], b["ss"], 0.0, 0.0, b["f"],
+                            b["grad"], b["cons"], b["jac"], b["hess"], b["kkt"], stream=stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local).start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        # keep the GPU busy long enough for the clock sampler to see the load
+        soak_end = time.time() + args.soak
+        k = 0
+        while k < args.warmup or time.time() < soak_end:
+            step(k)
+            k += 1
+            if k % 256 == 0:
+                stream.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        e1.record(stream)
+        barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        v = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        ms_max = float(v.item())
+    value = world * args.steps / (ms_max * 1e-3)
+
+    # per-phase durations (separate pass, events between the phases)
+    nprof = max(16, min(args.steps, 512))
+    with torch.cuda.stream(stream):
+        acopf.profile_begin(model, nprof)
+        for k in range(nprof):
+            step(k)
+        calls, p1, p2, tot = acopf.profile_end(model)
+    p1_ms, p2_ms, call_ms = p1 / calls, p2 / calls, tot / calls
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        hs = []
+        for r in range(2):
+            pt = synth.make_point(grid, synth.point_seed(seed, 5000 + 1000 * rank + r))
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+            hs.append(dict(x=pin(pt.x), y=pin(pt.y), sx=pin(pt.sigma_x), ss=pin(pt.sigma_s),
+                           out=[torch.empty(nn, dtype=torch.float64).pin_memory() for nn in
+                                (1, model.n, model.m, model.nnz_jac, model.nnz_hess,
+                                 model.nnz_kkt)]))
+
+        def hstep(k):
+            b = hs[k % 2]
+            acopf.eval_assemble_host(model, b["x"], b["y"], 1.0, b["sx"], b["ss"], 0.0, 0.0,
+                                     *b["out"], stream=stream)
+
+        for k in range(3):
+            hstep(k)
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            hstep(k)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            v = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            dt = float(v.item())
+        e2e = {"value": world * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (2 * model.n + 2 * model.m),
+               "d2h_bytes_per_step": 8 * (1 + model.n + model.m + model.nnz_jac
+                                          + model.nnz_hess + model.nnz_kkt)}
+
+    fp64_gflops = acopf.measure_fp64_gflops(local)
+    rp, _ = model.kkt_structure()
+    kkt_bus_rows = int(rp[model.n_bus * 2] - rp[0])
+    kkt_arc_gen = model.nnz_kkt - kkt_bus_rows
+    res = dict(value=value, ms=ms_max, p1_ms=p1_ms, p2_ms=p2_ms, call_ms=call_ms, e2e=e2e,
+               clocks=clocks.summary(), sizes=s, fp64_gflops=fp64_gflops,
+               kkt_arc_gen=kkt_arc_gen, gpu=torch.cuda.get_device_name(dev))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    model.close()
+    return res
+
+
+def cpu_baseline_sample(workload: str, calls: int):
+    import oracle
+    grid = synth.workload_grid(workload)
+    seed = synth.WORKLOADS[workload]["seed"]
+    st = oracle.kkt_structure(grid)
+    pts = [synth.make_point(grid, synth.point_seed(seed, 9000 + k)) for k in range(calls)]
+    t0 = time.perf_counter()
+    for pt in pts:
+        oracle.eval_assemble(grid, pt, structure=st)
+    dt = time.perf_counter() - t0
+    return calls / dt, dt
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: each step is one oracle call on the
+    10,000-bus grid of the same generator (a bounded sample); calls/s are
+    converted to 80,000-bus calls with the measured ratio of one 10k to one
+    80k oracle call."""
+    if rank != 0:
+        return
+    import oracle
+    full = synth.workload_grid(args.workload)
+    sample = synth.workload_grid("10kbus")
+    st_full = oracle.kkt_structure(full)
+    st_s = oracle.kkt_structure(sample)
+    pf = synth.make_point(full, 1)
+    ps = [synth.make_point(sample, synth.point_seed(1001, k)) for k in range(4)]
+    t0 = time.perf_counter()
+    oracle.eval_assemble(full, pf, structure=st_full)
+    t_full = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.eval_assemble(sample, ps[0], structure=st_s)
+    t_s = time.perf_counter() - t0
+    for k in range(args.warmup):
+        oracle.eval_assemble(sample, ps[k % 4], structure=st_s)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.eval_assemble(sample, ps[k % 4], structure=st_s)
+    dt = time.perf_counter() - t0
+    ratio = t_s / t_full
+    value = args.steps / dt * ratio
+    sample_desc = (f"{args.steps} oracle calls on the 10,000-bus grid, converted to 80,000-bus "
+                   f"calls by the measured per-call time ratio {ratio:.4f} "
+                   f"(one 80k call {t_full:.2f} s)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: 80,000 buses, 110,000 branches, 12,000 gens",
+                       "oracle": "numpy/scipy FP64, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="80kbus", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-calls", type=int, default=3)
+    ap.add_argument("--soak", type=float, default=1.0,
+                    help="seconds of untimed calls (at least --warmup) before timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    r = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and args.cpu_calls > 0:
+        v, dt = cpu_baseline_sample(args.workload, args.cpu_calls)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_calls} full {args.workload} oracle calls ({dt:.1f} s)"}
+    s = r["sizes"]
+    # roofline of the dominant kernel (phase 1)
+    p1_s = r["p1_ms"] * 1e-3
+    flops = FLOPS_PER_BRANCH * s["nl"] + FLOPS_PER_GEN * s["ng"]
+    by1 = phase1_bytes(s, r["kkt_arc_gen"])
+    ach_flops = flops / p1_s / 1e12
+    peak_flops = r["fp64_gflops"] / 1e3
+    ach_bw = by1 / p1_s / 1e9
+    hbm_peak = 6772.9
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    traffic = None
+    if NCU_TRAFFIC["kernels_sha"] == kernels_sha():
+        traffic = NCU_TRAFFIC["phase1_bytes"]
+    fp64_frac = ach_flops / peak_flops
+    hbm_frac = ach_bw / hbm_peak
+    if fp64_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": ach_flops, "peak": peak_flops, "unit": "TFLOP/s",
+                "frac": fp64_frac, "traffic": traffic,
+                "kernel": "k_phase1 (branch + generator threads)",
+                "peak_source": "FP64 FMA throughput measured live by acopf_measure_fp64_gflops",
+                "hbm_view": {"achieved_gbs": ach_bw, "peak_gbs": hbm_peak, "frac": hbm_frac}}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": traffic,
+                "kernel": "k_phase1 (branch + generator threads)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "fp64_view": {"achieved_tflops": ach_flops, "peak_tflops": peak_flops,
+                              "frac": fp64_frac}}
+    call_bytes = algorithmic_bytes(s)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: synthetic grid, {s['nb']} buses, {s['nl']} "
+                               f"branches, {s['ng']} generators; one call = obj+grad+cons+jac+"
+                               f"hess+condensed KKT at a fresh point",
+                   "n": s["n"], "m": s["m"], "nnz_jac": s["nnzj"], "nnz_hess": s["nnzh"],
+                   "nnz_kkt": s["nnzk"], "parallelism": f"replicas x{world}",
+                   "l2": f"inputs/outputs rotate over {ROTATE} sets of "
+                         f"{call_bytes / 1e6:.0f} MB (> 129 MB L2 together)"},
+        "hbm_roofline_call": {"algorithmic_bytes": call_bytes,
+                              "achieved_gbs": call_bytes / (r["ms"] / args.steps * 1e-3) / 1e9,
+                              "frac": call_bytes / (r["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak},
+        "phases_ms": {"phase1": r["p1_ms"], "phase2": r["p2_ms"], "call": r["call_ms"]},
+        "clocks": r["clocks"], "e2e": r["e2e"],
+        "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cpu,
+        "gpu": r["gpu"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * acopf.h - C ABI of libacopf: GB300-native (sm_103a, FP64) evaluation of the
+ * AC optimal power flow NLP callbacks and numeric assembly of the condensed
+ * KKT matrix of a condensed-space interior-point method.
+ *
+ * Paper: S. Shin, F. Pacaud, M. Anitescu, "Accelerating Optimal Power Flow
+ * with GPUs: SIMD Abstraction of Nonlinear Programs and Condensed-Space
+ * Interior-Point Methods" (arXiv 2307.16830).
+ *
+ * Formulation (the paper lists the 15 computational patterns of the ACOPF
+ * model in Sec. III.B but does not print the equations; the polar
+ * branch-flow form below is the model its experiments use, Sec. V.A):
+ *
+ *   variables  x = [va (nb), vm (nb), pg (ng), qg (ng), p (2 nl), q (2 nl)]
+ *              arc a < nl is the from end of branch a, arc nl + l the to end
+ *              of branch l;
+ *   constraints g = [ref (one per bus of type 3), pf, qf, pt, qt, ang, sf, st
+ *              (one each per branch), Pbal, Qbal (one each per bus)] with
+ *     ref  = va_i                         pf = p_l - P_f      qf = q_l - Q_f
+ *     pt   = p_{nl+l} - P_t               qt = q_{nl+l} - Q_t
+ *     ang  = va_f - va_t                  sf = p_l^2 + q_l^2  st = p_{nl+l}^2 + q_{nl+l}^2
+ *     Pbal = Pd + Gs vm^2 - sum_{gens at i} pg + sum_{arcs at i} p_a
+ *     Qbal = Qd - Bs vm^2 - sum_{gens at i} qg + sum_{arcs at i} q_a
+ *   where (P_f, Q_f, P_t, Q_t) are the pi-model branch flows with series
+ *   admittance 1/(r + jx), total charging b split half per end and a complex
+ *   tap tau e^{j shift} on the from side (tau = 0 is read as 1);
+ *   objective f = sum_g c2 pg^2 + c1 pg + c0.
+ *
+ * Sparse outputs, with the fixed orders that the *_structure calls return:
+ *   Jacobian A = dg/dx in COO: ref rows; pf rows [p_l, va_f, va_t, vm_f, vm_t]
+ *     per branch; qf [q_l, ...]; pt [p_{nl+l}, ...]; qt [q_{nl+l}, ...];
+ *     ang [va_f, va_t]; sf [p_l, q_l]; st [p_{nl+l}, q_{nl+l}]; balance vm
+ *     terms (all Pbal rows, then all Qbal rows); generator terms (Pbal then
+ *     Qbal, per generator); arc terms (Pbal then Qbal, per arc).
+ *   Lagrangian Hessian W = sigma d2f + sum_r y_r d2g_r, lower triangle in COO
+ *     with duplicates: per branch the 10 entries of its (va_f, va_t, vm_f,
+ *     vm_t) block in the order (va_f,va_f) (va_t,va_f) (va_t,va_t)
+ *     (vm_f,va_f) (vm_f,va_t) (vm_f,vm_f) (vm_t,va_f) (vm_t,va_t) (vm_t,vm_f)
+ *     (vm_t,vm_t), each stored (max, min) of the global indices; then per
+ *     branch the diagonals of p_l, q_l, p_{nl+l}, q_{nl+l}; then (pg,pg) per
+ *     generator; then (vm,vm) per bus.  The sign convention adds y_r g_r: the
+ *     paper's L = f - y'g (Sec. II.A) is obtained by passing -y.
+ *   Condensed KKT matrix M_cond = W + delta_w I + Sigma_x + A' D A with
+ *     C = (delta_c Sigma_s + (1 + delta_c delta_w) I)^-1, D = (Sigma_s +
+ *     delta_w I) C (Sec. IV.C), lower triangle in CSR: rows ascending,
+ *     columns ascending within a row, every diagonal present, the pattern
+ *     being the structural union of W, the diagonal and A'A.
+ *
+ * Conventions.  Indices are 0-based int32.  Host arrays passed to
+ * acopf_model_create are copied; the caller keeps ownership of everything it
+ * passes.  Every eval / assemble call takes DEVICE pointers to caller-owned
+ * memory (for instance torch tensors) on the model's device, is asynchronous
+ * on `stream` (NULL = the legacy default stream), never synchronises the
+ * host and never allocates.  Outputs are fully overwritten.  Calls on one
+ * model share the model's scratch (per-branch partial sums of the KKT
+ * assembly): calls on the same model must not overlap on the GPU, so issue
+ * them on one stream (or order them with events); different models are
+ * independent.  No CPU fallback exists: without a usable device every
+ * compute call returns ACOPF_E_CUDA or ACOPF_E_NO_DEVICE.
+ * No call throws; errors are returned as acopf_status, with a message
+ * readable through acopf_last_error() on the calling thread.
+ */
+#ifndef ACOPF_H_
+#define ACOPF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* acopf_stream;
+
+typedef int32_t acopf_status;
+#define ACOPF_OK 0
+#define ACOPF_E_INVALID_ARG (-1) /* null pointer, negative size, wrong model kind */
+#define ACOPF_E_BAD_MODEL (-2)   /* network data rejected by validation */
+#define ACOPF_E_CUDA (-3)        /* a CUDA runtime call or launch failed */
+#define ACOPF_E_OOM (-4)         /* device or host allocation failed */
+#define ACOPF_E_BUDGET (-5)      /* admission would exceed the memory budget */
+#define ACOPF_E_TIMEOUT (-6)     /* a bounded wait ran out */
+#define ACOPF_E_BUSY (-7)        /* resource in use (e.g. queue full) */
+#define ACOPF_E_NO_DEVICE (-8)   /* model created host-only (device = -1) */
+
+typedef struct acopf_model acopf_model;
+
+/* Bus data, per unit.  type 3 marks a reference bus (one va = 0 row each). */
+typedef struct {
+  int32_t n;
+  const int32_t* type;
+  const double *Pd, *Qd, *Gs, *Bs, *Vmin, *Vmax;
+} acopf_buses;
+
+/* Branch data, per unit and radians.  f != t; r and x not both zero;
+ * rate_a <= 0 means unrated (flow and thermal bounds infinite). */
+typedef struct {
+  int32_t n;
+  const int32_t *f, *t;
+  const double *r, *x, *b, *tap, *shift, *rate_a, *angmin, *angmax;
+} acopf_branches;
+
+/* Generator data; cost c2 pg^2 + c1 pg + c0. */
+typedef struct {
+  int32_t n;
+  const int32_t* bus;
+  const double *Pmin, *Pmax, *Qmin, *Qmax, *c2, *c1, *c0;
+} acopf_gens;
+
+/* Status name ("ACOPF_OK", ...).  Never NULL. */
+const char* acopf_status_string(acopf_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* acopf_last_error(void);
+
+/* Build a model: validate the network, fix the variable and constraint
+ * layout, the COO patterns of A and W and the CSR pattern of M_cond (the
+ * host symbolic phase; parameterised per pattern and expanded over its data,
+ * Sec. III.C), and upload the model to `device`.  device = -1 builds a
+ * host-only model that answers the dims / bounds / structure queries but
+ * returns ACOPF_E_NO_DEVICE from every compute call.  On success *out owns
+ * the model; release it with acopf_model_destroy.  Errors:
+ * ACOPF_E_INVALID_ARG, ACOPF_E_BAD_MODEL (the message names the first bad
+ * entry), ACOPF_E_OOM, ACOPF_E_CUDA. */
+acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* branches,
+                                const acopf_gens* gens, int device, acopf_model** out);
+
+/* Free the model and its device memory.  NULL is accepted.  The caller must
+ * make sure no call on the model is still running on the GPU. */
+acopf_status acopf_model_destroy(acopf_model* model);
+
+/* Sizes: n variables, m constraints, Jacobian / Hessian COO lengths, nnz of
+ * the lower CSR of M_cond, and the device bytes the model holds (model data
+ * plus its scratch).  Any output pointer may be NULL. */
+acopf_status acopf_model_dims(const acopf_model* model, int64_t* n, int64_t* m, int64_t* nnz_jac,
+                              int64_t* nnz_hess, int64_t* nnz_kkt, int64_t* device_bytes);
+
+/* Counts of buses, branches, generators and reference buses (NULL allowed). */
+acopf_status acopf_model_counts(const acopf_model* model, int32_t* n_bus, int32_t* n_branch,
+                                int32_t* n_gen, int32_t* n_ref);
+
+/* Host outputs: variable bounds xl, xu (length n), constraint bounds gl, gu
+ * (length m); +-INFINITY where unbounded.  Any pointer may be NULL. */
+acopf_status acopf_bounds(const acopf_model* model, double* xl, double* xu, double* gl, double* gu);
+
+/* Host outputs: COO rows/cols of A (length nnz_jac), of the lower W
+ * (length nnz_hess), and the lower CSR of M_cond (rowptr length n + 1,
+ * colind length nnz_kkt). */
+acopf_status acopf_jac_structure(const acopf_model* model, int32_t* rows, int32_t* cols);
+acopf_status acopf_hess_structure(const acopf_model* model, int32_t* rows, int32_t* cols);
+acopf_status acopf_kkt_structure(const acopf_model* model, int32_t* rowptr, int32_t* colind);
+
+/* ---- device callbacks (Algorithm 1's f, grad f, g, grad g, Hessian of L) ----
+ * x: device, length n.  y: device, length m.  Results are written to device
+ * memory: f_dev one double; grad length n; cons length m; jvals nnz_jac;
+ * hvals nnz_hess.  obj_weight is sigma in W = sigma d2f + sum_r y_r d2g_r. */
+acopf_status acopf_eval_obj(const acopf_model* model, const double* x, double* f_dev,
+                            acopf_stream stream);
+acopf_status acopf_eval_grad(const acopf_model* model, const double* x, double* grad,
+                             acopf_stream stream);
+acopf_status acopf_eval_cons(const acopf_model* model, const double* x, double* cons,
+                             acopf_stream stream);
+acopf_status acopf_eval_jac_coo(const acopf_model* model, const double* x, double* jvals,
+                                acopf_stream stream);
+acopf_status acopf_eval_hess_coo(const acopf_model* model, const double* x, const double* y,
+                                 double obj_weight, double* hvals, acopf_stream stream);
+
+/* Numeric assembly of the lower CSR values of M_cond (Sec. IV.C) from given
+ * Hessian and Jacobian values (device, in the COO orders above), Sigma_x
+ * (device, length n, the diagonal of Z_lo (X - X_lo)^-1 + Z_hi (X_hi - X)^-1)
+ * and Sigma_s (device, length m), with regularisation delta_w, delta_c >= 0
+ * (Algorithm 1 uses 0, 0).  kvals: device, length nnz_kkt.  Uses the
+ * model's scratch. */
+acopf_status acopf_assemble_condensed_kkt_csr(const acopf_model* model, const double* hvals,
+                                              const double* jvals, const double* sigma_x,
+                                              const double* sigma_s, double delta_w,
+                                              double delta_c, double* kvals, acopf_stream stream);
+
+/* The fused unit of work of one IPM iteration: f, grad f, g, A, W and M_cond
+ * at (x, y, Sigma_x, Sigma_s) in two kernel launches, the Jacobian and
+ * Hessian values feeding the assembly straight from registers.  All
+ * pointers device; every output must be non-NULL.  Results equal those of
+ * the separate calls above up to floating-point rounding order. */
+acopf_status acopf_eval_assemble(const acopf_model* model, const double* x, const double* y,
+                                 double obj_weight, const double* sigma_x, const double* sigma_s,
+                                 double delta_w, double delta_c, double* f_dev, double* grad,
+                                 double* cons, double* jvals, double* hvals, double* kvals,
+                                 acopf_stream stream);
+
+/* Same unit of work with HOST buffers (pinned memory makes the copies
+ * asynchronous DMA; pageable memory also works).  Copies x, y, Sigma_x,
+ * Sigma_s to the model's device staging buffers, runs acopf_eval_assemble,
+ * copies every output back and synchronises `stream` before returning.
+ * Host outputs: f (1), grad (n), cons (m), jvals, hvals, kvals.  The
+ * staging buffers are allocated on the first call and kept by the model. */
+acopf_status acopf_eval_assemble_host(acopf_model* model, const double* x, const double* y,
+                                      double obj_weight, const double* sigma_x,
+                                      const double* sigma_s, double delta_w, double delta_c,
+                                      double* f, double* grad, double* cons, double* jvals,
+                                      double* hvals, double* kvals, acopf_stream stream);
+
+/* Number of kernel launches one call of each kind issues (for launch
+ * accounting): kind 0 = eval_assemble, 1 = assemble_condensed_kkt_csr,
+ * 2 = eval_obj, 3 = eval_grad, 4 = eval_cons, 5 = eval_jac_coo,
+ * 6 = eval_hess_coo.  Returns -1 for an unknown kind. */
+int32_t acopf_launches_per_call(int32_t kind);
+
+/* Per-phase timing of acopf_eval_assemble, a measurement aid with no
+ * counterpart in the paper.  After acopf_profile_begin(model, capacity) with
+ * capacity > 0, the next `capacity` calls of acopf_eval_assemble on this
+ * model record CUDA events on their stream before phase 1, between the two
+ * phases and after phase 2 (profiled calls launch phase 2 without
+ * programmatic dependent launch, since an event sits between the phases).
+ * acopf_profile_end waits for the recorded events, returns the number of
+ * profiled calls and the summed phase-1, phase-2 and whole-call durations in
+ * milliseconds (NULL outputs allowed), and stops profiling.  Allocates and
+ * frees CUDA events. */
+acopf_status acopf_profile_begin(acopf_model* model, int32_t capacity);
+acopf_status acopf_profile_end(acopf_model* model, int32_t* calls, double* phase1_ms,
+                               double* phase2_ms, double* total_ms);
+
+/* Measured FP64 fused-multiply-add throughput of `device` in GFLOP/s (2
+ * flops per FMA), from a dependent-chain DFMA kernel of about 20 ms.  A
+ * measurement aid for rooflines: the paper has no counterpart.  Allocates
+ * and frees a small device buffer. */
+acopf_status acopf_measure_fp64_gflops(int device, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACOPF_H_ */

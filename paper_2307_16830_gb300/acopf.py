@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libacopf (include/acopf.h), with the C names.
+
+Argument marshalling only: every computation runs in the CUDA library.
+Device arrays are passed as torch tensors (float64, contiguous, on the
+model's device) or as raw integer device addresses; streams as
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or None for the
+current torch stream.  There is no CPU fallback: if ``libacopf.so`` has not
+been built, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libacopf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+        " (the ACOPF kernels have no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+E_INVALID_ARG = -1
+E_BAD_MODEL = -2
+E_CUDA = -3
+E_OOM = -4
+E_BUDGET = -5
+E_TIMEOUT = -6
+E_BUSY = -7
+E_NO_DEVICE = -8
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+
+
+class Buses(C.Structure):
+    _fields_ = [("n", C.c_int32), ("type", _i32p), ("Pd", _f64p), ("Qd", _f64p), ("Gs", _f64p),
+                ("Bs", _f64p), ("Vmin", _f64p), ("Vmax", _f64p)]
+
+
+class Branches(C.Structure):
+    _fields_ = [("n", C.c_int32), ("f", _i32p), ("t", _i32p), ("r", _f64p), ("x", _f64p),
+                ("b", _f64p), ("tap", _f64p), ("shift", _f64p), ("rate_a", _f64p),
+                ("angmin", _f64p), ("angmax", _f64p)]
+
+
+class Gens(C.Structure):
+    _fields_ = [("n", C.c_int32), ("bus", _i32p), ("Pmin", _f64p), ("Pmax", _f64p),
+                ("Qmin", _f64p), ("Qmax", _f64p), ("c2", _f64p), ("c1", _f64p), ("c0", _f64p)]
+
+
+def _sig(name, res, *args):
+    fn = getattr(_lib, name)
+    fn.restype = res
+    fn.argtypes = list(args)
+    return fn
+
+
+_vp = C.c_void_p
+_status_string = _sig("acopf_status_string", C.c_char_p, C.c_int32)
+_last_error = _sig("acopf_last_error", C.c_char_p)
+_model_create = _sig("acopf_model_create", C.c_int32, C.POINTER(Buses), C.POINTER(Branches),
+                     C.POINTER(Gens), C.c_int, C.POINTER(_vp))
+_model_destroy = _sig("acopf_model_destroy", C.c_int32, _vp)
+_model_dims = _sig("acopf_model_dims", C.c_int32, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p)
+_model_counts = _sig("acopf_model_counts", C.c_int32, _vp, _i32p, _i32p, _i32p, _i32p)
+_bounds = _sig("acopf_bounds", C.c_int32, _vp, _vp, _vp, _vp, _vp)
+_jac_structure = _sig("acopf_jac_structure", C.c_int32, _vp, _vp, _vp)
+_hess_structure = _sig("acopf_hess_structure", C.c_int32, _vp, _vp, _vp)
+_kkt_structure = _sig("acopf_kkt_structure", C.c_int32, _vp, _vp, _vp)
+_eval_obj = _sig("acopf_eval_obj", C.c_int32, _vp, _vp, _vp, _vp)
+_eval_grad = _sig("acopf_eval_grad", C.c_int32, _vp, _vp, _vp, _vp)
+_eval_cons = _sig("acopf_eval_cons", C.c_int32, _vp, _vp, _vp, _vp)
+_eval_jac_coo = _sig("acopf_eval_jac_coo", C.c_int32, _vp, _vp, _vp, _vp)
+_eval_hess_coo = _sig("acopf_eval_hess_coo", C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp)
+_assemble = _sig("acopf_assemble_condensed_kkt_csr", C.c_int32, _vp, _vp, _vp, _vp, _vp,
+                 C.c_double, C.c_double, _vp, _vp)
+_eval_assemble = _sig("acopf_eval_assemble", C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp,
+                      C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
+_eval_assemble_host = _sig("acopf_eval_assemble_host", C.c_int32, _vp, _vp, _vp, C.c_double, _vp,
+                           _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
+_launches_per_call = _sig("acopf_launches_per_call", C.c_int32, C.c_int32)
+_measure_fp64 = _sig("acopf_measure_fp64_gflops", C.c_int32, C.c_int, _f64p)
+_profile_begin = _sig("acopf_profile_begin", C.c_int32, _vp, C.c_int32)
+_profile_end = _sig("acopf_profile_end", C.c_int32, _vp, _i32p, _f64p, _f64p, _f64p)
+
+# Exported symbols the header declares (checked by the CPU tests).
+EXPORTED = [
+    "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
+    "acopf_model_dims", "acopf_model_counts", "acopf_bounds", "acopf_jac_structure",
+    "acopf_hess_structure", "acopf_kkt_structure", "acopf_eval_obj", "acopf_eval_grad",
+    "acopf_eval_cons", "acopf_eval_jac_coo", "acopf_eval_hess_coo",
+    "acopf_assemble_condensed_kkt_csr", "acopf_eval_assemble", "acopf_eval_assemble_host",
+    "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_profile_begin",
+    "acopf_profile_end",
+]
+
+
+class AcopfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _last_error().decode(errors="replace")
+        super().__init__(f"{where}: {status_string(status)}: {msg}")
+
+
+def status_string(status: int) -> str:
+    return _status_string(status).decode()
+
+
+def last_error() -> str:
+    return _last_error().decode(errors="replace")
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        raise AcopfError(status, where)
+
+
+def _ptr(a) -> int | None:
+    """Device address of a tensor (or an int address, or None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"expected a tensor or a device address, got {type(a)!r}")
+
+
+def _hptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream or None
+        except Exception:  # no torch / no CUDA: legacy default stream
+            return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+class Model:
+    """An ACOPF model (owner of an ``acopf_model*``)."""
+
+    def __init__(self, handle: int, keepalive):
+        self._h = C.c_void_p(handle)
+        self._keep = keepalive
+        n, m, nj, nh, nk, db = (C.c_int64() for _ in range(6))
+        _check(_model_dims(self._h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh),
+                           C.byref(nk), C.byref(db)), "acopf_model_dims")
+        self.n, self.m = n.value, m.value
+        self.nnz_jac, self.nnz_hess, self.nnz_kkt = nj.value, nh.value, nk.value
+        nb, nl, ng, nr = (C.c_int32() for _ in range(4))
+        _check(_model_counts(self._h, C.byref(nb), C.byref(nl), C.byref(ng), C.byref(nr)),
+               "acopf_model_counts")
+        self.n_bus, self.n_branch, self.n_gen, self.n_ref = nb.value, nl.value, ng.value, nr.value
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    @property
+    def device_bytes(self) -> int:
+        db = C.c_int64()
+        _check(_model_dims(self._h, None, None, None, None, None, C.byref(db)), "acopf_model_dims")
+        return db.value
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _model_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- host queries --------------------------------------------------------
+    def bounds(self):
+        xl, xu = np.empty(self.n), np.empty(self.n)
+        gl, gu = np.empty(self.m), np.empty(self.m)
+        _check(_bounds(self._h, _hptr(xl), _hptr(xu), _hptr(gl), _hptr(gu)), "acopf_bounds")
+        return xl, xu, gl, gu
+
+    def jac_structure(self):
+        r, c = np.empty(self.nnz_jac, np.int32), np.empty(self.nnz_jac, np.int32)
+        _check(_jac_structure(self._h, _hptr(r), _hptr(c)), "acopf_jac_structure")
+        return r, c
+
+    def hess_structure(self):
+        r, c = np.empty(self.nnz_hess, np.int32), np.empty(self.nnz_hess, np.int32)
+        _check(_hess_structure(self._h, _hptr(r), _hptr(c)), "acopf_hess_structure")
+        return r, c
+
+    def kkt_structure(self):
+        rp, ci = np.empty(self.n + 1, np.int32), np.empty(self.nnz_kkt, np.int32)
+        _check(_kkt_structure(self._h, _hptr(rp), _hptr(ci)), "acopf_kkt_structure")
+        return rp, ci
+
+
+def _as(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def model_create(grid, device: int = 0) -> Model:
+    """acopf_model_create from a grid object exposing the bus, branch and
+    generator arrays (see ``synth.Grid``); device = -1 builds a host-only
+    model (structure queries only)."""
+    keep = {}
+
+    def f64(name):
+        keep[name] = _as(getattr(grid, name), np.float64)
+        return keep[name].ctypes.data_as(_f64p)
+
+    def i32(name):
+        keep[name] = _as(getattr(grid, name), np.int32)
+        return keep[name].ctypes.data_as(_i32p)
+
+    nb, nl, ng = len(grid.Pd), len(grid.f), len(grid.gen_bus)
+    buses = Buses(nb, i32("bus_type"), f64("Pd"), f64("Qd"), f64("Gs"), f64("Bs"), f64("Vmin"),
+                  f64("Vmax"))
+    branches = Branches(nl, i32("f"), i32("t"), f64("r"), f64("x"), f64("b"), f64("tap"),
+                        f64("shift"), f64("rate_a"), f64("angmin"), f64("angmax"))
+    gens = Gens(ng, i32("gen_bus"), f64("Pmin"), f64("Pmax"), f64("Qmin"), f64("Qmax"),
+                f64("c2"), f64("c1"), f64("c0"))
+    h = C.c_void_p()
+    _check(_model_create(C.byref(buses), C.byref(branches), C.byref(gens), int(device),
+                         C.byref(h)), "acopf_model_create")
+    return Model(h.value, None)
+
+
+def eval_obj(model: Model, x, f_dev, stream=None) -> None:
+    _check(_eval_obj(model.handle, _ptr(x), _ptr(f_dev), _stream(stream)), "acopf_eval_obj")
+
+
+def eval_grad(model: Model, x, grad, stream=None) -> None:
+    _check(_eval_grad(model.handle, _ptr(x), _ptr(grad), _stream(stream)), "acopf_eval_grad")
+
+
+def eval_cons(model: Model, x, cons, stream=None) -> None:
+    _check(_eval_cons(model.handle, _ptr(x), _ptr(cons), _stream(stream)), "acopf_eval_cons")
+
+
+def eval_jac_coo(model: Model, x, jvals, stream=None) -> None:
+    _check(_eval_jac_coo(model.handle, _ptr(x), _ptr(jvals), _stream(stream)),
+           "acopf_eval_jac_coo")
+
+
+def eval_hess_coo(model: Model, x, y, obj_weight: float, hvals, stream=None) -> None:
+    _check(_eval_hess_coo(model.handle, _ptr(x), _ptr(y), float(obj_weight), _ptr(hvals),
+                          _stream(stream)), "acopf_eval_hess_coo")
+
+
+def assemble_condensed_kkt_csr(model: Model, hvals, jvals, sigma_x, sigma_s, delta_w: float,
+                               delta_c: float, kvals, stream=None) -> None:
+    _check(_assemble(model.handle, _ptr(hvals), _ptr(jvals), _ptr(sigma_x), _ptr(sigma_s),
+                     float(delta_w), float(delta_c), _ptr(kvals), _stream(stream)),
+           "acopf_assemble_condensed_kkt_csr")
+
+
+def eval_assemble(model: Model, x, y, obj_weight: float, sigma_x, sigma_s, delta_w: float,
+                  delta_c: float, f_dev, grad, cons, jvals, hvals, kvals, stream=None) -> None:
+    _check(_eval_assemble(model.handle, _ptr(x), _ptr(y), float(obj_weight), _ptr(sigma_x),
+                          _ptr(sigma_s), float(delta_w), float(delta_c), _ptr(f_dev), _ptr(grad),
+                          _ptr(cons), _ptr(jvals), _ptr(hvals), _ptr(kvals), _stream(stream)),
+           "acopf_eval_assemble")
+
+
+def eval_assemble_host(model: Model, x, y, obj_weight: float, sigma_x, sigma_s, delta_w: float,
+                       delta_c: float, f, grad, cons, jvals, hvals, kvals, stream=None) -> None:
+    """Host-buffer variant: numpy arrays (or pinned torch CPU tensors) in and out."""
+    def hp(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return _hptr(a)
+    _check(_eval_assemble_host(model.handle, hp(x), hp(y), float(obj_weight), hp(sigma_x),
+                               hp(sigma_s), float(delta_w), float(delta_c), hp(f), hp(grad),
+                               hp(cons), hp(jvals), hp(hvals), hp(kvals), _stream(stream)),
+           "acopf_eval_assemble_host")
+
+
+def launches_per_call(kind: int) -> int:
+    return int(_launches_per_call(int(kind)))
+
+
+def measure_fp64_gflops(device: int = 0) -> float:
+    v = C.c_double()
+    _check(_measure_fp64(int(device), C.byref(v)), "acopf_measure_fp64_gflops")
+    return v.value
+
+
+def profile_begin(model: Model, capacity: int) -> None:
+    _check(_profile_begin(model.handle, int(capacity)), "acopf_profile_begin")
+
+
+def profile_end(model: Model):
+    """Returns (calls, phase1_ms, phase2_ms, total_ms) summed over profiled calls."""
+    n = C.c_int32()
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(_profile_end(model.handle, C.byref(n), C.byref(a), C.byref(b), C.byref(c)),
+           "acopf_profile_end")
+    return n.value, a.value, b.value, c.value

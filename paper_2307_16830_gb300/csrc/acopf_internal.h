@@ -1,0 +1,142 @@
+// Internal declarations shared by the host symbolic phase, the kernels and
+// the C ABI of libacopf.  Not installed; the public interface is acopf.h.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/acopf.h"
+
+namespace acopf {
+
+// Offsets of the variable and constraint groups and of the COO sections.
+// Everything within one model fits int32 (checked at build time).
+struct Layout {
+  int32_t nb = 0, nl = 0, ng = 0, nref = 0;
+  // variables
+  int32_t VA = 0, VM = 0, PG = 0, QG = 0, P = 0, Q = 0, n = 0;
+  // constraints
+  int32_t REF = 0, PF = 0, QF = 0, PT = 0, QT = 0, ANG = 0, SF = 0, ST = 0, PB = 0, QB = 0, m = 0;
+  // Jacobian COO sections
+  int32_t JREF = 0, JPF = 0, JQF = 0, JPT = 0, JQT = 0, JANG = 0, JSF = 0, JST = 0;
+  int32_t JPBV = 0, JQBV = 0, JPBG = 0, JQBG = 0, JPBA = 0, JQBA = 0, nnzj = 0;
+  // Hessian COO sections
+  int32_t HBLK = 0, HTH = 0, HG = 0, HB = 0, nnzh = 0;
+  int32_t nnzk = 0;
+};
+
+// Branch pi-model coefficients, structure of arrays: coef[k * nl + l] with
+// k = 0..7 -> g_ff, b_ff, g_ft, b_ft, g_tf, b_tf, g_tt, b_tt.
+enum { CG_FF = 0, CB_FF, CG_FT, CB_FT, CG_TF, CB_TF, CG_TT, CB_TT, NCOEF };
+
+// Per-arc and per-branch partial sums that the branch phase of the KKT
+// assembly leaves for the bus phase (device scratch).
+//   arc a:    {aa, ma, mm, mx}: the branch's contributions to (va_i,va_i),
+//             (vm_i,va_i), (vm_i,vm_i) and (vm_i,va_j), i = bus of a, j = other end;
+//   branch l: {vv, ww}: contributions to (va_t,va_f) and (vm_t,vm_f).
+struct alignas(32) ArcPart {
+  double aa, ma, mm, mx;
+};
+struct alignas(16) BranchPart {
+  double vv, ww;
+};
+
+// Read-only device view of a model, passed to kernels by value.
+struct DevModel {
+  Layout L;
+  // branches
+  const int32_t* f;
+  const int32_t* t;
+  const double* coef;
+  // buses
+  const double* Pd;
+  const double* Qd;
+  const double* Gs;
+  const double* Bs;
+  const int32_t* ref_row;      // per bus: its reference row, or -1
+  const int32_t* arc_ptr;      // nb + 1
+  const int32_t* arcs_by_idx;  // 2 nl: arcs of each bus, ascending arc id
+  const int32_t* arcs_by_nbr;  // 2 nl: arcs of each bus, ascending (other end, arc id)
+  const int32_t* gen_ptr;      // nb + 1
+  const int32_t* gens_at;      // ng: generators of each bus, ascending id
+  // generators
+  const int32_t* gbus;
+  const double* c2;
+  const double* c1;
+  const double* c0;
+  // M_cond structure
+  const int32_t* krowptr;      // n + 1
+  // scratch
+  ArcPart* part_arc;           // 2 nl
+  BranchPart* part_br;         // nl
+  double* obj_part;            // one per generator block
+  int32_t obj_blocks;
+};
+
+// Host model: everything the symbolic phase builds.
+struct HostModel {
+  Layout L;
+  std::vector<int32_t> f, t, gbus, ref_row, ref_bus;
+  std::vector<double> coef;  // NCOEF * nl
+  std::vector<double> Pd, Qd, Gs, Bs, c2, c1, c0;
+  std::vector<int32_t> arc_ptr, arcs_by_idx, arcs_by_nbr, gen_ptr, gens_at;
+  std::vector<int32_t> jrows, jcols, hrows, hcols, krowptr, kcolind;
+  std::vector<double> xl, xu, gl, gu;
+};
+
+// Builds the host model; on failure returns a status and sets `err`.
+acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, const acopf_gens* G,
+                              HostModel& hm, std::string& err);
+
+// Kernel launch configuration.
+constexpr int kBranchThreads = 128;
+constexpr int kBusThreads = 128;
+constexpr int kGenThreads = 128;
+
+inline int32_t ceil_div(int64_t a, int64_t b) { return static_cast<int32_t>((a + b - 1) / b); }
+inline int32_t gen_blocks(const Layout& L) { return ceil_div(L.ng, kGenThreads); }
+
+// What a launch computes.
+enum : unsigned {
+  OUT_OBJ = 1u,
+  OUT_GRAD = 2u,
+  OUT_CONS = 4u,
+  OUT_JAC = 8u,
+  OUT_HESS = 16u,
+  OUT_KKT = 32u,
+  OUT_ALL = 63u,
+};
+
+struct EvalArgs {
+  const double* x;
+  const double* y;
+  double obj_weight;
+  const double* sigma_x;
+  const double* sigma_s;
+  double delta_w;
+  double delta_c;
+  // inputs of the array-fed assembly
+  const double* hvals_in;
+  const double* jvals_in;
+  // outputs
+  double* f;
+  double* grad;
+  double* cons;
+  double* jvals;
+  double* hvals;
+  double* kvals;
+};
+
+// Launchers (kernels.cu).  Each returns the CUDA error of its launches.
+// `mid`, when not null, is recorded between the two phases (phase 2 then
+// launches without programmatic dependent launch).
+cudaError_t launch_eval(const DevModel& dm, unsigned what, const EvalArgs& a, cudaStream_t s,
+                        cudaEvent_t mid = nullptr);
+cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+int launches_for(unsigned what);
+
+}  // namespace acopf

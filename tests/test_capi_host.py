@@ -1,0 +1,149 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol,
+and its host symbolic phase reproduces the oracle's index arrays bit for bit.
+
+No compute call runs here (models are created host-only, device = -1)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_16830_gb300 import synth
+
+acopf = pytest.importorskip("paper_2307_16830_gb300.acopf",
+                            reason="libacopf.so not built (run __graft_entry__.build())")
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "acopf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(acopf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 18
+    lib = acopf._lib
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(acopf.EXPORTED) == names
+
+
+def test_status_strings():
+    assert acopf.status_string(acopf.OK) == "ACOPF_OK"
+    assert acopf.status_string(acopf.E_BAD_MODEL) == "ACOPF_E_BAD_MODEL"
+    assert acopf.status_string(12345) == "ACOPF_E_UNKNOWN"
+
+
+def grids():
+    return [synth.workload_grid("30bus"), synth.make_edge_case_grid(7),
+            synth.make_edge_case_grid(11), synth.make_grid(300, 420, 40, seed=5)]
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_host_structures_match_oracle_bit_exactly(k):
+    g = grids()[k]
+    with acopf.model_create(g, device=-1) as m:
+        L = oracle.layout(g)
+        assert (m.n, m.m) == (L.n, L.m)
+        assert (m.n_bus, m.n_branch, m.n_gen, m.n_ref) == (g.n_bus, g.n_branch, g.n_gen, g.n_ref)
+        jr, jc = oracle.jac_structure(g)
+        r, c = m.jac_structure()
+        assert np.array_equal(r, jr) and np.array_equal(c, jc)
+        hr, hc = oracle.hess_structure(g)
+        r, c = m.hess_structure()
+        assert np.array_equal(r, hr) and np.array_equal(c, hc)
+        rp, ci = oracle.kkt_structure(g)
+        r, c = m.kkt_structure()
+        assert m.nnz_kkt == ci.size
+        assert np.array_equal(r, rp) and np.array_equal(c, ci)
+        xl, xu, gl, gu = oracle.bounds(g)
+        bl = m.bounds()
+        for got, want in zip(bl, (xl, xu, gl, gu)):
+            assert np.array_equal(got, want)
+
+
+def test_host_structures_10k_grid():
+    g = synth.workload_grid("10kbus")
+    with acopf.model_create(g, device=-1) as m:
+        rp, ci = oracle.kkt_structure(g)
+        r, c = m.kkt_structure()
+        assert np.array_equal(r, rp) and np.array_equal(c, ci)
+        jr, jc = oracle.jac_structure(g)
+        r, c = m.jac_structure()
+        assert np.array_equal(r, jr) and np.array_equal(c, jc)
+
+
+def test_sizes_match_formulas():
+    g = synth.workload_grid("10kbus")
+    with acopf.model_create(g, device=-1) as m:
+        nb, nl, ng = g.n_bus, g.n_branch, g.n_gen
+        assert m.n == 2 * nb + 2 * ng + 4 * nl == 78_000
+        assert m.m == 1 + 7 * nl + 2 * nb == 114_501
+        assert m.nnz_jac == 1 + 30 * nl + 2 * nb + 2 * ng == 429_001
+        assert m.nnz_hess == 14 * nl + ng + nb == 201_000
+
+
+def _bad(g, **changes):
+    g = g.copy()
+    for k, v in changes.items():
+        getattr(g, k)[...] = v
+    return g
+
+
+def test_validation_rejects_bad_networks():
+    g = synth.workload_grid("30bus")
+    cases = []
+    h = g.copy()
+    h.t[0] = h.f[0]
+    cases.append(("self-loop", h))
+    h = g.copy()
+    h.f[3] = g.n_bus
+    cases.append(("bus out of range", h))
+    h = g.copy()
+    h.r[2] = 0.0
+    h.x[2] = 0.0
+    cases.append(("zero impedance", h))
+    h = g.copy()
+    h.gen_bus[1] = -1
+    cases.append(("generator bus", h))
+    h = g.copy()
+    h.Pd[4] = math.nan
+    cases.append(("nan load", h))
+    for name, bad in cases:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.model_create(bad, device=-1)
+        assert ei.value.status == acopf.E_BAD_MODEL, name
+        assert acopf.last_error()
+
+
+def test_host_only_model_refuses_compute_calls():
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, device=-1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.eval_cons(m, 1, 2, stream=0)
+        assert ei.value.status == acopf.E_NO_DEVICE
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.eval_assemble(m, 1, 1, 1.0, 1, 1, 0.0, 0.0, 1, 1, 1, 1, 1, 1, stream=0)
+        assert ei.value.status == acopf.E_NO_DEVICE
+
+
+def test_null_arguments_rejected():
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, device=-1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.eval_cons(m, None, None, stream=0)
+        assert ei.value.status == acopf.E_INVALID_ARG
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.assemble_condensed_kkt_csr(m, 1, 1, 1, 1, -1.0, 0.0, 1, stream=0)
+        assert ei.value.status == acopf.E_INVALID_ARG
+
+
+def test_launch_accounting():
+    for kind in range(7):
+        assert acopf.launches_per_call(kind) == 2
+    assert acopf.launches_per_call(99) == -1
