@@ -32,16 +32,14 @@ struct Layout {
 // k = 0..7 -> g_ff, b_ff, g_ft, b_ft, g_tf, b_tf, g_tt, b_tt.
 enum { CG_FF = 0, CB_FF, CG_FT, CB_FT, CG_TF, CB_TF, CG_TT, CB_TT, NCOEF };
 
-// Per-arc and per-branch partial sums that the branch phase of the KKT
-// assembly leaves for the bus phase (device scratch).
-//   arc a:    {aa, ma, mm, mx}: the branch's contributions to (va_i,va_i),
-//             (vm_i,va_i), (vm_i,vm_i) and (vm_i,va_j), i = bus of a, j = other end;
-//   branch l: {vv, ww}: contributions to (va_t,va_f) and (vm_t,vm_f).
-struct alignas(32) ArcPart {
-  double aa, ma, mm, mx;
-};
-struct alignas(16) BranchPart {
-  double vv, ww;
+// Partial sums that the branch phase of the KKT assembly leaves for the bus
+// phase (device scratch), one per slot.  Slots list the arcs of each bus in
+// the order (other end, arc id); the slot of arc a at bus i (other end j,
+// branch l) holds the branch's contributions to
+//   aa: (va_i, va_i)   ma: (vm_i, va_i)   mm: (vm_i, vm_i)   mx: (vm_i, va_j)
+//   vv: (va_i, va_j)   ww: (vm_i, vm_j)   (vv, ww are the same at both ends).
+struct alignas(16) SlotPart {
+  double aa, ma, mm, mx, vv, ww;
 };
 
 // Read-only device view of a model, passed to kernels by value.
@@ -59,7 +57,9 @@ struct DevModel {
   const int32_t* ref_row;      // per bus: its reference row, or -1
   const int32_t* arc_ptr;      // nb + 1
   const int32_t* arcs_by_idx;  // 2 nl: arcs of each bus, ascending arc id
-  const int32_t* arcs_by_nbr;  // 2 nl: arcs of each bus, ascending (other end, arc id)
+  const int32_t* slot_arc;     // 2 nl: arcs of each bus, ascending (other end, arc id)
+  const int32_t* slot_nbr;     // 2 nl: other end of each slot's arc
+  const int32_t* slot_of_arc;  // 2 nl: slot of each arc
   const int32_t* gen_ptr;      // nb + 1
   const int32_t* gens_at;      // ng: generators of each bus, ascending id
   // generators
@@ -70,10 +70,8 @@ struct DevModel {
   // M_cond structure
   const int32_t* krowptr;      // n + 1
   // scratch
-  ArcPart* part_arc;           // 2 nl
-  BranchPart* part_br;         // nl
-  double* obj_part;            // one per generator block
-  int32_t obj_blocks;
+  SlotPart* part_slot;         // 2 nl
+  int32_t slot_cap;            // slots a bus block stages in shared memory
 };
 
 // Host model: everything the symbolic phase builds.
@@ -83,6 +81,7 @@ struct HostModel {
   std::vector<double> coef;  // NCOEF * nl
   std::vector<double> Pd, Qd, Gs, Bs, c2, c1, c0;
   std::vector<int32_t> arc_ptr, arcs_by_idx, arcs_by_nbr, gen_ptr, gens_at;
+  std::vector<int32_t> slot_nbr, slot_of_arc;
   std::vector<int32_t> jrows, jcols, hrows, hcols, krowptr, kcolind;
   std::vector<double> xl, xu, gl, gu;
 };
@@ -95,9 +94,16 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
 constexpr int kBranchThreads = 128;
 constexpr int kBusThreads = 128;
 constexpr int kGenThreads = 128;
+// Shared-memory staging of slot partials in the bus phase: at most this many
+// slots per block (48 KB of SlotPart + neighbour index); larger blocks read
+// global memory directly.
+constexpr int kSlotCapMax = 940;
+constexpr int kSlotBytes = sizeof(SlotPart) + sizeof(int32_t);
 
 inline int32_t ceil_div(int64_t a, int64_t b) { return static_cast<int32_t>((a + b - 1) / b); }
-inline int32_t gen_blocks(const Layout& L) { return ceil_div(L.ng, kGenThreads); }
+
+// Largest number of slots (arcs) over the bus blocks of a model.
+int32_t max_block_slots(const HostModel& hm);
 
 // What a launch computes.
 enum : unsigned {

@@ -1,4 +1,5 @@
 // extern "C" entry points of libacopf (declared in include/acopf.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -149,7 +150,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const acopf::Layout& L = hm.L;
   acopf::DevModel& dm = m->dm;
   dm.L = L;
-  dm.obj_blocks = acopf::gen_blocks(L);
+  dm.slot_cap = std::min(acopf::max_block_slots(hm), acopf::kSlotCapMax);
   if (device < 0) {
     *out = m;
     return ACOPF_OK;
@@ -169,13 +170,12 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const size_t o_ref = p.take<int32_t>(nb);
   const size_t o_aptr = p.take<int32_t>(nb + 1);
   const size_t o_aidx = p.take<int32_t>(2 * nl), o_anbr = p.take<int32_t>(2 * nl);
+  const size_t o_snbr = p.take<int32_t>(2 * nl), o_soa = p.take<int32_t>(2 * nl);
   const size_t o_gptr = p.take<int32_t>(nb + 1), o_gat = p.take<int32_t>(ng);
   const size_t o_gbus = p.take<int32_t>(ng);
   const size_t o_c2 = p.take<double>(ng), o_c1 = p.take<double>(ng), o_c0 = p.take<double>(ng);
   const size_t o_krp = p.take<int32_t>(n + 1);
-  const size_t o_pa = p.take<acopf::ArcPart>(2 * nl);
-  const size_t o_pb = p.take<acopf::BranchPart>(nl);
-  const size_t o_obj = p.take<double>(size_t(dm.obj_blocks) + 1);
+  const size_t o_ps = p.take<acopf::SlotPart>(2 * nl);
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, p.off);
   if (e != cudaSuccess) {
@@ -201,6 +201,8 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_aptr, hm.arc_ptr.data(), (nb + 1) * 4);
   if (e == cudaSuccess) e = up(o_aidx, hm.arcs_by_idx.data(), 2 * nl * 4);
   if (e == cudaSuccess) e = up(o_anbr, hm.arcs_by_nbr.data(), 2 * nl * 4);
+  if (e == cudaSuccess) e = up(o_snbr, hm.slot_nbr.data(), 2 * nl * 4);
+  if (e == cudaSuccess) e = up(o_soa, hm.slot_of_arc.data(), 2 * nl * 4);
   if (e == cudaSuccess) e = up(o_gptr, hm.gen_ptr.data(), (nb + 1) * 4);
   if (e == cudaSuccess) e = up(o_gat, hm.gens_at.data(), ng * 4);
   if (e == cudaSuccess) e = up(o_gbus, hm.gbus.data(), ng * 4);
@@ -208,7 +210,6 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_c1, hm.c1.data(), ng * 8);
   if (e == cudaSuccess) e = up(o_c0, hm.c0.data(), ng * 8);
   if (e == cudaSuccess) e = up(o_krp, hm.krowptr.data(), (n + 1) * 4);
-  if (e == cudaSuccess) e = cudaMemset(base + o_obj, 0, (size_t(dm.obj_blocks) + 1) * 8);
   if (e != cudaSuccess) {
     cudaFree(arena);
     delete m;
@@ -224,7 +225,9 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.ref_row = reinterpret_cast<const int32_t*>(base + o_ref);
   dm.arc_ptr = reinterpret_cast<const int32_t*>(base + o_aptr);
   dm.arcs_by_idx = reinterpret_cast<const int32_t*>(base + o_aidx);
-  dm.arcs_by_nbr = reinterpret_cast<const int32_t*>(base + o_anbr);
+  dm.slot_arc = reinterpret_cast<const int32_t*>(base + o_anbr);
+  dm.slot_nbr = reinterpret_cast<const int32_t*>(base + o_snbr);
+  dm.slot_of_arc = reinterpret_cast<const int32_t*>(base + o_soa);
   dm.gen_ptr = reinterpret_cast<const int32_t*>(base + o_gptr);
   dm.gens_at = reinterpret_cast<const int32_t*>(base + o_gat);
   dm.gbus = reinterpret_cast<const int32_t*>(base + o_gbus);
@@ -232,9 +235,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.c1 = reinterpret_cast<const double*>(base + o_c1);
   dm.c0 = reinterpret_cast<const double*>(base + o_c0);
   dm.krowptr = reinterpret_cast<const int32_t*>(base + o_krp);
-  dm.part_arc = reinterpret_cast<acopf::ArcPart*>(base + o_pa);
-  dm.part_br = reinterpret_cast<acopf::BranchPart*>(base + o_pb);
-  dm.obj_part = reinterpret_cast<double*>(base + o_obj);
+  dm.part_slot = reinterpret_cast<acopf::SlotPart*>(base + o_ps);
   *out = m;
   return ACOPF_OK;
 }

@@ -243,6 +243,12 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
                 return ja != jb ? ja < jb : a < b;
               });
   }
+  hm.slot_nbr.assign(2 * nl, 0);
+  hm.slot_of_arc.assign(2 * nl, 0);
+  for (int64_t s = 0; s < 2 * nl; ++s) {
+    hm.slot_nbr[s] = arc_nbr(hm.arcs_by_nbr[s]);
+    hm.slot_of_arc[hm.arcs_by_nbr[s]] = int32_t(s);
+  }
   hm.gen_ptr.assign(nb + 1, 0);
   for (int64_t g = 0; g < ng; ++g) hm.gen_ptr[hm.gbus[g] + 1]++;
   for (int64_t i = 0; i < nb; ++i) hm.gen_ptr[i + 1] += hm.gen_ptr[i];
@@ -466,6 +472,16 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     hm.gu[L.ST + l] = rate * rate;
   }
   return ACOPF_OK;
+}
+
+int32_t max_block_slots(const HostModel& hm) {
+  const int64_t nb = hm.L.nb;
+  int32_t mx = 0;
+  for (int64_t i0 = 0; i0 < nb; i0 += kBusThreads) {
+    const int64_t i1 = std::min<int64_t>(i0 + kBusThreads, nb);
+    mx = std::max(mx, hm.arc_ptr[i1] - hm.arc_ptr[i0]);
+  }
+  return mx;
 }
 
 }  // namespace acopf
