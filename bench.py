@@ -168,6 +168,7 @@ def run_ours(args, rank, world, local):
     grid = synth.workload_grid(args.workload)
     seed = synth.WORKLOADS[args.workload]["seed"]
     model = acopf.model_create(grid, local)
+    acopf.model_set_option(model, acopf.OPT_PDL, args.pdl)
     s = workload_sizes(model, grid)
     stream = torch.cuda.Stream(device=dev)
 
@@ -351,6 +352,8 @@ def main():
     ap.add_argument("--workload", default="80kbus", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-calls", type=int, default=3)
+    ap.add_argument("--pdl", type=int, default=1, choices=[0, 1],
+                    help="chain the two phases with programmatic dependent launch")
     ap.add_argument("--soak", type=float, default=1.0,
                     help="seconds of untimed calls (at least --warmup) before timing")
     args = ap.parse_args()

@@ -27,18 +27,20 @@
  *   objective f = sum_g c2 pg^2 + c1 pg + c0.
  *
  * Sparse outputs, with the fixed orders that the *_structure calls return:
- *   Jacobian A = dg/dx in COO: ref rows; pf rows [p_l, va_f, va_t, vm_f, vm_t]
- *     per branch; qf [q_l, ...]; pt [p_{nl+l}, ...]; qt [q_{nl+l}, ...];
- *     ang [va_f, va_t]; sf [p_l, q_l]; st [p_{nl+l}, q_{nl+l}]; balance vm
- *     terms (all Pbal rows, then all Qbal rows); generator terms (Pbal then
- *     Qbal, per generator); arc terms (Pbal then Qbal, per arc).
+ *   Jacobian A = dg/dx in COO: ref rows; pf rows with entries [p_l, va_f,
+ *     va_t, vm_f, vm_t]; qf [q_l, ...]; pt [p_{nl+l}, ...]; qt [q_{nl+l},
+ *     ...]; ang [va_f, va_t]; sf [p_l, q_l]; st [p_{nl+l}, q_{nl+l}];
+ *     balance vm terms (all Pbal rows, then all Qbal rows); generator terms
+ *     (Pbal then Qbal, per generator); arc terms (Pbal then Qbal, per arc).
+ *     Each branch pattern is stored entry-major: entry k of every branch,
+ *     then entry k + 1 (slot = section + k * n_branch + l).
  *   Lagrangian Hessian W = sigma d2f + sum_r y_r d2g_r, lower triangle in COO
- *     with duplicates: per branch the 10 entries of its (va_f, va_t, vm_f,
+ *     with duplicates: the 10 entries of each branch's (va_f, va_t, vm_f,
  *     vm_t) block in the order (va_f,va_f) (va_t,va_f) (va_t,va_t)
  *     (vm_f,va_f) (vm_f,va_t) (vm_f,vm_f) (vm_t,va_f) (vm_t,va_t) (vm_t,vm_f)
- *     (vm_t,vm_t), each stored (max, min) of the global indices; then per
- *     branch the diagonals of p_l, q_l, p_{nl+l}, q_{nl+l}; then (pg,pg) per
- *     generator; then (vm,vm) per bus.  The sign convention adds y_r g_r: the
+ *     (vm_t,vm_t), each stored (max, min) of the global indices, entry-major;
+ *     then the diagonals of p_l, q_l, p_{nl+l}, q_{nl+l}, entry-major; then
+ *     (pg,pg) per generator; then (vm,vm) per bus.  The sign convention adds y_r g_r: the
  *     paper's L = f - y'g (Sec. II.A) is obtained by passing -y.
  *   Condensed KKT matrix M_cond = W + delta_w I + Sigma_x + A' D A with
  *     C = (delta_c Sigma_s + (1 + delta_c delta_w) I)^-1, D = (Sigma_s +
@@ -199,6 +201,13 @@ acopf_status acopf_eval_assemble_host(acopf_model* model, const double* x, const
                                       const double* sigma_s, double delta_w, double delta_c,
                                       double* f, double* grad, double* cons, double* jvals,
                                       double* hvals, double* kvals, acopf_stream stream);
+
+/* Launch options of a model (not numerics: results are identical either way).
+ * ACOPF_OPT_PDL (default 1): launch the second phase of a call with
+ * programmatic dependent launch, so its independent work overlaps the first
+ * phase; 0 launches it after the first phase completes. */
+#define ACOPF_OPT_PDL 1
+acopf_status acopf_model_set_option(acopf_model* model, int32_t option, int64_t value);
 
 /* Number of kernel launches one call of each kind issues (for launch
  * accounting): kind 0 = eval_assemble, 1 = assemble_condensed_kkt_csr,

@@ -235,11 +235,13 @@ def bounds(grid):
 def jac_structure(grid):
     """(rows, cols) of the Jacobian in COO order, int32.
 
-    Order: ref rows; pf rows [p_l, va_f, va_t, vm_f, vm_t] per branch; qf
+    Order: ref rows; pf rows with entries [p_l, va_f, va_t, vm_f, vm_t]; qf
     [q_l, ...]; pt [p_{nl+l}, ...]; qt [q_{nl+l}, ...]; ang [va_f, va_t];
     sf [p_l, q_l]; st [p_{nl+l}, q_{nl+l}]; balance vm terms (P then Q, per
     bus); generator terms (P then Q, per generator); arc terms (P then Q, per
-    arc)."""
+    arc).  Within each branch pattern the entries are stored entry-major:
+    entry k of every branch, then entry k + 1 (the pattern's parameterised
+    sparsity expanded over its data, Sec. III.C)."""
     L = layout(grid)
     nl = L.nl
     f = np.asarray(grid.f, dtype=np.int64)
@@ -251,14 +253,14 @@ def jac_structure(grid):
     cols.append(L.VA + L.ref_buses)
     for base, var in ((L.PF, L.P + br), (L.QF, L.Q + br),
                       (L.PT, L.P + nl + br), (L.QT, L.Q + nl + br)):
-        rows.append(np.repeat(base + br, 5))
-        cols.append(np.concatenate([var[:, None], bus_cols], axis=1).ravel())
-    rows.append(np.repeat(L.ANG + br, 2))
-    cols.append(np.stack([L.VA + f, L.VA + t], axis=1).ravel())
-    rows.append(np.repeat(L.SF + br, 2))
-    cols.append(np.stack([L.P + br, L.Q + br], axis=1).ravel())
-    rows.append(np.repeat(L.ST + br, 2))
-    cols.append(np.stack([L.P + nl + br, L.Q + nl + br], axis=1).ravel())
+        rows.append(np.tile(base + br, 5))
+        cols.append(np.concatenate([var[:, None], bus_cols], axis=1).T.ravel())
+    rows.append(np.tile(L.ANG + br, 2))
+    cols.append(np.concatenate([L.VA + f, L.VA + t]))
+    rows.append(np.tile(L.SF + br, 2))
+    cols.append(np.concatenate([L.P + br, L.Q + br]))
+    rows.append(np.tile(L.ST + br, 2))
+    cols.append(np.concatenate([L.P + nl + br, L.Q + nl + br]))
     buses = np.arange(L.nb)
     rows += [L.PB + buses, L.QB + buses]
     cols += [L.VM + buses, L.VM + buses]
@@ -282,13 +284,13 @@ _HPAIRS = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 0), (3, 1), (3, 2
 def hess_structure(grid):
     """(rows, cols) of the lower-triangle Lagrangian Hessian in COO order.
 
-    Per branch the 10 entries of its (va_f, va_t, vm_f, vm_t) block in the
+    The 10 entries of each branch's (va_f, va_t, vm_f, vm_t) block in the
     local order (va_f,va_f) (va_t,va_f) (va_t,va_t) (vm_f,va_f) (vm_f,va_t)
     (vm_f,vm_f) (vm_t,va_f) (vm_t,va_t) (vm_t,vm_f) (vm_t,vm_t), each stored as
-    (max, min) of the global indices; then per branch the diagonals of
-    p_l, q_l, p_{nl+l}, q_{nl+l}; then (pg_g, pg_g) per generator; then
-    (vm_i, vm_i) per bus.  Entries with equal (row, col) are kept separately
-    (COO with duplicates)."""
+    (max, min) of the global indices, entry-major (entry e of every branch,
+    then entry e + 1); then the diagonals of p_l, q_l, p_{nl+l}, q_{nl+l},
+    entry-major; then (pg_g, pg_g) per generator; then (vm_i, vm_i) per bus.
+    Entries with equal (row, col) are kept separately (COO with duplicates)."""
     L = layout(grid)
     nl = L.nl
     f = np.asarray(grid.f, dtype=np.int64)
@@ -296,10 +298,10 @@ def hess_structure(grid):
     loc = np.stack([L.VA + f, L.VA + t, L.VM + f, L.VM + t], axis=1)
     ri = np.stack([loc[:, i] for i, _ in _HPAIRS], axis=1)
     ci = np.stack([loc[:, j] for _, j in _HPAIRS], axis=1)
-    r_blk = np.maximum(ri, ci).ravel()
-    c_blk = np.minimum(ri, ci).ravel()
+    r_blk = np.maximum(ri, ci).T.ravel()
+    c_blk = np.minimum(ri, ci).T.ravel()
     br = np.arange(nl)
-    th = np.stack([L.P + br, L.Q + br, L.P + nl + br, L.Q + nl + br], axis=1).ravel()
+    th = np.concatenate([L.P + br, L.Q + br, L.P + nl + br, L.Q + nl + br])
     gens = L.PG + np.arange(L.ng)
     buses = L.VM + np.arange(L.nb)
     rows = np.concatenate([r_blk, th, gens, buses])
@@ -440,17 +442,17 @@ def jacobian(grid, x):
     for form in _flow_forms(grid):
         d = _flow_value_and_derivs(form, vm_f, vm_t, c, s)
         # row = var - F:  [1, -dF/dva_f, -dF/dva_t, -dF/dvm_f, -dF/dvm_t]
-        v = np.stack([np.ones(nl), -d["th"][0], d["th"][0], -d["vmf"][0], -d["vmt"][0]], axis=1)
-        mm = np.stack([np.ones(nl), d["th"][1], d["th"][1], d["vmf"][1], d["vmt"][1]], axis=1)
-        vals.append(v.ravel())
-        mags.append(mm.ravel())
-    ang = np.stack([np.ones(nl), -np.ones(nl)], axis=1).ravel()
+        v = np.concatenate([np.ones(nl), -d["th"][0], d["th"][0], -d["vmf"][0], -d["vmt"][0]])
+        mm = np.concatenate([np.ones(nl), d["th"][1], d["th"][1], d["vmf"][1], d["vmt"][1]])
+        vals.append(v)
+        mags.append(mm)
+    ang = np.concatenate([np.ones(nl), -np.ones(nl)])
     vals.append(ang)
     mags.append(np.abs(ang))
     p = x[L.P:L.P + 2 * nl]
     q = x[L.Q:L.Q + 2 * nl]
     for sl in (slice(0, nl), slice(nl, 2 * nl)):
-        v = np.stack([2.0 * p[sl], 2.0 * q[sl]], axis=1).ravel()
+        v = np.concatenate([2.0 * p[sl], 2.0 * q[sl]])
         vals.append(v)
         mags.append(np.abs(v))
     vm = x[L.VM:L.VM + L.nb]
@@ -501,7 +503,7 @@ def hessian(grid, x, y, obj_weight=1.0):
             blkM[:, k] += np.abs(yr) * mag
     y_sf = y[L.SF:L.SF + nl]
     y_st = y[L.ST:L.ST + nl]
-    th = np.stack([2.0 * y_sf, 2.0 * y_sf, 2.0 * y_st, 2.0 * y_st], axis=1)
+    th = np.stack([2.0 * y_sf, 2.0 * y_sf, 2.0 * y_st, 2.0 * y_st], axis=0)
     c2 = np.asarray(grid.c2, dtype=np.float64)
     hg = obj_weight * 2.0 * c2
     Gs, Bs = np.asarray(grid.Gs, np.float64), np.asarray(grid.Bs, np.float64)
@@ -509,8 +511,8 @@ def hessian(grid, x, y, obj_weight=1.0):
     yQ = y[L.QB:L.QB + L.nb]
     hb = 2.0 * Gs * yP - 2.0 * Bs * yQ
     hbM = np.abs(2.0 * Gs * yP) + np.abs(2.0 * Bs * yQ)
-    vals = np.concatenate([blk.ravel(), th.ravel(), hg, hb])
-    mags = np.concatenate([blkM.ravel(), np.abs(th).ravel(), np.abs(hg), hbM])
+    vals = np.concatenate([blk.T.ravel(), th.ravel(), hg, hb])
+    mags = np.concatenate([blkM.T.ravel(), np.abs(th).ravel(), np.abs(hg), hbM])
     return vals, mags
 
 

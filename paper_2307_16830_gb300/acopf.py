@@ -86,6 +86,8 @@ _eval_assemble = _sig("acopf_eval_assemble", C.c_int32, _vp, _vp, _vp, C.c_doubl
 _eval_assemble_host = _sig("acopf_eval_assemble_host", C.c_int32, _vp, _vp, _vp, C.c_double, _vp,
                            _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _launches_per_call = _sig("acopf_launches_per_call", C.c_int32, C.c_int32)
+_model_set_option = _sig("acopf_model_set_option", C.c_int32, _vp, C.c_int32, C.c_int64)
+OPT_PDL = 1
 _measure_fp64 = _sig("acopf_measure_fp64_gflops", C.c_int32, C.c_int, _f64p)
 _profile_begin = _sig("acopf_profile_begin", C.c_int32, _vp, C.c_int32)
 _profile_end = _sig("acopf_profile_end", C.c_int32, _vp, _i32p, _f64p, _f64p, _f64p)
@@ -98,7 +100,7 @@ EXPORTED = [
     "acopf_eval_cons", "acopf_eval_jac_coo", "acopf_eval_hess_coo",
     "acopf_assemble_condensed_kkt_csr", "acopf_eval_assemble", "acopf_eval_assemble_host",
     "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_profile_begin",
-    "acopf_profile_end",
+    "acopf_profile_end", "acopf_model_set_option",
 ]
 
 
@@ -325,3 +327,7 @@ def profile_end(model: Model):
     _check(_profile_end(model.handle, C.byref(n), C.byref(a), C.byref(b), C.byref(c)),
            "acopf_profile_end")
     return n.value, a.value, b.value, c.value
+
+
+def model_set_option(model: Model, option: int, value: int) -> None:
+    _check(_model_set_option(model.handle, int(option), int(value)), "acopf_model_set_option")

@@ -42,6 +42,15 @@ struct alignas(16) SlotPart {
   double aa, ma, mm, mx, vv, ww;
 };
 
+// The bus's own terms of its two diagonal entries of M_cond, left by the
+// bus-input blocks of phase 1 for the bus rows of phase 2 (device scratch,
+// in the bus processing order):
+//   va = Sigma_x(va_i) + delta_w + D_ref (reference buses),
+//   vm = Sigma_x(vm_i) + delta_w + W_bus + D_P (2 Gs vm)^2 + D_Q (2 Bs vm)^2.
+struct alignas(16) BusDiag {
+  double va, vm;
+};
+
 // Read-only device view of a model, passed to kernels by value.
 struct DevModel {
   Layout L;
@@ -57,11 +66,18 @@ struct DevModel {
   const int32_t* ref_row;      // per bus: its reference row, or -1
   const int32_t* arc_ptr;      // nb + 1
   const int32_t* arcs_by_idx;  // 2 nl: arcs of each bus, ascending arc id
-  const int32_t* slot_arc;     // 2 nl: arcs of each bus, ascending (other end, arc id)
+  // Bus phase processing order: buses sorted by (number of arcs, number of
+  // generators) so that the 32 buses of a warp run loops of equal length.
+  // Slots and balance terms are laid out in this order.
+  const int32_t* porder;       // nb: bus at processing position p
+  const int32_t* pslot_ptr;    // nb + 1: slots of position p
   const int32_t* slot_nbr;     // 2 nl: other end of each slot's arc
   const int32_t* slot_of_arc;  // 2 nl: slot of each arc
   const int32_t* gen_ptr;      // nb + 1
   const int32_t* gens_at;      // ng: generators of each bus, ascending id
+  const int32_t* pbal_ptr;     // nb + 1: balance terms of position p
+  const int32_t* bal_idx;      // ng + 2 nl: x index of pg (generators, ascending) then of
+                               // p_a (arcs, ascending) in each bus's active balance row
   // generators
   const int32_t* gbus;
   const double* c2;
@@ -69,9 +85,21 @@ struct DevModel {
   const double* c0;
   // M_cond structure
   const int32_t* krowptr;      // n + 1
+  // Per branch: start of its four arc rows p_l, q_l, p_{nl+l}, q_{nl+l} in
+  // M_cond, and the generator count and rank (number of earlier arcs) at
+  // its from and to buses packed as ngf | rankf << 8 | ngt << 16 | rankt << 24
+  // (kCountsWide when one of them exceeds 255: the kernel then reads them
+  // from gen_ptr and the row starts).
+  const int4* brow;            // nl
+  const uint32_t* bcnt;        // nl
   // scratch
   SlotPart* part_slot;         // 2 nl
-  int32_t slot_cap;            // slots a bus block stages in shared memory
+  BusDiag* bus_diag;           // nb
+  double* obj_part;            // one per generator block
+  unsigned int* obj_ticket;    // arrival counter of the generator blocks (reset by the last)
+  // launch options
+  int32_t has_shunt;           // some bus has Gs != 0 or Bs != 0
+  int32_t pdl;                 // chain the phases with programmatic dependent launch
 };
 
 // Host model: everything the symbolic phase builds.
@@ -81,7 +109,9 @@ struct HostModel {
   std::vector<double> coef;  // NCOEF * nl
   std::vector<double> Pd, Qd, Gs, Bs, c2, c1, c0;
   std::vector<int32_t> arc_ptr, arcs_by_idx, arcs_by_nbr, gen_ptr, gens_at;
-  std::vector<int32_t> slot_nbr, slot_of_arc;
+  std::vector<int32_t> porder, pslot_ptr, slot_nbr, slot_of_arc, pbal_ptr, bal_idx;
+  std::vector<int32_t> brow;   // 4 per branch
+  std::vector<uint32_t> bcnt;
   std::vector<int32_t> jrows, jcols, hrows, hcols, krowptr, kcolind;
   std::vector<double> xl, xu, gl, gu;
 };
@@ -90,20 +120,18 @@ struct HostModel {
 acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, const acopf_gens* G,
                               HostModel& hm, std::string& err);
 
+constexpr uint32_t kCountsWide = 0xFFFFFFFFu;
+
 // Kernel launch configuration.
 constexpr int kBranchThreads = 128;
 constexpr int kBusThreads = 128;
 constexpr int kGenThreads = 128;
-// Shared-memory staging of slot partials in the bus phase: at most this many
-// slots per block (48 KB of SlotPart + neighbour index); larger blocks read
-// global memory directly.
-constexpr int kSlotCapMax = 940;
-constexpr int kSlotBytes = sizeof(SlotPart) + sizeof(int32_t);
+// Balance-row terms a warp of bus threads stages in shared memory (P and Q
+// values, 16 bytes each); warps with more terms sum from global memory.
+constexpr int kBalCap = 192;
 
 inline int32_t ceil_div(int64_t a, int64_t b) { return static_cast<int32_t>((a + b - 1) / b); }
 
-// Largest number of slots (arcs) over the bus blocks of a model.
-int32_t max_block_slots(const HostModel& hm);
 
 // What a launch computes.
 enum : unsigned {

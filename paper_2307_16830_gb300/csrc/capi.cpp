@@ -150,7 +150,10 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const acopf::Layout& L = hm.L;
   acopf::DevModel& dm = m->dm;
   dm.L = L;
-  dm.slot_cap = std::min(acopf::max_block_slots(hm), acopf::kSlotCapMax);
+  dm.has_shunt = 0;
+  for (int32_t i = 0; i < L.nb; ++i)
+    if (hm.Gs[i] != 0.0 || hm.Bs[i] != 0.0) dm.has_shunt = 1;
+  dm.pdl = 1;
   if (device < 0) {
     *out = m;
     return ACOPF_OK;
@@ -169,13 +172,20 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const size_t o_Gs = p.take<double>(nb), o_Bs = p.take<double>(nb);
   const size_t o_ref = p.take<int32_t>(nb);
   const size_t o_aptr = p.take<int32_t>(nb + 1);
-  const size_t o_aidx = p.take<int32_t>(2 * nl), o_anbr = p.take<int32_t>(2 * nl);
+  const size_t o_aidx = p.take<int32_t>(2 * nl);
   const size_t o_snbr = p.take<int32_t>(2 * nl), o_soa = p.take<int32_t>(2 * nl);
+  const size_t o_pord = p.take<int32_t>(nb), o_psp = p.take<int32_t>(nb + 1);
   const size_t o_gptr = p.take<int32_t>(nb + 1), o_gat = p.take<int32_t>(ng);
   const size_t o_gbus = p.take<int32_t>(ng);
+  const size_t o_bptr = p.take<int32_t>(nb + 1), o_bidx = p.take<int32_t>(ng + 2 * nl);
   const size_t o_c2 = p.take<double>(ng), o_c1 = p.take<double>(ng), o_c0 = p.take<double>(ng);
   const size_t o_krp = p.take<int32_t>(n + 1);
+  const size_t o_brow = p.take<int4>(nl), o_bcnt = p.take<uint32_t>(nl);
   const size_t o_ps = p.take<acopf::SlotPart>(2 * nl);
+  const size_t o_bd = p.take<acopf::BusDiag>(nb);
+  const size_t n_obj = size_t(acopf::ceil_div(L.ng, acopf::kGenThreads)) + 1;
+  const size_t o_obj = p.take<double>(n_obj);
+  const size_t o_tick = p.take<unsigned int>(1);
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, p.off);
   if (e != cudaSuccess) {
@@ -200,7 +210,6 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_ref, hm.ref_row.data(), nb * 4);
   if (e == cudaSuccess) e = up(o_aptr, hm.arc_ptr.data(), (nb + 1) * 4);
   if (e == cudaSuccess) e = up(o_aidx, hm.arcs_by_idx.data(), 2 * nl * 4);
-  if (e == cudaSuccess) e = up(o_anbr, hm.arcs_by_nbr.data(), 2 * nl * 4);
   if (e == cudaSuccess) e = up(o_snbr, hm.slot_nbr.data(), 2 * nl * 4);
   if (e == cudaSuccess) e = up(o_soa, hm.slot_of_arc.data(), 2 * nl * 4);
   if (e == cudaSuccess) e = up(o_gptr, hm.gen_ptr.data(), (nb + 1) * 4);
@@ -210,6 +219,14 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_c1, hm.c1.data(), ng * 8);
   if (e == cudaSuccess) e = up(o_c0, hm.c0.data(), ng * 8);
   if (e == cudaSuccess) e = up(o_krp, hm.krowptr.data(), (n + 1) * 4);
+  if (e == cudaSuccess) e = up(o_brow, hm.brow.data(), nl * 16);
+  if (e == cudaSuccess) e = up(o_bcnt, hm.bcnt.data(), nl * 4);
+  if (e == cudaSuccess) e = up(o_bptr, hm.pbal_ptr.data(), (nb + 1) * 4);
+  if (e == cudaSuccess) e = up(o_pord, hm.porder.data(), nb * 4);
+  if (e == cudaSuccess) e = up(o_psp, hm.pslot_ptr.data(), (nb + 1) * 4);
+  if (e == cudaSuccess) e = up(o_bidx, hm.bal_idx.data(), (ng + 2 * nl) * 4);
+  if (e == cudaSuccess) e = cudaMemset(base + o_obj, 0, n_obj * 8);
+  if (e == cudaSuccess) e = cudaMemset(base + o_tick, 0, sizeof(unsigned int));
   if (e != cudaSuccess) {
     cudaFree(arena);
     delete m;
@@ -225,7 +242,8 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.ref_row = reinterpret_cast<const int32_t*>(base + o_ref);
   dm.arc_ptr = reinterpret_cast<const int32_t*>(base + o_aptr);
   dm.arcs_by_idx = reinterpret_cast<const int32_t*>(base + o_aidx);
-  dm.slot_arc = reinterpret_cast<const int32_t*>(base + o_anbr);
+  dm.porder = reinterpret_cast<const int32_t*>(base + o_pord);
+  dm.pslot_ptr = reinterpret_cast<const int32_t*>(base + o_psp);
   dm.slot_nbr = reinterpret_cast<const int32_t*>(base + o_snbr);
   dm.slot_of_arc = reinterpret_cast<const int32_t*>(base + o_soa);
   dm.gen_ptr = reinterpret_cast<const int32_t*>(base + o_gptr);
@@ -235,7 +253,14 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.c1 = reinterpret_cast<const double*>(base + o_c1);
   dm.c0 = reinterpret_cast<const double*>(base + o_c0);
   dm.krowptr = reinterpret_cast<const int32_t*>(base + o_krp);
+  dm.brow = reinterpret_cast<const int4*>(base + o_brow);
+  dm.bcnt = reinterpret_cast<const uint32_t*>(base + o_bcnt);
   dm.part_slot = reinterpret_cast<acopf::SlotPart*>(base + o_ps);
+  dm.bus_diag = reinterpret_cast<acopf::BusDiag*>(base + o_bd);
+  dm.pbal_ptr = reinterpret_cast<const int32_t*>(base + o_bptr);
+  dm.bal_idx = reinterpret_cast<const int32_t*>(base + o_bidx);
+  dm.obj_part = reinterpret_cast<double*>(base + o_obj);
+  dm.obj_ticket = reinterpret_cast<unsigned int*>(base + o_tick);
   *out = m;
   return ACOPF_OK;
 }
@@ -527,6 +552,18 @@ acopf_status acopf_eval_assemble_host(acopf_model* model, const double* x, const
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_eval_assemble_host: download");
   return ACOPF_OK;
+}
+
+acopf_status acopf_model_set_option(acopf_model* model, int32_t option, int64_t value) {
+  if (!model) return fail(ACOPF_E_INVALID_ARG, "null model");
+  switch (option) {
+    case ACOPF_OPT_PDL:
+      if (value != 0 && value != 1) return fail(ACOPF_E_INVALID_ARG, "ACOPF_OPT_PDL takes 0 or 1");
+      model->dm.pdl = int32_t(value);
+      return ACOPF_OK;
+    default:
+      return fail(ACOPF_E_INVALID_ARG, "unknown option");
+  }
 }
 
 int32_t acopf_launches_per_call(int32_t kind) {

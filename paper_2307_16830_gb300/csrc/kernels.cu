@@ -4,21 +4,25 @@
 // Jacobian, Lagrangian Hessian and the condensed KKT matrix of Sec. IV.C)
 // is two launches:
 //
-//   phase 1  one thread per branch: patterns 3-9 fused around one sincos per
-//            branch, which values, Jacobian, the merged Hessian block and the
-//            branch's KKT contributions all share.  The branch writes the
-//            four arc rows of M_cond directly and leaves its contributions to
-//            the bus rows in the slot scratch.
-//   phase 2  one thread per bus (patterns 2, 10-15: balance rows summed over
-//            the bus's generators and arcs in a fixed order, no atomics; the
-//            bus rows of M_cond gathered from the slot partials staged in
-//            shared memory), one thread per generator (pattern 1 and the
-//            generator rows of M_cond), and one block that reduces the
-//            objective in a fixed order.
+//   phase 1  branch blocks, one thread per branch: patterns 3-9 fused around
+//            one sincos per branch, which values, Jacobian, the merged
+//            Hessian block and the branch's KKT contributions all share; the
+//            branch writes the four arc rows of M_cond directly and leaves its
+//            contributions to the bus rows in the slot scratch.
+//            Bus-input blocks, one thread per bus: patterns 2, 10-15 (balance
+//            rows summed over the bus's generators and arcs in a fixed order,
+//            no atomics) and the bus's own diagonal terms of M_cond.
+//            Generator blocks, one thread per generator: pattern 1, the
+//            generator rows of M_cond, and the objective reduced in a fixed
+//            order.  The bus and generator blocks depend on nothing the
+//            branch blocks write; they run behind them and fill the tail.
+//   phase 2  one thread per bus: the bus rows of M_cond, gathered from the
+//            slot partials of its incident branches.
 //
-// Phase 2 is launched with programmatic dependent launch: its blocks start
-// while phase 1 drains and do all the work that reads only the call's inputs
-// before waiting on the grid dependency; only the bus rows of M_cond wait.
+// Calls that do not assemble M_cond are the single phase-1 launch.  Phase 2
+// is launched with programmatic dependent launch: its blocks load the
+// structure they need while phase 1 drains and wait on the grid dependency
+// before reading phase 1's partial sums.
 //
 // Every K entry has one owner thread that writes it (arc rows: branch
 // threads; generator rows: generator threads; bus rows: bus threads), so the
@@ -26,12 +30,14 @@
 // the ones model.cpp documents.
 //
 // FP64 throughput on this part is about 0.6 T FMA/s, far below what its
-// memory bandwidth could feed, so the kernels are written to minimise FP64
-// pipe instructions: the four flows share two trigonometric brackets, the
-// Hessians of the four flow rows merge into one weighted bracket, the
-// condensation factor is a plain copy when delta_w = delta_c = 0, KKT
-// entries of the form D (+-1) J are copies, and stored negations flip the
-// sign bit with an integer instruction instead of an FP64 one.
+// memory bandwidth could feed, and an FP64 warp instruction occupies the
+// SM's FP64 unit for the same time however many of its lanes are active.
+// So the kernels minimise FP64 warp instructions: the four flows share two
+// trigonometric brackets, the Hessians of the four flow rows merge into one
+// weighted bracket, the condensation factor is a plain copy when
+// delta_w = delta_c = 0, KKT entries of the form D (+-1) J are copies,
+// stored negations and exact doublings use integer instructions, and the
+// buses are processed in an order that gives every warp loops of one length.
 #include <cstdint>
 
 #include "acopf_internal.h"
@@ -52,6 +58,18 @@ __device__ __forceinline__ T ld(const T* p) {
 // -x with an integer sign-bit flip (keeps the negation off the FP64 pipe).
 __device__ __forceinline__ double neg(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ULL));
+}
+
+__device__ __noinline__ double twice_slow(double x) { return x + x; }
+
+// 2x.  For a normal x whose double does not overflow this adds one to the
+// exponent field with an integer instruction (exact, and off the FP64 pipe);
+// zeros, subnormals, infinities and NaNs take x + x.
+__device__ __forceinline__ double twice(double x) {
+  const long long b = __double_as_longlong(x);
+  const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
+  if (e - 1u < 0x7FDu) return __longlong_as_double(b + (1LL << 52));
+  return twice_slow(x);
 }
 
 // D = (Sigma_s + delta_w) / (delta_c Sigma_s + 1 + delta_c delta_w)  (Sec. IV.C);
@@ -110,7 +128,9 @@ __device__ __forceinline__ void put4(double* __restrict__ K, int r0, bool f_lo, 
 // ===========================================================================
 // Phase 1, fused path: branch thread.
 // ===========================================================================
-template <unsigned W, bool REG>
+// SHUNT = false: every bus has Gs = Bs = 0, so the balance rows' vm
+// coefficients 2 Gs vm and -2 Bs vm vanish from the arc rows of M_cond.
+template <unsigned W, bool REG, bool SHUNT>
 __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs& a, int l) {
   const Layout& L = dm.L;
   const int nl = L.nl;
@@ -126,12 +146,12 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
   }
   if constexpr ((W & OUT_JAC) != 0) {
     double* __restrict__ J = a.jvals;
-    J[L.JPF + 5 * l] = 1.0;
-    J[L.JQF + 5 * l] = 1.0;
-    J[L.JPT + 5 * l] = 1.0;
-    J[L.JQT + 5 * l] = 1.0;
-    J[L.JANG + 2 * l] = 1.0;
-    J[L.JANG + 2 * l + 1] = -1.0;
+    J[L.JPF + l] = 1.0;
+    J[L.JQF + l] = 1.0;
+    J[L.JPT + l] = 1.0;
+    J[L.JQT + l] = 1.0;
+    J[L.JANG + l] = 1.0;
+    J[L.JANG + nl + l] = -1.0;
     J[L.JPBA + l] = 1.0;
     J[L.JPBA + nl + l] = 1.0;
     J[L.JQBA + l] = 1.0;
@@ -164,7 +184,7 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
     const double vfE_t = vm_f * E_t, vfEp_t = vm_f * Ep_t;
     const double VE_f = vm_f * vtE_f, VEp_f = vm_f * vtEp_f;
     const double VE_t = vm_t * vfE_t, VEp_t = vm_t * vfEp_t;
-    const double tvf = vm_f + vm_f, tvt = vm_t + vm_t;
+    const double tvf = twice(vm_f), tvt = twice(vm_t);
 
     // dF/dth, dF/dvm_f, dF/dvm_t of each flow (th_qt = -VE_t is used negated).
     const double th_pf = VEp_f, th_qf = VE_f, th_pt = VEp_t;
@@ -186,34 +206,35 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
       g[L.SF + l] = fma(p_f, p_f, q_f * q_f);
       g[L.ST + l] = fma(p_t, p_t, q_t * q_t);
     }
-    const double jp_f = p_f + p_f, jq_f = q_f + q_f, jp_t = p_t + p_t, jq_t = q_t + q_t;
+    const double jp_f = twice(p_f), jq_f = twice(q_f), jp_t = twice(p_t), jq_t = twice(q_t);
     if constexpr ((W & OUT_JAC) != 0) {
-      // J row = [1, -dF/dth, dF/dth, -dF/dvm_f, -dF/dvm_t]
+      // J row = [1, -dF/dth, dF/dth, -dF/dvm_f, -dF/dvm_t], entry k of every
+      // branch's row stored contiguously (section + k nl + l).
       double* __restrict__ J = a.jvals;
-      double* jp = J + L.JPF + 5 * l;
-      jp[1] = neg(th_pf);
-      jp[2] = th_pf;
-      jp[3] = neg(mf_pf);
-      jp[4] = neg(mt_pf);
-      jp = J + L.JQF + 5 * l;
-      jp[1] = neg(th_qf);
-      jp[2] = th_qf;
-      jp[3] = neg(mf_qf);
-      jp[4] = nmt_qf;
-      jp = J + L.JPT + 5 * l;
-      jp[1] = neg(th_pt);
-      jp[2] = th_pt;
-      jp[3] = neg(mf_pt);
-      jp[4] = neg(mt_pt);
-      jp = J + L.JQT + 5 * l;
-      jp[1] = VE_t;
-      jp[2] = neg(VE_t);
-      jp[3] = neg(mf_qt);
-      jp[4] = neg(mt_qt);
-      J[L.JSF + 2 * l] = jp_f;
-      J[L.JSF + 2 * l + 1] = jq_f;
-      J[L.JST + 2 * l] = jp_t;
-      J[L.JST + 2 * l + 1] = jq_t;
+      double* jp = J + L.JPF + l;
+      jp[nl] = neg(th_pf);
+      jp[2 * nl] = th_pf;
+      jp[3 * nl] = neg(mf_pf);
+      jp[4 * nl] = neg(mt_pf);
+      jp = J + L.JQF + l;
+      jp[nl] = neg(th_qf);
+      jp[2 * nl] = th_qf;
+      jp[3 * nl] = neg(mf_qf);
+      jp[4 * nl] = nmt_qf;
+      jp = J + L.JPT + l;
+      jp[nl] = neg(th_pt);
+      jp[2 * nl] = th_pt;
+      jp[3 * nl] = neg(mf_pt);
+      jp[4 * nl] = neg(mt_pt);
+      jp = J + L.JQT + l;
+      jp[nl] = VE_t;
+      jp[2 * nl] = neg(VE_t);
+      jp[3 * nl] = neg(mf_qt);
+      jp[4 * nl] = neg(mt_qt);
+      J[L.JSF + l] = jp_f;
+      J[L.JSF + nl + l] = jq_f;
+      J[L.JST + l] = jp_t;
+      J[L.JST + nl + l] = jq_t;
     }
     constexpr bool kNeedH = (W & (OUT_HESS | OUT_KKT)) != 0;
     if constexpr (kNeedH) {
@@ -231,25 +252,25 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
       const double V = vm_f * vm_t;
       const double VnTH = V * nTH;
       const double vtTP = vm_t * nTP, vfTP = vm_f * nTP;  // = -(vm TP)
-      const double AF2 = AF + AF, AT2 = AT + AT;
-      const double hs_f = y_sf + y_sf, hs_t = y_st + y_st;
+      const double AF2 = twice(AF), AT2 = twice(AT);
+      const double hs_f = twice(y_sf), hs_t = twice(y_st);
       if constexpr ((W & OUT_HESS) != 0) {
-        double* __restrict__ H = a.hvals + L.HBLK + 10 * l;
+        double* __restrict__ H = a.hvals + L.HBLK + l;
         H[0] = VnTH;
-        H[1] = neg(VnTH);
-        H[2] = VnTH;
-        H[3] = neg(vtTP);
-        H[4] = vtTP;
-        H[5] = AF2;
-        H[6] = neg(vfTP);
-        H[7] = vfTP;
-        H[8] = neg(nTH);
-        H[9] = AT2;
-        double* __restrict__ Ht = a.hvals + L.HTH + 4 * l;
+        H[nl] = neg(VnTH);
+        H[2 * nl] = VnTH;
+        H[3 * nl] = neg(vtTP);
+        H[4 * nl] = vtTP;
+        H[5 * nl] = AF2;
+        H[6 * nl] = neg(vfTP);
+        H[7 * nl] = vfTP;
+        H[8 * nl] = neg(nTH);
+        H[9 * nl] = AT2;
+        double* __restrict__ Ht = a.hvals + L.HTH + l;
         Ht[0] = hs_f;
-        Ht[1] = hs_f;
-        Ht[2] = hs_t;
-        Ht[3] = hs_t;
+        Ht[nl] = hs_f;
+        Ht[2 * nl] = hs_t;
+        Ht[3 * nl] = hs_t;
       }
       if constexpr ((W & OUT_KKT) != 0) {
         const double* __restrict__ ss = a.sigma_s;
@@ -297,63 +318,78 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
 
         // Arc rows.  Balance-row coefficient of vm at the arc's bus:
         // Pbal: 2 Gs vm, Qbal: -2 Bs vm.
-        const double jPv_f = ld(dm.Gs + f) * tvf, jQv_f = -(ld(dm.Bs + f) * tvf);
-        const double jPv_t = ld(dm.Gs + t) * tvt, jQv_t = -(ld(dm.Bs + t) * tvt);
+        double e_Pf = neg(B_pf), e_Qf = neg(B_qf), e_Pt = neg(C_pt), e_Qt = neg(C_qt);
+        if constexpr (SHUNT) {
+          const double jPv_f = ld(dm.Gs + f) * tvf, jQv_f = -(ld(dm.Bs + f) * tvf);
+          const double jPv_t = ld(dm.Gs + t) * tvt, jQv_t = -(ld(dm.Bs + t) * tvt);
+          e_Pf = fma(D_Pf, jPv_f, -B_pf);
+          e_Qf = fma(D_Qf, jQv_f, -B_qf);
+          e_Pt = fma(D_Pt, jPv_t, -C_pt);
+          e_Qt = fma(D_Qt, jQv_t, -C_qt);
+        }
         const double Dsp_f = D_sf * jp_f, Dsp_t = D_st * jp_t;
-        const int* __restrict__ rp = dm.krowptr;
         double* __restrict__ K = a.kvals;
         const bool f_lo = f < t;
-        const int ngf = ld(dm.gen_ptr + f + 1) - ld(dm.gen_ptr + f);
-        const int ngt = ld(dm.gen_ptr + t + 1) - ld(dm.gen_ptr + t);
+        // Row starts and, per bus, generator count and arc rank (row
+        // p_a = [4 bus entries][generators][earlier arcs][diagonal],
+        // row q_a = [4 bus entries][generators][p_a][earlier arcs][diagonal]).
+        const int4 rs = ld(dm.brow + l);
+        const uint32_t cnt = ld(dm.bcnt + l);
+        int ngf, rkf, ngt, rkt;
+        if (cnt != kCountsWide) {
+          ngf = cnt & 0xFF;
+          rkf = (cnt >> 8) & 0xFF;
+          ngt = (cnt >> 16) & 0xFF;
+          rkt = cnt >> 24;
+        } else {
+          const int* __restrict__ rp = dm.krowptr;
+          ngf = ld(dm.gen_ptr + f + 1) - ld(dm.gen_ptr + f);
+          ngt = ld(dm.gen_ptr + t + 1) - ld(dm.gen_ptr + t);
+          rkf = ld(rp + iPf + 1) - rs.x - 5 - ngf;
+          rkt = ld(rp + iPt + 1) - rs.z - 5 - ngt;
+        }
         const double nD_Pf = neg(D_Pf), nD_Qf = neg(D_Qf), nD_Pt = neg(D_Pt), nD_Qt = neg(D_Qt);
         // row p_l (from arc, bus f)
         {
-          const int r0 = ld(rp + iPf), r1 = ld(rp + iPf + 1);
-          put4(K, r0, f_lo, neg(A_pf), A_pf, fma(D_Pf, jPv_f, -B_pf), neg(C_pf));
+          const int r0 = rs.x;
+          put4(K, r0, f_lo, neg(A_pf), A_pf, e_Pf, neg(C_pf));
           int k = r0 + 4;
           for (int e = 0; e < ngf; ++e) K[k++] = nD_Pf;
-          for (; k < r1 - 1; ++k) K[k] = D_Pf;
-          K[r1 - 1] = sxw<REG>(ld(sx + iPf), dw) + hs_f + D_pf + fma(Dsp_f, jp_f, D_Pf);
+          for (int e = 0; e < rkf; ++e) K[k++] = D_Pf;
+          K[k] = sxw<REG>(ld(sx + iPf), dw) + hs_f + D_pf + fma(Dsp_f, jp_f, D_Pf);
         }
         // row q_l
         {
-          const int r0 = ld(rp + iQf), r1 = ld(rp + iQf + 1);
-          put4(K, r0, f_lo, neg(A_qf), A_qf, fma(D_Qf, jQv_f, -B_qf), nC_qf);
+          const int r0 = rs.y;
+          put4(K, r0, f_lo, neg(A_qf), A_qf, e_Qf, nC_qf);
           int k = r0 + 4;
           for (int e = 0; e < ngf; ++e) K[k++] = nD_Qf;
           K[k++] = Dsp_f * jq_f;
-          for (; k < r1 - 1; ++k) K[k] = D_Qf;
-          K[r1 - 1] = sxw<REG>(ld(sx + iQf), dw) + hs_f + D_qf + fma(D_sf * jq_f, jq_f, D_Qf);
+          for (int e = 0; e < rkf; ++e) K[k++] = D_Qf;
+          K[k] = sxw<REG>(ld(sx + iQf), dw) + hs_f + D_qf + fma(D_sf * jq_f, jq_f, D_Qf);
         }
         // row p_{nl+l} (to arc, bus t)
         {
-          const int r0 = ld(rp + iPt), r1 = ld(rp + iPt + 1);
-          put4(K, r0, f_lo, neg(A_pt), A_pt, neg(B_pt), fma(D_Pt, jPv_t, -C_pt));
+          const int r0 = rs.z;
+          put4(K, r0, f_lo, neg(A_pt), A_pt, neg(B_pt), e_Pt);
           int k = r0 + 4;
           for (int e = 0; e < ngt; ++e) K[k++] = nD_Pt;
-          for (; k < r1 - 1; ++k) K[k] = D_Pt;
-          K[r1 - 1] = sxw<REG>(ld(sx + iPt), dw) + hs_t + D_pt + fma(Dsp_t, jp_t, D_Pt);
+          for (int e = 0; e < rkt; ++e) K[k++] = D_Pt;
+          K[k] = sxw<REG>(ld(sx + iPt), dw) + hs_t + D_pt + fma(Dsp_t, jp_t, D_Pt);
         }
         // row q_{nl+l}
         {
-          const int r0 = ld(rp + iQt), r1 = ld(rp + iQt + 1);
-          put4(K, r0, f_lo, nA_qt, neg(nA_qt), neg(B_qt), fma(D_Qt, jQv_t, -C_qt));
+          const int r0 = rs.w;
+          put4(K, r0, f_lo, nA_qt, neg(nA_qt), neg(B_qt), e_Qt);
           int k = r0 + 4;
           for (int e = 0; e < ngt; ++e) K[k++] = nD_Qt;
           K[k++] = Dsp_t * jq_t;
-          for (; k < r1 - 1; ++k) K[k] = D_Qt;
-          K[r1 - 1] = sxw<REG>(ld(sx + iQt), dw) + hs_t + D_qt + fma(D_st * jq_t, jq_t, D_Qt);
+          for (int e = 0; e < rkt; ++e) K[k++] = D_Qt;
+          K[k] = sxw<REG>(ld(sx + iQt), dw) + hs_t + D_qt + fma(D_st * jq_t, jq_t, D_Qt);
         }
       }
     }
   }
-}
-
-template <unsigned W, bool REG>
-__global__ void __launch_bounds__(kBranchThreads, 6) k_phase1(DevModel dm, EvalArgs a) {
-  pdl_trigger();
-  const int l = blockIdx.x * kBranchThreads + threadIdx.x;
-  if (l < dm.L.nl) branch_fused<W, REG>(dm, a, l);
 }
 
 // ===========================================================================
@@ -375,10 +411,10 @@ __device__ __forceinline__ void branch_from_arrays(const DevModel& dm, const Eva
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
 #pragma unroll
-    for (int e = 0; e < 5; ++e) j[q][e] = ld(J + base[q] + 5 * l + e);
+    for (int e = 0; e < 5; ++e) j[q][e] = ld(J + base[q] + e * nl + l);
     D[q] = dcond<REG>(ld(ss + crow[q] + l), dw, dc);
   }
-  const double ja0 = ld(J + L.JANG + 2 * l), ja1 = ld(J + L.JANG + 2 * l + 1);
+  const double ja0 = ld(J + L.JANG + l), ja1 = ld(J + L.JANG + nl + l);
   const double D_an = dcond<REG>(ld(ss + L.ANG + l), dw, dc);
   // block over local (va_f, va_t, vm_f, vm_t) = Jacobian columns 1..4
   double blk[10];
@@ -386,7 +422,7 @@ __device__ __forceinline__ void branch_from_arrays(const DevModel& dm, const Eva
   const int pv[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
 #pragma unroll
   for (int e = 0; e < 10; ++e) {
-    double acc = ld(Hv + L.HBLK + 10 * l + e);
+    double acc = ld(Hv + L.HBLK + e * nl + l);
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc = fma(D[q] * j[q][1 + pu[e]], j[q][1 + pv[e]], acc);
     blk[e] = acc;
@@ -401,8 +437,8 @@ __device__ __forceinline__ void branch_from_arrays(const DevModel& dm, const Eva
       SlotPart{blk[2], blk[7], blk[9], blk[6], blk[1], blk[8]};
 
   // arc rows
-  const double js_f0 = ld(J + L.JSF + 2 * l), js_f1 = ld(J + L.JSF + 2 * l + 1);
-  const double js_t0 = ld(J + L.JST + 2 * l), js_t1 = ld(J + L.JST + 2 * l + 1);
+  const double js_f0 = ld(J + L.JSF + l), js_f1 = ld(J + L.JSF + nl + l);
+  const double js_t0 = ld(J + L.JST + l), js_t1 = ld(J + L.JST + nl + l);
   const double D_sf = dcond<REG>(ld(ss + L.SF + l), dw, dc);
   const double D_st = dcond<REG>(ld(ss + L.ST + l), dw, dc);
   const int* __restrict__ rp = dm.krowptr;
@@ -440,21 +476,14 @@ __device__ __forceinline__ void branch_from_arrays(const DevModel& dm, const Eva
     const int a0 = ld(dm.arc_ptr + bus);
     for (int e = a0; k < r1 - 1; ++e) K[k++] = DBa * ld(J + asec + ld(dm.arcs_by_idx + e));
     const double jsv = isq ? js1 : js0;
-    const double hth = ld(Hv + L.HTH + 4 * l + q);
+    const double hth = ld(Hv + L.HTH + q * nl + l);
     K[r1 - 1] =
         sxw<REG>(ld(sx + var), dw) + hth + fma(Dj0, j[q][0], fma(D_s * jsv, jsv, DBa * jBa));
   }
 }
 
-template <bool REG>
-__global__ void __launch_bounds__(kBranchThreads) k_asm_phase1(DevModel dm, EvalArgs a) {
-  pdl_trigger();
-  const int l = blockIdx.x * kBranchThreads + threadIdx.x;
-  if (l < dm.L.nl) branch_from_arrays<REG>(dm, a, l);
-}
-
 // ===========================================================================
-// Phase 2: generator threads (no dependency on phase 1).
+// Generator threads (no dependency on the branch threads).
 // ===========================================================================
 template <unsigned W, bool REG>
 __device__ __forceinline__ void gen_fused(const DevModel& dm, const EvalArgs& a, int g) {
@@ -526,51 +555,301 @@ __device__ __forceinline__ void gen_from_arrays(const DevModel& dm, const EvalAr
 }
 
 // ===========================================================================
-// Phase 2: bus rows of M_cond from the slot partials.
+// Bus-input blocks (phase 1): everything about a bus that reads only the
+// call's inputs.  Buses are taken in the processing order, so the 32 buses
+// of a warp have equal arc and generator counts and run loops of equal
+// length.  Leaves the bus's diagonal terms of M_cond for phase 2.
 // ===========================================================================
-// sp / sn: the block's slot partials and neighbours (shared memory or
-// global), indexed from the block's first slot s0.
-__device__ __forceinline__ void bus_kkt_rows(const DevModel& dm, const EvalArgs& a, int i, int s0,
-                                             const SlotPart* sp, const int* sn, double d_va,
-                                             double d_vm) {
+// Warp w of bus block blk (of nblk) takes the buses at processing positions
+// [32 g, 32 g + 32) with g = w * nblk + (nblk - 1 - blk): every block gets
+// one warp from each quarter of the degree-sorted order, and block 0, which
+// starts first, the heaviest ones.
+__device__ __forceinline__ int bus_warp_base(int blk, int nblk) {
+  const int w = threadIdx.x >> 5;
+  return 32 * (w * nblk + (nblk - 1 - blk));
+}
+
+template <unsigned W, bool REG, bool ARRAYS, bool SHUNT>
+__device__ __forceinline__ void bus_input_block(const DevModel& dm, const EvalArgs& a, int blk,
+                                                int nblk, double* smem) {
   const Layout& L = dm.L;
-  const int* __restrict__ rp = dm.krowptr;
+  const int pw0 = bus_warp_base(blk, nblk);
+  const int p = pw0 + (threadIdx.x & 31);
+  const bool active = p < L.nb;
+  const int i = active ? ld(dm.porder + p) : 0;
+  const double* __restrict__ x = a.x;
+  if constexpr (!ARRAYS && (W & OUT_CONS) != 0) {
+    // Balance rows.  The warp's buses own a contiguous range of the term list
+    // (generators then arcs of each bus); lanes fetch the terms together with
+    // all loads in flight at once, stage them in shared memory, and each lane
+    // then sums its own bus's terms in list order.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (pw0 < L.nb) {
+      const int pw1 = min(pw0 + 32, L.nb);
+      const int e0 = ld(dm.pbal_ptr + pw0), e1 = ld(dm.pbal_ptr + pw1);
+      const int ne = e1 - e0;
+      double2* buf = reinterpret_cast<double2*>(smem) + warp * kBalCap;
+      const bool staged = ne <= kBalCap;
+      if (staged) {
+        constexpr int R = kBalCap / 32;
+        int idx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int k = lane + 32 * r;
+          idx[r] = k < ne ? ld(dm.bal_idx + e0 + k) : -1;
+        }
+        double vp[R], vq[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (idx[r] >= 0) {
+            const int off = idx[r] < L.P ? L.ng : 2 * L.nl;  // pg -> qg, p_a -> q_a
+            vp[r] = ld(x + idx[r]);
+            vq[r] = ld(x + idx[r] + off);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (idx[r] >= 0) {
+            const bool gen = idx[r] < L.P;  // generators enter with a minus sign
+            buf[lane + 32 * r] = gen ? make_double2(neg(vp[r]), neg(vq[r])) : make_double2(vp[r], vq[r]);
+          }
+        }
+        __syncwarp();
+      }
+      if (active) {
+        double P = ld(dm.Pd + i), Q = ld(dm.Qd + i);
+        if constexpr (SHUNT) {
+          const double vm = ld(x + L.VM + i);
+          P = fma(ld(dm.Gs + i) * vm, vm, P);
+          Q = fma(-(ld(dm.Bs + i) * vm), vm, Q);
+        }
+        const int k0 = ld(dm.pbal_ptr + p) - e0, k1 = ld(dm.pbal_ptr + p + 1) - e0;
+        for (int k = k0; k < k1; ++k) {
+          double2 v;
+          if (staged) {
+            v = buf[k];
+          } else {
+            const int id = ld(dm.bal_idx + e0 + k);
+            const bool gen = id < L.P;
+            const double vp = ld(x + id), vq = ld(x + id + (gen ? L.ng : 2 * L.nl));
+            v = gen ? make_double2(neg(vp), neg(vq)) : make_double2(vp, vq);
+          }
+          P += v.x;
+          Q += v.y;
+        }
+        a.cons[L.PB + i] = P;
+        a.cons[L.QB + i] = Q;
+      }
+    }
+  }
+  if (!active) return;
+  const int r = ld(dm.ref_row + i);
+  double d_va = 0.0, d_vm = 0.0;
+  if constexpr (!ARRAYS) {
+    double jPv = 0.0, jQv = 0.0, hb = 0.0;
+    if constexpr (SHUNT) {
+      const double vm = ld(x + L.VM + i);
+      const double Gs = ld(dm.Gs + i), Bs = ld(dm.Bs + i);
+      const double tv = vm + vm;
+      jPv = Gs * tv;
+      jQv = -(Bs * tv);
+      if constexpr ((W & (OUT_HESS | OUT_KKT)) != 0)
+        hb = fma(Gs + Gs, ld(a.y + L.PB + i), -((Bs + Bs) * ld(a.y + L.QB + i)));
+    }
+    if constexpr ((W & OUT_GRAD) != 0) {
+      a.grad[L.VA + i] = 0.0;
+      a.grad[L.VM + i] = 0.0;
+    }
+    if constexpr ((W & OUT_CONS) != 0) {
+      if (r >= 0) a.cons[L.REF + r] = ld(x + L.VA + i);
+    }
+    if constexpr ((W & OUT_JAC) != 0) {
+      if (r >= 0) a.jvals[L.JREF + r] = 1.0;
+      a.jvals[L.JPBV + i] = jPv;
+      a.jvals[L.JQBV + i] = jQv;
+    }
+    if constexpr ((W & OUT_HESS) != 0) a.hvals[L.HB + i] = hb;
+    if constexpr ((W & OUT_KKT) != 0) {
+      const double dw = a.delta_w, dc = a.delta_c;
+      d_va = sxw<REG>(ld(a.sigma_x + L.VA + i), dw);
+      if (r >= 0) d_va += dcond<REG>(ld(a.sigma_s + L.REF + r), dw, dc);
+      d_vm = sxw<REG>(ld(a.sigma_x + L.VM + i), dw);
+      if constexpr (SHUNT) {
+        const double D_P = dcond<REG>(ld(a.sigma_s + L.PB + i), dw, dc);
+        const double D_Q = dcond<REG>(ld(a.sigma_s + L.QB + i), dw, dc);
+        d_vm += hb + fma(D_P * jPv, jPv, D_Q * jQv * jQv);
+      }
+    }
+  } else {
+    const double* __restrict__ J = a.jvals_in;
+    const double dw = a.delta_w, dc = a.delta_c;
+    const double jPv = ld(J + L.JPBV + i), jQv = ld(J + L.JQBV + i);
+    const double D_P = dcond<REG>(ld(a.sigma_s + L.PB + i), dw, dc);
+    const double D_Q = dcond<REG>(ld(a.sigma_s + L.QB + i), dw, dc);
+    d_va = sxw<REG>(ld(a.sigma_x + L.VA + i), dw);
+    if (r >= 0) {
+      const double jr = ld(J + L.JREF + r);
+      d_va += dcond<REG>(ld(a.sigma_s + L.REF + r), dw, dc) * jr * jr;
+    }
+    d_vm = sxw<REG>(ld(a.sigma_x + L.VM + i), dw) + ld(a.hvals_in + L.HB + i) +
+           fma(D_P * jPv, jPv, D_Q * jQv * jQv);
+  }
+  if constexpr ((W & OUT_KKT) != 0) dm.bus_diag[p] = BusDiag{d_va, d_vm};
+}
+
+// Generator block: generator rows, and the objective.  Each block reduces
+// its generators' cost terms in a fixed tree order; the last block to
+// arrive (an arrival counter, not an accumulation) adds the block sums in
+// block order, so the result does not depend on scheduling.
+template <unsigned W, bool REG, bool ARRAYS>
+__device__ __forceinline__ void gen_block(const DevModel& dm, const EvalArgs& a, int gb, int ngen,
+                                          double* smem) {
+  const Layout& L = dm.L;
+  const int g = gb * kGenThreads + threadIdx.x;
+  if (g < L.ng) {
+    if constexpr (ARRAYS)
+      gen_from_arrays<REG>(dm, a, g);
+    else
+      gen_fused<W, REG>(dm, a, g);
+  }
+  if constexpr (!ARRAYS && (W & OUT_OBJ) != 0) {
+    double v = 0.0;
+    if (g < L.ng) {
+      const double pg = ld(a.x + L.PG + g);
+      v = fma(fma(ld(dm.c2 + g), pg, ld(dm.c1 + g)), pg, ld(dm.c0 + g));
+    }
+    const double s = block_sum<kGenThreads>(v, smem);
+    int* last = reinterpret_cast<int*>(smem + kGenThreads / 32);
+    if (threadIdx.x == 0) {
+      dm.obj_part[gb] = s;
+      __threadfence();
+      const unsigned int t = atomicAdd(dm.obj_ticket, 1u);
+      *last = (t == static_cast<unsigned int>(ngen - 1));
+    }
+    __syncthreads();
+    if (*last && threadIdx.x < 32) {
+      __threadfence();
+      double r = 0.0;
+      for (int k = threadIdx.x; k < ngen; k += 32) r += __ldcg(dm.obj_part + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+      if (threadIdx.x == 0) {
+        *a.f = r;
+        *dm.obj_ticket = 0u;
+      }
+    }
+  }
+}
+
+// Phase 1: block roles [0, nbb) branch blocks, [nbb, nbb + nbi) bus-input
+// blocks, then ngb generator blocks.
+template <unsigned W, bool REG, bool SHUNT>
+__global__ void __launch_bounds__(kBranchThreads, 6) k_phase1(DevModel dm, EvalArgs a, int nbb,
+                                                             int nbi, int ngb) {
+  pdl_trigger();
+  __shared__ double smem[(kBranchThreads / 32) * kBalCap * 2];
+  const int b = blockIdx.x;
+  if (b < nbb) {
+    const int l = b * kBranchThreads + threadIdx.x;
+    if (l < dm.L.nl) branch_fused<W, REG, SHUNT>(dm, a, l);
+  } else if (b < nbb + nbi) {
+    bus_input_block<W, REG, false, SHUNT>(dm, a, b - nbb, nbi, smem);
+  } else {
+    gen_block<W, REG, false>(dm, a, b - nbb - nbi, ngb, smem);
+  }
+}
+
+// Phase 1 of the array-fed assembly (M_cond from given H and J values).
+template <bool REG>
+__global__ void __launch_bounds__(kBranchThreads) k_asm_phase1(DevModel dm, EvalArgs a, int nbb,
+                                                              int nbi, int ngb) {
+  pdl_trigger();
+  __shared__ double smem[8];
+  const int b = blockIdx.x;
+  if (b < nbb) {
+    const int l = b * kBranchThreads + threadIdx.x;
+    if (l < dm.L.nl) branch_from_arrays<REG>(dm, a, l);
+  } else if (b < nbb + nbi) {
+    bus_input_block<OUT_KKT, REG, true, true>(dm, a, b - nbb, nbi, smem);
+  } else {
+    gen_block<OUT_KKT, REG, true>(dm, a, b - nbb - nbi, ngb, smem);
+  }
+}
+
+// ===========================================================================
+// Phase 2: the bus rows of M_cond, gathered from the slot partials.
+// ===========================================================================
+// Row va_i = [va_j (j < i) ..., va_i]; row vm_i = [va_j / va_i ascending
+// (nu + 1)][vm_j (j < i)][vm_i], or just [vm_i] for a bus without branches.
+// The bus's slots run over its arcs by (other end, arc id), so parallel
+// branches (equal other end) are adjacent and their entries are summed.
+__global__ void __launch_bounds__(kBusThreads, 5) k_bus_rows(DevModel dm, EvalArgs a) {
+  const Layout& L = dm.L;
+  const int p = bus_warp_base(blockIdx.x, gridDim.x) + (threadIdx.x & 31);
+  const bool active = p < L.nb;
+  int i = 0, bva = 0, eva = 0, bvm = 0, evm = 0, k0 = 0, k1 = 0;
+  if (active) {  // structure only: independent of phase 1
+    i = ld(dm.porder + p);
+    const int* __restrict__ rp = dm.krowptr;
+    bva = ld(rp + L.VA + i);
+    eva = ld(rp + L.VA + i + 1);
+    bvm = ld(rp + L.VM + i);
+    evm = ld(rp + L.VM + i + 1);
+    k0 = ld(dm.pslot_ptr + p);
+    k1 = ld(dm.pslot_ptr + p + 1);
+  }
+  pdl_wait();
+  if (!active) return;
   double* __restrict__ K = a.kvals;
-  const int bva = ld(rp + L.VA + i), eva = ld(rp + L.VA + i + 1);
-  const int bvm = ld(rp + L.VM + i), evm = ld(rp + L.VM + i + 1);
   const int nlo = eva - bva - 1;  // distinct neighbours below i
-  // Row va_i = [va_j (j < i) ..., va_i];
-  // row vm_i = [va_j / va_i ascending (nu + 1)][vm_j (j < i)][vm_i], or just
-  // [vm_i] for a bus without branches.
   const int nu = evm - bvm - nlo - 2;
   int pva = bva, pvmva = bvm, pvmvm = bvm + nu + 1;
   double aa = 0.0, ma = 0.0, mm = 0.0;
   double gv = 0.0, gx = 0.0, gw = 0.0;
   int cur = -1;
-  const int k0 = ld(dm.arc_ptr + i) - s0, k1 = ld(dm.arc_ptr + i + 1) - s0;
-  for (int k = k0; k < k1; ++k) {
-    const int j = sn[k];
-    const SlotPart p = sp[k];
-    aa += p.aa;
-    ma += p.ma;
-    mm += p.mm;
-    if (j != cur) {
-      if (cur >= 0) {
-        if (cur > i && pvmva == bvm + nlo) ++pvmva;  // skip the (vm_i, va_i) slot
-        K[pvmva++] = gx;
-        if (cur < i) {
-          K[pva++] = gv;
-          K[pvmvm++] = gw;
+  const double2 dd = __ldcg(reinterpret_cast<const double2*>(dm.bus_diag + p));
+  const BusDiag d{dd.x, dd.y};
+  constexpr int U = 4;  // slots fetched per round, all loads in flight together
+  for (int k = k0; k < k1; k += U) {
+    double2 q0[U], q1[U], q2[U];
+    int jj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k + u < k1) {
+        const double2* src = reinterpret_cast<const double2*>(dm.part_slot + k + u);
+        q0[u] = __ldcg(src);
+        q1[u] = __ldcg(src + 1);
+        q2[u] = __ldcg(src + 2);
+        jj[u] = ld(dm.slot_nbr + k + u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k + u < k1) {
+        // SlotPart {aa, ma | mm, mx | vv, ww}
+        aa += q0[u].x;
+        ma += q0[u].y;
+        mm += q1[u].x;
+        const int j = jj[u];
+        if (j != cur) {
+          if (cur >= 0) {
+            if (cur > i && pvmva == bvm + nlo) ++pvmva;  // skip the (vm_i, va_i) slot
+            K[pvmva++] = gx;
+            if (cur < i) {
+              K[pva++] = gv;
+              K[pvmvm++] = gw;
+            }
+          }
+          cur = j;
+          gv = q2[u].x;
+          gx = q1[u].y;
+          gw = q2[u].y;
+        } else {  // parallel branches between i and j
+          gv += q2[u].x;
+          gx += q1[u].y;
+          gw += q2[u].y;
         }
       }
-      cur = j;
-      gv = p.vv;
-      gx = p.mx;
-      gw = p.ww;
-    } else {
-      gv += p.vv;
-      gx += p.mx;
-      gw += p.ww;
     }
   }
   if (cur >= 0) {
@@ -581,133 +860,9 @@ __device__ __forceinline__ void bus_kkt_rows(const DevModel& dm, const EvalArgs&
       K[pvmvm++] = gw;
     }
   }
-  K[bva + nlo] = d_va + aa;
+  K[bva + nlo] = d.va + aa;
   if (k1 > k0) K[bvm + nlo] = ma;  // (vm_i, va_i) exists only when bus i has a branch
-  K[evm - 1] = d_vm + mm;
-}
-
-template <unsigned W, bool REG, bool ARRAYS>
-__device__ __forceinline__ void bus_block(const DevModel& dm, const EvalArgs& a, int blk,
-                                          double* smem) {
-  const Layout& L = dm.L;
-  const int i0 = blk * kBusThreads;
-  const int i = i0 + threadIdx.x;
-  const bool active = i < L.nb;
-  const double* __restrict__ x = a.x;
-  // Work that reads only the call's inputs.
-  double d_va = 0.0, d_vm = 0.0;
-  if (active) {
-    const int r = ld(dm.ref_row + i);
-    if constexpr (!ARRAYS) {
-      const double vm = ld(x + L.VM + i);
-      const double Gs = ld(dm.Gs + i), Bs = ld(dm.Bs + i);
-      const double tv = vm + vm;
-      const double jPv = Gs * tv, jQv = -(Bs * tv);
-      if constexpr ((W & OUT_GRAD) != 0) {
-        a.grad[L.VA + i] = 0.0;
-        a.grad[L.VM + i] = 0.0;
-      }
-      if constexpr ((W & OUT_CONS) != 0) {
-        if (r >= 0) a.cons[L.REF + r] = ld(x + L.VA + i);
-        double P = fma(Gs * vm, vm, ld(dm.Pd + i));
-        double Q = fma(-(Bs * vm), vm, ld(dm.Qd + i));
-        const int g0 = ld(dm.gen_ptr + i), g1 = ld(dm.gen_ptr + i + 1);
-        for (int k = g0; k < g1; ++k) {
-          const int g = ld(dm.gens_at + k);
-          P -= ld(x + L.PG + g);
-          Q -= ld(x + L.QG + g);
-        }
-        const int k0 = ld(dm.arc_ptr + i), k1 = ld(dm.arc_ptr + i + 1);
-        for (int k = k0; k < k1; ++k) {
-          const int arc = ld(dm.arcs_by_idx + k);
-          P += ld(x + L.P + arc);
-          Q += ld(x + L.Q + arc);
-        }
-        a.cons[L.PB + i] = P;
-        a.cons[L.QB + i] = Q;
-      }
-      if constexpr ((W & OUT_JAC) != 0) {
-        if (r >= 0) a.jvals[L.JREF + r] = 1.0;
-        a.jvals[L.JPBV + i] = jPv;
-        a.jvals[L.JQBV + i] = jQv;
-      }
-      if constexpr ((W & (OUT_HESS | OUT_KKT)) != 0) {
-        const double hb = fma(Gs + Gs, ld(a.y + L.PB + i), -((Bs + Bs) * ld(a.y + L.QB + i)));
-        if constexpr ((W & OUT_HESS) != 0) a.hvals[L.HB + i] = hb;
-        if constexpr ((W & OUT_KKT) != 0) {
-          const double dw = a.delta_w, dc = a.delta_c;
-          const double D_P = dcond<REG>(ld(a.sigma_s + L.PB + i), dw, dc);
-          const double D_Q = dcond<REG>(ld(a.sigma_s + L.QB + i), dw, dc);
-          d_va = sxw<REG>(ld(a.sigma_x + L.VA + i), dw);
-          if (r >= 0) d_va += dcond<REG>(ld(a.sigma_s + L.REF + r), dw, dc);
-          d_vm = sxw<REG>(ld(a.sigma_x + L.VM + i), dw) + hb +
-                 fma(D_P * jPv, jPv, D_Q * jQv * jQv);
-        }
-      }
-    } else {
-      const double* __restrict__ J = a.jvals_in;
-      const double dw = a.delta_w, dc = a.delta_c;
-      const double jPv = ld(J + L.JPBV + i), jQv = ld(J + L.JQBV + i);
-      const double D_P = dcond<REG>(ld(a.sigma_s + L.PB + i), dw, dc);
-      const double D_Q = dcond<REG>(ld(a.sigma_s + L.QB + i), dw, dc);
-      d_va = sxw<REG>(ld(a.sigma_x + L.VA + i), dw);
-      if (r >= 0) {
-        const double jr = ld(J + L.JREF + r);
-        d_va += dcond<REG>(ld(a.sigma_s + L.REF + r), dw, dc) * jr * jr;
-      }
-      d_vm = sxw<REG>(ld(a.sigma_x + L.VM + i), dw) + ld(a.hvals_in + L.HB + i) +
-             fma(D_P * jPv, jPv, D_Q * jQv * jQv);
-    }
-  }
-  if constexpr ((W & OUT_KKT) != 0) {
-    pdl_wait();
-    const int i1 = min(i0 + kBusThreads, L.nb);
-    const int s0 = ld(dm.arc_ptr + i0), s1 = ld(dm.arc_ptr + i1);
-    const int ns = s1 - s0;
-    const SlotPart* sp = dm.part_slot + s0;
-    const int* sn = dm.slot_nbr + s0;
-    if (ns <= dm.slot_cap) {
-      // Stage the block's slot partials (contiguous in global memory) in shared memory.
-      double2* d2 = reinterpret_cast<double2*>(smem);
-      const double2* g2 = reinterpret_cast<const double2*>(dm.part_slot + s0);
-      for (int k = threadIdx.x; k < 3 * ns; k += kBusThreads) d2[k] = g2[k];
-      int* si = reinterpret_cast<int*>(smem + 6 * dm.slot_cap);
-      for (int k = threadIdx.x; k < ns; k += kBusThreads) si[k] = ld(dm.slot_nbr + s0 + k);
-      __syncthreads();
-      sp = reinterpret_cast<const SlotPart*>(smem);
-      sn = si;
-    }
-    if (active) bus_kkt_rows(dm, a, i, s0, sp, sn, d_va, d_vm);
-  }
-}
-
-// Block roles: [0, nbus) bus blocks, [nbus, nbus + ngen) generator blocks,
-// then one objective block when W has OUT_OBJ.
-template <unsigned W, bool REG, bool ARRAYS>
-__global__ void __launch_bounds__(kBusThreads) k_phase2(DevModel dm, EvalArgs a, int nbus,
-                                                       int ngen) {
-  extern __shared__ double smem[];
-  const int b = blockIdx.x;
-  if (b < nbus) {
-    bus_block<W, REG, ARRAYS>(dm, a, b, smem);
-  } else if (b < nbus + ngen) {
-    const int g = (b - nbus) * kGenThreads + threadIdx.x;
-    if (g < dm.L.ng) {
-      if constexpr (ARRAYS)
-        gen_from_arrays<REG>(dm, a, g);
-      else
-        gen_fused<W, REG>(dm, a, g);
-    }
-  } else if constexpr ((W & OUT_OBJ) != 0) {
-    // objective: fixed-order sum over all generators
-    const Layout& L = dm.L;
-    double s = 0.0;
-    for (int g = threadIdx.x; g < L.ng; g += kGenThreads)
-      s += fma(fma(ld(dm.c2 + g), ld(a.x + L.PG + g), ld(dm.c1 + g)), ld(a.x + L.PG + g),
-               ld(dm.c0 + g));
-    s = block_sum<kGenThreads>(s, smem);
-    if (threadIdx.x == 0) *a.f = s;
-  }
+  K[evm - 1] = d.vm + mm;
 }
 
 // FP64 FMA throughput probe: 8 independent dependent chains per thread.
@@ -747,41 +902,36 @@ cudaError_t launch_ex(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-size_t phase2_smem(const DevModel& dm) {
-  const size_t b = size_t(dm.slot_cap) * kSlotBytes;
-  return b < 64 ? 64 : (b + 15) / 16 * 16;
-}
-
-template <unsigned W, bool REG, bool ARRAYS>
-cudaError_t launch_phase2(const DevModel& dm, const EvalArgs& a, cudaStream_t s, bool pdl) {
-  const Layout& L = dm.L;
-  constexpr bool kBus = (W & (OUT_GRAD | OUT_CONS | OUT_JAC | OUT_HESS | OUT_KKT)) != 0;
-  constexpr bool kGen = (W & (OUT_GRAD | OUT_JAC | OUT_HESS | OUT_KKT)) != 0;
-  const int nbus = kBus ? ceil_div(L.nb, kBusThreads) : 0;
-  const int ngen = kGen ? ceil_div(L.ng, kGenThreads) : 0;
-  const int nobj = (W & OUT_OBJ) != 0 ? 1 : 0;
-  const int blocks = nbus + ngen + nobj;
-  if (blocks == 0) return cudaSuccess;
-  return launch_ex(k_phase2<W, REG, ARRAYS>, dim3(blocks), dim3(kBusThreads), phase2_smem(dm), s,
-                   pdl, dm, a, nbus, ngen);
-}
-
 template <unsigned W, bool REG>
 cudaError_t launch_eval_t(const DevModel& dm, const EvalArgs& a, cudaStream_t s,
                           cudaEvent_t mid) {
   const Layout& L = dm.L;
   constexpr bool kBranch = (W & (OUT_GRAD | OUT_CONS | OUT_JAC | OUT_HESS | OUT_KKT)) != 0;
+  constexpr bool kBus = kBranch;
+  constexpr bool kGen = (W & (OUT_OBJ | OUT_GRAD | OUT_JAC | OUT_HESS | OUT_KKT)) != 0;
   const int nbb = kBranch ? ceil_div(L.nl, kBranchThreads) : 0;
-  if (nbb > 0) {
-    k_phase1<W, REG><<<nbb, kBranchThreads, 0, s>>>(dm, a);
+  const int nbi = kBus ? ceil_div(L.nb, kBusThreads) : 0;
+  int ngb = kGen ? ceil_div(L.ng, kGenThreads) : 0;
+  if ((W & OUT_OBJ) != 0 && ngb == 0) ngb = 1;  // the objective of a model without generators
+  const int blocks = nbb + nbi + ngb;
+  if (blocks > 0) {
+    if ((W & OUT_KKT) == 0 || dm.has_shunt)
+      k_phase1<W, REG, true><<<blocks, kBranchThreads, 0, s>>>(dm, a, nbb, nbi, ngb);
+    else
+      k_phase1<W, REG, false><<<blocks, kBranchThreads, 0, s>>>(dm, a, nbb, nbi, ngb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (mid) {
-    cudaError_t e = cudaEventRecord(mid, s);
-    if (e != cudaSuccess) return e;
+  if constexpr ((W & OUT_KKT) == 0) {
+    return cudaSuccess;
+  } else {
+    if (mid) {
+      cudaError_t e = cudaEventRecord(mid, s);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_ex(k_bus_rows, dim3(ceil_div(L.nb, kBusThreads)), dim3(kBusThreads), 0, s,
+                     blocks > 0 && !mid && dm.pdl, dm, a);
   }
-  return launch_phase2<W, REG, false>(dm, a, s, nbb > 0 && !mid);
 }
 
 template <unsigned W>
@@ -814,15 +964,15 @@ cudaError_t launch_eval(const DevModel& dm, unsigned what, const EvalArgs& a, cu
 
 int launches_for(unsigned what) {
   switch (what) {
-    case OUT_OBJ:
-      return 1;
     case OUT_ALL:
+    case OUT_KKT:
+      return 2;
+    case OUT_OBJ:
     case OUT_GRAD:
     case OUT_CONS:
     case OUT_JAC:
     case OUT_HESS:
-    case OUT_KKT:
-      return 2;
+      return 1;
     default:
       return -1;
   }
@@ -832,16 +982,16 @@ cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t 
   const Layout& L = dm.L;
   const bool reg = a.delta_w != 0.0 || a.delta_c != 0.0;
   const int nbb = ceil_div(L.nl, kBranchThreads);
-  if (nbb > 0) {
-    if (reg)
-      k_asm_phase1<true><<<nbb, kBranchThreads, 0, s>>>(dm, a);
-    else
-      k_asm_phase1<false><<<nbb, kBranchThreads, 0, s>>>(dm, a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (reg) return launch_phase2<OUT_KKT, true, true>(dm, a, s, nbb > 0);
-  return launch_phase2<OUT_KKT, false, true>(dm, a, s, nbb > 0);
+  const int nbi = ceil_div(L.nb, kBusThreads);
+  const int ngb = ceil_div(L.ng, kGenThreads);
+  const int blocks = nbb + nbi + ngb;
+  if (reg)
+    k_asm_phase1<true><<<blocks, kBranchThreads, 0, s>>>(dm, a, nbb, nbi, ngb);
+  else
+    k_asm_phase1<false><<<blocks, kBranchThreads, 0, s>>>(dm, a, nbb, nbi, ngb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_ex(k_bus_rows, dim3(nbi), dim3(kBusThreads), 0, s, dm.pdl != 0, dm, a);
 }
 
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {

@@ -243,12 +243,6 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
                 return ja != jb ? ja < jb : a < b;
               });
   }
-  hm.slot_nbr.assign(2 * nl, 0);
-  hm.slot_of_arc.assign(2 * nl, 0);
-  for (int64_t s = 0; s < 2 * nl; ++s) {
-    hm.slot_nbr[s] = arc_nbr(hm.arcs_by_nbr[s]);
-    hm.slot_of_arc[hm.arcs_by_nbr[s]] = int32_t(s);
-  }
   hm.gen_ptr.assign(nb + 1, 0);
   for (int64_t g = 0; g < ng; ++g) hm.gen_ptr[hm.gbus[g] + 1]++;
   for (int64_t i = 0; i < nb; ++i) hm.gen_ptr[i + 1] += hm.gen_ptr[i];
@@ -256,6 +250,35 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
   {
     std::vector<int32_t> pos(hm.gen_ptr.begin(), hm.gen_ptr.end() - 1);
     for (int64_t g = 0; g < ng; ++g) hm.gens_at[pos[hm.gbus[g]]++] = int32_t(g);
+  }
+
+  // Bus-phase processing order (by arc count, then generator count, then
+  // id), and in that order: the slots of each bus (its arcs by (other end,
+  // arc id)) and its balance-row terms (generators, then arcs, ascending).
+  hm.porder.resize(nb);
+  std::iota(hm.porder.begin(), hm.porder.end(), 0);
+  std::stable_sort(hm.porder.begin(), hm.porder.end(), [&](int32_t a, int32_t b) {
+    const int32_t da = hm.arc_ptr[a + 1] - hm.arc_ptr[a], db = hm.arc_ptr[b + 1] - hm.arc_ptr[b];
+    if (da != db) return da < db;
+    return hm.gen_ptr[a + 1] - hm.gen_ptr[a] < hm.gen_ptr[b + 1] - hm.gen_ptr[b];
+  });
+  hm.pslot_ptr.assign(nb + 1, 0);
+  hm.pbal_ptr.assign(nb + 1, 0);
+  hm.slot_nbr.assign(2 * nl, 0);
+  hm.slot_of_arc.assign(2 * nl, 0);
+  hm.bal_idx.assign(ng + 2 * nl, 0);
+  for (int64_t p = 0; p < nb; ++p) {
+    const int32_t i = hm.porder[p];
+    int32_t s = hm.pslot_ptr[p];
+    for (int32_t k = hm.arc_ptr[i]; k < hm.arc_ptr[i + 1]; ++k, ++s) {
+      hm.slot_nbr[s] = arc_nbr(hm.arcs_by_nbr[k]);
+      hm.slot_of_arc[hm.arcs_by_nbr[k]] = s;
+    }
+    hm.pslot_ptr[p + 1] = s;
+    int32_t b = hm.pbal_ptr[p];
+    for (int32_t e = hm.gen_ptr[i]; e < hm.gen_ptr[i + 1]; ++e) hm.bal_idx[b++] = L.PG + hm.gens_at[e];
+    for (int32_t e = hm.arc_ptr[i]; e < hm.arc_ptr[i + 1]; ++e) hm.bal_idx[b++] = L.P + hm.arcs_by_idx[e];
+    hm.pbal_ptr[p + 1] = b;
   }
 
   // ---- Jacobian COO pattern --------------------------------------------------
@@ -271,28 +294,20 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     for (int64_t r = 0; r < nref; ++r) put(L.REF + r, L.VA + hm.ref_bus[r]);
     const int64_t flow_row[4] = {L.PF, L.QF, L.PT, L.QT};
     const int64_t flow_var[4] = {L.P, L.Q, L.P + nl, L.Q + nl};
+    // Branch patterns store entry k of every branch's row contiguously.
     for (int q = 0; q < 4; ++q) {
-      for (int64_t l = 0; l < nl; ++l) {
-        const int64_t r = flow_row[q] + l;
-        put(r, flow_var[q] + l);
-        put(r, L.VA + hm.f[l]);
-        put(r, L.VA + hm.t[l]);
-        put(r, L.VM + hm.f[l]);
-        put(r, L.VM + hm.t[l]);
-      }
+      for (int64_t l = 0; l < nl; ++l) put(flow_row[q] + l, flow_var[q] + l);
+      for (int64_t l = 0; l < nl; ++l) put(flow_row[q] + l, L.VA + hm.f[l]);
+      for (int64_t l = 0; l < nl; ++l) put(flow_row[q] + l, L.VA + hm.t[l]);
+      for (int64_t l = 0; l < nl; ++l) put(flow_row[q] + l, L.VM + hm.f[l]);
+      for (int64_t l = 0; l < nl; ++l) put(flow_row[q] + l, L.VM + hm.t[l]);
     }
-    for (int64_t l = 0; l < nl; ++l) {
-      put(L.ANG + l, L.VA + hm.f[l]);
-      put(L.ANG + l, L.VA + hm.t[l]);
-    }
-    for (int64_t l = 0; l < nl; ++l) {
-      put(L.SF + l, L.P + l);
-      put(L.SF + l, L.Q + l);
-    }
-    for (int64_t l = 0; l < nl; ++l) {
-      put(L.ST + l, L.P + nl + l);
-      put(L.ST + l, L.Q + nl + l);
-    }
+    for (int64_t l = 0; l < nl; ++l) put(L.ANG + l, L.VA + hm.f[l]);
+    for (int64_t l = 0; l < nl; ++l) put(L.ANG + l, L.VA + hm.t[l]);
+    for (int64_t l = 0; l < nl; ++l) put(L.SF + l, L.P + l);
+    for (int64_t l = 0; l < nl; ++l) put(L.SF + l, L.Q + l);
+    for (int64_t l = 0; l < nl; ++l) put(L.ST + l, L.P + nl + l);
+    for (int64_t l = 0; l < nl; ++l) put(L.ST + l, L.Q + nl + l);
     for (int64_t i = 0; i < nb; ++i) put(L.PB + i, L.VM + i);
     for (int64_t i = 0; i < nb; ++i) put(L.QB + i, L.VM + i);
     for (int64_t g = 0; g < ng; ++g) put(L.PB + hm.gbus[g], L.PG + g);
@@ -308,19 +323,20 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     static const int kPair[10][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1},
                                      {2, 2}, {3, 0}, {3, 1}, {3, 2}, {3, 3}};
     int64_t k = 0;
-    for (int64_t l = 0; l < nl; ++l) {
-      const int32_t loc[4] = {L.VA + hm.f[l], L.VA + hm.t[l], L.VM + hm.f[l], L.VM + hm.t[l]};
-      for (int e = 0; e < 10; ++e) {
+    // entry e of every branch's block stored contiguously
+    for (int e = 0; e < 10; ++e) {
+      for (int64_t l = 0; l < nl; ++l) {
+        const int32_t loc[4] = {L.VA + hm.f[l], L.VA + hm.t[l], L.VM + hm.f[l], L.VM + hm.t[l]};
         const int32_t a = loc[kPair[e][0]], b = loc[kPair[e][1]];
         hm.hrows[k] = std::max(a, b);
         hm.hcols[k] = std::min(a, b);
         ++k;
       }
     }
-    for (int64_t l = 0; l < nl; ++l) {
-      const int32_t d[4] = {int32_t(L.P + l), int32_t(L.Q + l), int32_t(L.P + nl + l),
-                            int32_t(L.Q + nl + l)};
-      for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 4; ++e) {
+      for (int64_t l = 0; l < nl; ++l) {
+        const int32_t d[4] = {int32_t(L.P + l), int32_t(L.Q + l), int32_t(L.P + nl + l),
+                              int32_t(L.Q + nl + l)};
         hm.hrows[k] = d[e];
         hm.hcols[k] = d[e];
         ++k;
@@ -439,6 +455,28 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     }
   }
 
+  // per-branch arc-row descriptors
+  hm.brow.assign(4 * nl, 0);
+  hm.bcnt.assign(nl, 0);
+  {
+    std::vector<int32_t> rank(2 * nl, 0);
+    for (int64_t i = 0; i < nb; ++i)
+      for (int32_t k = hm.arc_ptr[i]; k < hm.arc_ptr[i + 1]; ++k)
+        rank[hm.arcs_by_idx[k]] = k - hm.arc_ptr[i];
+    for (int64_t l = 0; l < nl; ++l) {
+      hm.brow[4 * l + 0] = hm.krowptr[L.P + l];
+      hm.brow[4 * l + 1] = hm.krowptr[L.Q + l];
+      hm.brow[4 * l + 2] = hm.krowptr[L.P + nl + l];
+      hm.brow[4 * l + 3] = hm.krowptr[L.Q + nl + l];
+      const int64_t ngf = hm.gen_ptr[hm.f[l] + 1] - hm.gen_ptr[hm.f[l]];
+      const int64_t ngt = hm.gen_ptr[hm.t[l] + 1] - hm.gen_ptr[hm.t[l]];
+      const int64_t rf = rank[l], rt = rank[nl + l];
+      hm.bcnt[l] = (ngf > 255 || ngt > 255 || rf > 255 || rt > 255)
+                       ? kCountsWide
+                       : uint32_t(ngf | (rf << 8) | (ngt << 16) | (rt << 24));
+    }
+  }
+
   // ---- bounds -----------------------------------------------------------------
   const double inf = std::numeric_limits<double>::infinity();
   hm.xl.assign(n, 0.0);
@@ -472,16 +510,6 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     hm.gu[L.ST + l] = rate * rate;
   }
   return ACOPF_OK;
-}
-
-int32_t max_block_slots(const HostModel& hm) {
-  const int64_t nb = hm.L.nb;
-  int32_t mx = 0;
-  for (int64_t i0 = 0; i0 < nb; i0 += kBusThreads) {
-    const int64_t i1 = std::min<int64_t>(i0 + kBusThreads, nb);
-    mx = std::max(mx, hm.arc_ptr[i1] - hm.arc_ptr[i0]);
-  }
-  return mx;
 }
 
 }  // namespace acopf

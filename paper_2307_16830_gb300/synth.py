@@ -267,6 +267,33 @@ def make_edge_case_grid(seed: int = 7) -> Grid:
                 name=f"edge-cases-seed{seed}")
 
 
+def make_star_grid(n_leaves: int = 300, gens_at_hub: int = 260, seed: int = 5) -> Grid:
+    """A hub bus joined to every other bus, carrying most generators: one bus
+    with hundreds of arcs and generators (wide rows of the KKT matrix)."""
+    rng = np.random.default_rng(seed)
+    nb = n_leaves + 1
+    leaves = np.arange(1, nb, dtype=np.int32)
+    flip = rng.random(n_leaves) < 0.5
+    f = np.where(flip, leaves, 0).astype(np.int32)
+    t = np.where(flip, 0, leaves).astype(np.int32)
+    nl = n_leaves
+    gen_bus = np.concatenate([np.zeros(gens_at_hub, np.int32),
+                              rng.choice(np.arange(1, nb), size=5, replace=False).astype(np.int32)])
+    ng = gen_bus.shape[0]
+    Pmax = rng.uniform(1.0, 5.0, ng)
+    bus_type = np.ones(nb, dtype=np.int32)
+    bus_type[0] = REF_BUS_TYPE
+    Pd = rng.uniform(0.0, 1.0, nb)
+    return Grid(bus_type=bus_type, Pd=Pd, Qd=0.3 * Pd, Gs=np.zeros(nb), Bs=np.zeros(nb),
+                Vmin=np.full(nb, 0.9), Vmax=np.full(nb, 1.1), f=f, t=t,
+                r=rng.uniform(0.001, 0.05, nl), x=rng.uniform(0.01, 0.3, nl),
+                b=rng.uniform(0.0, 0.1, nl), tap=np.ones(nl), shift=np.zeros(nl),
+                rate_a=rng.uniform(1.0, 5.0, nl), angmin=np.full(nl, -math.pi / 6),
+                angmax=np.full(nl, math.pi / 6), gen_bus=gen_bus, Pmin=np.zeros(ng), Pmax=Pmax,
+                Qmin=-0.5 * Pmax, Qmax=0.5 * Pmax, c2=rng.uniform(0.0, 0.1, ng),
+                c1=rng.uniform(10.0, 40.0, ng), c0=np.zeros(ng), name=f"star-{n_leaves}")
+
+
 def scale_loads(grid: Grid, seed: int, lo: float = 0.9, hi: float = 1.1) -> Grid:
     """Load scenario: every bus's Pd (and Qd) scaled by its own U(lo, hi) draw."""
     rng = np.random.default_rng(seed)

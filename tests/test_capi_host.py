@@ -41,10 +41,11 @@ def test_status_strings():
 
 def grids():
     return [synth.workload_grid("30bus"), synth.make_edge_case_grid(7),
-            synth.make_edge_case_grid(11), synth.make_grid(300, 420, 40, seed=5)]
+            synth.make_edge_case_grid(11), synth.make_grid(300, 420, 40, seed=5),
+            synth.make_star_grid()]
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 def test_host_structures_match_oracle_bit_exactly(k):
     g = grids()[k]
     with acopf.model_create(g, device=-1) as m:
@@ -145,5 +146,5 @@ def test_null_arguments_rejected():
 
 def test_launch_accounting():
     for kind in range(7):
-        assert acopf.launches_per_call(kind) == (1 if kind == 2 else 2)
+        assert acopf.launches_per_call(kind) == (2 if kind in (0, 1) else 1)
     assert acopf.launches_per_call(99) == -1

@@ -40,10 +40,11 @@ def small_cases():
         ("edge11", synth.make_edge_case_grid(11)),
         ("ragged", synth.make_grid(517, 777, 61, seed=3)),   # 7 branch blocks, ragged tail
         ("tree", synth.make_grid(200, 199, 20, seed=4)),      # radial: every bus a tree node
+        ("star", synth.make_star_grid()),                      # hub with 300 arcs, 260 generators
     ]
 
 
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(6))
 def test_fused_matches_oracle(dev, acopf, idx):
     name, g = small_cases()[idx]
     with acopf.model_create(g, 0) as m:
@@ -62,7 +63,7 @@ def test_fused_regularised(dev, acopf, dw, dc):
         gu.assert_parity(got, gu.oracle_all(g, pt), label=f"dw={dw} dc={dc}")
 
 
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(6))
 def test_separate_callbacks_match_oracle(dev, acopf, idx):
     name, g = small_cases()[idx]
     with acopf.model_create(g, 0) as m:
@@ -171,3 +172,14 @@ def test_streams_and_profiling(dev, acopf):
         assert calls == 3 and p1 > 0 and p2 > 0 and tot >= p1
         for k in gu.KEYS:
             assert np.array_equal(ref[k], got[k]), k
+
+
+def test_pdl_option_does_not_change_results(dev, acopf):
+    g = synth.make_edge_case_grid(7)
+    with acopf.model_create(g, 0) as m:
+        pt = synth.make_point(g, 13)
+        a = gu.run_fused(torch, acopf, m, pt, dev)
+        acopf.model_set_option(m, acopf.OPT_PDL, 0)
+        b = gu.run_fused(torch, acopf, m, pt, dev)
+        for k in gu.KEYS:
+            assert np.array_equal(a[k], b[k]), k

@@ -502,8 +502,8 @@ def test_pin_catches_hessian_index_swap(monkeypatch):
         v, m = real(grid, x, y, obj_weight)
         v = v.copy()
         nl = grid.n_branch
-        blk = v[:10 * nl].reshape(nl, 10)
-        blk[:, [6, 4]] = blk[:, [4, 6]]          # (vm_t,va_f) <-> (vm_f,va_t)
+        blk = v[:10 * nl].reshape(10, nl)
+        blk[[6, 4], :] = blk[[4, 6], :]          # (vm_t,va_f) <-> (vm_f,va_t)
         return v, m
 
     monkeypatch.setattr(oracle, "hessian", wrong)
