@@ -235,6 +235,28 @@ acopf_status acopf_profile_end(acopf_model* model, int32_t* calls, double* phase
  * and frees a small device buffer. */
 acopf_status acopf_measure_fp64_gflops(int device, double* gflops);
 
+/* Objective f = sum_g c2_g pg_g^2 + c1_g pg_g + c0_g, for callers that must
+ * not allocate device memory.  The paper has no counterpart: it is a
+ * variant of this library's objective reduction for code that may not call
+ * cudaMalloc at all, such as a component running inside a host application
+ * whose own allocator owns the device memory, or a solver loop under a
+ * fixed memory budget.  It needs no model: pg, c2, c1, c0 are device arrays
+ * of n_gen doubles (for instance pg = x + 2 n_bus of a model's point) and
+ * f_dev one device double, all owned by the caller.
+ * The call allocates nothing.  Its scratch, one partial sum per block plus
+ * an arrival counter (about 8 KB), is a static device array that every GPU
+ * loading this library holds until the process exits; n_gen is limited to
+ * 16777216 (2^24) and larger values return ACOPF_E_INVALID_ARG.  The first
+ * call on a device resolves the array's device address (with that device
+ * current), so make that first call before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's contents: the
+ * call clears the counter in stream order before its kernel, and calls that
+ * overlap on the GPU (different streams without ordering) race.  The sum is
+ * reduced in a fixed order, so equal inputs give bit-identical results. */
+acopf_status acopf_objective_noalloc(int64_t n_gen, const double* pg, const double* c2,
+                                     const double* c1, const double* c0, double* f_dev,
+                                     acopf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

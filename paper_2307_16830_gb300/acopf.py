@@ -87,6 +87,8 @@ _eval_assemble_host = _sig("acopf_eval_assemble_host", C.c_int32, _vp, _vp, _vp,
                            _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _launches_per_call = _sig("acopf_launches_per_call", C.c_int32, C.c_int32)
 _model_set_option = _sig("acopf_model_set_option", C.c_int32, _vp, C.c_int32, C.c_int64)
+_objective_noalloc = _sig("acopf_objective_noalloc", C.c_int32, C.c_int64, _vp, _vp, _vp, _vp,
+                          _vp, _vp)
 OPT_PDL = 1
 _measure_fp64 = _sig("acopf_measure_fp64_gflops", C.c_int32, C.c_int, _f64p)
 _profile_begin = _sig("acopf_profile_begin", C.c_int32, _vp, C.c_int32)
@@ -100,7 +102,7 @@ EXPORTED = [
     "acopf_eval_cons", "acopf_eval_jac_coo", "acopf_eval_hess_coo",
     "acopf_assemble_condensed_kkt_csr", "acopf_eval_assemble", "acopf_eval_assemble_host",
     "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_profile_begin",
-    "acopf_profile_end", "acopf_model_set_option",
+    "acopf_profile_end", "acopf_model_set_option", "acopf_objective_noalloc",
 ]
 
 
@@ -331,3 +333,10 @@ def profile_end(model: Model):
 
 def model_set_option(model: Model, option: int, value: int) -> None:
     _check(_model_set_option(model.handle, int(option), int(value)), "acopf_model_set_option")
+
+
+def objective_noalloc(n_gen: int, pg, c2, c1, c0, f_dev, stream=None) -> None:
+    """acopf_objective_noalloc: sum c2 pg^2 + c1 pg + c0 over n_gen device
+    doubles, for callers that may not allocate (static scratch, no model)."""
+    _check(_objective_noalloc(int(n_gen), _ptr(pg), _ptr(c2), _ptr(c1), _ptr(c0), _ptr(f_dev),
+                              _stream(stream)), "acopf_objective_noalloc")

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libacopf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["model.cpp", "capi.cpp", "kernels.cu"]
+SOURCES = ["model.cpp", "capi.cpp", "kernels.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

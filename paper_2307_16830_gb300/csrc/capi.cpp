@@ -97,6 +97,10 @@ acopf::EvalArgs empty_args() {
 
 }  // namespace
 
+namespace acopf {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace acopf
+
 extern "C" {
 
 const char* acopf_status_string(acopf_status s) {
