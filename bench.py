@@ -40,16 +40,42 @@ METRIC = "eval+KKT-assembly calls/s and % HBM roofline; served p50/p99 vs plain 
 UNIT = "calls/s"
 ROTATE = 4
 
-# DRAM traffic (read + write bytes) per launch of the fused phase-1 kernel on
-# the 80k-bus workload, from `ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum` (see profiles/), valid for the kernels.cu whose hash
-# is recorded with it; reported as null once the kernel source changes.
-NCU_TRAFFIC = {"kernels_sha": None, "phase1_bytes": None, "phase2_bytes": None}
+# Counters of the phase-1 kernel on the 80,000-bus workload from one ncu
+# capture (profiles/k_phase1_80kbus.md): DRAM read + write bytes per launch,
+# and its executed FP64 arithmetic (FMA counted as 2 flops), valid for the
+# kernels.cu whose hash is recorded; the traffic is reported as null once the
+# kernel source changes.
+PHASE1_NCU = {
+    "kernels_sha": "bed03878db742c5d",
+    "workload": "80kbus",
+    "dram_bytes": 44_424_192 + 38_437_888,
+    "fp64_dfma": 6_746_000, "fp64_dadd": 6_960_000, "fp64_dmul": 6_330_000,
+}
+# FP64 flops of phase 1 per branch (the kernel's arithmetic on the fused
+# path without regularisation, bus and generator work folded in), from the
+# capture above: (2 dfma + dadd + dmul) / n_branch.
+FLOPS_PER_BRANCH = (2 * 6_746_000 + 6_960_000 + 6_330_000) / 110_000
 
 
 def kernels_sha() -> str:
     p = os.path.join(ROOT, "paper_2307_16830_gb300", "csrc", "kernels.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank value over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, steps: int, ms_max: float) -> float:
+    """Calls per second of the whole job: every rank runs `steps` calls."""
+    return world * steps / (ms_max * 1e-3)
 
 
 def dist_env():
@@ -131,25 +157,17 @@ def algorithmic_bytes(s):
 
 
 def phase1_bytes(s, kkt_arc_gen):
-    """Compulsory bytes of the phase-1 kernel (branch and generator threads):
-    branch and generator model data; x of the buses' va/vm (read once), of
-    the generators and arcs; y and Sigma_s of the branch rows; Sigma_x of the
-    arc and generator variables; outputs it writes (branch constraint rows,
-    all Jacobian and Hessian entries but the bus terms, gradient of arc and
-    generator variables, and the arc and generator rows of M_cond)."""
-    nb, nl, ng = s["nb"], s["nl"], s["ng"]
-    reads = 72 * nl + 28 * ng + 8 * (2 * nb + 2 * ng + 4 * nl) + 8 * (6 * nl + 7 * nl) \
-        + 8 * (2 * nb) + 8 * (4 * nl + 2 * ng)
-    writes = 8 * (7 * nl + (30 * nl + 2 * ng) + (14 * nl + ng) + (4 * nl + 2 * ng) + kkt_arc_gen)
+    """Compulsory bytes of the phase-1 launch: branch (f, t, 8 coefficients),
+    bus (Pd, Qd) and generator (c2, c1, c0, bus) data; x and Sigma_x read once
+    (8 n each); y and Sigma_s of the branch rows (13 per branch) and Sigma_s
+    of the balance rows (2 per bus); writes of f, the gradient, all
+    constraints, Jacobian and Hessian values, the arc and generator rows of
+    M_cond, and the bus diagonal terms left for phase 2 (2 per bus).  Index
+    metadata and the slot partials (scratch) are excluded."""
+    nb, nl, ng, n, m = s["nb"], s["nl"], s["ng"], s["n"], s["m"]
+    reads = 72 * nl + 16 * nb + 28 * ng + 8 * (2 * n + 13 * nl + 2 * nb)
+    writes = 8 * (1 + n + m + s["nnzj"] + s["nnzh"] + kkt_arc_gen + 2 * nb)
     return reads + writes
-
-
-# FP64 flops per unit of the phase-1 kernel (FMA = 2), counted from the
-# kernel's arithmetic on the fused path without regularisation; the sincos
-# pair is counted as the 2 x 11 FMA of a degree-11 polynomial pair after a
-# 3-FMA argument reduction.
-FLOPS_PER_BRANCH = 2 * 3 + 2 * 2 * 11 + 262
-FLOPS_PER_GEN = 11
 
 
 # ---------------------------------------------------------------------------
@@ -219,13 +237,8 @@ def run_ours(args, rank, world, local):
         barrier()
     clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        v = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        ms_max = float(v.item())
-    value = world * args.steps / (ms_max * 1e-3)
+    ms_max = reduce_max(ms, world, dev)
+    value = throughput(world, args.steps, ms_max)
 
     # per-phase durations (separate pass, events between the phases)
     nprof = max(16, min(args.steps, 512))
@@ -260,13 +273,8 @@ def run_ours(args, rank, world, local):
         for k in range(args.e2e_steps):
             hstep(k)
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            v = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(v, op=dist.ReduceOp.MAX)
-            dt = float(v.item())
-        e2e = {"value": world * args.e2e_steps / dt, "unit": UNIT,
+        dt = reduce_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": throughput(world, args.e2e_steps, 1e3 * dt), "unit": UNIT,
                "h2d_bytes_per_step": 8 * (2 * model.n + 2 * model.m),
                "d2h_bytes_per_step": 8 * (1 + model.n + model.m + model.nnz_jac
                                           + model.nnz_hess + model.nnz_kkt)}
@@ -374,7 +382,14 @@ def main():
     s = r["sizes"]
     # roofline of the dominant kernel (phase 1)
     p1_s = r["p1_ms"] * 1e-3
-    flops = FLOPS_PER_BRANCH * s["nl"] + FLOPS_PER_GEN * s["ng"]
+    measured = NCU_MATCH = (PHASE1_NCU["kernels_sha"] == kernels_sha()
+                            and PHASE1_NCU["workload"] == args.workload)
+    if measured:
+        flops = 2 * PHASE1_NCU["fp64_dfma"] + PHASE1_NCU["fp64_dadd"] + PHASE1_NCU["fp64_dmul"]
+        traffic = PHASE1_NCU["dram_bytes"]
+    else:
+        flops = FLOPS_PER_BRANCH * s["nl"]
+        traffic = None
     by1 = phase1_bytes(s, r["kkt_arc_gen"])
     ach_flops = flops / p1_s / 1e12
     peak_flops = r["fp64_gflops"] / 1e3
@@ -384,22 +399,21 @@ def main():
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except Exception:
         pass
-    traffic = None
-    if NCU_TRAFFIC["kernels_sha"] == kernels_sha():
-        traffic = NCU_TRAFFIC["phase1_bytes"]
     fp64_frac = ach_flops / peak_flops
     hbm_frac = ach_bw / hbm_peak
+    roof_common = {"traffic": traffic, "kernel": "k_phase1 (branch, bus-input and generator blocks)",
+                   "launch_ms": r["p1_ms"], "fp64_flops_per_launch": flops,
+                   "fp64_flops_source": "ncu capture of this kernel" if NCU_MATCH
+                   else "per-branch figure of the last ncu capture x branches",
+                   "algorithmic_bytes_per_launch": by1}
     if fp64_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ach_flops, "peak": peak_flops, "unit": "TFLOP/s",
-                "frac": fp64_frac, "traffic": traffic,
-                "kernel": "k_phase1 (branch + generator threads)",
-                "peak_source": "FP64 FMA throughput measured live by acopf_measure_fp64_gflops",
+                "frac": fp64_frac, **roof_common,
+                "peak_source": "FP64 FMA throughput measured live (acopf_measure_fp64_gflops)",
                 "hbm_view": {"achieved_gbs": ach_bw, "peak_gbs": hbm_peak, "frac": hbm_frac}}
     else:
         roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": traffic,
-                "kernel": "k_phase1 (branch + generator threads)",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "frac": hbm_frac, **roof_common, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "fp64_view": {"achieved_tflops": ach_flops, "peak_tflops": peak_flops,
                               "frac": fp64_frac}}
     call_bytes = algorithmic_bytes(s)

@@ -230,7 +230,8 @@ acopf_status acopf_profile_end(acopf_model* model, int32_t* calls, double* phase
                                double* phase2_ms, double* total_ms);
 
 /* Measured FP64 fused-multiply-add throughput of `device` in GFLOP/s (2
- * flops per FMA), from a dependent-chain DFMA kernel of about 20 ms.  A
+ * flops per FMA): the best of five runs of a kernel of about 70 ms running
+ * eight independent DFMA chains per thread on eight blocks per SM.  A
  * measurement aid for rooflines: the paper has no counterpart.  Allocates
  * and frees a small device buffer. */
 acopf_status acopf_measure_fp64_gflops(int device, double* gflops);

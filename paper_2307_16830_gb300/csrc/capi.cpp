@@ -598,7 +598,7 @@ acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, device);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64_gflops");
-  const int blocks = prop.multiProcessorCount * 8, iters = 4096;
+  const int blocks = prop.multiProcessorCount * 8, iters = 16384;
   double* buf = nullptr;
   e = cudaMalloc(&buf, size_t(blocks) * 256 * 8);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64_gflops: cudaMalloc");
@@ -608,7 +608,7 @@ acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
   e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+  for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = acopf::launch_fp64_probe(buf, blocks, iters, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
