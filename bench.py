@@ -294,6 +294,177 @@ def run_ours(args, rank, world, local):
     return res
 
 
+def _pinned(torch, a):
+    """Page-locked host copy of a numpy array (numpy view, torch owner)."""
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t.numpy(), t
+
+
+def run_batch_bench(args, local):
+    """Batched form: the batch workload (128 load scenarios of one 2,000-bus
+    network on one shared model + 128 networks of 30..20,000 buses) in one
+    autotuned batched evaluation, against the same 256 instances as plain
+    single-instance calls on the same stream."""
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    base, scen, mixed = synth.batch_workload()
+    base_m = acopf.model_create(base, local)
+    mixed_m = [acopf.model_create(g, local) for g in mixed]
+    scen_m = [acopf.model_create(g, local) for g in scen]  # the plain path has no load override
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    ios = []
+    nb = nl = ng = 0
+    for k, g in enumerate(scen + mixed):
+        m = base_m if k < len(scen) else mixed_m[k - len(scen)]
+        pt = synth.make_point(g, synth.point_seed(1003 * 1000 + k, 0))
+        d = dict(x=t(pt.x), y=t(pt.y), sigma_x=t(pt.sigma_x), sigma_s=t(pt.sigma_s),
+                 obj_weight=1.0, delta_w=0.0, delta_c=0.0,
+                 f=torch.empty(1, dtype=torch.float64, device=dev),
+                 grad=torch.empty(m.n, dtype=torch.float64, device=dev),
+                 cons=torch.empty(m.m, dtype=torch.float64, device=dev),
+                 jvals=torch.empty(m.nnz_jac, dtype=torch.float64, device=dev),
+                 hvals=torch.empty(m.nnz_hess, dtype=torch.float64, device=dev),
+                 kvals=torch.empty(m.nnz_kkt, dtype=torch.float64, device=dev))
+        if k < len(scen):
+            d["Pd"], d["Qd"] = t(g.Pd), t(g.Qd)
+        ios.append(d)
+        nb, nl, ng = nb + g.n_bus, nl + g.n_branch, ng + g.n_gen
+    count = len(ios)
+    batch = acopf.batch_create([base_m] * len(scen) + mixed_m)
+    with torch.cuda.stream(stream):
+        acopf.batch_set_io(batch, ios, stream=stream)
+        best, times = acopf.batch_autotune(batch, reps=args.batch_tune_reps, stream=stream)
+    sched, n1, n2, _ = acopf.batch_info(batch)
+
+    def timed(fn, reps, warm=3):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    ms_batch = timed(lambda: acopf.batch_eval_assemble(batch, stream=stream), args.batch_steps)
+    plain_models = scen_m + mixed_m
+
+    def plain():
+        for m, d in zip(plain_models, ios):
+            acopf.eval_assemble(m, d["x"], d["y"], 1.0, d["sigma_x"], d["sigma_s"], 0.0, 0.0,
+                                d["f"], d["grad"], d["cons"], d["jvals"], d["hvals"],
+                                d["kvals"], stream=stream)
+
+    ms_plain = timed(plain, max(3, args.batch_steps // 10))
+    variants = 1  # no shunts and no regularisation in this workload: one phase-1 launch
+    out_bytes = sum(8 * (1 + d[k].numel()) for d in ios for k in ("grad", "cons", "jvals",
+                                                                  "hvals", "kvals"))
+    in_bytes = sum(8 * d[k].numel() for d in ios for k in ("x", "y", "sigma_x", "sigma_s"))
+    batch.close()
+    for m in [base_m] + mixed_m + scen_m:
+        m.close()
+    return {
+        "workload": f"{len(scen)} load scenarios of one {base.n_bus}-bus network (one model, "
+                    f"Pd/Qd per instance) + {len(mixed)} networks of 30..20,000 buses "
+                    f"(log-uniform); {nb} buses, {nl} branches, {ng} generators in total",
+        "instances": count, "schedule": sched,
+        "autotune_ms": {str(k): round(v, 4) for k, v in sorted(times.items())},
+        "work_items": {"phase1": n1, "phase2": n2},
+        "launches_per_batch": variants + 1,
+        "ms_per_batch": ms_batch, "instances_per_s": count / (ms_batch * 1e-3),
+        "plain_ms_per_256_calls": ms_plain, "plain_instances_per_s": count / (ms_plain * 1e-3),
+        "plain_launches": 2 * count, "speedup_vs_plain": ms_plain / ms_batch,
+        "io_bytes_per_batch": in_bytes + out_bytes,
+        "io_gbs": (in_bytes + out_bytes) / (ms_batch * 1e-3) / 1e9,
+        "fp64_tflops_est": FLOPS_PER_BRANCH * nl / (ms_batch * 1e-3) / 1e12,
+    }
+
+
+def run_serve_bench(args, local):
+    """Served form: a Poisson request stream over resident models (16 networks
+    of 30..80,000 buses, log-uniform), each request 50 evaluate+assemble calls
+    over 2 point sets; continuous batching against FIFO plain launches, both
+    under a 40 GB device-memory budget, at arrival rates 0.1..1.2 x the
+    measured saturation rate.  Latency = submission to completion (host
+    steady clock)."""
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    rng = np.random.default_rng(2004)
+    sizes = synth.log_uniform_sizes(rng, args.serve_models, 30, 80_000)
+    pool, hold = [], []
+    for k, nbus in enumerate(sizes):
+        g = synth.grid_for_size(int(nbus), 3000 + k)
+        m = acopf.model_create(g, local)
+        pts = [synth.make_point(g, synth.point_seed(3000 + k, c)) for c in range(2)]
+        arrs = {}
+        for key in ("x", "y", "sigma_x", "sigma_s"):
+            arrs[key], own = _pinned(torch, np.stack([getattr(p, key) for p in pts]))
+            hold.append(own)
+        pool.append((m, arrs))
+    R, calls = args.serve_requests, 50
+    pick = rng.integers(0, len(pool), R)
+    outs = []
+    for _ in range(R):
+        a, own = _pinned(torch, np.zeros(calls))
+        outs.append(a)
+        hold.append(own)
+    budget = 40 << 30
+
+    def run(mode, lam):
+        arrive = np.cumsum(rng.exponential(1.0 / lam, R)) if lam else np.zeros(R)
+        with acopf.server_create(local, budget, mode, 256) as srv:
+            tickets = []
+            t0 = time.perf_counter()
+            for i in range(R):
+                wait = arrive[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                m, a = pool[pick[i]]
+                tickets.append(srv.submit(m, calls, a["x"], a["y"], a["sigma_x"], a["sigma_s"],
+                                          f_calls=outs[i]))
+            for tk in tickets:
+                if srv.wait(tk, 600.0) != acopf.OK:
+                    raise RuntimeError("served request failed")
+            t1 = time.perf_counter()
+            lat = np.array([srv.times(tk)[1] for tk in tickets])
+            st = srv.stats()
+        return {"lambda_req_s": lam, "p50_ms": float(1e3 * np.percentile(lat, 50)),
+                "p99_ms": float(1e3 * np.percentile(lat, 99)),
+                "throughput_req_s": R / (t1 - t0), "calls_per_s": R * calls / (t1 - t0),
+                "launches": st["launches"], "ticks": st["ticks"],
+                "peak_active": st["peak_active"], "peak_gb": st["peak_bytes"] / 1e9}
+
+    names = {acopf.SERVE_CONTINUOUS: "continuous", acopf.SERVE_FIFO: "fifo_plain"}
+    for mode in names:  # warm-up
+        run(mode, 0)
+    sat = {names[m]: run(m, 0)["throughput_req_s"] for m in names}
+    mu = max(sat.values())
+    sweep = {names[m]: [] for m in names}
+    for frac in args.serve_fracs:
+        for mode in names:
+            r = run(mode, frac * mu)
+            r["lambda_frac"] = frac
+            sweep[names[mode]].append(r)
+    for m, _ in pool:
+        m.close()
+    return {"workload": f"{len(pool)} resident networks of {int(sizes.min())}..{int(sizes.max())} "
+                        f"buses (log-uniform, mean {sizes.mean():.0f}); {R} requests per rate, "
+                        f"{calls} calls each over 2 point sets; budget 40 GB",
+            "saturation_req_s": sat, "sweep": sweep}
+
+
 def cpu_baseline_sample(workload: str, calls: int):
     import oracle
     grid = synth.workload_grid(workload)
@@ -364,6 +535,15 @@ def main():
                     help="chain the two phases with programmatic dependent launch")
     ap.add_argument("--soak", type=float, default=1.0,
                     help="seconds of untimed calls (at least --warmup) before timing")
+    ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
+                    help="also time the batched form (256 instances) against plain calls")
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-tune-reps", type=int, default=10)
+    ap.add_argument("--serve", type=int, default=1, choices=[0, 1],
+                    help="also run the served form (Poisson requests, p50/p99)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-models", type=int, default=16)
+    ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.1, 0.3, 0.6, 0.9, 1.2])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -372,6 +552,8 @@ def main():
         run_reference(args, rank, world)
         return
     r = run_ours(args, rank, world, local)
+    batch = run_batch_bench(args, local) if args.batch and world == 1 else None
+    serve = run_serve_bench(args, local) if args.serve and world == 1 else None
     if rank != 0:
         return
     cpu = None
@@ -434,7 +616,7 @@ def main():
         "phases_ms": {"phase1": r["p1_ms"], "phase2": r["p2_ms"], "call": r["call_ms"]},
         "clocks": r["clocks"], "e2e": r["e2e"],
         "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cpu,
-        "gpu": r["gpu"],
+        "gpu": r["gpu"], "batch": batch, "serve": serve,
     }
     print(json.dumps(line), flush=True)
 

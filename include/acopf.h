@@ -258,6 +258,218 @@ acopf_status acopf_objective_noalloc(int64_t n_gen, const double* pg, const doub
                                      const double* c1, const double* c0, double* f_dev,
                                      acopf_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batched evaluation: many instances in one pair of launches.
+ *
+ * The paper evaluates one network per kernel launch (Sec. III.C: one GPU
+ * thread per pattern instance); it mentions batched solvers only as related
+ * work (Sec. I).  Here the same per-branch, per-bus and per-generator threads
+ * of several instances, of uneven sizes, run together: phase 1 (objective,
+ * gradient, constraints, Jacobian, Hessian and the branch-local part of
+ * M_cond) over a flattened list of work items (instance, pattern group,
+ * block) and phase 2 (the bus rows of M_cond) over a second list, each one
+ * kernel launch, optionally replayed as a CUDA graph.
+ *
+ * An instance is (model, inputs, outputs): the same model may appear
+ * several times (each instance has its own scratch), for instance as load
+ * scenarios of one network that differ only in Pd and Qd.  Every instance's
+ * outputs are bit-identical to those of acopf_eval_assemble on its model
+ * (with the instance's Pd and Qd) at the same inputs: the same device code
+ * runs on the same data in the same order.
+ * ------------------------------------------------------------------------ */
+typedef struct acopf_batch acopf_batch;
+
+/* Inputs and outputs of one instance: DEVICE pointers, with the meaning,
+ * sizes and ownership of acopf_eval_assemble's arguments.  Pd and Qd
+ * (n_bus doubles each, device) replace the model's loads for this instance;
+ * NULL keeps the model's.  The caller owns all of it and keeps it valid
+ * while evaluations that use it are in flight. */
+typedef struct {
+  const double* x;
+  const double* y;
+  const double* sigma_x;
+  const double* sigma_s;
+  double obj_weight;
+  double delta_w;
+  double delta_c;
+  const double* Pd;
+  const double* Qd;
+  double* f;
+  double* grad;
+  double* cons;
+  double* jvals;
+  double* hvals;
+  double* kvals;
+} acopf_batch_io;
+
+/* Schedule of a batch: how its work items are ordered and launched (never
+ * the numerics).  Bits 0-1 item order: 0 instances in the given order, 1
+ * instances by decreasing size (largest first, so the long blocks start
+ * early and small instances fill the tail), 2 pattern-group major (every
+ * instance's branch blocks, then bus blocks, then generator blocks).  Bit 2
+ * (ACOPF_SCHED_PDL): phase 2 with programmatic dependent launch.  Bit 3
+ * (ACOPF_SCHED_GRAPH): the pair of launches replayed as a CUDA graph.  Bit 4
+ * (ACOPF_SCHED_PERSISTENT): a grid of resident blocks (occupancy x SM
+ * count) that strides over the item list instead of one block per item.
+ * Schedules 0 .. ACOPF_BATCH_SCHEDULES - 1 with order < 3 are valid. */
+#define ACOPF_SCHED_ORDER_GIVEN 0
+#define ACOPF_SCHED_ORDER_SIZE 1
+#define ACOPF_SCHED_ORDER_GROUP 2
+#define ACOPF_SCHED_PDL 4
+#define ACOPF_SCHED_GRAPH 8
+#define ACOPF_SCHED_PERSISTENT 16
+#define ACOPF_BATCH_SCHEDULES 32
+
+/* Creates a batch of `count` >= 1 instances; instance i evaluates models[i]
+ * (device models on one device; repeats allowed; the models must outlive
+ * the batch).  Allocates the instances' scratch and the device tables.
+ * Default schedule: ACOPF_SCHED_ORDER_SIZE | ACOPF_SCHED_PDL. */
+acopf_status acopf_batch_create(acopf_model* const* models, int32_t count, acopf_batch** out);
+acopf_status acopf_batch_destroy(acopf_batch* batch);
+
+/* Sets the inputs and outputs of all `count` instances (io: HOST array of
+ * count records holding device pointers; must equal the batch's count).
+ * Validates them (non-NULL pointers, finite obj_weight, finite delta_w,
+ * delta_c >= 0) and copies the per-instance tables to the device in order
+ * on `stream`, so later evaluations on `stream` (or a graph replay) use
+ * them.  Nothing is evaluated. */
+acopf_status acopf_batch_set_io(acopf_batch* batch, const acopf_batch_io* io, int32_t count,
+                                acopf_stream stream);
+
+/* One fused evaluation (acopf_eval_assemble's unit of work) of every
+ * instance, asynchronously on `stream`: two kernel launches, or one graph
+ * launch.  ACOPF_E_INVALID_ARG before the first acopf_batch_set_io.
+ * Evaluations of one batch must not overlap on the GPU (shared scratch). */
+acopf_status acopf_batch_eval_assemble(acopf_batch* batch, acopf_stream stream);
+
+/* Selects a schedule (see above); ACOPF_E_INVALID_ARG if not valid. */
+acopf_status acopf_batch_set_schedule(acopf_batch* batch, int32_t schedule);
+
+/* Autotuner: times every valid schedule (two warm-up evaluations, then
+ * `reps` >= 1 timed with CUDA events on `stream`), selects the fastest and
+ * returns it in *best.  times_ms (NULL or ACOPF_BATCH_SCHEDULES floats)
+ * receives each schedule's mean milliseconds per evaluation, -1 for invalid
+ * schedules.  Needs acopf_batch_set_io first; synchronises `stream`. */
+acopf_status acopf_batch_autotune(acopf_batch* batch, acopf_stream stream, int32_t reps,
+                                  int32_t* best, float* times_ms);
+
+/* Current schedule, work items of each phase and device bytes the batch
+ * holds (scratch and tables; not the models).  NULL outputs allowed. */
+acopf_status acopf_batch_info(const acopf_batch* batch, int32_t* schedule, int64_t* items_phase1,
+                              int64_t* items_phase2, int64_t* device_bytes);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over resident models.  The paper has no
+ * counterpart (it runs one solve at a time); this is the serving form of
+ * the evaluate-and-assemble unit of work (Sec. IV.C) for many IPM solves
+ * that share one GPU.
+ *
+ * A request names a resident model (created by the caller with
+ * acopf_model_create and kept for as long as requests use it) and asks for
+ * n_calls fused evaluations (IPM iterations) at given points.  A server
+ * thread admits queued requests in arrival order while the device bytes of
+ * the admitted requests (inputs, outputs and scratch, allocated from the
+ * server's stream-ordered pool) stay within the budget, and runs them:
+ *   ACOPF_SERVE_CONTINUOUS: continuous batching.  Each step ("tick") is one
+ *     batched evaluation (the acopf_batch kernels) of every admitted request
+ *     that has calls left, one call each; requests join at the next tick
+ *     after admission and leave when their last call is done, so requests
+ *     that arrive while others run share launches with them.  At most two
+ *     ticks are in flight.
+ *   ACOPF_SERVE_FIFO: plain launches.  Each admitted request's calls are
+ *     queued as single-instance launches (acopf_eval_assemble's kernels) in
+ *     arrival order on the server's stream.
+ * Results do not depend on the mode or on co-scheduled requests: each
+ * request has its own scratch and runs the code its single-instance call
+ * runs, so its outputs are bit-identical to those of acopf_eval_assemble.
+ * ------------------------------------------------------------------------ */
+typedef struct acopf_server acopf_server;
+
+/* A request.  All arrays are HOST memory owned by the caller, which keeps
+ * them valid and unchanged until the request is done; page-locked memory
+ * keeps the copies asynchronous (pageable memory works but makes the
+ * server thread wait for the copies).  Inputs: n_points >= 1 point sets,
+ * set k at x + k n, y + k m, sigma_x + k n, sigma_s + k m; call c uses set
+ * c mod n_points.  Pd, Qd (n_bus each, or both NULL) replace the model's
+ * loads.  Outputs (each may be NULL): f_calls receives the objective of
+ * every call (n_calls doubles), grad, cons, jvals, hvals, kvals those of
+ * the last call. */
+typedef struct {
+  const acopf_model* model;
+  int32_t n_calls;
+  int32_t n_points;
+  const double* x;
+  const double* y;
+  const double* sigma_x;
+  const double* sigma_s;
+  double obj_weight;
+  double delta_w;
+  double delta_c;
+  const double* Pd;
+  const double* Qd;
+  double* f_calls;
+  double* grad;
+  double* cons;
+  double* jvals;
+  double* hvals;
+  double* kvals;
+} acopf_request;
+
+#define ACOPF_SERVE_CONTINUOUS 0
+#define ACOPF_SERVE_FIFO 1
+
+/* Server counters (totals since creation, and current / peak levels). */
+typedef struct {
+  int64_t submitted;
+  int64_t completed;
+  int64_t ticks;        /* batched evaluations (continuous mode) */
+  int64_t launches;     /* kernel launches issued */
+  int64_t bytes_in_use; /* device bytes of admitted requests */
+  int64_t peak_bytes;
+  int32_t active;       /* admitted, not yet done */
+  int32_t queued;       /* waiting for admission */
+  int32_t peak_active;
+} acopf_server_stats;
+
+/* Starts a server on `device` with its own stream, memory pool and thread.
+ * budget_bytes > 0 caps the device bytes of admitted requests; max_active
+ * >= 1 caps the number of admitted requests.  Returns ACOPF_E_NO_DEVICE for
+ * device < 0. */
+acopf_status acopf_server_create(int device, int64_t budget_bytes, int32_t mode,
+                                 int32_t max_active, acopf_server** out);
+
+/* Stops the server: requests still queued complete with ACOPF_E_BUSY,
+ * admitted ones run to the end; then frees everything. */
+acopf_status acopf_server_destroy(acopf_server* server);
+
+/* Queues a request and returns its ticket.  ACOPF_E_BUDGET when the
+ * request alone needs more device bytes than the budget; ACOPF_E_INVALID_ARG
+ * for a bad request (NULL inputs, model on another device or host-only,
+ * n_calls or n_points < 1, invalid scalars). */
+acopf_status acopf_server_submit(acopf_server* server, const acopf_request* req,
+                                 uint64_t* ticket);
+
+/* Non-blocking state of a ticket: *done = 1 when finished, with the
+ * request's status in *result (NULL allowed). */
+acopf_status acopf_server_poll(acopf_server* server, uint64_t ticket, int32_t* done,
+                               acopf_status* result);
+
+/* Waits at most timeout_s seconds for a ticket; ACOPF_E_TIMEOUT if it is not
+ * done by then (the request keeps running). */
+acopf_status acopf_server_wait(acopf_server* server, uint64_t ticket, double timeout_s,
+                               acopf_status* result);
+
+/* Times of a finished ticket in seconds from submission: admission and
+ * completion (host steady clock; completion is when the server saw the
+ * request's last copy finish). */
+acopf_status acopf_server_request_times(acopf_server* server, uint64_t ticket, double* admitted_s,
+                                        double* done_s);
+
+/* Forgets a finished ticket (its record is kept until then). */
+acopf_status acopf_server_release(acopf_server* server, uint64_t ticket);
+
+acopf_status acopf_server_get_stats(acopf_server* server, acopf_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,60 @@ _measure_fp64 = _sig("acopf_measure_fp64_gflops", C.c_int32, C.c_int, _f64p)
 _profile_begin = _sig("acopf_profile_begin", C.c_int32, _vp, C.c_int32)
 _profile_end = _sig("acopf_profile_end", C.c_int32, _vp, _i32p, _f64p, _f64p, _f64p)
 
+class BatchIO(C.Structure):
+    """One instance's inputs and outputs in a batch (device addresses)."""
+    _fields_ = [("x", _vp), ("y", _vp), ("sigma_x", _vp), ("sigma_s", _vp),
+                ("obj_weight", C.c_double), ("delta_w", C.c_double), ("delta_c", C.c_double),
+                ("Pd", _vp), ("Qd", _vp), ("f", _vp), ("grad", _vp), ("cons", _vp),
+                ("jvals", _vp), ("hvals", _vp), ("kvals", _vp)]
+
+
+SCHED_ORDER_GIVEN = 0
+SCHED_ORDER_SIZE = 1
+SCHED_ORDER_GROUP = 2
+SCHED_PDL = 4
+SCHED_GRAPH = 8
+SCHED_PERSISTENT = 16
+BATCH_SCHEDULES = 32
+
+_batch_create = _sig("acopf_batch_create", C.c_int32, C.POINTER(_vp), C.c_int32, C.POINTER(_vp))
+_batch_destroy = _sig("acopf_batch_destroy", C.c_int32, _vp)
+_batch_set_io = _sig("acopf_batch_set_io", C.c_int32, _vp, C.POINTER(BatchIO), C.c_int32, _vp)
+_batch_eval_assemble = _sig("acopf_batch_eval_assemble", C.c_int32, _vp, _vp)
+_batch_set_schedule = _sig("acopf_batch_set_schedule", C.c_int32, _vp, C.c_int32)
+_batch_autotune = _sig("acopf_batch_autotune", C.c_int32, _vp, _vp, C.c_int32, _i32p,
+                       C.POINTER(C.c_float))
+_batch_info = _sig("acopf_batch_info", C.c_int32, _vp, _i32p, _i64p, _i64p, _i64p)
+
+class Request(C.Structure):
+    """A served request (host addresses)."""
+    _fields_ = [("model", _vp), ("n_calls", C.c_int32), ("n_points", C.c_int32),
+                ("x", _vp), ("y", _vp), ("sigma_x", _vp), ("sigma_s", _vp),
+                ("obj_weight", C.c_double), ("delta_w", C.c_double), ("delta_c", C.c_double),
+                ("Pd", _vp), ("Qd", _vp), ("f_calls", _vp), ("grad", _vp), ("cons", _vp),
+                ("jvals", _vp), ("hvals", _vp), ("kvals", _vp)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("ticks", C.c_int64),
+                ("launches", C.c_int64), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
+                ("active", C.c_int32), ("queued", C.c_int32), ("peak_active", C.c_int32)]
+
+
+SERVE_CONTINUOUS = 0
+SERVE_FIFO = 1
+
+_server_create = _sig("acopf_server_create", C.c_int32, C.c_int, C.c_int64, C.c_int32, C.c_int32,
+                      C.POINTER(_vp))
+_server_destroy = _sig("acopf_server_destroy", C.c_int32, _vp)
+_server_submit = _sig("acopf_server_submit", C.c_int32, _vp, C.POINTER(Request),
+                      C.POINTER(C.c_uint64))
+_server_poll = _sig("acopf_server_poll", C.c_int32, _vp, C.c_uint64, _i32p, _i32p)
+_server_wait = _sig("acopf_server_wait", C.c_int32, _vp, C.c_uint64, C.c_double, _i32p)
+_server_times = _sig("acopf_server_request_times", C.c_int32, _vp, C.c_uint64, _f64p, _f64p)
+_server_release = _sig("acopf_server_release", C.c_int32, _vp, C.c_uint64)
+_server_stats = _sig("acopf_server_get_stats", C.c_int32, _vp, C.POINTER(ServerStats))
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -103,6 +157,11 @@ EXPORTED = [
     "acopf_assemble_condensed_kkt_csr", "acopf_eval_assemble", "acopf_eval_assemble_host",
     "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_profile_begin",
     "acopf_profile_end", "acopf_model_set_option", "acopf_objective_noalloc",
+    "acopf_batch_create", "acopf_batch_destroy", "acopf_batch_set_io",
+    "acopf_batch_eval_assemble", "acopf_batch_set_schedule", "acopf_batch_autotune",
+    "acopf_batch_info", "acopf_server_create", "acopf_server_destroy", "acopf_server_submit",
+    "acopf_server_poll", "acopf_server_wait", "acopf_server_request_times",
+    "acopf_server_release", "acopf_server_get_stats",
 ]
 
 
@@ -340,3 +399,179 @@ def objective_noalloc(n_gen: int, pg, c2, c1, c0, f_dev, stream=None) -> None:
     doubles, for callers that may not allocate (static scratch, no model)."""
     _check(_objective_noalloc(int(n_gen), _ptr(pg), _ptr(c2), _ptr(c1), _ptr(c0), _ptr(f_dev),
                               _stream(stream)), "acopf_objective_noalloc")
+
+
+class Batch:
+    """A batch of instances (owner of an ``acopf_batch*``); the models must
+    outlive it."""
+
+    def __init__(self, models):
+        self.models = list(models)
+        arr = (_vp * len(self.models))(*[m.handle.value for m in self.models])
+        h = _vp()
+        _check(_batch_create(arr, len(self.models), C.byref(h)), "acopf_batch_create")
+        self._h = h
+        self._io = None
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_create(models) -> Batch:
+    return Batch(models)
+
+
+def batch_set_io(batch: Batch, ios, stream=None) -> None:
+    """ios: one dict per instance with keys x, y, sigma_x, sigma_s, obj_weight,
+    delta_w, delta_c, f, grad, cons, jvals, hvals, kvals and optionally Pd, Qd
+    (tensors or device addresses)."""
+    arr = (BatchIO * len(ios))()
+    for k, d in enumerate(ios):
+        r = arr[k]
+        for name in ("x", "y", "sigma_x", "sigma_s", "f", "grad", "cons", "jvals", "hvals",
+                     "kvals", "Pd", "Qd"):
+            setattr(r, name, _ptr(d.get(name)))
+        r.obj_weight = float(d.get("obj_weight", 1.0))
+        r.delta_w = float(d.get("delta_w", 0.0))
+        r.delta_c = float(d.get("delta_c", 0.0))
+    _check(_batch_set_io(batch.handle, arr, len(ios), _stream(stream)), "acopf_batch_set_io")
+    batch._io = ios  # keep the tensors alive with the batch
+
+
+def batch_eval_assemble(batch: Batch, stream=None) -> None:
+    _check(_batch_eval_assemble(batch.handle, _stream(stream)), "acopf_batch_eval_assemble")
+
+
+def batch_set_schedule(batch: Batch, schedule: int) -> None:
+    _check(_batch_set_schedule(batch.handle, schedule), "acopf_batch_set_schedule")
+
+
+def batch_autotune(batch: Batch, reps: int = 10, stream=None):
+    """Returns (best schedule, {schedule: ms per evaluation})."""
+    best = C.c_int32()
+    times = (C.c_float * BATCH_SCHEDULES)()
+    _check(_batch_autotune(batch.handle, _stream(stream), reps, C.byref(best), times),
+           "acopf_batch_autotune")
+    return best.value, {k: times[k] for k in range(BATCH_SCHEDULES) if times[k] >= 0}
+
+
+def batch_info(batch: Batch):
+    """Returns (schedule, phase-1 items, phase-2 items, device bytes)."""
+    s, a, b, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_batch_info(batch.handle, C.byref(s), C.byref(a), C.byref(b), C.byref(d)),
+           "acopf_batch_info")
+    return s.value, a.value, b.value, d.value
+
+
+class Server:
+    """A request server (owner of an ``acopf_server*``)."""
+
+    def __init__(self, device: int, budget_bytes: int, mode: int = SERVE_CONTINUOUS,
+                 max_active: int = 256):
+        h = _vp()
+        _check(_server_create(device, int(budget_bytes), mode, max_active, C.byref(h)),
+               "acopf_server_create")
+        self._h = h
+        self._keep = {}  # ticket -> host arrays the server reads or writes
+
+    def submit(self, model: Model, n_calls: int, x, y, sigma_x, sigma_s, *, obj_weight=1.0,
+               delta_w=0.0, delta_c=0.0, Pd=None, Qd=None, f_calls=None, grad=None, cons=None,
+               jvals=None, hvals=None, kvals=None) -> int:
+        """Queues a request.  x, y, sigma_x, sigma_s: host arrays of n_points
+        point sets (shape (n_points, n) or (n,)); outputs are host arrays the
+        server fills (page-locked memory keeps the copies asynchronous).
+        Returns the ticket."""
+        arrays = dict(x=x, y=y, sigma_x=sigma_x, sigma_s=sigma_s, Pd=Pd, Qd=Qd, f_calls=f_calls,
+                      grad=grad, cons=cons, jvals=jvals, hvals=hvals, kvals=kvals)
+        for k, a in arrays.items():
+            if a is not None and (not isinstance(a, np.ndarray) or a.dtype != np.float64):
+                raise TypeError(f"{k} must be a float64 numpy array")
+        n_points = 1 if x.ndim == 1 else x.shape[0]
+        if x.size != n_points * model.n or sigma_x.size != n_points * model.n:
+            raise ValueError("x / sigma_x must hold n_points * n values")
+        if y.size != n_points * model.m or sigma_s.size != n_points * model.m:
+            raise ValueError("y / sigma_s must hold n_points * m values")
+        sizes = dict(f_calls=n_calls, grad=model.n, cons=model.m, jvals=model.nnz_jac,
+                     hvals=model.nnz_hess, kvals=model.nnz_kkt, Pd=model.n_bus, Qd=model.n_bus)
+        for k, n in sizes.items():
+            if arrays[k] is not None and arrays[k].size != n:
+                raise ValueError(f"{k} must hold {n} values")
+        r = Request()
+        r.model = model.handle.value
+        r.n_calls, r.n_points = n_calls, n_points
+        for k, a in arrays.items():
+            setattr(r, k, _hptr(a))
+        r.obj_weight, r.delta_w, r.delta_c = float(obj_weight), float(delta_w), float(delta_c)
+        t = C.c_uint64()
+        _check(_server_submit(self._h, C.byref(r), C.byref(t)), "acopf_server_submit")
+        self._keep[t.value] = (model, arrays)
+        return t.value
+
+    def poll(self, ticket: int):
+        """Returns (done, status)."""
+        d, st = C.c_int32(), C.c_int32()
+        _check(_server_poll(self._h, ticket, C.byref(d), C.byref(st)), "acopf_server_poll")
+        return bool(d.value), st.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        """Waits for a ticket; returns its status (raises on timeout)."""
+        st = C.c_int32()
+        _check(_server_wait(self._h, ticket, float(timeout_s), C.byref(st)), "acopf_server_wait")
+        return st.value
+
+    def times(self, ticket: int):
+        """(admitted, done) in seconds after submission."""
+        a, d = C.c_double(), C.c_double()
+        _check(_server_times(self._h, ticket, C.byref(a), C.byref(d)),
+               "acopf_server_request_times")
+        return a.value, d.value
+
+    def release(self, ticket: int) -> None:
+        _check(_server_release(self._h, ticket), "acopf_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_server_stats(self._h, C.byref(s)), "acopf_server_get_stats")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _server_destroy(self._h)
+        self._h = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def server_create(device: int, budget_bytes: int, mode: int = SERVE_CONTINUOUS,
+                  max_active: int = 256) -> Server:
+    return Server(device, budget_bytes, mode, max_active)

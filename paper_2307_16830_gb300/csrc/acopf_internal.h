@@ -171,6 +171,17 @@ cudaError_t launch_eval(const DevModel& dm, unsigned what, const EvalArgs& a, cu
                         cudaEvent_t mid = nullptr);
 cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+// Batched fused evaluation over work lists.  Phase-1 items (instance, role,
+// block, blocks of the role) are grouped by code variant c = 2 reg + shunt
+// (reg: delta_w or delta_c nonzero; shunt: the model has a shunt), variant
+// c owning items1[seg1[c], seg1[c + 1]); each present variant is one launch
+// of min(items, cap1) blocks.  Phase 2 runs n2 items on grid2 blocks (grid
+// < items: persistent blocks stride over the list).
+cudaError_t launch_batch(const DevModel* models, const EvalArgs* ios, const int4* items1,
+                         const int64_t* seg1, int64_t cap1, const int4* items2, int n2, int grid2,
+                         bool pdl, cudaStream_t s);
+// Resident blocks per SM of the two batch kernels.
+cudaError_t batch_occupancy(int* phase1, int* phase2);
 int launches_for(unsigned what);
 
 }  // namespace acopf

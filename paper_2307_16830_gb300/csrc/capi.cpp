@@ -6,26 +6,13 @@
 #include <string>
 #include <vector>
 
-#include "acopf_internal.h"
+#include "host_internal.h"
 
-struct acopf_model {
-  acopf::HostModel hm;
-  int device = -1;
-  acopf::DevModel dm{};
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  // device staging for acopf_eval_assemble_host
-  double* stage = nullptr;
-  size_t stage_bytes = 0;
-  // per-phase profiling (acopf_profile_begin / _end)
-  std::vector<cudaEvent_t> prof_events;  // 3 per profiled call
-  int32_t prof_capacity = 0;
-  int32_t prof_calls = 0;
-};
-
-namespace {
+namespace acopf {
 
 thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 acopf_status fail(acopf_status s, const std::string& msg) {
   g_last_error = msg;
@@ -37,39 +24,32 @@ acopf_status cuda_fail(cudaError_t e, const char* where) {
   return fail(e == cudaErrorMemoryAllocation ? ACOPF_E_OOM : ACOPF_E_CUDA, m);
 }
 
-// Makes the model's device current for the scope of a call.
-class DeviceScope {
- public:
-  explicit DeviceScope(int dev) {
-    err_ = cudaGetDevice(&prev_);
-    if (err_ == cudaSuccess && prev_ != dev) {
-      err_ = cudaSetDevice(dev);
-      switched_ = err_ == cudaSuccess;
-    }
-  }
-  ~DeviceScope() {
-    if (switched_) cudaSetDevice(prev_);
-  }
-  cudaError_t error() const { return err_; }
+acopf_status check_eval_scalars(double obj_weight, double delta_w, double delta_c) {
+  if (!(delta_w >= 0.0) || !(delta_c >= 0.0) || !std::isfinite(delta_w) || !std::isfinite(delta_c))
+    return fail(ACOPF_E_INVALID_ARG, "delta_w and delta_c must be finite and >= 0");
+  if (!std::isfinite(obj_weight)) return fail(ACOPF_E_INVALID_ARG, "obj_weight must be finite");
+  return ACOPF_OK;
+}
 
- private:
-  int prev_ = 0;
-  bool switched_ = false;
-  cudaError_t err_ = cudaSuccess;
-};
+void append_items(const Layout& L, int32_t inst, std::vector<int4>& p1, std::vector<int4>& p2) {
+  const int nbb = ceil_div(L.nl, kBranchThreads);
+  const int nbi = ceil_div(L.nb, kBusThreads);
+  const int ngb = std::max(1, ceil_div(L.ng, kGenThreads));
+  for (int k = 0; k < nbb; ++k) p1.push_back(make_int4(inst, 0, k, nbb));
+  for (int k = 0; k < nbi; ++k) p1.push_back(make_int4(inst, 1, k, nbi));
+  for (int k = 0; k < ngb; ++k) p1.push_back(make_int4(inst, 2, k, ngb));
+  for (int k = 0; k < nbi; ++k) p2.push_back(make_int4(inst, 3, k, nbi));
+}
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+}  // namespace acopf
 
-// Carves the model's device arena.
-struct ArenaPlan {
-  size_t off = 0;
-  template <typename T>
-  size_t take(size_t count) {
-    const size_t o = off;
-    off = align_up(off + count * sizeof(T), 256);
-    return o;
-  }
-};
+namespace {
+
+using acopf::ArenaPlan;
+using acopf::cuda_fail;
+using acopf::DeviceScope;
+using acopf::fail;
+using acopf::g_last_error;
 
 acopf_status check_device_model(const acopf_model* m) {
   if (!m) return fail(ACOPF_E_INVALID_ARG, "null model");
@@ -96,10 +76,6 @@ acopf::EvalArgs empty_args() {
 }
 
 }  // namespace
-
-namespace acopf {
-void set_last_error(const std::string& msg) { g_last_error = msg; }
-}  // namespace acopf
 
 extern "C" {
 
@@ -420,9 +396,8 @@ acopf_status acopf_eval_assemble(const acopf_model* model, const double* x, cons
                                  acopf_stream stream) {
   if (!x || !y || !sigma_x || !sigma_s || !f_dev || !grad || !cons || !jvals || !hvals || !kvals)
     return fail(ACOPF_E_INVALID_ARG, "acopf_eval_assemble: null pointer");
-  if (!(delta_w >= 0.0) || !(delta_c >= 0.0) || !std::isfinite(delta_w) || !std::isfinite(delta_c))
-    return fail(ACOPF_E_INVALID_ARG, "delta_w and delta_c must be finite and >= 0");
-  if (!std::isfinite(obj_weight)) return fail(ACOPF_E_INVALID_ARG, "obj_weight must be finite");
+  acopf_status st0 = acopf::check_eval_scalars(obj_weight, delta_w, delta_c);
+  if (st0 != ACOPF_OK) return st0;
   acopf::EvalArgs a = empty_args();
   a.x = x;
   a.y = y;

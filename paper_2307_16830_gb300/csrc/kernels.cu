@@ -747,7 +747,7 @@ template <unsigned W, bool REG, bool SHUNT>
 __global__ void __launch_bounds__(kBranchThreads, 6) k_phase1(DevModel dm, EvalArgs a, int nbb,
                                                              int nbi, int ngb) {
   pdl_trigger();
-  __shared__ double smem[(kBranchThreads / 32) * kBalCap * 2];
+  __shared__ __align__(16) double smem[(kBranchThreads / 32) * kBalCap * 2];  // read as double2
   const int b = blockIdx.x;
   if (b < nbb) {
     const int l = b * kBranchThreads + threadIdx.x;
@@ -783,9 +783,11 @@ __global__ void __launch_bounds__(kBranchThreads) k_asm_phase1(DevModel dm, Eval
 // (nu + 1)][vm_j (j < i)][vm_i], or just [vm_i] for a bus without branches.
 // The bus's slots run over its arcs by (other end, arc id), so parallel
 // branches (equal other end) are adjacent and their entries are summed.
-__global__ void __launch_bounds__(kBusThreads, 5) k_bus_rows(DevModel dm, EvalArgs a) {
+// Bus block blk of nblk (bus_warp_base interleaving).
+__device__ __forceinline__ void bus_rows_block(const DevModel& dm, const EvalArgs& a, int blk,
+                                               int nblk) {
   const Layout& L = dm.L;
-  const int p = bus_warp_base(blockIdx.x, gridDim.x) + (threadIdx.x & 31);
+  const int p = bus_warp_base(blk, nblk) + (threadIdx.x & 31);
   const bool active = p < L.nb;
   int i = 0, bva = 0, eva = 0, bvm = 0, evm = 0, k0 = 0, k1 = 0;
   if (active) {  // structure only: independent of phase 1
@@ -863,6 +865,72 @@ __global__ void __launch_bounds__(kBusThreads, 5) k_bus_rows(DevModel dm, EvalAr
   K[bva + nlo] = d.va + aa;
   if (k1 > k0) K[bvm + nlo] = ma;  // (vm_i, va_i) exists only when bus i has a branch
   K[evm - 1] = d.vm + mm;
+}
+
+__global__ void __launch_bounds__(kBusThreads, 5) k_bus_rows(DevModel dm, EvalArgs a) {
+  bus_rows_block(dm, a, blockIdx.x, gridDim.x);
+}
+
+// ===========================================================================
+// Batched evaluation: many instances in one launch per phase.  Work item
+// {instance, role, block, blocks of that role in the instance}; roles 0
+// branch, 1 bus input, 2 generators (phase 1); phase 2 items are bus-row
+// blocks.  Each block runs items[b], items[b + gridDim.x], ... (one item per
+// block when the grid covers the list; fewer, persistent blocks otherwise).
+// Per item the instance's model view and arguments are copied to shared
+// memory.  Phase 1 is compiled per code variant (regularised or not, shunts
+// or not) and launched once per variant present, over the items of the
+// instances of that variant: each instance runs the variant its own call
+// takes, so its results are bit-identical to those of that call.
+// ===========================================================================
+template <typename Fn>
+__device__ __forceinline__ void for_items(const DevModel* __restrict__ models,
+                                          const EvalArgs* __restrict__ ios,
+                                          const int4* __restrict__ items, int n, DevModel& sdm,
+                                          EvalArgs& sa, Fn fn) {
+  int cur = -1;
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    const int4 it = items[b];
+    if (it.x != cur) {  // uniform over the block
+      __syncthreads();  // every thread is done with the previous instance
+      if (threadIdx.x == 0) {
+        sdm = models[it.x];
+        sa = ios[it.x];
+      }
+      cur = it.x;
+    }
+    __syncthreads();
+    fn(it);
+  }
+}
+
+template <bool REG, bool SHUNT>
+__global__ void __launch_bounds__(kBranchThreads, 6) k_batch_phase1(
+    const DevModel* __restrict__ models, const EvalArgs* __restrict__ ios,
+    const int4* __restrict__ items, int n) {
+  __shared__ DevModel sdm;
+  __shared__ EvalArgs sa;
+  __shared__ __align__(16) double smem[(kBranchThreads / 32) * kBalCap * 2];  // read as double2
+  pdl_trigger();
+  for_items(models, ios, items, n, sdm, sa, [&](const int4& it) {
+    if (it.y == 0) {
+      const int l = it.z * kBranchThreads + threadIdx.x;
+      if (l < sdm.L.nl) branch_fused<OUT_ALL, REG, SHUNT>(sdm, sa, l);
+    } else if (it.y == 1) {
+      bus_input_block<OUT_ALL, REG, false, SHUNT>(sdm, sa, it.z, it.w, smem);
+    } else {
+      gen_block<OUT_ALL, REG, false>(sdm, sa, it.z, it.w, smem);
+    }
+  });
+}
+
+__global__ void __launch_bounds__(kBusThreads, 5) k_batch_bus_rows(
+    const DevModel* __restrict__ models, const EvalArgs* __restrict__ ios,
+    const int4* __restrict__ items, int n) {
+  __shared__ DevModel sdm;
+  __shared__ EvalArgs sa;
+  for_items(models, ios, items, n, sdm, sa,
+            [&](const int4& it) { bus_rows_block(sdm, sa, it.z, it.w); });
 }
 
 // FP64 FMA throughput probe: 8 independent dependent chains per thread.
@@ -992,6 +1060,38 @@ cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_ex(k_bus_rows, dim3(nbi), dim3(kBusThreads), 0, s, dm.pdl != 0, dm, a);
+}
+
+cudaError_t launch_batch(const DevModel* models, const EvalArgs* ios, const int4* items1,
+                         const int64_t* seg1, int64_t cap1, const int4* items2, int n2, int grid2,
+                         bool pdl, cudaStream_t s) {
+  bool any1 = false;
+  for (int c = 0; c < 4; ++c) {
+    const int n = static_cast<int>(seg1[c + 1] - seg1[c]);
+    if (n == 0) continue;
+    const int grid = static_cast<int>(n < cap1 ? n : cap1);
+    const int4* it = items1 + seg1[c];
+    switch (c) {
+      case 0: k_batch_phase1<false, false><<<grid, kBranchThreads, 0, s>>>(models, ios, it, n); break;
+      case 1: k_batch_phase1<false, true><<<grid, kBranchThreads, 0, s>>>(models, ios, it, n); break;
+      case 2: k_batch_phase1<true, false><<<grid, kBranchThreads, 0, s>>>(models, ios, it, n); break;
+      default: k_batch_phase1<true, true><<<grid, kBranchThreads, 0, s>>>(models, ios, it, n); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    any1 = true;
+  }
+  if (n2 == 0) return cudaSuccess;
+  return launch_ex(k_batch_bus_rows, dim3(grid2), dim3(kBusThreads), 0, s, pdl && any1, models,
+                   ios, items2, n2);
+}
+
+cudaError_t batch_occupancy(int* phase1, int* phase2) {
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(phase1, k_batch_phase1<false, false>,
+                                                    kBranchThreads, 0);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(phase2, k_batch_bus_rows, kBusThreads, 0);
 }
 
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {

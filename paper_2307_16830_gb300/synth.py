@@ -348,3 +348,39 @@ def workload_grid(name: str) -> Grid:
 
 def point_seed(grid_seed: int, call_index: int) -> int:
     return grid_seed * 7919 + call_index
+
+
+def grid_for_size(n_bus: int, seed: int, name: str | None = None) -> Grid:
+    """Grid of n_bus buses with the proportions of the workloads above: 1.35
+    branches and 0.2 generators per bus (at least a spanning tree, at least
+    one generator, at most one branch per bus pair)."""
+    n_bus = int(n_bus)
+    n_branch = max(n_bus - 1, int(round(1.35 * n_bus)))
+    n_branch = min(n_branch, n_bus * (n_bus - 1) // 2)
+    n_gen = max(1, int(round(0.2 * n_bus)))
+    return make_grid(n_bus, n_branch, n_gen, seed, name=name)
+
+
+def log_uniform_sizes(rng: np.random.Generator, count: int, lo: int, hi: int) -> np.ndarray:
+    """Bus counts drawn log-uniformly in [lo, hi]."""
+    return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
+
+
+# The batch workload: load scenarios of one network plus networks of mixed size.
+BATCH_WORKLOAD = dict(n_scenarios=128, scenario_bus=2000, scenario_branch=2700, scenario_gen=400,
+                      n_mixed=128, mixed_lo=30, mixed_hi=20000, seed=1003)
+
+
+def batch_workload(n_scenarios: int = 128, n_mixed: int = 128, seed: int = 1003,
+                   scenario_bus: int = 2000, scenario_branch: int = 2700,
+                   scenario_gen: int = 400, mixed_lo: int = 30, mixed_hi: int = 20000):
+    """Returns (base, scenarios, mixed): the base network, n_scenarios load
+    scenarios of it (every bus's Pd and Qd scaled by its own U(0.9, 1.1)) and
+    n_mixed networks with log-uniform bus counts in [mixed_lo, mixed_hi]."""
+    base = make_grid(scenario_bus, scenario_branch, scenario_gen, seed,
+                     name=f"synthetic-{scenario_bus}bus-seed{seed}")
+    scenarios = [scale_loads(base, seed * 1000 + k) for k in range(n_scenarios)]
+    rng = np.random.default_rng(seed + 1)
+    sizes = log_uniform_sizes(rng, n_mixed, mixed_lo, mixed_hi)
+    mixed = [grid_for_size(int(nb), seed + 10 + k) for k, nb in enumerate(sizes)]
+    return base, scenarios, mixed

@@ -148,3 +148,28 @@ def test_launch_accounting():
     for kind in range(7):
         assert acopf.launches_per_call(kind) == (2 if kind in (0, 1) else 1)
     assert acopf.launches_per_call(99) == -1
+
+
+def test_batch_create_rejects_without_device_work():
+    """Argument checks of acopf_batch_create that come before any CUDA call."""
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, device=-1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.batch_create([m])
+        assert ei.value.status == acopf.E_NO_DEVICE
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.batch_create([])
+        assert ei.value.status == acopf.E_INVALID_ARG
+
+
+
+def test_server_create_rejects_without_device_work():
+    """Argument checks of acopf_server_create that come before any CUDA call."""
+    with pytest.raises(acopf.AcopfError) as ei:
+        acopf.server_create(-1, 1 << 30)
+    assert ei.value.status == acopf.E_NO_DEVICE
+    for budget, mode, max_active in ((0, acopf.SERVE_CONTINUOUS, 4), (1 << 30, 7, 4),
+                                     (1 << 30, acopf.SERVE_FIFO, 0)):
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.server_create(0, budget, mode, max_active)
+        assert ei.value.status == acopf.E_INVALID_ARG
