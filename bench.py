@@ -46,9 +46,9 @@ ROTATE = 4
 # kernels.cu whose hash is recorded; the traffic is reported as null once the
 # kernel source changes.
 PHASE1_NCU = {
-    "kernels_sha": "bed03878db742c5d",
+    "kernels_sha": "cc517454119fd7aa",
     "workload": "80kbus",
-    "dram_bytes": 44_424_192 + 38_437_888,
+    "dram_bytes": 43_885_568 + 37_445_888,
     "fp64_dfma": 6_746_000, "fp64_dadd": 6_960_000, "fp64_dmul": 6_330_000,
 }
 # FP64 flops of phase 1 per branch (the kernel's arithmetic on the fused
@@ -391,8 +391,9 @@ def run_batch_bench(args, local):
 
 
 def run_serve_bench(args, local):
-    """Served form: a Poisson request stream over resident models (16 networks
-    of 30..80,000 buses, log-uniform), each request 50 evaluate+assemble calls
+    """Served form: a Poisson request stream over resident models (24 networks
+    of 30..80,000 buses at the log-uniform quantiles; a request picks one
+    uniformly, so request sizes are log-uniform), each request 50 evaluate+assemble calls
     over 2 point sets; continuous batching against FIFO plain launches, both
     under a 40 GB device-memory budget, at arrival rates 0.1..1.2 x the
     measured saturation rate.  Latency = submission to completion (host
@@ -402,7 +403,7 @@ def run_serve_bench(args, local):
     from paper_2307_16830_gb300 import acopf
 
     rng = np.random.default_rng(2004)
-    sizes = synth.log_uniform_sizes(rng, args.serve_models, 30, 80_000)
+    sizes = synth.stratified_log_uniform_sizes(args.serve_models, 30, 80_000)
     pool, hold = [], []
     for k, nbus in enumerate(sizes):
         g = synth.grid_for_size(int(nbus), 3000 + k)
@@ -542,7 +543,7 @@ def main():
     ap.add_argument("--serve", type=int, default=1, choices=[0, 1],
                     help="also run the served form (Poisson requests, p50/p99)")
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-models", type=int, default=16)
+    ap.add_argument("--serve-models", type=int, default=24)
     ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.1, 0.3, 0.6, 0.9, 1.2])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -374,7 +374,7 @@ acopf_status acopf_batch_info(const acopf_batch* batch, int32_t* schedule, int64
  *     batched evaluation (the acopf_batch kernels) of every admitted request
  *     that has calls left, one call each; requests join at the next tick
  *     after admission and leave when their last call is done, so requests
- *     that arrive while others run share launches with them.  At most two
+ *     that arrive while others run share launches with them.  At most four
  *     ticks are in flight.
  *   ACOPF_SERVE_FIFO: plain launches.  Each admitted request's calls are
  *     queued as single-instance launches (acopf_eval_assemble's kernels) in

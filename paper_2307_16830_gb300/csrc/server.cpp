@@ -26,7 +26,7 @@ using acopf::fail;
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kMaxInflightTicks = 2;
+constexpr int kMaxInflightTicks = 4;
 constexpr int kRing = kMaxInflightTicks + 1;
 
 enum class St { Queued, Active, Draining, Done };

@@ -366,6 +366,13 @@ def log_uniform_sizes(rng: np.random.Generator, count: int, lo: int, hi: int) ->
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
 
 
+def stratified_log_uniform_sizes(count: int, lo: int, hi: int) -> np.ndarray:
+    """count bus counts at the midpoint quantiles of the log-uniform
+    distribution on [lo, hi] (a deterministic, evenly spread sample)."""
+    q = (np.arange(count) + 0.5) / count
+    return np.rint(np.exp(math.log(lo) + q * (math.log(hi) - math.log(lo)))).astype(np.int64)
+
+
 # The batch workload: load scenarios of one network plus networks of mixed size.
 BATCH_WORKLOAD = dict(n_scenarios=128, scenario_bus=2000, scenario_branch=2700, scenario_gen=400,
                       n_mixed=128, mixed_lo=30, mixed_hi=20000, seed=1003)
