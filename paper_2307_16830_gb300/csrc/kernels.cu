@@ -125,13 +125,58 @@ __device__ __forceinline__ void put4(double* __restrict__ K, int r0, bool f_lo, 
   }
 }
 
+// Writes one arc row of M_cond from position k of `out`: the four bus
+// entries, ng generator entries vg, the optional entry vx (the p_a column of
+// row q_a), rk earlier-arc entries vr and the diagonal vd.
+__device__ __forceinline__ void row_write(double* out, int k, bool f_lo, double e_vaf, double e_vat,
+                                          double e_vmf, double e_vmt, int ng, double vg, bool hasx,
+                                          double vx, int rk, double vr, double vd) {
+  put4(out, k, f_lo, e_vaf, e_vat, e_vmf, e_vmt);
+  k += 4;
+  for (int e = 0; e < ng; ++e) out[k++] = vg;
+  if (hasx) out[k++] = vx;
+  for (int e = 0; e < rk; ++e) out[k++] = vr;
+  out[k] = vd;
+}
+
+// Per-warp staging capacity for the arc rows (doubles): the branch blocks
+// reuse the bus-input blocks' shared buffer, kBalCap double2 per warp.
+constexpr int kRowStageCap = 2 * kBalCap;
+
+// One arc row per lane, rows r0 of the warp's 32 branches being consecutive
+// rows of the CSR (so the warp's rows tile one contiguous range of K).
+// With a staging buffer (a full warp) the rows are assembled in shared
+// memory and the range is written with coalesced stores; without one, or
+// when the range exceeds the buffer, each lane stores its own row.
+__device__ __forceinline__ void arc_row(double* __restrict__ K, double* stage, int r0, bool f_lo,
+                                        double e_vaf, double e_vat, double e_vmf, double e_vmt,
+                                        int ng, double vg, bool hasx, double vx, int rk, double vr,
+                                        double vd) {
+  if (stage != nullptr) {  // uniform over the warp: all 32 lanes are here
+    const int len = 5 + ng + (hasx ? 1 : 0) + rk;
+    const int base = __shfl_sync(0xffffffffu, r0, 0);
+    const int n = __shfl_sync(0xffffffffu, r0 + len, 31) - base;
+    if (n <= kRowStageCap) {
+      row_write(stage, r0 - base, f_lo, e_vaf, e_vat, e_vmf, e_vmt, ng, vg, hasx, vx, rk, vr, vd);
+      __syncwarp();
+      for (int i = threadIdx.x & 31; i < n; i += 32) K[base + i] = stage[i];
+      __syncwarp();
+      return;
+    }
+  }
+  row_write(K, r0, f_lo, e_vaf, e_vat, e_vmf, e_vmt, ng, vg, hasx, vx, rk, vr, vd);
+}
+
 // ===========================================================================
 // Phase 1, fused path: branch thread.
 // ===========================================================================
 // SHUNT = false: every bus has Gs = Bs = 0, so the balance rows' vm
 // coefficients 2 Gs vm and -2 Bs vm vanish from the arc rows of M_cond.
+// `stage`: the warp's slice of the block's shared buffer when all 32 lanes
+// of the warp run a branch (nullptr otherwise); used for the arc rows.
 template <unsigned W, bool REG, bool SHUNT>
-__device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs& a, int l) {
+__device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs& a, int l,
+                                             double* stage) {
   const Layout& L = dm.L;
   const int nl = L.nl;
   const int f = ld(dm.f + l), t = ld(dm.t + l);
@@ -348,45 +393,20 @@ __device__ __forceinline__ void branch_fused(const DevModel& dm, const EvalArgs&
           rkf = ld(rp + iPf + 1) - rs.x - 5 - ngf;
           rkt = ld(rp + iPt + 1) - rs.z - 5 - ngt;
         }
-        const double nD_Pf = neg(D_Pf), nD_Qf = neg(D_Qf), nD_Pt = neg(D_Pt), nD_Qt = neg(D_Qt);
         // row p_l (from arc, bus f)
-        {
-          const int r0 = rs.x;
-          put4(K, r0, f_lo, neg(A_pf), A_pf, e_Pf, neg(C_pf));
-          int k = r0 + 4;
-          for (int e = 0; e < ngf; ++e) K[k++] = nD_Pf;
-          for (int e = 0; e < rkf; ++e) K[k++] = D_Pf;
-          K[k] = sxw<REG>(ld(sx + iPf), dw) + hs_f + D_pf + fma(Dsp_f, jp_f, D_Pf);
-        }
+        arc_row(K, stage, rs.x, f_lo, neg(A_pf), A_pf, e_Pf, neg(C_pf), ngf, neg(D_Pf), false, 0.0,
+                rkf, D_Pf, sxw<REG>(ld(sx + iPf), dw) + hs_f + D_pf + fma(Dsp_f, jp_f, D_Pf));
         // row q_l
-        {
-          const int r0 = rs.y;
-          put4(K, r0, f_lo, neg(A_qf), A_qf, e_Qf, nC_qf);
-          int k = r0 + 4;
-          for (int e = 0; e < ngf; ++e) K[k++] = nD_Qf;
-          K[k++] = Dsp_f * jq_f;
-          for (int e = 0; e < rkf; ++e) K[k++] = D_Qf;
-          K[k] = sxw<REG>(ld(sx + iQf), dw) + hs_f + D_qf + fma(D_sf * jq_f, jq_f, D_Qf);
-        }
+        arc_row(K, stage, rs.y, f_lo, neg(A_qf), A_qf, e_Qf, nC_qf, ngf, neg(D_Qf), true,
+                Dsp_f * jq_f, rkf, D_Qf,
+                sxw<REG>(ld(sx + iQf), dw) + hs_f + D_qf + fma(D_sf * jq_f, jq_f, D_Qf));
         // row p_{nl+l} (to arc, bus t)
-        {
-          const int r0 = rs.z;
-          put4(K, r0, f_lo, neg(A_pt), A_pt, neg(B_pt), e_Pt);
-          int k = r0 + 4;
-          for (int e = 0; e < ngt; ++e) K[k++] = nD_Pt;
-          for (int e = 0; e < rkt; ++e) K[k++] = D_Pt;
-          K[k] = sxw<REG>(ld(sx + iPt), dw) + hs_t + D_pt + fma(Dsp_t, jp_t, D_Pt);
-        }
+        arc_row(K, stage, rs.z, f_lo, neg(A_pt), A_pt, neg(B_pt), e_Pt, ngt, neg(D_Pt), false, 0.0,
+                rkt, D_Pt, sxw<REG>(ld(sx + iPt), dw) + hs_t + D_pt + fma(Dsp_t, jp_t, D_Pt));
         // row q_{nl+l}
-        {
-          const int r0 = rs.w;
-          put4(K, r0, f_lo, nA_qt, neg(nA_qt), neg(B_qt), e_Qt);
-          int k = r0 + 4;
-          for (int e = 0; e < ngt; ++e) K[k++] = nD_Qt;
-          K[k++] = Dsp_t * jq_t;
-          for (int e = 0; e < rkt; ++e) K[k++] = D_Qt;
-          K[k] = sxw<REG>(ld(sx + iQt), dw) + hs_t + D_qt + fma(D_st * jq_t, jq_t, D_Qt);
-        }
+        arc_row(K, stage, rs.w, f_lo, nA_qt, neg(nA_qt), neg(B_qt), e_Qt, ngt, neg(D_Qt), true,
+                Dsp_t * jq_t, rkt, D_Qt,
+                sxw<REG>(ld(sx + iQt), dw) + hs_t + D_qt + fma(D_st * jq_t, jq_t, D_Qt));
       }
     }
   }
@@ -751,7 +771,9 @@ __global__ void __launch_bounds__(kBranchThreads, 6) k_phase1(DevModel dm, EvalA
   const int b = blockIdx.x;
   if (b < nbb) {
     const int l = b * kBranchThreads + threadIdx.x;
-    if (l < dm.L.nl) branch_fused<W, REG, SHUNT>(dm, a, l);
+    const bool full = (l | 31) < dm.L.nl;  // the whole warp has branches
+    if (l < dm.L.nl)
+      branch_fused<W, REG, SHUNT>(dm, a, l, full ? smem + (threadIdx.x >> 5) * kRowStageCap : nullptr);
   } else if (b < nbb + nbi) {
     bus_input_block<W, REG, false, SHUNT>(dm, a, b - nbb, nbi, smem);
   } else {
@@ -915,7 +937,10 @@ __global__ void __launch_bounds__(kBranchThreads, 6) k_batch_phase1(
   for_items(models, ios, items, n, sdm, sa, [&](const int4& it) {
     if (it.y == 0) {
       const int l = it.z * kBranchThreads + threadIdx.x;
-      if (l < sdm.L.nl) branch_fused<OUT_ALL, REG, SHUNT>(sdm, sa, l);
+      const bool full = (l | 31) < sdm.L.nl;  // the whole warp has branches
+      if (l < sdm.L.nl)
+        branch_fused<OUT_ALL, REG, SHUNT>(sdm, sa, l,
+                                          full ? smem + (threadIdx.x >> 5) * kRowStageCap : nullptr);
     } else if (it.y == 1) {
       bus_input_block<OUT_ALL, REG, false, SHUNT>(sdm, sa, it.z, it.w, smem);
     } else {

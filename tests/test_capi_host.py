@@ -173,3 +173,30 @@ def test_server_create_rejects_without_device_work():
         with pytest.raises(acopf.AcopfError) as ei:
             acopf.server_create(0, budget, mode, max_active)
         assert ei.value.status == acopf.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_arc_rows_tile_contiguous_ranges(k):
+    """The kernels stage the arc rows of a warp's 32 consecutive branches in
+    shared memory and write them as one range: row p_l of M_cond must hold
+    exactly 5 + (generators at the from bus) + (earlier arcs at that bus)
+    entries and row q_l one more, and consecutive branches' rows must be
+    consecutive CSR rows (likewise p_{nl+l}, q_{nl+l} at the to bus)."""
+    g = [synth.make_edge_case_grid(7), synth.make_grid(517, 777, 61, seed=3),
+         synth.make_star_grid()][k]
+    with acopf.model_create(g, device=-1) as m:
+        rp, _ = m.kkt_structure()
+        nb, nl, ng = m.n_bus, m.n_branch, m.n_gen
+        P, Q = 2 * nb + 2 * ng, 2 * nb + 2 * ng + 2 * nl
+        gens = np.bincount(np.asarray(g.gen_bus), minlength=nb)
+        bus_of_arc = np.concatenate([np.asarray(g.f), np.asarray(g.t)])
+        seen = np.zeros(nb, dtype=np.int64)
+        rank = np.zeros(2 * nl, dtype=np.int64)
+        for a in range(2 * nl):  # earlier arcs (smaller arc index) at the same bus
+            rank[a] = seen[bus_of_arc[a]]
+            seen[bus_of_arc[a]] += 1
+        ln = np.diff(rp)
+        for a in range(2 * nl):
+            i = bus_of_arc[a]
+            assert ln[P + a] == 5 + gens[i] + rank[a], (a, ln[P + a])
+            assert ln[Q + a] == 6 + gens[i] + rank[a], (a, ln[Q + a])
