@@ -279,12 +279,12 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": 8 * (1 + model.n + model.m + model.nnz_jac
                                           + model.nnz_hess + model.nnz_kkt)}
 
-    fp64_gflops = acopf.measure_fp64_gflops(local)
+    fp64_rates = acopf.measure_fp64_rates(local)  # G lane-ops/s of fma, add, mul
     rp, _ = model.kkt_structure()
     kkt_bus_rows = int(rp[model.n_bus * 2] - rp[0])
     kkt_arc_gen = model.nnz_kkt - kkt_bus_rows
     res = dict(value=value, ms=ms_max, p1_ms=p1_ms, p2_ms=p2_ms, call_ms=call_ms, e2e=e2e,
-               clocks=clocks.summary(), sizes=s, fp64_gflops=fp64_gflops,
+               clocks=clocks.summary(), sizes=s, fp64_rates=fp64_rates,
                kkt_arc_gen=kkt_arc_gen, gpu=torch.cuda.get_device_name(dev))
     if world > 1:
         import torch.distributed as dist
@@ -567,15 +567,20 @@ def main():
     p1_s = r["p1_ms"] * 1e-3
     measured = NCU_MATCH = (PHASE1_NCU["kernels_sha"] == kernels_sha()
                             and PHASE1_NCU["workload"] == args.workload)
+    ops = {k: PHASE1_NCU[k] for k in ("fp64_dfma", "fp64_dadd", "fp64_dmul")}
     if measured:
-        flops = 2 * PHASE1_NCU["fp64_dfma"] + PHASE1_NCU["fp64_dadd"] + PHASE1_NCU["fp64_dmul"]
         traffic = PHASE1_NCU["dram_bytes"]
-    else:
-        flops = FLOPS_PER_BRANCH * s["nl"]
+    else:  # scale the captured counts by the branch count
+        ops = {k: v * s["nl"] / 110_000 for k, v in ops.items()}
         traffic = None
+    flops = 2 * ops["fp64_dfma"] + ops["fp64_dadd"] + ops["fp64_dmul"]
     by1 = phase1_bytes(s, r["kkt_arc_gen"])
     ach_flops = flops / p1_s / 1e12
-    peak_flops = r["fp64_gflops"] / 1e3
+    r_fma, r_add, r_mul = r["fp64_rates"]
+    peak_flops = 2 * r_fma / 1e3
+    # FP64 issue bound of this kernel's operation mix (adds and multiplies
+    # are one flop per issue, FMAs two, and each has its own measured rate)
+    t_mix = (ops["fp64_dfma"] / r_fma + ops["fp64_dadd"] / r_add + ops["fp64_dmul"] / r_mul) / 1e9
     ach_bw = by1 / p1_s / 1e9
     hbm_peak = 6772.9
     try:
@@ -592,13 +597,16 @@ def main():
     if fp64_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ach_flops, "peak": peak_flops, "unit": "TFLOP/s",
                 "frac": fp64_frac, **roof_common,
-                "peak_source": "FP64 FMA throughput measured live (acopf_measure_fp64_gflops)",
+                "peak_source": "FP64 FMA throughput measured live (acopf_measure_fp64_rates)",
+                "fp64_mix_view": {"issue_bound_us": t_mix * 1e6, "frac": t_mix / p1_s,
+                                  "rates_gops": {"fma": r_fma, "add": r_add, "mul": r_mul},
+                                  "ops_per_launch": ops},
                 "hbm_view": {"achieved_gbs": ach_bw, "peak_gbs": hbm_peak, "frac": hbm_frac}}
     else:
         roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_frac, **roof_common, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "fp64_view": {"achieved_tflops": ach_flops, "peak_tflops": peak_flops,
-                              "frac": fp64_frac}}
+                              "frac": fp64_frac, "issue_bound_us": t_mix * 1e6}}
     call_bytes = algorithmic_bytes(s)
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

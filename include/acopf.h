@@ -230,11 +230,17 @@ acopf_status acopf_profile_end(acopf_model* model, int32_t* calls, double* phase
                                double* phase2_ms, double* total_ms);
 
 /* Measured FP64 fused-multiply-add throughput of `device` in GFLOP/s (2
- * flops per FMA): the best of five runs of a kernel of about 70 ms running
- * eight independent DFMA chains per thread on eight blocks per SM.  A
- * measurement aid for rooflines: the paper has no counterpart.  Allocates
- * and frees a small device buffer. */
+ * flops per FMA): the best of five runs (after one warm-up) of a kernel of 8
+ * blocks per SM x 256 threads, each thread running eight independent chains
+ * of 16,384 dependent FMAs.  A measurement aid for rooflines: the paper has
+ * no counterpart.  Allocates and frees a small device buffer. */
 acopf_status acopf_measure_fp64_gflops(int device, double* gflops);
+
+/* The same probe for each FP64 operation: G instructions per second of
+ * FMA, add and multiply (per thread, i.e. lane operations).  Kernels whose
+ * FP64 work mixes the three are bound by sum_op count_op / rate_op.  NULL
+ * outputs are skipped. */
+acopf_status acopf_measure_fp64_rates(int device, double* dfma, double* dadd, double* dmul);
 
 /* Objective f = sum_g c2_g pg_g^2 + c1_g pg_g + c0_g, for callers that must
  * not allocate device memory.  The paper has no counterpart: it is a
@@ -374,8 +380,8 @@ acopf_status acopf_batch_info(const acopf_batch* batch, int32_t* schedule, int64
  *     batched evaluation (the acopf_batch kernels) of every admitted request
  *     that has calls left, one call each; requests join at the next tick
  *     after admission and leave when their last call is done, so requests
- *     that arrive while others run share launches with them.  At most four
- *     ticks are in flight.
+ *     that arrive while others run share launches with them.  A bounded
+ *     number of ticks is in flight (ACOPF_SERVE_OPT_INFLIGHT).
  *   ACOPF_SERVE_FIFO: plain launches.  Each admitted request's calls are
  *     queued as single-instance launches (acopf_eval_assemble's kernels) in
  *     arrival order on the server's stream.
@@ -469,6 +475,13 @@ acopf_status acopf_server_request_times(acopf_server* server, uint64_t ticket, d
 acopf_status acopf_server_release(acopf_server* server, uint64_t ticket);
 
 acopf_status acopf_server_get_stats(acopf_server* server, acopf_server_stats* out);
+
+/* Server options (scheduling only; results never change).
+ * ACOPF_SERVE_OPT_INFLIGHT (default 4, range 1..16): continuous-mode ticks
+ * queued on the GPU ahead of completion.  More hides the host's per-tick
+ * work behind the GPU's; fewer lets a new request join sooner. */
+#define ACOPF_SERVE_OPT_INFLIGHT 1
+acopf_status acopf_server_set_option(acopf_server* server, int32_t option, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -91,6 +91,7 @@ _objective_noalloc = _sig("acopf_objective_noalloc", C.c_int32, C.c_int64, _vp, 
                           _vp, _vp)
 OPT_PDL = 1
 _measure_fp64 = _sig("acopf_measure_fp64_gflops", C.c_int32, C.c_int, _f64p)
+_measure_fp64_rates = _sig("acopf_measure_fp64_rates", C.c_int32, C.c_int, _f64p, _f64p, _f64p)
 _profile_begin = _sig("acopf_profile_begin", C.c_int32, _vp, C.c_int32)
 _profile_end = _sig("acopf_profile_end", C.c_int32, _vp, _i32p, _f64p, _f64p, _f64p)
 
@@ -147,6 +148,8 @@ _server_wait = _sig("acopf_server_wait", C.c_int32, _vp, C.c_uint64, C.c_double,
 _server_times = _sig("acopf_server_request_times", C.c_int32, _vp, C.c_uint64, _f64p, _f64p)
 _server_release = _sig("acopf_server_release", C.c_int32, _vp, C.c_uint64)
 _server_stats = _sig("acopf_server_get_stats", C.c_int32, _vp, C.POINTER(ServerStats))
+_server_set_option = _sig("acopf_server_set_option", C.c_int32, _vp, C.c_int32, C.c_int64)
+SERVE_OPT_INFLIGHT = 1
 
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
@@ -155,13 +158,14 @@ EXPORTED = [
     "acopf_hess_structure", "acopf_kkt_structure", "acopf_eval_obj", "acopf_eval_grad",
     "acopf_eval_cons", "acopf_eval_jac_coo", "acopf_eval_hess_coo",
     "acopf_assemble_condensed_kkt_csr", "acopf_eval_assemble", "acopf_eval_assemble_host",
-    "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_profile_begin",
+    "acopf_launches_per_call", "acopf_measure_fp64_gflops", "acopf_measure_fp64_rates",
+    "acopf_profile_begin",
     "acopf_profile_end", "acopf_model_set_option", "acopf_objective_noalloc",
     "acopf_batch_create", "acopf_batch_destroy", "acopf_batch_set_io",
     "acopf_batch_eval_assemble", "acopf_batch_set_schedule", "acopf_batch_autotune",
     "acopf_batch_info", "acopf_server_create", "acopf_server_destroy", "acopf_server_submit",
     "acopf_server_poll", "acopf_server_wait", "acopf_server_request_times",
-    "acopf_server_release", "acopf_server_get_stats",
+    "acopf_server_release", "acopf_server_get_stats", "acopf_server_set_option",
 ]
 
 
@@ -377,6 +381,14 @@ def measure_fp64_gflops(device: int = 0) -> float:
     return v.value
 
 
+def measure_fp64_rates(device: int = 0):
+    """(fma, add, mul) lane operations per second, in G/s."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(_measure_fp64_rates(device, C.byref(a), C.byref(b), C.byref(c)),
+           "acopf_measure_fp64_rates")
+    return a.value, b.value, c.value
+
+
 def profile_begin(model: Model, capacity: int) -> None:
     _check(_profile_begin(model.handle, int(capacity)), "acopf_profile_begin")
 
@@ -552,6 +564,9 @@ class Server:
         s = ServerStats()
         _check(_server_stats(self._h, C.byref(s)), "acopf_server_get_stats")
         return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def set_option(self, option: int, value: int) -> None:
+        _check(_server_set_option(self._h, option, value), "acopf_server_set_option")
 
     def close(self) -> None:
         if self._h is not None and self._h.value:

@@ -170,7 +170,9 @@ struct EvalArgs {
 cudaError_t launch_eval(const DevModel& dm, unsigned what, const EvalArgs& a, cudaStream_t s,
                         cudaEvent_t mid = nullptr);
 cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t s);
-cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+// FP64 throughput probe: op 0 fma, 1 add, 2 mul; 256 threads x blocks, each
+// 8 chains of `iters` operations.
+cudaError_t launch_fp64_probe(int op, double* out, int blocks, int iters, cudaStream_t s);
 // Batched fused evaluation over work lists.  Phase-1 items (instance, role,
 // block, blocks of the role) are grouped by code variant c = 2 reg + shunt
 // (reg: delta_w or delta_c nonzero; shunt: the model has a shunt), variant

@@ -566,17 +566,21 @@ int32_t acopf_launches_per_call(int32_t kind) {
   }
 }
 
-acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
-  if (!gflops || device < 0) return fail(ACOPF_E_INVALID_ARG, "bad argument");
+}  // extern "C"
+
+namespace {
+
+// Best-of-5 rate (G operations / s) of the FP64 probe for `op`.
+acopf_status measure_fp64_op(int device, int op, double* ginst) {
   DeviceScope ds(device);
-  if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_measure_fp64_gflops");
+  if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_measure_fp64");
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, device);
-  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64_gflops");
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64");
   const int blocks = prop.multiProcessorCount * 8, iters = 16384;
   double* buf = nullptr;
   e = cudaMalloc(&buf, size_t(blocks) * 256 * 8);
-  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64_gflops: cudaMalloc");
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64: cudaMalloc");
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float best = 1e30f;
@@ -585,7 +589,7 @@ acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
     e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess) e = acopf::launch_fp64_probe(buf, blocks, iters, s);
+    if (e == cudaSuccess) e = acopf::launch_fp64_probe(op, buf, blocks, iters, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0;
@@ -596,9 +600,32 @@ acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
   if (e1) cudaEventDestroy(e1);
   if (s) cudaStreamDestroy(s);
   cudaFree(buf);
-  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64_gflops");
-  const double fmas = double(blocks) * 256 * 8 * iters;
-  *gflops = 2.0 * fmas / (double(best) * 1e-3) / 1e9;
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_measure_fp64");
+  const double ops = double(blocks) * 256 * 8 * iters;
+  *ginst = ops / (double(best) * 1e-3) / 1e9;
+  return ACOPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+acopf_status acopf_measure_fp64_gflops(int device, double* gflops) {
+  if (!gflops || device < 0) return fail(ACOPF_E_INVALID_ARG, "bad argument");
+  double r = 0.0;
+  acopf_status st = measure_fp64_op(device, 0, &r);
+  if (st == ACOPF_OK) *gflops = 2.0 * r;
+  return st;
+}
+
+acopf_status acopf_measure_fp64_rates(int device, double* dfma, double* dadd, double* dmul) {
+  if (device < 0) return fail(ACOPF_E_INVALID_ARG, "bad argument");
+  double* out[3] = {dfma, dadd, dmul};
+  for (int op = 0; op < 3; ++op) {
+    if (!out[op]) continue;
+    acopf_status st = measure_fp64_op(device, op, out[op]);
+    if (st != ACOPF_OK) return st;
+  }
   return ACOPF_OK;
 }
 

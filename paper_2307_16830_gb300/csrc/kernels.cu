@@ -910,14 +910,22 @@ __device__ __forceinline__ void for_items(const DevModel* __restrict__ models,
                                           const EvalArgs* __restrict__ ios,
                                           const int4* __restrict__ items, int n, DevModel& sdm,
                                           EvalArgs& sa, Fn fn) {
+  static_assert(sizeof(DevModel) % 8 == 0 && sizeof(EvalArgs) % 8 == 0, "copied as 8-byte words");
+  constexpr int kM = sizeof(DevModel) / 8, kA = sizeof(EvalArgs) / 8;
+  static_assert(kM <= 64 && 64 + kA <= kBranchThreads && 64 + kA <= kBusThreads, "copy layout");
   int cur = -1;
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     const int4 it = items[b];
     if (it.x != cur) {  // uniform over the block
       __syncthreads();  // every thread is done with the previous instance
-      if (threadIdx.x == 0) {
-        sdm = models[it.x];
-        sa = ios[it.x];
+      // Word-parallel copy: threads 0.. the model view, threads 64.. the arguments.
+      const int t = threadIdx.x;
+      if (t < kM) {
+        reinterpret_cast<unsigned long long*>(&sdm)[t] =
+            __ldg(reinterpret_cast<const unsigned long long*>(models + it.x) + t);
+      } else if (t >= 64 && t < 64 + kA) {
+        reinterpret_cast<unsigned long long*>(&sa)[t - 64] =
+            __ldg(reinterpret_cast<const unsigned long long*>(ios + it.x) + (t - 64));
       }
       cur = it.x;
     }
@@ -930,8 +938,11 @@ template <bool REG, bool SHUNT>
 __global__ void __launch_bounds__(kBranchThreads, 6) k_batch_phase1(
     const DevModel* __restrict__ models, const EvalArgs* __restrict__ ios,
     const int4* __restrict__ items, int n) {
-  __shared__ DevModel sdm;
-  __shared__ EvalArgs sa;
+  // Raw storage (the views are trivially copied in; no constructor runs).
+  __shared__ alignas(8) unsigned char sdm_raw[sizeof(DevModel)];
+  __shared__ alignas(8) unsigned char sa_raw[sizeof(EvalArgs)];
+  DevModel& sdm = *reinterpret_cast<DevModel*>(sdm_raw);
+  EvalArgs& sa = *reinterpret_cast<EvalArgs*>(sa_raw);
   __shared__ __align__(16) double smem[(kBranchThreads / 32) * kBalCap * 2];  // read as double2
   pdl_trigger();
   for_items(models, ios, items, n, sdm, sa, [&](const int4& it) {
@@ -952,26 +963,32 @@ __global__ void __launch_bounds__(kBranchThreads, 6) k_batch_phase1(
 __global__ void __launch_bounds__(kBusThreads, 5) k_batch_bus_rows(
     const DevModel* __restrict__ models, const EvalArgs* __restrict__ ios,
     const int4* __restrict__ items, int n) {
-  __shared__ DevModel sdm;
-  __shared__ EvalArgs sa;
+  // Raw storage (the views are trivially copied in; no constructor runs).
+  __shared__ alignas(8) unsigned char sdm_raw[sizeof(DevModel)];
+  __shared__ alignas(8) unsigned char sa_raw[sizeof(EvalArgs)];
+  DevModel& sdm = *reinterpret_cast<DevModel*>(sdm_raw);
+  EvalArgs& sa = *reinterpret_cast<EvalArgs*>(sa_raw);
   for_items(models, ios, items, n, sdm, sa,
             [&](const int4& it) { bus_rows_block(sdm, sa, it.z, it.w); });
 }
 
-// FP64 FMA throughput probe: 8 independent dependent chains per thread.
-__global__ void k_fp64_probe(double* out, int iters) {
+// FP64 throughput probe: 8 independent dependent chains per thread of one
+// operation (0 fma, 1 add, 2 mul); the operands a, b are kernel arguments.
+template <int OP>
+__global__ void k_fp64_probe(double* out, int iters, double a, double b) {
   double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
   double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
-  const double m = 0.9999999, c = 1e-7;
   for (int i = 0; i < iters; ++i) {
-    x0 = fma(x0, m, c);
-    x1 = fma(x1, m, c);
-    x2 = fma(x2, m, c);
-    x3 = fma(x3, m, c);
-    x4 = fma(x4, m, c);
-    x5 = fma(x5, m, c);
-    x6 = fma(x6, m, c);
-    x7 = fma(x7, m, c);
+    if constexpr (OP == 0) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    } else if constexpr (OP == 1) {
+      x0 = x0 + b; x1 = x1 + b; x2 = x2 + b; x3 = x3 + b;
+      x4 = x4 + b; x5 = x5 + b; x6 = x6 + b; x7 = x7 + b;
+    } else {
+      x0 = x0 * a; x1 = x1 * a; x2 = x2 * a; x3 = x3 * a;
+      x4 = x4 * a; x5 = x5 * a; x6 = x6 * a; x7 = x7 * a;
+    }
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
@@ -1119,8 +1136,13 @@ cudaError_t batch_occupancy(int* phase1, int* phase2) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(phase2, k_batch_bus_rows, kBusThreads, 0);
 }
 
-cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
-  k_fp64_probe<<<blocks, 256, 0, s>>>(out, iters);
+cudaError_t launch_fp64_probe(int op, double* out, int blocks, int iters, cudaStream_t s) {
+  if (op == 0)
+    k_fp64_probe<0><<<blocks, 256, 0, s>>>(out, iters, 0.9999999, 1e-7);
+  else if (op == 1)
+    k_fp64_probe<1><<<blocks, 256, 0, s>>>(out, iters, 0.9999999, 1e-7);
+  else
+    k_fp64_probe<2><<<blocks, 256, 0, s>>>(out, iters, 0.9999999, 1e-7);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 // the loop; client threads only queue requests and read their records
 // under the mutex.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -26,8 +27,8 @@ using acopf::fail;
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kMaxInflightTicks = 4;
-constexpr int kRing = kMaxInflightTicks + 1;
+constexpr int kMaxInflightLimit = 16;  // upper bound of ACOPF_SERVE_OPT_INFLIGHT
+constexpr int kRing = kMaxInflightLimit + 1;
 
 enum class St { Queued, Active, Draining, Done };
 
@@ -119,6 +120,7 @@ struct acopf_server {
   int64_t budget = 0;
   int32_t mode = ACOPF_SERVE_CONTINUOUS;
   int32_t max_active = 1;
+  std::atomic<int> max_inflight{4};  // ticks in flight (continuous mode)
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
   std::thread th;
@@ -422,7 +424,7 @@ void serve(acopf_server* S) {
     if (err == cudaSuccess && S->mode == ACOPF_SERVE_CONTINUOUS) {
       bool calls_left = false;
       for (Req* q : S->active) calls_left |= q->st == St::Active && q->issued < q->r.n_calls;
-      if (calls_left && int(S->inflight.size()) < kMaxInflightTicks) {
+      if (calls_left && int(S->inflight.size()) < S->max_inflight.load()) {
         err = tick(S);
         progressed = true;
       } else if (!S->inflight.empty()) {
@@ -627,6 +629,18 @@ acopf_status acopf_server_release(acopf_server* server, uint64_t ticket) {
   server->reqs.erase(ticket);
   delete q;
   return ACOPF_OK;
+}
+
+acopf_status acopf_server_set_option(acopf_server* server, int32_t option, int64_t value) {
+  if (!server) return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: null server");
+  if (option == ACOPF_SERVE_OPT_INFLIGHT) {
+    if (value < 1 || value > kMaxInflightLimit)
+      return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: in-flight ticks must be in [1, 16]");
+    server->max_inflight.store(int(value));
+    server->cv_work.notify_all();
+    return ACOPF_OK;
+  }
+  return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: unknown option");
 }
 
 acopf_status acopf_server_get_stats(acopf_server* server, acopf_server_stats* out) {

@@ -183,3 +183,17 @@ def test_pdl_option_does_not_change_results(dev, acopf):
         b = gu.run_fused(torch, acopf, m, pt, dev)
         for k in gu.KEYS:
             assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("spread", [20.0, 3e5])
+def test_fused_at_wide_angles(dev, acopf, spread):
+    """Branch angles far outside the operating range (every quadrant, up to
+    hundreds of thousands of radians) still match the oracle."""
+    g = synth.make_grid(517, 777, 61, seed=3)
+    rng = np.random.default_rng(77)
+    with acopf.model_create(g, 0) as m:
+        pt = synth.make_point(g, 9, obj_weight=1.1)
+        pt.x = pt.x.copy()
+        pt.x[:g.n_bus] = rng.uniform(-spread, spread, g.n_bus)
+        got = gu.run_fused(torch, acopf, m, pt, dev)
+        gu.assert_parity(got, gu.oracle_all(g, pt), label=f"spread {spread}")

@@ -164,6 +164,27 @@ def test_served_results_same_alone_and_in_mix(dev, acopf):
         m.close()
 
 
+def test_inflight_option_keeps_results(dev, acopf):
+    js, models = jobs(acopf)
+    ref = [run_alone(acopf, j, acopf.SERVE_CONTINUOUS) for j in js]
+    for depth in (1, 16):
+        with acopf.server_create(0, BIG, acopf.SERVE_CONTINUOUS) as s:
+            s.set_option(acopf.SERVE_OPT_INFLIGHT, depth)
+            tickets = [j.submit(s) for j in js]
+            for t in tickets:
+                assert s.wait(t, 120.0) == acopf.OK
+            for k, j in enumerate(js):
+                assert_request_equal(j.result(), ref[k], f"inflight {depth} request {k}")
+    with acopf.server_create(0, BIG, acopf.SERVE_CONTINUOUS) as s:
+        for bad_opt, bad_val in ((acopf.SERVE_OPT_INFLIGHT, 0), (acopf.SERVE_OPT_INFLIGHT, 17),
+                                 (99, 1)):
+            with pytest.raises(acopf.AcopfError) as e:
+                s.set_option(bad_opt, bad_val)
+            assert e.value.status == acopf.E_INVALID_ARG
+    for m in models:
+        m.close()
+
+
 def test_admission_respects_budget(dev, acopf):
     js, models = jobs(acopf)
     ref = [run_alone(acopf, j, acopf.SERVE_CONTINUOUS) for j in js]
