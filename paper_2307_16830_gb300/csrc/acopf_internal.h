@@ -95,8 +95,8 @@ struct DevModel {
   // scratch
   SlotPart* part_slot;         // 2 nl
   BusDiag* bus_diag;           // nb
-  double* obj_part;            // one per generator block
-  unsigned int* obj_ticket;    // arrival counter of the generator blocks (reset by the last)
+  double* obj_part;            // one per generator warp
+  unsigned int* obj_ticket;    // arrival counter of the generator warps (reset by the last)
   // launch options
   int32_t has_shunt;           // some bus has Gs != 0 or Bs != 0
   int32_t pdl;                 // chain the phases with programmatic dependent launch

@@ -161,11 +161,8 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const size_t o_c2 = p.take<double>(ng), o_c1 = p.take<double>(ng), o_c0 = p.take<double>(ng);
   const size_t o_krp = p.take<int32_t>(n + 1);
   const size_t o_brow = p.take<int4>(nl), o_bcnt = p.take<uint32_t>(nl);
-  const size_t o_ps = p.take<acopf::SlotPart>(2 * nl);
-  const size_t o_bd = p.take<acopf::BusDiag>(nb);
-  const size_t n_obj = size_t(acopf::ceil_div(L.ng, acopf::kGenThreads)) + 1;
-  const size_t o_obj = p.take<double>(n_obj);
-  const size_t o_tick = p.take<unsigned int>(1);
+  const acopf::WorkspacePlan wsp = acopf::workspace_plan(L);
+  const size_t o_ws = p.take<char>(wsp.bytes);
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, p.off);
   if (e != cudaSuccess) {
@@ -205,8 +202,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_pord, hm.porder.data(), nb * 4);
   if (e == cudaSuccess) e = up(o_psp, hm.pslot_ptr.data(), (nb + 1) * 4);
   if (e == cudaSuccess) e = up(o_bidx, hm.bal_idx.data(), (ng + 2 * nl) * 4);
-  if (e == cudaSuccess) e = cudaMemset(base + o_obj, 0, n_obj * 8);
-  if (e == cudaSuccess) e = cudaMemset(base + o_tick, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(base + o_ws, 0, wsp.bytes);  // counters start at zero
   if (e != cudaSuccess) {
     cudaFree(arena);
     delete m;
@@ -235,12 +231,9 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.krowptr = reinterpret_cast<const int32_t*>(base + o_krp);
   dm.brow = reinterpret_cast<const int4*>(base + o_brow);
   dm.bcnt = reinterpret_cast<const uint32_t*>(base + o_bcnt);
-  dm.part_slot = reinterpret_cast<acopf::SlotPart*>(base + o_ps);
-  dm.bus_diag = reinterpret_cast<acopf::BusDiag*>(base + o_bd);
   dm.pbal_ptr = reinterpret_cast<const int32_t*>(base + o_bptr);
   dm.bal_idx = reinterpret_cast<const int32_t*>(base + o_bidx);
-  dm.obj_part = reinterpret_cast<double*>(base + o_obj);
-  dm.obj_ticket = reinterpret_cast<unsigned int*>(base + o_tick);
+  acopf::bind_workspace(dm, base + o_ws, wsp);
   *out = m;
   return ACOPF_OK;
 }

@@ -68,9 +68,9 @@ struct ArenaPlan {
 };
 
 // The scratch one evaluation writes and reads back (slot partials, bus
-// diagonals, generator-block objective sums, their arrival counter).  Every
-// evaluation in flight at the same time needs its own; the counter must be
-// zero before first use (each call leaves it zero).
+// diagonals, generator-warp objective sums and their arrival counter).
+// Every evaluation in flight at the same time needs its own; the counter
+// must be zero before first use (each call leaves it zero).
 struct WorkspacePlan {
   size_t part_slot = 0, bus_diag = 0, obj_part = 0, ticket = 0, bytes = 0;
 };
@@ -80,7 +80,7 @@ inline WorkspacePlan workspace_plan(const Layout& L) {
   WorkspacePlan w;
   w.part_slot = p.take<SlotPart>(2 * size_t(L.nl));
   w.bus_diag = p.take<BusDiag>(size_t(L.nb));
-  w.obj_part = p.take<double>(size_t(ceil_div(L.ng, kGenThreads)) + 1);
+  w.obj_part = p.take<double>(size_t(ceil_div(L.ng, 32)) + 1);
   w.ticket = p.take<unsigned int>(1);
   w.bytes = p.off;
   return w;

@@ -589,11 +589,12 @@ __device__ __forceinline__ int bus_warp_base(int blk, int nblk) {
   return 32 * (w * nblk + (nblk - 1 - blk));
 }
 
+// One warp: the 32 buses at processing positions [pw0, pw0 + 32), with
+// `buf` the warp's shared staging buffer (kBalCap double2).
 template <unsigned W, bool REG, bool ARRAYS, bool SHUNT>
-__device__ __forceinline__ void bus_input_block(const DevModel& dm, const EvalArgs& a, int blk,
-                                                int nblk, double* smem) {
+__device__ __forceinline__ void bus_input_warp(const DevModel& dm, const EvalArgs& a, int pw0,
+                                               double2* buf) {
   const Layout& L = dm.L;
-  const int pw0 = bus_warp_base(blk, nblk);
   const int p = pw0 + (threadIdx.x & 31);
   const bool active = p < L.nb;
   const int i = active ? ld(dm.porder + p) : 0;
@@ -603,12 +604,11 @@ __device__ __forceinline__ void bus_input_block(const DevModel& dm, const EvalAr
     // (generators then arcs of each bus); lanes fetch the terms together with
     // all loads in flight at once, stage them in shared memory, and each lane
     // then sums its own bus's terms in list order.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     if (pw0 < L.nb) {
       const int pw1 = min(pw0 + 32, L.nb);
       const int e0 = ld(dm.pbal_ptr + pw0), e1 = ld(dm.pbal_ptr + pw1);
       const int ne = e1 - e0;
-      double2* buf = reinterpret_cast<double2*>(smem) + warp * kBalCap;
       const bool staged = ne <= kBalCap;
       if (staged) {
         constexpr int R = kBalCap / 32;
@@ -717,15 +717,23 @@ __device__ __forceinline__ void bus_input_block(const DevModel& dm, const EvalAr
   if constexpr ((W & OUT_KKT) != 0) dm.bus_diag[p] = BusDiag{d_va, d_vm};
 }
 
-// Generator block: generator rows, and the objective.  Each block reduces
-// its generators' cost terms in a fixed tree order; the last block to
-// arrive (an arrival counter, not an accumulation) adds the block sums in
-// block order, so the result does not depend on scheduling.
+// Bus-input block blk of nblk: its four warps (bus_warp_base interleaving).
+template <unsigned W, bool REG, bool ARRAYS, bool SHUNT>
+__device__ __forceinline__ void bus_input_block(const DevModel& dm, const EvalArgs& a, int blk,
+                                                int nblk, double* smem) {
+  bus_input_warp<W, REG, ARRAYS, SHUNT>(
+      dm, a, bus_warp_base(blk, nblk), reinterpret_cast<double2*>(smem) + (threadIdx.x >> 5) * kBalCap);
+}
+
+// Generator warp gw of ngw: generator rows, and the objective.  Each warp
+// reduces its generators' cost terms in a fixed shuffle order; the last
+// warp to arrive (an arrival counter, not an accumulation) adds the warp
+// sums in warp order, so the result does not depend on scheduling.
 template <unsigned W, bool REG, bool ARRAYS>
-__device__ __forceinline__ void gen_block(const DevModel& dm, const EvalArgs& a, int gb, int ngen,
-                                          double* smem) {
+__device__ __forceinline__ void gen_warp(const DevModel& dm, const EvalArgs& a, int gw, int ngw) {
   const Layout& L = dm.L;
-  const int g = gb * kGenThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int g = gw * 32 + lane;
   if (g < L.ng) {
     if constexpr (ARRAYS)
       gen_from_arrays<REG>(dm, a, g);
@@ -738,27 +746,38 @@ __device__ __forceinline__ void gen_block(const DevModel& dm, const EvalArgs& a,
       const double pg = ld(a.x + L.PG + g);
       v = fma(fma(ld(dm.c2 + g), pg, ld(dm.c1 + g)), pg, ld(dm.c0 + g));
     }
-    const double s = block_sum<kGenThreads>(v, smem);
-    int* last = reinterpret_cast<int*>(smem + kGenThreads / 32);
-    if (threadIdx.x == 0) {
-      dm.obj_part[gb] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int last = 0;
+    if (lane == 0) {
+      dm.obj_part[gw] = v;
       __threadfence();
-      const unsigned int t = atomicAdd(dm.obj_ticket, 1u);
-      *last = (t == static_cast<unsigned int>(ngen - 1));
+      last = atomicAdd(dm.obj_ticket, 1u) == static_cast<unsigned int>(ngw - 1);
     }
-    __syncthreads();
-    if (*last && threadIdx.x < 32) {
+    if (__shfl_sync(0xffffffffu, last, 0)) {
       __threadfence();
       double r = 0.0;
-      for (int k = threadIdx.x; k < ngen; k += 32) r += __ldcg(dm.obj_part + k);
+      for (int k = lane; k < ngw; k += 32) r += __ldcg(dm.obj_part + k);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         *a.f = r;
         *dm.obj_ticket = 0u;
       }
     }
   }
+}
+
+// Generator warps of ng generators (at least one when the objective is
+// evaluated, so that a model without generators still writes f = 0).
+__device__ __forceinline__ int gen_warps(int ng) { return ng > 0 ? (ng + 31) / 32 : 1; }
+
+// Generator block gb: its four warps.
+template <unsigned W, bool REG, bool ARRAYS>
+__device__ __forceinline__ void gen_block(const DevModel& dm, const EvalArgs& a, int gb) {
+  const int ngw = gen_warps(dm.L.ng);
+  const int gw = gb * (kGenThreads / 32) + (threadIdx.x >> 5);
+  if (gw < ngw) gen_warp<W, REG, ARRAYS>(dm, a, gw, ngw);
 }
 
 // Phase 1: block roles [0, nbb) branch blocks, [nbb, nbb + nbi) bus-input
@@ -777,7 +796,7 @@ __global__ void __launch_bounds__(kBranchThreads, 6) k_phase1(DevModel dm, EvalA
   } else if (b < nbb + nbi) {
     bus_input_block<W, REG, false, SHUNT>(dm, a, b - nbb, nbi, smem);
   } else {
-    gen_block<W, REG, false>(dm, a, b - nbb - nbi, ngb, smem);
+    gen_block<W, REG, false>(dm, a, b - nbb - nbi);
   }
 }
 
@@ -794,7 +813,7 @@ __global__ void __launch_bounds__(kBranchThreads) k_asm_phase1(DevModel dm, Eval
   } else if (b < nbb + nbi) {
     bus_input_block<OUT_KKT, REG, true, true>(dm, a, b - nbb, nbi, smem);
   } else {
-    gen_block<OUT_KKT, REG, true>(dm, a, b - nbb - nbi, ngb, smem);
+    gen_block<OUT_KKT, REG, true>(dm, a, b - nbb - nbi);
   }
 }
 
@@ -955,7 +974,7 @@ __global__ void __launch_bounds__(kBranchThreads, 6) k_batch_phase1(
     } else if (it.y == 1) {
       bus_input_block<OUT_ALL, REG, false, SHUNT>(sdm, sa, it.z, it.w, smem);
     } else {
-      gen_block<OUT_ALL, REG, false>(sdm, sa, it.z, it.w, smem);
+      gen_block<OUT_ALL, REG, false>(sdm, sa, it.z);
     }
   });
 }

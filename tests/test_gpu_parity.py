@@ -197,3 +197,4 @@ def test_fused_at_wide_angles(dev, acopf, spread):
         pt.x[:g.n_bus] = rng.uniform(-spread, spread, g.n_bus)
         got = gu.run_fused(torch, acopf, m, pt, dev)
         gu.assert_parity(got, gu.oracle_all(g, pt), label=f"spread {spread}")
+
