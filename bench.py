@@ -39,6 +39,7 @@ from paper_2307_16830_gb300 import synth  # noqa: E402
 METRIC = "eval+KKT-assembly calls/s and % HBM roofline; served p50/p99 vs plain launches"
 UNIT = "calls/s"
 ROTATE = 4
+GRAPH_CALLS = 100  # calls captured in one CUDA graph (rotating over the ROTATE sets)
 
 # Counters of the phase-1 kernel on the 80,000-bus workload from one ncu
 # capture (profiles/k_phase1_80kbus.md): DRAM read + write bytes per launch,
@@ -46,15 +47,16 @@ ROTATE = 4
 # kernels.cu whose hash is recorded; the traffic is reported as null once the
 # kernel source changes.
 PHASE1_NCU = {
-    "kernels_sha": "cc517454119fd7aa",
+    "kernels_sha": "6b89e1989b970c3d",
     "workload": "80kbus",
-    "dram_bytes": 43_885_568 + 37_445_888,
-    "fp64_dfma": 6_746_000, "fp64_dadd": 6_960_000, "fp64_dmul": 6_330_000,
+    "dram_bytes": 40_702_464 + 34_138_112,
+    "fp64_dfma": 6_746_000, "fp64_dadd": 6_944_803, "fp64_dmul": 6_220_000,
 }
 # FP64 flops of phase 1 per branch (the kernel's arithmetic on the fused
 # path without regularisation, bus and generator work folded in), from the
 # capture above: (2 dfma + dadd + dmul) / n_branch.
-FLOPS_PER_BRANCH = (2 * 6_746_000 + 6_960_000 + 6_330_000) / 110_000
+FLOPS_PER_BRANCH = (2 * PHASE1_NCU["fp64_dfma"] + PHASE1_NCU["fp64_dadd"]
+                    + PHASE1_NCU["fp64_dmul"]) / 110_000
 
 
 def kernels_sha() -> str:
@@ -240,6 +242,36 @@ def run_ours(args, rank, world, local):
     ms_max = reduce_max(ms, world, dev)
     value = throughput(world, args.steps, ms_max)
 
+    # the same calls replayed from a CUDA graph (GRAPH_CALLS calls per replay)
+    graph_ms = None
+    if args.graph_replays > 0:
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(stream):
+                for k in range(ROTATE):
+                    step(k)
+            stream.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                for k in range(GRAPH_CALLS):
+                    step(k)
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    g.replay()
+                barrier()
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for _ in range(args.graph_replays):
+                    g.replay()
+                g1.record(stream)
+                barrier()
+            graph_ms = (reduce_max(g0.elapsed_time(g1), world, dev)
+                        / (args.graph_replays * GRAPH_CALLS))
+            del g
+        except RuntimeError as exc:  # report, keep the plain-launch result
+            print(f"graph replay not timed: {exc}", file=sys.stderr)
+            graph_ms = None
+
     # per-phase durations (separate pass, events between the phases)
     nprof = max(16, min(args.steps, 512))
     with torch.cuda.stream(stream):
@@ -284,6 +316,7 @@ def run_ours(args, rank, world, local):
     kkt_bus_rows = int(rp[model.n_bus * 2] - rp[0])
     kkt_arc_gen = model.nnz_kkt - kkt_bus_rows
     res = dict(value=value, ms=ms_max, p1_ms=p1_ms, p2_ms=p2_ms, call_ms=call_ms, e2e=e2e,
+               graph_ms=graph_ms,
                clocks=clocks.summary(), sizes=s, fp64_rates=fp64_rates,
                kkt_arc_gen=kkt_arc_gen, gpu=torch.cuda.get_device_name(dev))
     if world > 1:
@@ -292,6 +325,69 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
     model.close()
     return res
+
+
+def run_small_workloads(local):
+    """Per-call time of the 30-bus and 10,000-bus workloads: plain launches
+    and the same calls replayed from a CUDA graph (4 rotating point sets;
+    both fit in L2, so these are latency and L2 figures, not HBM ones)."""
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, calls in (("30bus", 2000), ("10kbus", 1000)):
+        grid = synth.workload_grid(name)
+        seed = synth.WORKLOADS[name]["seed"]
+        model = acopf.model_create(grid, local)
+
+        def t(a):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+        sets = []
+        for r in range(ROTATE):
+            pt = synth.make_point(grid, synth.point_seed(seed, r))
+            sets.append([t(pt.x), t(pt.y), t(pt.sigma_x), t(pt.sigma_s)] + [
+                torch.empty(k, dtype=torch.float64, device=dev) for k in
+                (1, model.n, model.m, model.nnz_jac, model.nnz_hess, model.nnz_kkt)])
+
+        def step(k):
+            b = sets[k % ROTATE]
+            acopf.eval_assemble(model, b[0], b[1], 1.0, b[2], b[3], 0.0, 0.0, *b[4:],
+                                stream=stream)
+
+        with torch.cuda.stream(stream):
+            for k in range(50):
+                step(k)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(calls):
+                step(k)
+            e1.record(stream)
+            stream.synchronize()
+        plain_us = 1e3 * e0.elapsed_time(e1) / calls
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for k in range(GRAPH_CALLS):
+                step(k)
+        with torch.cuda.stream(stream):
+            g.replay()
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(calls // GRAPH_CALLS):
+                g.replay()
+            e1.record(stream)
+            stream.synchronize()
+        graph_us = 1e3 * e0.elapsed_time(e1) / (calls // GRAPH_CALLS * GRAPH_CALLS)
+        del g
+        out[name] = {"buses": grid.n_bus, "branches": grid.n_branch, "generators": grid.n_gen,
+                     "plain_us_per_call": plain_us, "graph_us_per_call": graph_us,
+                     "calls_per_s_plain": 1e6 / plain_us, "calls_per_s_graph": 1e6 / graph_us}
+        model.close()
+    return out
 
 
 def _pinned(torch, a):
@@ -536,6 +632,10 @@ def main():
                     help="chain the two phases with programmatic dependent launch")
     ap.add_argument("--soak", type=float, default=1.0,
                     help="seconds of untimed calls (at least --warmup) before timing")
+    ap.add_argument("--graph-replays", type=int, default=20,
+                    help="also time the calls replayed from a CUDA graph of 100 calls")
+    ap.add_argument("--small-workloads", type=int, default=1, choices=[0, 1],
+                    help="also time the 30-bus and 10,000-bus workloads (plain and graph)")
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)
@@ -553,6 +653,7 @@ def main():
         run_reference(args, rank, world)
         return
     r = run_ours(args, rank, world, local)
+    small = run_small_workloads(local) if args.small_workloads and world == 1 else None
     batch = run_batch_bench(args, local) if args.batch and world == 1 else None
     serve = run_serve_bench(args, local) if args.serve and world == 1 else None
     if rank != 0:
@@ -625,6 +726,10 @@ def main():
         "phases_ms": {"phase1": r["p1_ms"], "phase2": r["p2_ms"], "call": r["call_ms"]},
         "clocks": r["clocks"], "e2e": r["e2e"],
         "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cpu,
+        "graph": None if r["graph_ms"] is None else {
+            "ms_per_call": r["graph_ms"], "calls_per_s": 1e3 / r["graph_ms"],
+            "note": f"{GRAPH_CALLS} calls per CUDA graph, {args.graph_replays} replays"},
+        "small_workloads": small,
         "gpu": r["gpu"], "batch": batch, "serve": serve,
     }
     print(json.dumps(line), flush=True)

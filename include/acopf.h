@@ -57,8 +57,10 @@
  * model share the model's scratch (per-branch partial sums of the KKT
  * assembly): calls on the same model must not overlap on the GPU, so issue
  * them on one stream (or order them with events); different models are
- * independent.  No CPU fallback exists: without a usable device every
- * compute call returns ACOPF_E_CUDA or ACOPF_E_NO_DEVICE.
+ * independent.  To evaluate one model concurrently on several streams, give
+ * each stream its own batch of that model (acopf_batch_create): every batch
+ * instance has its own scratch.  No CPU fallback exists: without a usable
+ * device every compute call returns ACOPF_E_CUDA or ACOPF_E_NO_DEVICE.
  * No call throws; errors are returned as acopf_status, with a message
  * readable through acopf_last_error() on the calling thread.
  */

@@ -277,3 +277,29 @@ def test_batch_workload_256(dev, acopf):
     for m in mixed_models:
         m.close()
     base_m.close()
+
+
+def test_one_model_on_two_streams_through_batches(dev, acopf):
+    """A model's own calls share its scratch; concurrent evaluations of one
+    model on several streams go through batches, each with its own scratch:
+    two one-instance batches of the same model, evaluated concurrently on
+    two streams, give the results of sequential single-instance calls."""
+    g = synth.make_grid(517, 777, 61, seed=3)
+    with acopf.model_create(g, 0) as m:
+        insts = [Inst(g, m, synth.make_point(g, 300 + k)) for k in range(2)]
+        for it in insts:
+            it.alloc(dev)
+        alone = [gu.run_fused(torch, acopf, m, it.pt, dev) for it in insts]
+        streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        batches = [acopf.batch_create([m]) for _ in range(2)]
+        for b, it, s in zip(batches, insts, streams):
+            acopf.batch_set_io(b, [it.io()], stream=s)
+        torch.cuda.synchronize()
+        for rep in range(20):
+            for b, s in zip(batches, streams):
+                acopf.batch_eval_assemble(b, stream=s)
+        torch.cuda.synchronize()
+        for k, it in enumerate(insts):
+            assert_same_bits(it.result(), alone[k], f"stream {k}")
+        for b in batches:
+            b.close()
