@@ -204,6 +204,30 @@ acopf_status acopf_eval_assemble_host(acopf_model* model, const double* x, const
                                       double* f, double* grad, double* cons, double* jvals,
                                       double* hvals, double* kvals, acopf_stream stream);
 
+/* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of
+ * one model with HOST inputs and outputs, whose host-to-device copies,
+ * kernels and device-to-host copies overlap (three streams, `depth` device
+ * staging slots of one call each: inputs and outputs).  The paper has no
+ * counterpart; it is the host-side form of the same unit of work.
+ * acopf_pipeline_submit queues one call and returns without waiting (host
+ * buffers as in acopf_eval_assemble_host; page-locked memory makes the
+ * copies asynchronous); the caller keeps every buffer it passed valid and
+ * unchanged, and reads no output, until acopf_pipeline_wait returns, and
+ * gives calls in flight together distinct output buffers.  Calls
+ * run in submission order and use the model's scratch, so no other call on
+ * the model may overlap them.  depth in [2, 8]; the slots take depth x (the
+ * bytes of one call's inputs and outputs) of device memory.  Destroy waits
+ * for the submitted calls. */
+typedef struct acopf_pipeline acopf_pipeline;
+acopf_status acopf_pipeline_create(acopf_model* model, int32_t depth, acopf_pipeline** out);
+acopf_status acopf_pipeline_destroy(acopf_pipeline* pipeline);
+acopf_status acopf_pipeline_submit(acopf_pipeline* pipeline, const double* x, const double* y,
+                                   double obj_weight, const double* sigma_x,
+                                   const double* sigma_s, double delta_w, double delta_c,
+                                   double* f, double* grad, double* cons, double* jvals,
+                                   double* hvals, double* kvals);
+acopf_status acopf_pipeline_wait(acopf_pipeline* pipeline);
+
 /* Launch options of a model (not numerics: results are identical either way).
  * ACOPF_OPT_PDL (default 1): launch the second phase of a call with
  * programmatic dependent launch, so its independent work overlaps the first

@@ -7,3 +7,4 @@ nothing from the library except the seeded data generator
 ``paper_2307_16830_gb300.synth`` (which holds no arithmetic of the method).
 """
 from .acopf import *  # noqa: F401,F403
+from .step import *  # noqa: F401,F403

@@ -151,6 +151,12 @@ _server_stats = _sig("acopf_server_get_stats", C.c_int32, _vp, C.POINTER(ServerS
 _server_set_option = _sig("acopf_server_set_option", C.c_int32, _vp, C.c_int32, C.c_int64)
 SERVE_OPT_INFLIGHT = 1
 
+_pipeline_create = _sig("acopf_pipeline_create", C.c_int32, _vp, C.c_int32, C.POINTER(_vp))
+_pipeline_destroy = _sig("acopf_pipeline_destroy", C.c_int32, _vp)
+_pipeline_submit = _sig("acopf_pipeline_submit", C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp,
+                        C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp)
+_pipeline_wait = _sig("acopf_pipeline_wait", C.c_int32, _vp)
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -166,6 +172,8 @@ EXPORTED = [
     "acopf_batch_info", "acopf_server_create", "acopf_server_destroy", "acopf_server_submit",
     "acopf_server_poll", "acopf_server_wait", "acopf_server_request_times",
     "acopf_server_release", "acopf_server_get_stats", "acopf_server_set_option",
+    "acopf_pipeline_create", "acopf_pipeline_destroy", "acopf_pipeline_submit",
+    "acopf_pipeline_wait",
 ]
 
 
@@ -590,3 +598,54 @@ class Server:
 def server_create(device: int, budget_bytes: int, mode: int = SERVE_CONTINUOUS,
                   max_active: int = 256) -> Server:
     return Server(device, budget_bytes, mode, max_active)
+
+
+class Pipeline:
+    """Pipelined host-buffer evaluation of one model (owner of an
+    ``acopf_pipeline*``)."""
+
+    def __init__(self, model: Model, depth: int = 2):
+        h = _vp()
+        _check(_pipeline_create(model.handle, depth, C.byref(h)), "acopf_pipeline_create")
+        self._h = h
+        self.model = model
+        self._keep = []
+
+    def submit(self, x, y, obj_weight: float, sigma_x, sigma_s, delta_w: float, delta_c: float,
+               f, grad, cons, jvals, hvals, kvals) -> None:
+        """Queues one call; host numpy arrays (kept alive until wait())."""
+        arrs = (x, y, sigma_x, sigma_s, f, grad, cons, jvals, hvals, kvals)
+        for a in arrs:
+            if not isinstance(a, np.ndarray) or a.dtype != np.float64:
+                raise TypeError("pipeline buffers must be float64 numpy arrays")
+        _check(_pipeline_submit(self._h, _hptr(x), _hptr(y), float(obj_weight), _hptr(sigma_x),
+                                _hptr(sigma_s), float(delta_w), float(delta_c), _hptr(f),
+                                _hptr(grad), _hptr(cons), _hptr(jvals), _hptr(hvals),
+                                _hptr(kvals)), "acopf_pipeline_submit")
+        self._keep.append(arrs)
+
+    def wait(self) -> None:
+        _check(_pipeline_wait(self._h), "acopf_pipeline_wait")
+        self._keep.clear()
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _pipeline_destroy(self._h)
+        self._h = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def pipeline_create(model: Model, depth: int = 2) -> Pipeline:
+    return Pipeline(model, depth)

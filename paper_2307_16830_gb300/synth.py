@@ -391,3 +391,48 @@ def batch_workload(n_scenarios: int = 128, n_mixed: int = 128, seed: int = 1003,
     sizes = log_uniform_sizes(rng, n_mixed, mixed_lo, mixed_hi)
     mixed = [grid_for_size(int(nb), seed + 10 + k) for k, nb in enumerate(sizes)]
     return base, scenarios, mixed
+
+
+def make_iterate(xl, xu, gl, gu, seed: int, *, z_range=(-4.0, 2.0), gap_floor=0.0):
+    """Interior iterate of the barrier problem with the right-hand sides of
+    its Newton system (random data, the model's bounds given): slack bounds
+    sl = gl - r, su = gu + r with r ~ U(1e-4, 1e-2) (the solver's relaxation
+    of the constraint bounds, so every equality row has an interior), x and s
+    strictly inside their bounds (free components ~ N(0, 1), one-sided ones
+    at 10^U(-3, 1) from the bound, boxed ones at U(0.01, 0.99) of the box,
+    at least gap_floor from each bound), bound duals 10^U(z_range) at finite
+    bounds and 0 at infinite ones, right-hand sides ~ N(0, 1) (0 for absent
+    bounds).  Returns a dict keyed like the oracle's Iterate."""
+    rng = np.random.default_rng(seed)
+    xl, xu, gl, gu = (np.asarray(a, dtype=np.float64) for a in (xl, xu, gl, gu))
+    m = gl.shape[0]
+    sl = np.where(np.isfinite(gl), gl - rng.uniform(1e-4, 1e-2, m), -np.inf)
+    su = np.where(np.isfinite(gu), gu + rng.uniform(1e-4, 1e-2, m), np.inf)
+
+    def inside(lo, hi):
+        k = lo.shape[0]
+        v = rng.standard_normal(k)
+        lf, hf = np.isfinite(lo), np.isfinite(hi)
+        off = 10.0 ** rng.uniform(-3.0, 1.0, k) + gap_floor
+        t = rng.uniform(0.01, 0.99, k)
+        both = lf & hf
+        lo0, hi0 = np.where(lf, lo, 0.0), np.where(hf, hi, 0.0)
+        v = np.where(lf & ~hf, lo0 + off, v)
+        v = np.where(hf & ~lf, hi0 - off, v)
+        v = np.where(both, lo0 + t * (hi0 - lo0), v)
+        return v
+
+    def duals(b):
+        return np.where(np.isfinite(b), 10.0 ** rng.uniform(*z_range, b.shape[0]), 0.0)
+
+    def rhs(b):
+        return np.where(np.isfinite(b), rng.standard_normal(b.shape[0]), 0.0)
+
+    x = inside(xl, xu)
+    s = inside(sl, su)
+    n = xl.shape[0]
+    return dict(x=x, s=s, xl=xl, xu=xu, sl=sl, su=su,
+                zl_x=duals(xl), zu_x=duals(xu), zl_s=duals(sl), zu_s=duals(su),
+                p_x=rng.standard_normal(n), p_s=rng.standard_normal(m),
+                p_y=rng.standard_normal(m), p_zl_x=rhs(xl), p_zu_x=rhs(xu),
+                p_zl_s=rhs(sl), p_zu_s=rhs(su))

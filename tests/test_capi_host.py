@@ -200,3 +200,11 @@ def test_arc_rows_tile_contiguous_ranges(k):
             i = bus_of_arc[a]
             assert ln[P + a] == 5 + gens[i] + rank[a], (a, ln[P + a])
             assert ln[Q + a] == 6 + gens[i] + rank[a], (a, ln[Q + a])
+
+
+def test_pipeline_create_rejects_without_device_work():
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, device=-1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.pipeline_create(m, 2)
+        assert ei.value.status == acopf.E_NO_DEVICE

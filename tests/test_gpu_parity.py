@@ -198,3 +198,32 @@ def test_fused_at_wide_angles(dev, acopf, spread):
         got = gu.run_fused(torch, acopf, m, pt, dev)
         gu.assert_parity(got, gu.oracle_all(g, pt), label=f"spread {spread}")
 
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_pipeline_matches_single_calls(dev, acopf, depth):
+    """Pipelined host-buffer calls (copies and kernels of consecutive calls
+    overlapping) give each call's single-call results bit for bit."""
+    g = synth.make_grid(517, 777, 61, seed=3)
+    with acopf.model_create(g, 0) as m:
+        pts = [synth.make_point(g, 40 + k, obj_weight=0.9 + 0.05 * k,
+                                delta_w=0.02 if k == 3 else 0.0) for k in range(5)]
+        ref = [gu.run_fused(torch, acopf, m, pt, dev) for pt in pts]
+        outs = []
+        with acopf.pipeline_create(m, depth) as p:
+            for pt in pts:
+                o = {k: np.full(n, np.nan) for k, n in (("f", 1), ("grad", m.n), ("cons", m.m),
+                                                         ("jac", m.nnz_jac), ("hess", m.nnz_hess),
+                                                         ("kkt", m.nnz_kkt))}
+                p.submit(pt.x, pt.y, pt.obj_weight, pt.sigma_x, pt.sigma_s, pt.delta_w,
+                         pt.delta_c, o["f"], o["grad"], o["cons"], o["jac"], o["hess"], o["kkt"])
+                outs.append(o)
+            p.wait()
+        for k in range(len(pts)):
+            for key in gu.KEYS:
+                assert np.array_equal(outs[k][key].view(np.uint64), ref[k][key].view(np.uint64)), \
+                    (k, key)
+        for bad in (1, 9):
+            with pytest.raises(acopf.AcopfError) as e:
+                acopf.pipeline_create(m, bad)
+            assert e.value.status == acopf.E_INVALID_ARG
