@@ -397,6 +397,87 @@ def run_small_workloads(local):
     return out
 
 
+def run_step_bench(args, local):
+    """Condensation around M_cond (acopf_condense: Sigma_x, Sigma_s, q_s and
+    the condensed right-hand side) and step recovery (acopf_recover_step) on
+    the 80,000-bus workload, each timed over calls rotating between 2
+    iterates (2 x 160 MB of inputs > L2), against the HBM floor of their
+    algorithmic bytes (inputs read once, outputs written once; the Jacobian's
+    row and column lists and the row scratch excluded, as index metadata)."""
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    grid = synth.workload_grid("80kbus")
+    model = acopf.model_create(grid, local)
+    n, m, nj = model.n, model.m, model.nnz_jac
+
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    pt = synth.make_point(grid, 11)
+    jv = torch.empty(nj, dtype=torch.float64, device=dev)
+    acopf.eval_jac_coo(model, t(pt.x), jv, stream=stream)
+    xl, xu, gl, gu = model.bounds()
+    sets = []
+    for r in range(2):
+        it = {k: t(v) for k, v in synth.make_iterate(xl, xu, gl, gu, 400 + r).items()}
+        e = lambda k: torch.empty(k, dtype=torch.float64, device=dev)  # noqa: E731
+        sets.append(dict(it=it, dx=t(np.random.default_rng(500 + r).standard_normal(n)),
+                         sx=e(n), ss=e(m), qs=e(m), rhs=e(n), ds=e(m), dy=e(m), zlx=e(n),
+                         zux=e(n), zls=e(m), zus=e(m)))
+
+    def condense(k):
+        b = sets[k % 2]
+        acopf.condense(model, b["it"], jv, 0.0, 0.0, b["sx"], b["ss"], b["qs"], b["rhs"],
+                       stream=stream)
+
+    def recover(k):
+        b = sets[k % 2]
+        acopf.recover_step(model, b["it"], jv, 0.0, 0.0, b["ss"], b["qs"], b["dx"], b["ds"],
+                           b["dy"], b["zlx"], b["zux"], b["zls"], b["zus"], stream=stream)
+
+    def timed(fn, reps=200):
+        with torch.cuda.stream(stream):
+            for k in range(10):
+                fn(k)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(reps):
+                fn(k)
+            e1.record(stream)
+            stream.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        condense(0)
+        recover(0)
+    c_us = timed(condense)
+    r_us = timed(recover)
+    hbm = 6772.9
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    c_bytes = 8 * (10 * n + 11 * m + nj)
+    r_bytes = 8 * (10 * n + 14 * m + nj)
+    model.close()
+    return {
+        "workload": "80kbus: condensation (Sigma_x, Sigma_s, q_s, rhs = q_x + A'(C q_s + D q_y)) "
+                    "and step recovery (ds, dy, 4 bound-dual steps) at an interior iterate",
+        "condense_us": c_us, "condense_bytes": c_bytes,
+        "condense_gbs": c_bytes / (c_us * 1e-6) / 1e9,
+        "condense_frac_hbm": c_bytes / (c_us * 1e-6) / 1e9 / hbm,
+        "recover_us": r_us, "recover_bytes": r_bytes,
+        "recover_gbs": r_bytes / (r_us * 1e-6) / 1e9,
+        "recover_frac_hbm": r_bytes / (r_us * 1e-6) / 1e9 / hbm,
+        "launches": {"condense": 2, "recover": 1},
+    }
+
+
 def _pinned(torch, a):
     """Page-locked host copy of a numpy array (numpy view, torch owner)."""
     t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -645,6 +726,8 @@ def main():
                     help="also time the calls replayed from a CUDA graph of 100 calls")
     ap.add_argument("--small-workloads", type=int, default=1, choices=[0, 1],
                     help="also time the 30-bus and 10,000-bus workloads (plain and graph)")
+    ap.add_argument("--step", type=int, default=1, choices=[0, 1],
+                    help="also time the condensation and step recovery (80k workload)")
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)
@@ -663,6 +746,7 @@ def main():
         return
     r = run_ours(args, rank, world, local)
     small = run_small_workloads(local) if args.small_workloads and world == 1 else None
+    step = run_step_bench(args, local) if args.step and world == 1 else None
     batch = run_batch_bench(args, local) if args.batch and world == 1 else None
     serve = run_serve_bench(args, local) if args.serve and world == 1 else None
     if rank != 0:
@@ -738,7 +822,7 @@ def main():
         "graph": None if r["graph_ms"] is None else {
             "ms_per_call": r["graph_ms"], "calls_per_s": 1e3 / r["graph_ms"],
             "note": f"{GRAPH_CALLS} calls per CUDA graph, {args.graph_replays} replays"},
-        "small_workloads": small,
+        "small_workloads": small, "step": step,
         "gpu": r["gpu"], "batch": batch, "serve": serve,
     }
     print(json.dumps(line), flush=True)

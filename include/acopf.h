@@ -204,6 +204,57 @@ acopf_status acopf_eval_assemble_host(acopf_model* model, const double* x, const
                                       double* f, double* grad, double* cons, double* jvals,
                                       double* hvals, double* kvals, acopf_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Condensation around M_cond and step recovery (Sec. IV.C).
+ *
+ * The Newton system of the barrier problem (Sec. IV.B-C: unknowns dx, ds,
+ * dy and the bound-dual steps dzl_x, dzu_x, dzl_s, dzu_s; right-hand sides
+ * p_x, p_s, p_y, p_zl_x, p_zu_x, p_zl_s, p_zu_s) reduces to M_cond dx = rhs.
+ * acopf_condense computes, at an interior iterate (x strictly inside
+ * [xl, xu], slacks s strictly inside [sl, su]):
+ *   Sigma_x = Zl_x (X - Xl)^-1 + Zu_x (Xu - X)^-1            (n)
+ *   Sigma_s = Zl_s (S - Sl)^-1 + Zu_s (Su - S)^-1            (m)
+ *   q_s     = p_s + (S - Sl)^-1 p_zl_s - (Su - S)^-1 p_zu_s  (m)
+ *   rhs     = q_x + A' (C q_s + D q_y),  q_x = p_x + (X - Xl)^-1 p_zl_x - (Xu - X)^-1 p_zu_x,
+ *             q_y = p_y, C = (delta_c Sigma_s + (1 + delta_c delta_w) I)^-1,
+ *             D = (Sigma_s + delta_w I) C                    (n)
+ * Sigma_x and Sigma_s are the diagonals acopf_eval_assemble takes.
+ * acopf_recover_step computes, from a solution dx of M_cond dx = rhs,
+ *   ds = C (A dx + delta_c q_s - q_y),  dy = (Sigma_s + delta_w I) ds - q_s,
+ *   dzl_x = (X - Xl)^-1 (p_zl_x - Zl_x dx),  dzu_x = (Xu - X)^-1 (p_zu_x + Zu_x dx),
+ *   dzl_s = (S - Sl)^-1 (p_zl_s - Zl_s ds),  dzu_s = (Su - S)^-1 (p_zu_s + Zu_s ds).
+ * (Sec. IV.C prints ds = C (delta_c q_s - (q_y + A dx)); the sign of A dx
+ * here is the one that solves the printed augmented system.)  A bound at
+ * +-inf has no dual and no barrier term: its inverse gap is taken as zero
+ * (pass zero duals and right-hand sides there).  A is the Jacobian at the
+ * iterate, values in acopf_jac_structure's order.  All arrays are DEVICE
+ * memory owned by the caller; calls are asynchronous on `stream` and
+ * deterministic (fixed summation order).  The first call on a model
+ * allocates the Jacobian's row and column lists and a row scratch (about
+ * 16 bytes per Jacobian entry) and synchronises; make it before any stream
+ * capture.  The row scratch is the model's, so these calls on one model must
+ * not overlap on the GPU.  acopf_condense is two kernel launches,
+ * acopf_recover_step one. */
+typedef struct {
+  const double *x, *s;           /* n, m */
+  const double *xl, *xu;         /* n: variable bounds (+-inf allowed) */
+  const double *sl, *su;         /* m: slack bounds (+-inf allowed) */
+  const double *zl_x, *zu_x;     /* n: bound duals */
+  const double *zl_s, *zu_s;     /* m */
+  const double *p_x, *p_s, *p_y; /* n, m, m: right-hand sides */
+  const double *p_zl_x, *p_zu_x; /* n */
+  const double *p_zl_s, *p_zu_s; /* m */
+} acopf_iterate;
+
+acopf_status acopf_condense(acopf_model* model, const acopf_iterate* it, const double* jvals,
+                            double delta_w, double delta_c, double* sigma_x, double* sigma_s,
+                            double* q_s, double* rhs, acopf_stream stream);
+acopf_status acopf_recover_step(acopf_model* model, const acopf_iterate* it, const double* jvals,
+                                double delta_w, double delta_c, const double* sigma_s,
+                                const double* q_s, const double* dx, double* ds, double* dy,
+                                double* dzl_x, double* dzu_x, double* dzl_s, double* dzu_s,
+                                acopf_stream stream);
+
 /* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of
  * one model with HOST inputs and outputs, whose host-to-device copies,
  * kernels and device-to-host copies overlap (three streams, `depth` device

@@ -157,6 +157,20 @@ _pipeline_submit = _sig("acopf_pipeline_submit", C.c_int32, _vp, _vp, _vp, C.c_d
                         C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp)
 _pipeline_wait = _sig("acopf_pipeline_wait", C.c_int32, _vp)
 
+ITERATE_FIELDS = ("x", "s", "xl", "xu", "sl", "su", "zl_x", "zu_x", "zl_s", "zu_s", "p_x", "p_s",
+                  "p_y", "p_zl_x", "p_zu_x", "p_zl_s", "p_zu_s")
+
+
+class Iterate(C.Structure):
+    """An interior iterate and its Newton right-hand sides (device addresses)."""
+    _fields_ = [(k, _vp) for k in ITERATE_FIELDS]
+
+
+_condense = _sig("acopf_condense", C.c_int32, _vp, C.POINTER(Iterate), _vp, C.c_double,
+                 C.c_double, _vp, _vp, _vp, _vp, _vp)
+_recover_step = _sig("acopf_recover_step", C.c_int32, _vp, C.POINTER(Iterate), _vp, C.c_double,
+                     C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -173,7 +187,7 @@ EXPORTED = [
     "acopf_server_poll", "acopf_server_wait", "acopf_server_request_times",
     "acopf_server_release", "acopf_server_get_stats", "acopf_server_set_option",
     "acopf_pipeline_create", "acopf_pipeline_destroy", "acopf_pipeline_submit",
-    "acopf_pipeline_wait",
+    "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step",
 ]
 
 
@@ -649,3 +663,29 @@ class Pipeline:
 
 def pipeline_create(model: Model, depth: int = 2) -> Pipeline:
     return Pipeline(model, depth)
+
+
+def _iterate(it) -> Iterate:
+    """it: mapping (or object) with the ITERATE_FIELDS as tensors / addresses."""
+    get = it.get if isinstance(it, dict) else (lambda k: getattr(it, k))
+    r = Iterate()
+    for k in ITERATE_FIELDS:
+        setattr(r, k, _ptr(get(k)))
+    return r
+
+
+def condense(model: Model, it, jvals, delta_w: float, delta_c: float, sigma_x, sigma_s, q_s,
+             rhs, stream=None) -> None:
+    r = _iterate(it)
+    _check(_condense(model.handle, C.byref(r), _ptr(jvals), float(delta_w), float(delta_c),
+                     _ptr(sigma_x), _ptr(sigma_s), _ptr(q_s), _ptr(rhs), _stream(stream)),
+           "acopf_condense")
+
+
+def recover_step(model: Model, it, jvals, delta_w: float, delta_c: float, sigma_s, q_s, dx, ds,
+                 dy, dzl_x, dzu_x, dzl_s, dzu_s, stream=None) -> None:
+    r = _iterate(it)
+    _check(_recover_step(model.handle, C.byref(r), _ptr(jvals), float(delta_w), float(delta_c),
+                         _ptr(sigma_s), _ptr(q_s), _ptr(dx), _ptr(ds), _ptr(dy), _ptr(dzl_x),
+                         _ptr(dzu_x), _ptr(dzl_s), _ptr(dzu_s), _stream(stream)),
+           "acopf_recover_step")

@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libacopf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "kernels.cu",
-           "noalloc.cu"]
+SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "stepapi.cpp",
+           "kernels.cu", "step.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

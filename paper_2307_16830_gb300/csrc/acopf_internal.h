@@ -164,6 +164,36 @@ struct EvalArgs {
   double* kvals;
 };
 
+// Condensation around M_cond and step recovery (step.cu): device views.
+// The Jacobian's COO entries by row (jr_*) and by column (jt_*), each list in
+// ascending slot order; `w` is the per-row scratch C q_s + D q_y.
+struct DevStep {
+  int32_t n, m;
+  const int32_t* jr_ptr;   // m + 1
+  const int32_t* jr_slot;  // nnzj
+  const int32_t* jr_col;   // nnzj
+  const int32_t* jt_ptr;   // n + 1
+  const int32_t* jt_slot;  // nnzj
+  const int32_t* jt_row;   // nnzj
+  double* w;               // m
+};
+
+// An interior iterate and the right-hand sides of its Newton system (device).
+struct StepIterate {
+  const double *x, *s, *xl, *xu, *sl, *su;
+  const double *zl_x, *zu_x, *zl_s, *zu_s;
+  const double *p_x, *p_s, *p_y, *p_zl_x, *p_zu_x, *p_zl_s, *p_zu_s;
+};
+
+cudaError_t launch_condense(const DevStep& st, const StepIterate& it, const double* jvals,
+                            double delta_w, double delta_c, double* sigma_x, double* sigma_s,
+                            double* q_s, double* rhs, bool pdl, cudaStream_t s);
+cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const double* jvals,
+                           double delta_w, double delta_c, const double* sigma_s,
+                           const double* q_s, const double* dx, double* ds, double* dy,
+                           double* dzl_x, double* dzu_x, double* dzl_s, double* dzu_s,
+                           cudaStream_t s);
+
 // Launchers (kernels.cu).  Each returns the CUDA error of its launches.
 // `mid`, when not null, is recorded between the two phases (phase 2 then
 // launches without programmatic dependent launch).

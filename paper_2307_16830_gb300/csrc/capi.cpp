@@ -245,6 +245,7 @@ acopf_status acopf_model_destroy(acopf_model* model) {
   if (model->device >= 0) {
     DeviceScope ds(model->device);
     destroy_profile_events(model);
+    acopf::free_step(model);
     if (model->arena) cudaFree(model->arena);
     if (model->stage) cudaFree(model->stage);
   }

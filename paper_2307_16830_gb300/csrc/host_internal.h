@@ -22,6 +22,10 @@ struct acopf_model {
   std::vector<cudaEvent_t> prof_events;  // 3 per profiled call
   int32_t prof_capacity = 0;
   int32_t prof_calls = 0;
+  // condensation / step recovery: Jacobian by rows and by columns, row
+  // scratch (allocated by the first acopf_condense / acopf_recover_step)
+  void* step_arena = nullptr;
+  acopf::DevStep step{};
 };
 
 namespace acopf {
@@ -100,6 +104,9 @@ inline size_t model_device_bytes(const acopf_model* m) { return m->arena_bytes; 
 // Phase-1 and phase-2 work items of one fused evaluation of `L` (instance
 // index `inst`), in the block order of the single-instance launch.
 void append_items(const Layout& L, int32_t inst, std::vector<int4>& p1, std::vector<int4>& p2);
+
+// Frees the model's condensation arena (stepapi.cpp).
+void free_step(acopf_model* m);
 
 // Validates the scalar arguments of an evaluation.
 acopf_status check_eval_scalars(double obj_weight, double delta_w, double delta_c);

@@ -1,0 +1,169 @@
+// Condensation around M_cond and step recovery (Sec. IV.C), sm_103a, FP64.
+//
+// Elementwise work per variable and per constraint row, plus the two
+// sparse products with the Jacobian the path needs: A' w for the condensed
+// right-hand side (gathered per variable over its Jacobian entries) and A dx
+// for the slack step (gathered per row).  Every sum runs in a fixed order
+// (ascending Jacobian slot), so results do not depend on scheduling.  A
+// bound at +-inf contributes nothing: its inverse gap is taken as zero.
+#include <cuda_runtime.h>
+
+#include "acopf_internal.h"
+
+namespace acopf {
+namespace {
+
+constexpr int kStepThreads = 256;
+
+__device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
+
+// (v - lo)^-1 and (hi - v)^-1 (correctly rounded reciprocals), zero at an
+// infinite bound.
+__device__ __forceinline__ void inv_gaps(double v, double lo, double hi, double& il,
+                                         double& iu) {
+  il = isinf(lo) ? 0.0 : __drcp_rn(v - lo);
+  iu = isinf(hi) ? 0.0 : __drcp_rn(hi - v);
+}
+
+// Rows: Sigma_s, q_s and w = C q_s + D q_y, with C = (dc Sigma_s + 1 + dc dw)^-1
+// and D = (Sigma_s + dw) C (C = 1, D = Sigma_s without regularisation).
+template <bool REG>
+__global__ void __launch_bounds__(kStepThreads) k_condense_rows(DevStep st, StepIterate it,
+                                                                double dw, double dc,
+                                                                double* __restrict__ sigma_s,
+                                                                double* __restrict__ q_s) {
+  const int r = blockIdx.x * kStepThreads + threadIdx.x;
+  if (r < st.m) {
+    double il, iu;
+    inv_gaps(ldg(it.s + r), ldg(it.sl + r), ldg(it.su + r), il, iu);
+    const double sig = fma(ldg(it.zl_s + r), il, ldg(it.zu_s + r) * iu);
+    const double q = fma(il, ldg(it.p_zl_s + r), fma(-iu, ldg(it.p_zu_s + r), ldg(it.p_s + r)));
+    const double py = ldg(it.p_y + r);
+    double w;
+    if constexpr (REG) {
+      const double C = __drcp_rn(fma(dc, sig, fma(dc, dw, 1.0)));
+      w = C * fma(sig + dw, py, q);  // C q_s + D q_y with D = (Sigma_s + dw) C
+    } else {
+      w = fma(sig, py, q);
+    }
+    sigma_s[r] = sig;
+    q_s[r] = q;
+    st.w[r] = w;
+  }
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Columns: Sigma_x, q_x and rhs = q_x + A' w (w from the row kernel).
+__global__ void __launch_bounds__(kStepThreads) k_condense_cols(DevStep st, StepIterate it,
+                                                               const double* __restrict__ J,
+                                                               double* __restrict__ sigma_x,
+                                                               double* __restrict__ rhs) {
+  const int j = blockIdx.x * kStepThreads + threadIdx.x;
+  double q = 0.0;
+  int k0 = 0, k1 = 0;
+  if (j < st.n) {  // independent of the row kernel: before the grid dependency
+    double il, iu;
+    inv_gaps(ldg(it.x + j), ldg(it.xl + j), ldg(it.xu + j), il, iu);
+    sigma_x[j] = fma(ldg(it.zl_x + j), il, ldg(it.zu_x + j) * iu);
+    q = fma(il, ldg(it.p_zl_x + j), fma(-iu, ldg(it.p_zu_x + j), ldg(it.p_x + j)));
+    k0 = __ldg(st.jt_ptr + j);
+    k1 = __ldg(st.jt_ptr + j + 1);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (j >= st.n) return;
+  double acc = 0.0;
+  for (int k = k0; k < k1; ++k)
+    acc = fma(ldg(J + __ldg(st.jt_slot + k)), __ldcg(st.w + __ldg(st.jt_row + k)), acc);
+  rhs[j] = q + acc;
+}
+
+// Recovery.  Blocks [0, nrb) take rows: A dx, ds = C (A dx + dc q_s - q_y),
+// dy = (Sigma_s + dw) ds - q_s, dzl_s, dzu_s; the rest take columns: dzl_x, dzu_x.
+template <bool REG>
+__global__ void __launch_bounds__(kStepThreads) k_recover(
+    DevStep st, StepIterate it, const double* __restrict__ J, double dw, double dc,
+    const double* __restrict__ sigma_s, const double* __restrict__ q_s,
+    const double* __restrict__ dx, double* __restrict__ ds_out, double* __restrict__ dy_out,
+    double* __restrict__ dzl_x, double* __restrict__ dzu_x, double* __restrict__ dzl_s,
+    double* __restrict__ dzu_s, int nrb) {
+  if (static_cast<int>(blockIdx.x) < nrb) {
+    const int r = blockIdx.x * kStepThreads + threadIdx.x;
+    if (r >= st.m) return;
+    const int k0 = __ldg(st.jr_ptr + r), k1 = __ldg(st.jr_ptr + r + 1);
+    double adx = 0.0;
+    for (int k = k0; k < k1; ++k)
+      adx = fma(ldg(J + __ldg(st.jr_slot + k)), ldg(dx + __ldg(st.jr_col + k)), adx);
+    const double sig = ldg(sigma_s + r), q = ldg(q_s + r), py = ldg(it.p_y + r);
+    double ds;
+    if constexpr (REG) {
+      const double C = __drcp_rn(fma(dc, sig, fma(dc, dw, 1.0)));
+      ds = C * (fma(dc, q, adx) - py);
+    } else {
+      ds = adx - py;
+    }
+    ds_out[r] = ds;
+    dy_out[r] = fma(sig + dw, ds, -q);
+    double il, iu;
+    inv_gaps(ldg(it.s + r), ldg(it.sl + r), ldg(it.su + r), il, iu);
+    dzl_s[r] = il * fma(-ldg(it.zl_s + r), ds, ldg(it.p_zl_s + r));
+    dzu_s[r] = iu * fma(ldg(it.zu_s + r), ds, ldg(it.p_zu_s + r));
+  } else {
+    const int j = (blockIdx.x - nrb) * kStepThreads + threadIdx.x;
+    if (j >= st.n) return;
+    const double d = ldg(dx + j);
+    double il, iu;
+    inv_gaps(ldg(it.x + j), ldg(it.xl + j), ldg(it.xu + j), il, iu);
+    dzl_x[j] = il * fma(-ldg(it.zl_x + j), d, ldg(it.p_zl_x + j));
+    dzu_x[j] = iu * fma(ldg(it.zu_x + j), d, ldg(it.p_zu_x + j));
+  }
+}
+
+int blocks_for(int count) { return (count + kStepThreads - 1) / kStepThreads; }
+
+}  // namespace
+
+cudaError_t launch_condense(const DevStep& st, const StepIterate& it, const double* jvals,
+                            double delta_w, double delta_c, double* sigma_x, double* sigma_s,
+                            double* q_s, double* rhs, bool pdl, cudaStream_t s) {
+  const bool reg = delta_w != 0.0 || delta_c != 0.0;
+  const int rb = blocks_for(st.m), cb = blocks_for(st.n);
+  if (rb > 0) {
+    if (reg)
+      k_condense_rows<true><<<rb, kStepThreads, 0, s>>>(st, it, delta_w, delta_c, sigma_s, q_s);
+    else
+      k_condense_rows<false><<<rb, kStepThreads, 0, s>>>(st, it, delta_w, delta_c, sigma_s, q_s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (cb == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cb);
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (pdl && rb > 0) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_condense_cols, st, it, jvals, sigma_x, rhs);
+}
+
+cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const double* jvals,
+                           double delta_w, double delta_c, const double* sigma_s,
+                           const double* q_s, const double* dx, double* ds, double* dy,
+                           double* dzl_x, double* dzu_x, double* dzl_s, double* dzu_s,
+                           cudaStream_t s) {
+  const int rb = blocks_for(st.m), cb = blocks_for(st.n);
+  if (rb + cb == 0) return cudaSuccess;
+  if (delta_w != 0.0 || delta_c != 0.0)
+    k_recover<true><<<rb + cb, kStepThreads, 0, s>>>(st, it, jvals, delta_w, delta_c, sigma_s,
+                                                     q_s, dx, ds, dy, dzl_x, dzu_x, dzl_s,
+                                                     dzu_s, rb);
+  else
+    k_recover<false><<<rb + cb, kStepThreads, 0, s>>>(st, it, jvals, delta_w, delta_c, sigma_s,
+                                                      q_s, dx, ds, dy, dzl_x, dzu_x, dzl_s,
+                                                      dzu_s, rb);
+  return cudaGetLastError();
+}
+
+}  // namespace acopf
