@@ -17,12 +17,32 @@ constexpr int kStepThreads = 256;
 
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 
-// (v - lo)^-1 and (hi - v)^-1 (correctly rounded reciprocals), zero at an
-// infinite bound.
+// Tests on the bit pattern (integer pipe; the FP64 pipe is the scarce one):
+// a finite value, and |v| in [2^-500, 2^500).
+__device__ __forceinline__ bool is_finite_bits(double v) {
+  return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool mid_range(double v) {
+  const unsigned e = static_cast<unsigned>(__double_as_longlong(v) >> 52) & 0x7ffu;
+  return e - 523u < 1000u;
+}
+
+// (v - lo)^-1 and (hi - v)^-1, zero at an infinite bound.  With both bounds
+// finite one reciprocal serves both: with a = v - lo, b = hi - v,
+// 1/a = b (ab)^-1 and 1/b = a (ab)^-1 (a few ulps), when a and b are in a
+// range where ab cannot overflow or underflow.
 __device__ __forceinline__ void inv_gaps(double v, double lo, double hi, double& il,
                                          double& iu) {
-  il = isinf(lo) ? 0.0 : __drcp_rn(v - lo);
-  iu = isinf(hi) ? 0.0 : __drcp_rn(hi - v);
+  const bool fl = is_finite_bits(lo), fh = is_finite_bits(hi);
+  const double a = v - lo, b = hi - v;
+  if (fl && fh && mid_range(a) && mid_range(b)) {
+    const double r = __drcp_rn(a * b);
+    il = b * r;
+    iu = a * r;
+    return;
+  }
+  il = fl ? __drcp_rn(a) : 0.0;
+  iu = fh ? __drcp_rn(b) : 0.0;
 }
 
 // Rows: Sigma_s, q_s and w = C q_s + D q_y, with C = (dc Sigma_s + 1 + dc dw)^-1
