@@ -149,6 +149,17 @@ def workload_sizes(model, grid):
                 nnzh=model.nnz_hess, nnzk=model.nnz_kkt)
 
 
+def workload_config(args, s, world):
+    """The `config` object of both arms (sizes from the model or the oracle)."""
+    return {"workload": f"{args.workload}: synthetic grid, {s['nb']} buses, {s['nl']} "
+                        f"branches, {s['ng']} generators; one call = obj+grad+cons+jac+"
+                        f"hess+condensed KKT at a fresh point",
+            "n": s["n"], "m": s["m"], "nnz_jac": s["nnzj"], "nnz_hess": s["nnzh"],
+            "nnz_kkt": s["nnzk"], "parallelism": f"replicas x{world}",
+            "l2": f"inputs/outputs rotate over {ROTATE} sets of "
+                  f"{algorithmic_bytes(s) / 1e6:.0f} MB (> 129 MB L2 together)"}
+
+
 def algorithmic_bytes(s):
     """Compulsory bytes of one call: inputs read once, model data read once,
     outputs written once (index metadata excluded)."""
@@ -691,6 +702,10 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     ratio = t_s / t_full
     value = args.steps / dt * ratio
+    L = oracle.layout(full)
+    sizes = dict(nb=full.n_bus, nl=full.n_branch, ng=full.n_gen, n=L.n, m=L.m,
+                 nnzj=len(oracle.jac_structure(full)[0]), nnzh=len(oracle.hess_structure(full)[0]),
+                 nnzk=int(st_full[0][-1]))
     sample_desc = (f"{args.steps} oracle calls on the 10,000-bus grid, converted to 80,000-bus "
                    f"calls by the measured per-call time ratio {ratio:.4f} "
                    f"(one 80k call {t_full:.2f} s)")
@@ -698,10 +713,9 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: 80,000 buses, 110,000 branches, 12,000 gens",
-                       "oracle": "numpy/scipy FP64, 1 thread"},
+            "config": workload_config(args, sizes, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample_desc},
+                             "sample": sample_desc + "; numpy/scipy FP64, 1 thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -806,13 +820,7 @@ def main():
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: synthetic grid, {s['nb']} buses, {s['nl']} "
-                               f"branches, {s['ng']} generators; one call = obj+grad+cons+jac+"
-                               f"hess+condensed KKT at a fresh point",
-                   "n": s["n"], "m": s["m"], "nnz_jac": s["nnzj"], "nnz_hess": s["nnzh"],
-                   "nnz_kkt": s["nnzk"], "parallelism": f"replicas x{world}",
-                   "l2": f"inputs/outputs rotate over {ROTATE} sets of "
-                         f"{call_bytes / 1e6:.0f} MB (> 129 MB L2 together)"},
+        "config": workload_config(args, s, world),
         "hbm_roofline_call": {"algorithmic_bytes": call_bytes,
                               "achieved_gbs": call_bytes / (r["ms"] / args.steps * 1e-3) / 1e9,
                               "frac": call_bytes / (r["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak},
