@@ -36,7 +36,8 @@ import numpy as np
 
 from .acopf import _jac_matrix, condensation_diag
 
-__all__ = ["Iterate", "inv_gap", "condense", "recover"]
+__all__ = ["Iterate", "inv_gap", "condense", "recover", "kkt_parts", "kkt_residual",
+           "residual_scaling", "S_MAX"]
 
 
 @dataclasses.dataclass
@@ -143,3 +144,61 @@ def recover(grid, jvals, it: Iterate, dx, delta_w=0.0, delta_c=0.0, jmag=None):
         mag = np.abs(inv) * (np.abs(p) + np.abs(z) * dm)
         out[name] = (val, mag)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Scaled residual of the first-order conditions (the termination test of
+# Algorithm 1; Sec. IV calls it a scaled version of the residual of Eq. first
+# and refers to Waechter and Biegler 2006 for the details).  Reading: the
+# scaling of that reference, eq. (5), with s_max = 100:
+#   E = max(||r_d||_inf / s_d, ||r_p||_inf, ||r_c||_inf / s_c),
+#   s_d = max(s_max, (||y||_1 + ||z||_1) / (m + n_z)) / s_max,
+#   s_c = max(s_max, ||z||_1 / n_z) / s_max,
+# over the conditions of Eq. first:
+#   r_d = [grad f - A'y - zl_x + zu_x ; y - zl_s + zu_s]   (n + m)
+#   r_p = g(x) - s                                         (m)
+#   r_c = [Zl_x (x - xl) - mu ; Zu_x (xu - x) - mu ; Zl_s (s - sl) - mu ; Zu_s (su - s) - mu]
+# with only the finite bounds carrying a dual (n_z of them).
+# ---------------------------------------------------------------------------
+S_MAX = 100.0
+
+
+def residual_scaling(y_l1, z_l1, m, n_z):
+    """(s_d, s_c) of the scaled residual."""
+    s_d = max(S_MAX, (y_l1 + z_l1) / (m + n_z)) / S_MAX
+    s_c = max(S_MAX, z_l1 / n_z) / S_MAX if n_z else 1.0
+    return s_d, s_c
+
+
+def kkt_parts(grid, grad, cons, jvals, it: Iterate, y, mu):
+    """The residual vectors: (r_d_x, r_d_s, r_p, r_c, z of the finite bounds)."""
+    grad, cons, y = (np.asarray(a, dtype=np.float64) for a in (grad, cons, y))
+    A = _jac_matrix(grid, np.asarray(jvals, dtype=np.float64))
+    rdx = grad - A.T @ y - it.zl_x + it.zu_x
+    rds = y - it.zl_s + it.zu_s
+    rp = cons - it.s
+    parts = []
+    zs = []
+    for v, b, z, sign in ((it.x, it.xl, it.zl_x, 1.0), (it.x, it.xu, it.zu_x, -1.0),
+                          (it.s, it.sl, it.zl_s, 1.0), (it.s, it.su, it.zu_s, -1.0)):
+        f = np.isfinite(b)
+        parts.append(z[f] * (sign * (v[f] - b[f])) - mu)
+        zs.append(z[f])
+    return rdx, rds, rp, np.concatenate(parts), np.concatenate(zs)
+
+
+def kkt_residual(grid, grad, cons, jvals, it: Iterate, y, mu):
+    """The parts of the scaled residual: dict with dual_inf, primal_inf,
+    compl_inf, y_l1, z_l1, n_z, s_d, s_c, residual."""
+    y = np.asarray(y, dtype=np.float64)
+    rdx, rds, rp, rc, zall = kkt_parts(grid, grad, cons, jvals, it, y, mu)
+    n_z = zall.size
+    m = y.size
+    y_l1, z_l1 = float(np.sum(np.abs(y))), float(np.sum(np.abs(zall)))
+    s_d, s_c = residual_scaling(y_l1, z_l1, m, n_z)
+    dual_inf = float(max(np.max(np.abs(rdx)), np.max(np.abs(rds))))
+    primal_inf = float(np.max(np.abs(rp)))
+    compl_inf = float(np.max(np.abs(rc))) if n_z else 0.0
+    return {"dual_inf": dual_inf, "primal_inf": primal_inf, "compl_inf": compl_inf,
+            "y_l1": y_l1, "z_l1": z_l1, "n_z": n_z, "s_d": s_d, "s_c": s_c,
+            "residual": max(dual_inf / s_d, primal_inf, compl_inf / s_c)}

@@ -172,3 +172,45 @@ def test_pin_catches_planted_mistakes(monkeypatch):
     monkeypatch.setattr(oracle, "recover", bad_recover)
     with pytest.raises(AssertionError):
         test_condensed_route_solves_the_printed_newton_system(0.3, 0.0)
+
+
+def test_dual_residual_is_the_gradient_of_the_lagrangian():
+    """r_d = [grad f - A'y - zl_x + zu_x ; y - zl_s + zu_s] is the gradient in
+    (x, s) of L = f(x) - y'(g(x) - s) - zl_x'(x - xl) - zu_x'(xu - x)
+    - zl_s'(s - sl) - zu_s'(su - s) (finite bounds only), checked by central
+    differences of L built from the objective and constraint values alone."""
+    g = synth.workload_grid("30bus")
+    L = oracle.layout(g)
+    xl, xu, gl, gu = oracle.bounds(g)
+    it = oracle.Iterate(**synth.make_iterate(xl, xu, gl, gu, 21))
+    y = np.random.default_rng(22).standard_normal(L.m)
+    fx = lambda v: np.where(np.isfinite(v), v, 0.0)  # noqa: E731
+
+    def lagr(x, s):
+        val = oracle.objective(g, x)[0] - y @ (oracle.constraints(g, x)[0] - s)
+        val -= it.zl_x @ (fx(x - it.xl)) + it.zu_x @ (fx(it.xu - x))
+        val -= it.zl_s @ (fx(s - it.sl)) + it.zu_s @ (fx(it.su - s))
+        return val
+
+    rdx, rds, _, _, _ = oracle.kkt_parts(g, oracle.gradient(g, it.x)[0],
+                                         oracle.constraints(g, it.x)[0],
+                                         oracle.jacobian(g, it.x)[0], it, y, 0.1)
+    h = 1e-6
+    for j in np.random.default_rng(23).choice(L.n, 40, replace=False):
+        e = np.zeros(L.n)
+        e[j] = h * max(1.0, abs(it.x[j]))
+        fd = (lagr(it.x + e, it.s) - lagr(it.x - e, it.s)) / (2 * e[j])
+        assert abs(fd - rdx[j]) <= 1e-5 * max(1.0, abs(rdx[j])), (j, fd, rdx[j])
+    for r in np.random.default_rng(24).choice(L.m, 40, replace=False):
+        e = np.zeros(L.m)
+        e[r] = h * max(1.0, abs(it.s[r]))
+        fd = (lagr(it.x, it.s + e) - lagr(it.x, it.s - e)) / (2 * e[r])
+        assert abs(fd - rds[r]) <= 1e-5 * max(1.0, abs(rds[r])), (r, fd, rds[r])
+
+
+def test_residual_scaling_golden():
+    """s_d, s_c by hand (s_max = 100): small multipliers leave the residual
+    unscaled; large ones divide it by their mean magnitude / 100."""
+    assert oracle.residual_scaling(3.0, 7.0, 2, 2) == (1.0, 1.0)
+    s_d, s_c = oracle.residual_scaling(3e4, 7e4, 2, 2)
+    assert s_d == 250.0 and s_c == 350.0
