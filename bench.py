@@ -468,6 +468,19 @@ def run_step_bench(args, local):
         recover(0)
     c_us = timed(condense)
     r_us = timed(recover)
+    y = t(np.random.default_rng(600).standard_normal(m))
+    grad = torch.empty(n, dtype=torch.float64, device=dev)
+    cons = torch.empty(m, dtype=torch.float64, device=dev)
+    res = torch.empty(9, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        acopf.eval_grad(model, sets[0]["it"]["x"], grad, stream=stream)
+        acopf.eval_cons(model, sets[0]["it"]["x"], cons, stream=stream)
+
+    def residual(k):
+        b = sets[k % 2]
+        acopf.kkt_residual(model, b["it"], y, grad, cons, jv, 0.1, res, stream=stream)
+
+    e_us = timed(residual)
     hbm = 6772.9
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -475,17 +488,22 @@ def run_step_bench(args, local):
         pass
     c_bytes = 8 * (10 * n + 11 * m + nj)
     r_bytes = 8 * (10 * n + 14 * m + nj)
+    e_bytes = 8 * (6 * n + 8 * m + nj)  # x, bounds, duals, grad (n); s, bounds, duals, y, g (m); J
     model.close()
     return {
-        "workload": "80kbus: condensation (Sigma_x, Sigma_s, q_s, rhs = q_x + A'(C q_s + D q_y)) "
-                    "and step recovery (ds, dy, 4 bound-dual steps) at an interior iterate",
+        "workload": "80kbus: condensation (Sigma_x, Sigma_s, q_s, rhs = q_x + A'(C q_s + D q_y)), "
+                    "step recovery (ds, dy, 4 bound-dual steps) and the scaled KKT residual "
+                    "at an interior iterate",
         "condense_us": c_us, "condense_bytes": c_bytes,
         "condense_gbs": c_bytes / (c_us * 1e-6) / 1e9,
         "condense_frac_hbm": c_bytes / (c_us * 1e-6) / 1e9 / hbm,
         "recover_us": r_us, "recover_bytes": r_bytes,
         "recover_gbs": r_bytes / (r_us * 1e-6) / 1e9,
         "recover_frac_hbm": r_bytes / (r_us * 1e-6) / 1e9 / hbm,
-        "launches": {"condense": 2, "recover": 1},
+        "residual_us": e_us, "residual_bytes": e_bytes,
+        "residual_gbs": e_bytes / (e_us * 1e-6) / 1e9,
+        "residual_frac_hbm": e_bytes / (e_us * 1e-6) / 1e9 / hbm,
+        "launches": {"condense": 2, "recover": 1, "residual": 1},
     }
 
 

@@ -255,6 +255,27 @@ acopf_status acopf_recover_step(acopf_model* model, const acopf_iterate* it, con
                                 double* dzl_x, double* dzu_x, double* dzl_s, double* dzu_s,
                                 acopf_stream stream);
 
+/* Scaled residual of the first-order conditions (the termination test of
+ * Algorithm 1, Sec. IV: "a scaled version of the residual" of Eq. first,
+ * with the scaling of the interior-point reference the paper cites, s_max =
+ * 100):
+ *   r_d = [grad f - A'y - zl_x + zu_x ; y - zl_s + zu_s],  r_p = g(x) - s,
+ *   r_c = [Zl_x (x - xl) - mu ; Zu_x (xu - x) - mu ; Zl_s (s - sl) - mu ;
+ *          Zu_s (su - s) - mu] over finite bounds (n_z of them),
+ *   s_d = max(100, (||y||_1 + ||z||_1) / (m + n_z)) / 100,
+ *   s_c = max(100, ||z||_1 / n_z) / 100,
+ *   E   = max(||r_d||_inf / s_d, ||r_p||_inf, ||r_c||_inf / s_c).
+ * it: x, s, the bounds and the bound duals (the p_* fields are not read);
+ * y (m), grad (n: acopf_eval_grad at x), cons (m: acopf_eval_cons at x),
+ * jvals (acopf_eval_jac_coo at x): DEVICE arrays.  out: DEVICE array of 9
+ * doubles receiving [E, ||r_d||_inf, ||r_p||_inf, ||r_c||_inf, ||y||_1,
+ * ||z||_1, n_z, s_d, s_c].  Two kernel launches, asynchronous on `stream`;
+ * sums in a fixed order.  Shares the model's condensation scratch (see
+ * above): calls on one model must not overlap. */
+acopf_status acopf_kkt_residual(acopf_model* model, const acopf_iterate* it, const double* y,
+                                const double* grad, const double* cons, const double* jvals,
+                                double mu, double* out, acopf_stream stream);
+
 /* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of
  * one model with HOST inputs and outputs, whose host-to-device copies,
  * kernels and device-to-host copies overlap (three streams, `depth` device

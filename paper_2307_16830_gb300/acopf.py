@@ -171,6 +171,11 @@ _condense = _sig("acopf_condense", C.c_int32, _vp, C.POINTER(Iterate), _vp, C.c_
 _recover_step = _sig("acopf_recover_step", C.c_int32, _vp, C.POINTER(Iterate), _vp, C.c_double,
                      C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 
+_kkt_residual = _sig("acopf_kkt_residual", C.c_int32, _vp, C.POINTER(Iterate), _vp, _vp, _vp,
+                     _vp, C.c_double, _vp, _vp)
+RESIDUAL_FIELDS = ("residual", "dual_inf", "primal_inf", "compl_inf", "y_l1", "z_l1", "n_z",
+                   "s_d", "s_c")
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -187,7 +192,7 @@ EXPORTED = [
     "acopf_server_poll", "acopf_server_wait", "acopf_server_request_times",
     "acopf_server_release", "acopf_server_get_stats", "acopf_server_set_option",
     "acopf_pipeline_create", "acopf_pipeline_destroy", "acopf_pipeline_submit",
-    "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step",
+    "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step", "acopf_kkt_residual",
 ]
 
 
@@ -689,3 +694,10 @@ def recover_step(model: Model, it, jvals, delta_w: float, delta_c: float, sigma_
                          _ptr(sigma_s), _ptr(q_s), _ptr(dx), _ptr(ds), _ptr(dy), _ptr(dzl_x),
                          _ptr(dzu_x), _ptr(dzl_s), _ptr(dzu_s), _stream(stream)),
            "acopf_recover_step")
+
+
+def kkt_residual(model: Model, it, y, grad, cons, jvals, mu: float, out, stream=None) -> None:
+    """out: device array of 9 doubles (see RESIDUAL_FIELDS)."""
+    r = _iterate(it)
+    _check(_kkt_residual(model.handle, C.byref(r), _ptr(y), _ptr(grad), _ptr(cons), _ptr(jvals),
+                         float(mu), _ptr(out), _stream(stream)), "acopf_kkt_residual")

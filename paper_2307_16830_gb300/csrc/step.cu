@@ -140,6 +140,140 @@ __global__ void __launch_bounds__(kStepThreads) k_recover(
 
 int blocks_for(int count) { return (count + kStepThreads - 1) / kStepThreads; }
 
+// Scaled residual of the first-order conditions.  A grid of a fixed number
+// of blocks per device strides over the variables (dual residual grad f -
+// A'y - zl_x + zu_x, complementarity of the variable bounds), then over the
+// rows (y - zl_s + zu_s, g - s, complementarity of the slack bounds, |y|).
+// Each block leaves max |r_d|, max |r_p|, max |r_c|, sum |y|, sum |z| and the
+// count of finite bounds (sums in a fixed order for the fixed grid; maxima
+// are order-free) for k_residual_final, which writes
+// out = [E, max|r_d|, max|r_p|, max|r_c|, ||y||_1, ||z||_1, n_z, s_d, s_c].
+__global__ void __launch_bounds__(kStepThreads) k_kkt_residual(
+    DevStep st, StepIterate it, const double* __restrict__ y, const double* __restrict__ grad,
+    const double* __restrict__ cons, const double* __restrict__ J, double mu) {
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // dmax, pmax, cmax, ysum, zsum, nz
+  const int stride = gridDim.x * kStepThreads;
+  for (int j = blockIdx.x * kStepThreads + threadIdx.x; j < st.n; j += stride) {
+    double aty = 0.0;
+    for (int k = __ldg(st.jt_ptr + j), k1 = __ldg(st.jt_ptr + j + 1); k < k1; ++k)
+      aty = fma(ldg(J + __ldg(st.jt_slot + k)), ldg(y + __ldg(st.jt_row + k)), aty);
+    const double zl = ldg(it.zl_x + j), zu = ldg(it.zu_x + j), x = ldg(it.x + j);
+    v[0] = fmax(v[0], fabs(ldg(grad + j) - aty - zl + zu));
+    const double lo = ldg(it.xl + j), hi = ldg(it.xu + j);
+    if (is_finite_bits(lo)) {
+      v[2] = fmax(v[2], fabs(fma(zl, x - lo, -mu)));
+      v[4] += fabs(zl);
+      v[5] += 1.0;
+    }
+    if (is_finite_bits(hi)) {
+      v[2] = fmax(v[2], fabs(fma(zu, hi - x, -mu)));
+      v[4] += fabs(zu);
+      v[5] += 1.0;
+    }
+  }
+  for (int r = blockIdx.x * kStepThreads + threadIdx.x; r < st.m; r += stride) {
+    const double yr = ldg(y + r), zl = ldg(it.zl_s + r), zu = ldg(it.zu_s + r);
+    const double sr = ldg(it.s + r);
+    v[0] = fmax(v[0], fabs(yr - zl + zu));
+    v[1] = fmax(v[1], fabs(ldg(cons + r) - sr));
+    v[3] += fabs(yr);
+    const double lo = ldg(it.sl + r), hi = ldg(it.su + r);
+    if (is_finite_bits(lo)) {
+      v[2] = fmax(v[2], fabs(fma(zl, sr - lo, -mu)));
+      v[4] += fabs(zl);
+      v[5] += 1.0;
+    }
+    if (is_finite_bits(hi)) {
+      v[2] = fmax(v[2], fabs(fma(zu, hi - sr, -mu)));
+      v[4] += fabs(zu);
+      v[5] += 1.0;
+    }
+  }
+  // Block reduction: shuffle trees (fixed order), then the warps in order.
+  __shared__ double sh[kStepThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+#pragma unroll
+    for (int q = 3; q < 6; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[warp][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < kStepThreads / 32; ++w) {
+      for (int q = 0; q < 3; ++q) b[q] = fmax(b[q], sh[w][q]);
+      for (int q = 3; q < 6; ++q) b[q] += sh[w][q];
+    }
+    for (int q = 0; q < 6; ++q) st.res_part[6 * blockIdx.x + q] = b[q];
+  }
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// One block: the blocks' parts in a fixed order (each thread a strided
+// subset in ascending order, then fixed trees), and the scaled residual.
+__global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int nb,
+                                                                 double* __restrict__ out) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  double c[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  constexpr int U = 4;  // blocks fetched per round, all loads in flight together
+  for (int b0 = threadIdx.x; b0 < nb; b0 += U * kStepThreads) {
+    double t[U][6];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int b = b0 + u * kStepThreads;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) t[u][q] = b < nb ? __ldcg(st.res_part + 6 * b + q) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], t[u][q]);
+#pragma unroll
+      for (int q = 3; q < 6; ++q) c[q] += t[u][q];
+    }
+  }
+  __shared__ double sh[kStepThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], __shfl_down_sync(0xffffffffu, c[q], o));
+#pragma unroll
+    for (int q = 3; q < 6; ++q) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[warp][q] = c[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) c[q] = sh[0][q];
+    for (int w = 1; w < kStepThreads / 32; ++w) {
+      for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], sh[w][q]);
+      for (int q = 3; q < 6; ++q) c[q] += sh[w][q];
+    }
+    const double smax = 100.0;  // s_max of the scaling
+    const double nz = c[5];
+    const double s_d = fmax(smax, (c[3] + c[4]) / (static_cast<double>(st.m) + nz)) / smax;
+    const double s_c = nz > 0.0 ? fmax(smax, c[4] / nz) / smax : 1.0;
+    out[0] = fmax(fmax(c[0] / s_d, c[1]), c[2] / s_c);
+    out[1] = c[0];
+    out[2] = c[1];
+    out[3] = c[2];
+    out[4] = c[3];
+    out[5] = c[4];
+    out[6] = nz;
+    out[7] = s_d;
+    out[8] = s_c;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_condense(const DevStep& st, const StepIterate& it, const double* jvals,
@@ -166,6 +300,26 @@ cudaError_t launch_condense(const DevStep& st, const StepIterate& it, const doub
   cfg.attrs = attr;
   cfg.numAttrs = (pdl && rb > 0) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k_condense_cols, st, it, jvals, sigma_x, rhs);
+}
+
+int residual_blocks(int sms) { return 4 * sms; }
+
+cudaError_t launch_kkt_residual(const DevStep& st, const StepIterate& it, const double* y,
+                                const double* grad, const double* cons, const double* jvals,
+                                double mu, double* out, cudaStream_t s) {
+  k_kkt_residual<<<st.res_blocks, kStepThreads, 0, s>>>(st, it, y, grad, cons, jvals, mu);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_residual_final, st, st.res_blocks, out);
 }
 
 cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const double* jvals,

@@ -42,6 +42,11 @@ acopf_status ensure_step(acopf_model* m) {
   const size_t o_rc = p.take<int32_t>(nnz), o_cp = p.take<int32_t>(cp.size());
   const size_t o_cs = p.take<int32_t>(nnz), o_cr = p.take<int32_t>(nnz);
   const size_t o_w = p.take<double>(size_t(mm));
+  int sms = 0;
+  cudaError_t ae = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (ae != cudaSuccess) return cuda_fail(ae, "acopf_condense: device attribute");
+  const int res_blocks = acopf::residual_blocks(sms > 0 ? sms : 1);
+  const size_t o_rp2 = p.take<double>(6 * size_t(res_blocks));
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, p.off);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_condense: cudaMalloc");
@@ -70,6 +75,8 @@ acopf_status ensure_step(acopf_model* m) {
   st.jt_slot = reinterpret_cast<const int32_t*>(base + o_cs);
   st.jt_row = reinterpret_cast<const int32_t*>(base + o_cr);
   st.w = reinterpret_cast<double*>(base + o_w);
+  st.res_part = reinterpret_cast<double*>(base + o_rp2);
+  st.res_blocks = res_blocks;
   m->step_arena = arena;
   return ACOPF_OK;
 }
@@ -143,6 +150,39 @@ acopf_status acopf_recover_step(acopf_model* model, const acopf_iterate* it, con
                                         dx, ds, dy, dzl_x, dzu_x, dzl_s, dzu_s,
                                         reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "acopf_recover_step");
+  return ACOPF_OK;
+}
+
+acopf_status acopf_kkt_residual(acopf_model* model, const acopf_iterate* it, const double* y,
+                                const double* grad, const double* cons, const double* jvals,
+                                double mu, double* out, acopf_stream stream) {
+  if (!model) return fail(ACOPF_E_INVALID_ARG, "acopf_kkt_residual: null model");
+  if (model->device < 0) return fail(ACOPF_E_NO_DEVICE, "model was created host-only (device = -1)");
+  if (!it || !it->x || !it->s || !it->xl || !it->xu || !it->sl || !it->su || !it->zl_x ||
+      !it->zu_x || !it->zl_s || !it->zu_s)
+    return fail(ACOPF_E_INVALID_ARG, "acopf_kkt_residual: null iterate array");
+  if (!y || !grad || !cons || !jvals || !out)
+    return fail(ACOPF_E_INVALID_ARG, "acopf_kkt_residual: null pointer");
+  if (!std::isfinite(mu) || mu < 0.0)
+    return fail(ACOPF_E_INVALID_ARG, "acopf_kkt_residual: mu must be finite and >= 0");
+  DeviceScope dsc(model->device);
+  if (dsc.error() != cudaSuccess) return cuda_fail(dsc.error(), "acopf_kkt_residual");
+  acopf_status st = ensure_step(model);
+  if (st != ACOPF_OK) return st;
+  acopf::StepIterate si{};
+  si.x = it->x;
+  si.s = it->s;
+  si.xl = it->xl;
+  si.xu = it->xu;
+  si.sl = it->sl;
+  si.su = it->su;
+  si.zl_x = it->zl_x;
+  si.zu_x = it->zu_x;
+  si.zl_s = it->zl_s;
+  si.zu_s = it->zu_s;
+  cudaError_t e = acopf::launch_kkt_residual(model->step, si, y, grad, cons, jvals, mu, out,
+                                             reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_kkt_residual");
   return ACOPF_OK;
 }
 

@@ -122,3 +122,47 @@ def test_condense_rejects_bad_arguments(dev, acopf):
         with pytest.raises(acopf.AcopfError) as e:
             acopf.condense(m, it_dev, z, -1.0, 0.0, z, z, z, z)
         assert e.value.status == acopf.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,make,scale", [
+    ("30bus", lambda: synth.workload_grid("30bus"), 1.0),
+    ("edge7", lambda: synth.make_edge_case_grid(7), 1.0),
+    ("ragged", lambda: synth.make_grid(517, 777, 61, seed=3), 1e4),
+    ("10kbus", lambda: synth.workload_grid("10kbus"), 1.0)])
+def test_kkt_residual_matches_oracle(dev, acopf, name, make, scale):
+    """The scaled residual from the library's own callbacks at x equals the
+    oracle's from its callbacks (norms to 1e-10 relative, the bound count
+    exactly); scale multiplies y and the duals, so the scaling engages."""
+    g = make()
+    with acopf.model_create(g, 0) as m:
+        d, _ = _iterate(m, 700, dev)
+        for k in ("zl_x", "zu_x", "zl_s", "zu_s"):
+            d[k] = d[k] * scale
+        it_dev = {k: gu.t64(torch, v, dev) for k, v in d.items()}
+        y = np.random.default_rng(701).standard_normal(m.m) * scale
+        xd = it_dev["x"]
+        grad = torch.empty(m.n, dtype=torch.float64, device=dev)
+        cons = torch.empty(m.m, dtype=torch.float64, device=dev)
+        jv = torch.empty(m.nnz_jac, dtype=torch.float64, device=dev)
+        acopf.eval_grad(m, xd, grad)
+        acopf.eval_cons(m, xd, cons)
+        acopf.eval_jac_coo(m, xd, jv)
+        out = torch.full((9,), float("nan"), dtype=torch.float64, device=dev)
+        yd = gu.t64(torch, y, dev)
+        acopf.kkt_residual(m, it_dev, yd, grad, cons, jv, 0.1, out)
+        torch.cuda.synchronize()
+        got = dict(zip(acopf.RESIDUAL_FIELDS, out.cpu().numpy()))
+        it = oracle.Iterate(**d)
+        ref = oracle.kkt_residual(g, oracle.gradient(g, it.x)[0], oracle.constraints(g, it.x)[0],
+                                  oracle.jacobian(g, it.x)[0], it, y, 0.1)
+        assert got["n_z"] == ref["n_z"]
+        for k in acopf.RESIDUAL_FIELDS:
+            if k == "n_z":
+                continue
+            assert abs(got[k] - ref[k]) <= 1e-10 * max(1.0, abs(ref[k])), (name, k, got[k], ref[k])
+        if scale > 1.0:
+            assert got["s_d"] > 1.0 and got["s_c"] > 1.0
+        again = torch.full((9,), float("nan"), dtype=torch.float64, device=dev)
+        acopf.kkt_residual(m, it_dev, yd, grad, cons, jv, 0.1, again)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), again.cpu().numpy().view(np.uint64))
