@@ -507,6 +507,89 @@ def run_step_bench(args, local):
     }
 
 
+def run_chol_bench(args, local):
+    """Sparse Cholesky of M_cond (acopf_chol_*) on the 10,000- and 80,000-bus
+    workloads, random and near-planar: the host symbolic phase once, then the
+    numeric factorization
+    (value gather, library factorization, pivot test, which returns to the
+    host) and the solve (permutation, two triangular solves, permutation
+    back), M_cond assembled by the library at a convex point (no constraint
+    multipliers, delta_w = 1e-4, so positive definite)."""
+    import time
+
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, factor in (("10kbus", True), ("10kbus-geo", True)):
+        grid = synth.workload_grid(name)
+        model = acopf.model_create(grid, local)
+        n, m = model.n, model.m
+        pt = synth.make_point(grid, 90)
+        rng = np.random.default_rng(91)
+
+        def t(a):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+        bufs = {k: torch.empty(c, dtype=torch.float64, device=dev) for k, c in
+                (("f", 1), ("g", n), ("c", m), ("j", model.nnz_jac), ("h", model.nnz_hess),
+                 ("k", model.nnz_kkt))}
+        with torch.cuda.stream(stream):
+            acopf.eval_assemble(model, t(pt.x), torch.zeros(m, dtype=torch.float64, device=dev),
+                                1.0, t(10.0 ** rng.uniform(-2, 2, n)),
+                                t(10.0 ** rng.uniform(-2, 2, m)), 1e-4, 0.0, bufs["f"],
+                                bufs["g"], bufs["c"], bufs["j"], bufs["h"], bufs["k"],
+                                stream=stream)
+        stream.synchronize()
+        stats = acopf.chol_analyze(model)
+        if not factor:
+            # the library's analysis returns an error on this pattern (its
+            # random chords give separators of linear size): symbolic counts only
+            out[name] = {**stats, "factor_gflop": stats["factor_flops"] / 1e9,
+                         "factorized": False}
+            model.close()
+            continue
+        t0 = time.perf_counter()
+        ch = acopf.chol_create(model)
+        create_s = time.perf_counter() - t0
+        info = ch.info()
+        for _ in range(3):
+            assert ch.factor(bufs["k"], stream=stream) == -1
+        reps = 10
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ch.factor(bufs["k"], stream=stream)
+        factor_ms = 1e3 * (time.perf_counter() - t0) / reps
+        b = t(rng.standard_normal(n))
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                ch.solve(b, x, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(50):
+                ch.solve(b, x, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        solve_ms = e0.elapsed_time(e1) / 50
+        ch.close()
+        model.close()
+        out[name] = {"n": n, "nnz_lower": int(model.nnz_kkt), "nnz_factor": info["nnz_factor"],
+                     "factor_gflop": info["factor_flops"] / 1e9, "max_col": info["max_col"],
+                     "symbolic_s": create_s, "factor_ms": factor_ms,
+                     "factor_gflops": info["factor_flops"] / (factor_ms * 1e-3) / 1e9,
+                     "solve_ms": solve_ms,
+                     "solve_gbs_L_twice": 2 * 12 * info["nnz_factor"] / (solve_ms * 1e-3) / 1e9,
+                     "device_bytes": info["device_bytes"]}
+    out["timing"] = ("factor: host wall clock per call (each call returns the pivot test to the "
+                     "host); solve: CUDA events over 50 calls")
+    return out
+
+
 def _pinned(torch, a):
     """Page-locked host copy of a numpy array (numpy view, torch owner)."""
     t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -760,6 +843,8 @@ def main():
                     help="also time the 30-bus and 10,000-bus workloads (plain and graph)")
     ap.add_argument("--step", type=int, default=1, choices=[0, 1],
                     help="also time the condensation and step recovery (80k workload)")
+    ap.add_argument("--chol", type=int, default=1, choices=[0, 1],
+                    help="also time the sparse Cholesky of M_cond (10k and 80k workloads)")
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)
@@ -779,6 +864,7 @@ def main():
     r = run_ours(args, rank, world, local)
     small = run_small_workloads(local) if args.small_workloads and world == 1 else None
     step = run_step_bench(args, local) if args.step and world == 1 else None
+    chol = run_chol_bench(args, local) if args.chol and world == 1 else None
     batch = run_batch_bench(args, local) if args.batch and world == 1 else None
     serve = run_serve_bench(args, local) if args.serve and world == 1 else None
     if rank != 0:
@@ -848,7 +934,7 @@ def main():
         "graph": None if r["graph_ms"] is None else {
             "ms_per_call": r["graph_ms"], "calls_per_s": 1e3 / r["graph_ms"],
             "note": f"{GRAPH_CALLS} calls per CUDA graph, {args.graph_replays} replays"},
-        "small_workloads": small, "step": step,
+        "small_workloads": small, "step": step, "chol": chol,
         "gpu": r["gpu"], "batch": batch, "serve": serve,
     }
     print(json.dumps(line), flush=True)

@@ -176,6 +176,25 @@ _kkt_residual = _sig("acopf_kkt_residual", C.c_int32, _vp, C.POINTER(Iterate), _
 RESIDUAL_FIELDS = ("residual", "dual_inf", "primal_inf", "compl_inf", "y_l1", "z_l1", "n_z",
                    "s_d", "s_c")
 
+_chol_create = _sig("acopf_chol_create", C.c_int32, _vp, C.POINTER(_vp))
+_chol_destroy = _sig("acopf_chol_destroy", C.c_int32, _vp)
+_chol_factor = _sig("acopf_chol_factor", C.c_int32, _vp, _vp, C.c_double, C.POINTER(C.c_int32),
+                    _vp)
+_chol_solve = _sig("acopf_chol_solve", C.c_int32, _vp, _vp, _vp, _vp)
+
+
+class CholStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz_full", C.c_int64), ("nnz_factor", C.c_int64),
+                ("max_col", C.c_int64), ("factor_flops", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_chol_info = _sig("acopf_chol_info", C.c_int32, _vp, C.POINTER(CholStats), C.POINTER(C.c_int64))
+_chol_analyze = _sig("acopf_chol_analyze", C.c_int32, _vp, C.POINTER(CholStats))
+_chol_permutation = _sig("acopf_chol_permutation", C.c_int32, _vp, _vp)
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -193,6 +212,8 @@ EXPORTED = [
     "acopf_server_release", "acopf_server_get_stats", "acopf_server_set_option",
     "acopf_pipeline_create", "acopf_pipeline_destroy", "acopf_pipeline_submit",
     "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step", "acopf_kkt_residual",
+    "acopf_chol_create", "acopf_chol_destroy", "acopf_chol_factor", "acopf_chol_solve",
+    "acopf_chol_info", "acopf_chol_permutation", "acopf_chol_analyze",
 ]
 
 
@@ -701,3 +722,67 @@ def kkt_residual(model: Model, it, y, grad, cons, jvals, mu: float, out, stream=
     r = _iterate(it)
     _check(_kkt_residual(model.handle, C.byref(r), _ptr(y), _ptr(grad), _ptr(cons), _ptr(jvals),
                          float(mu), _ptr(out), _stream(stream)), "acopf_kkt_residual")
+
+
+class Chol:
+    """Sparse Cholesky factorization of a model's M_cond (owner of an
+    ``acopf_chol*``)."""
+
+    def __init__(self, model: Model):
+        h = _vp()
+        _check(_chol_create(model.handle, C.byref(h)), "acopf_chol_create")
+        self._h = h
+        self.model = model
+
+    def factor(self, kvals, pivot_tol: float = 0.0, stream=None) -> int:
+        """Factorizes M_cond from its lower-CSR values (device); returns -1
+        when every pivot passes (positive definite), else the first failing
+        pivot's position in the factorization order."""
+        pos = C.c_int32(0)
+        _check(_chol_factor(self._h, _ptr(kvals), float(pivot_tol), C.byref(pos),
+                            _stream(stream)), "acopf_chol_factor")
+        return pos.value
+
+    def solve(self, b, x, stream=None) -> None:
+        _check(_chol_solve(self._h, _ptr(b), _ptr(x), _stream(stream)), "acopf_chol_solve")
+
+    def info(self) -> dict:
+        """The symbolic counts (CholStats fields) and device_bytes (the
+        library's factor and workspace)."""
+        st, nbytes = CholStats(), C.c_int64(0)
+        _check(_chol_info(self._h, C.byref(st), C.byref(nbytes)), "acopf_chol_info")
+        return {**st.as_dict(), "device_bytes": nbytes.value}
+
+    def permutation(self) -> np.ndarray:
+        """The fill-reducing order (row i of P M_cond P' is row perm[i])."""
+        p = np.empty(self.model.n, dtype=np.int32)
+        _check(_chol_permutation(self._h, p.ctypes.data), "acopf_chol_permutation")
+        return p
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _chol_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def chol_create(model: Model) -> Chol:
+    return Chol(model)
+
+
+def chol_analyze(model: Model) -> dict:
+    """Symbolic counts of a factorization of the model's M_cond."""
+    st = CholStats()
+    _check(_chol_analyze(model.handle, C.byref(st)), "acopf_chol_analyze")
+    return st.as_dict()

@@ -18,7 +18,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libacopf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "stepapi.cpp",
-           "kernels.cu", "step.cu", "noalloc.cu"]
+           "cholapi.cpp", "kernels.cu", "step.cu", "chol.cu", "noalloc.cu"]
+# the sparse Cholesky factorization of M_cond is cuSOLVER's
+LIBS = ["-lcusolver", "-lcusparse"]
 
 
 def nvcc() -> str:
@@ -46,7 +48,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, *LIBS]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

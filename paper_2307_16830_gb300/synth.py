@@ -11,7 +11,12 @@ benchmarks (Section V.A), which are not available here:
 
 * topology: a uniformly random recursive spanning tree over a random bus
   permutation, then unique random extra edges (no self-loops, no parallel
-  lines) up to the requested branch count;
+  lines) up to the requested branch count; or, for the workloads of the
+  sparse factorization ("-geo"), a near-planar network: buses at random
+  points of the unit square joined by their Euclidean minimum spanning tree
+  and then by random pairs of near neighbours (real transmission networks
+  are near-planar, with small separators; the random chords of the first
+  recipe give separators of linear size);
 * branches: r ~ U(0.001, 0.05), x ~ U(0.01, 0.3), total charging b ~ U(0, 0.1),
   tap 1 except U(0.95, 1.05) on 10 % of branches, shift 0,
   rate_a ~ U(1, 5) p.u., angle-difference limits +-30 degrees;
@@ -159,13 +164,60 @@ def _random_topology(rng: np.random.Generator, n_bus: int, n_branch: int):
     return f[order].astype(np.int32), t[order].astype(np.int32)
 
 
+def _geometric_topology(rng: np.random.Generator, n_bus: int, n_branch: int):
+    """Buses at uniform random points of the unit square; the Euclidean
+    minimum spanning tree of their 8-nearest-neighbour graph, then extra
+    branches drawn uniformly among the remaining pairs of 4-nearest
+    neighbours, up to the requested branch count.  Bus numbers carry no
+    geometry (the points are drawn in random order)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components, minimum_spanning_tree
+    from scipy.spatial import cKDTree
+
+    if n_bus < 10:
+        raise ValueError("the geometric recipe needs at least 10 buses")
+    if n_branch < n_bus - 1:
+        raise ValueError("need at least n_bus - 1 branches for a spanning tree")
+    pts = rng.random((n_bus, 2))
+    d, nbr = cKDTree(pts).query(pts, k=9)
+    rank = np.tile(np.arange(1, 9), n_bus)
+    a = np.repeat(np.arange(n_bus), 8)
+    b = nbr[:, 1:].ravel()
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keys, first = np.unique(lo.astype(np.int64) * n_bus + hi, return_index=True)
+    w, rank = d[:, 1:].ravel()[first], rank[first]
+    G = coo_matrix((w + 1e-300, (keys // n_bus, keys % n_bus)), shape=(n_bus, n_bus)).tocsr()
+    if connected_components(G, directed=False)[0] != 1:
+        raise ValueError("the 8-nearest-neighbour graph of the points is not connected")
+    mst = minimum_spanning_tree(G).tocoo()
+    tkeys = (np.minimum(mst.row, mst.col).astype(np.int64) * n_bus
+             + np.maximum(mst.row, mst.col))
+    rest = keys[~np.isin(keys, tkeys) & (rank <= 4)]
+    need = n_branch - tkeys.size
+    if need > rest.size:
+        raise ValueError("more branches than neighbour pairs")
+    keys = np.concatenate([tkeys, rng.choice(rest, size=need, replace=False)])
+    lo, hi = keys // n_bus, keys % n_bus
+    swap = rng.random(keys.shape[0]) < 0.5
+    f = np.where(swap, hi, lo)
+    t = np.where(swap, lo, hi)
+    order = rng.permutation(keys.shape[0])
+    return f[order].astype(np.int32), t[order].astype(np.int32)
+
+
 def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
-              name: str | None = None) -> Grid:
-    """Synthetic grid with the recipe of the module docstring."""
+              name: str | None = None, topology: str = "random") -> Grid:
+    """Synthetic grid with the recipe of the module docstring (topology
+    "random", or "geometric": see _geometric_topology)."""
     if not 1 <= n_gen <= n_bus:
         raise ValueError("need 1 <= n_gen <= n_bus")
     rng = np.random.default_rng(seed)
-    f, t = _random_topology(rng, n_bus, n_branch)
+    if topology == "random":
+        f, t = _random_topology(rng, n_bus, n_branch)
+    elif topology == "geometric":
+        f, t = _geometric_topology(rng, n_bus, n_branch)
+    else:
+        raise ValueError(f"unknown topology {topology!r}")
     nl = f.shape[0]
     r = rng.uniform(0.001, 0.05, nl)
     x = rng.uniform(0.01, 0.3, nl)
@@ -337,13 +389,19 @@ WORKLOADS = {
     "30bus": dict(n_bus=30, n_branch=41, n_gen=6, seed=1000),
     "10kbus": dict(n_bus=10_000, n_branch=13_500, n_gen=2_000, seed=1001),
     "80kbus": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1002),
+    # near-planar networks of the same counts: the workloads of the sparse
+    # factorization, whose cost is set by the network's separators
+    "10kbus-geo": dict(n_bus=10_000, n_branch=13_500, n_gen=2_000, seed=1011,
+                       topology="geometric"),
+    "80kbus-geo": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1012,
+                       topology="geometric"),
 }
 
 
 def workload_grid(name: str) -> Grid:
     spec = WORKLOADS[name]
     return make_grid(spec["n_bus"], spec["n_branch"], spec["n_gen"], spec["seed"],
-                     name=f"synthetic-{name}")
+                     name=f"synthetic-{name}", topology=spec.get("topology", "random"))
 
 
 def point_seed(grid_seed: int, call_index: int) -> int:

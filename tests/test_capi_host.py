@@ -208,3 +208,19 @@ def test_pipeline_create_rejects_without_device_work():
         with pytest.raises(acopf.AcopfError) as ei:
             acopf.pipeline_create(m, 2)
         assert ei.value.status == acopf.E_NO_DEVICE
+
+
+def test_chol_create_rejects_without_device_work():
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, -1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.chol_create(m)
+        assert ei.value.status == acopf.E_NO_DEVICE
+
+
+def test_chol_analyze_rejects_without_device_work():
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, -1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.chol_analyze(m)
+        assert ei.value.status == acopf.E_NO_DEVICE

@@ -1,0 +1,192 @@
+"""GPU sparse Cholesky of M_cond (acopf_chol_*) against the oracle
+(oracle/chol.py).
+
+* Small networks, M_cond from the oracle's own callbacks: a convex case
+  (no constraint multipliers and delta_w > 0, positive definite by
+  construction, and so by the oracle's dense test) must factor with every
+  pivot passing; a nonconvex case the oracle finds indefinite must fail the
+  test.  Solves: the normwise backward error (computed by the oracle) at
+  most 1e-13, and the forward error against the oracle's solve within
+  10 n kappa eps (kappa the 2-norm condition number, computed densely).
+* The chain at full size (the 10,000-bus workload and the near-planar
+  10,000- and 80,000-bus ones): the library assembles M_cond, factors it
+  and solves; backward error against the oracle's M_cond; a planted
+  negative diagonal entry fails the pivot test, and the original values
+  factor again.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_16830_gb300 import synth
+
+import gpu_util as gu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def acopf():
+    from paper_2307_16830_gb300 import acopf as lib
+    return lib
+
+
+def _sigmas(L, seed):
+    rng = np.random.default_rng(seed)
+    return 10.0 ** rng.uniform(-2, 2, L.n), 10.0 ** rng.uniform(-2, 2, L.m)
+
+
+def _oracle_kvals(g, seed, y_scale, dw, dc):
+    L = oracle.layout(g)
+    pt = synth.make_point(g, seed)
+    sx, ss = _sigmas(L, seed + 1)
+    H = oracle.hessian(g, pt.x, pt.y * y_scale, 1.0)[0]
+    J = oracle.jacobian(g, pt.x)[0]
+    kv, _ = oracle.condensed_kkt(g, H, J, sx, ss, dw, dc)
+    return kv
+
+
+CASES = [("30bus", lambda: synth.workload_grid("30bus")),
+         ("edge7", lambda: synth.make_edge_case_grid(7)),
+         ("star", lambda: synth.make_star_grid()),
+         ("ragged", lambda: synth.make_grid(517, 777, 61, seed=3))]
+
+
+@pytest.mark.parametrize("idx", range(len(CASES)))
+@pytest.mark.parametrize("dc", [0.0, 1e-3])
+def test_convex_case_factors_and_solves(dev, acopf, idx, dc):
+    name, make = CASES[idx]
+    g = make()
+    L = oracle.layout(g)
+    kv = _oracle_kvals(g, 40 + idx, 0.0, 1e-4, dc)
+    if L.n <= 1500:
+        assert oracle.is_positive_definite(g, kv)
+    b = np.random.default_rng(50 + idx).standard_normal(L.n)
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        kd = gu.t64(torch, kv, dev)
+        assert ch.factor(kd) == -1, name
+        bd = gu.t64(torch, b, dev)
+        xd = torch.full((L.n,), float("nan"), dtype=torch.float64, device=dev)
+        ch.solve(bd, xd)
+        torch.cuda.synchronize()
+        x = xd.cpu().numpy()
+        assert oracle.backward_error(g, kv, x, b) <= 1e-13, name
+        if L.n <= 1500:
+            ref = oracle.solve_condensed(g, kv, b)
+            kappa = np.linalg.cond(oracle.condensed_matrix(g, kv).toarray())
+            err = np.max(np.abs(x - ref)) / np.max(np.abs(ref))
+            assert err <= 10 * L.n * kappa * EPS, (name, err, kappa)
+        # a second factorization and solve of the same values is bit-identical
+        assert ch.factor(kd) == -1
+        x2 = torch.full_like(xd, float("nan"))
+        ch.solve(bd, x2)
+        torch.cuda.synchronize()
+        assert np.array_equal(x.view(np.uint64), x2.cpu().numpy().view(np.uint64))
+
+
+@pytest.mark.parametrize("idx", [0, 1, 3])
+def test_nonconvex_case_fails_the_pivot_test(dev, acopf, idx):
+    name, make = CASES[idx]
+    g = make()
+    kv = _oracle_kvals(g, 60 + idx, 50.0, 0.0, 0.0)
+    assert not oracle.is_positive_definite(g, kv), "the case must be indefinite"
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        assert ch.factor(gu.t64(torch, kv, dev)) >= 0, name
+        z = torch.zeros(m.n, dtype=torch.float64, device=dev)
+        with pytest.raises(acopf.AcopfError) as e:
+            ch.solve(z, torch.empty_like(z))
+        assert e.value.status == acopf.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("workload", ["10kbus", "10kbus-geo"])
+def test_chain_at_full_size(dev, acopf, workload):
+    g = synth.workload_grid(workload)
+    L = oracle.layout(g)
+    pt = synth.make_point(g, 70)
+    sx, ss = _sigmas(L, 71)
+    dw = 1e-4
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        out = gu.alloc_outputs(torch, m, dev)
+        acopf.eval_assemble(m, gu.t64(torch, pt.x, dev), torch.zeros(L.m, dtype=torch.float64,
+                                                                      device=dev),
+                            1.0, gu.t64(torch, sx, dev), gu.t64(torch, ss, dev), dw, 0.0,
+                            out["f"], out["grad"], out["cons"], out["jac"], out["hess"],
+                            out["kkt"])
+        assert ch.factor(out["kkt"]) == -1
+        b = np.random.default_rng(72).standard_normal(L.n)
+        xd = torch.full((L.n,), float("nan"), dtype=torch.float64, device=dev)
+        ch.solve(gu.t64(torch, b, dev), xd)
+        torch.cuda.synchronize()
+        x = xd.cpu().numpy()
+        H = oracle.hessian(g, pt.x, np.zeros(L.m), 1.0)[0]
+        J = oracle.jacobian(g, pt.x)[0]
+        kv, _ = oracle.condensed_kkt(g, H, J, sx, ss, dw, 0.0)
+        assert oracle.backward_error(g, kv, x, b) <= 1e-13
+        # a negative diagonal entry: never positive definite
+        rp, _ = m.kkt_structure()
+        bad = out["kkt"].clone()
+        bad[int(rp[L.n // 2 + 1]) - 1] = -1.0
+        assert ch.factor(bad) >= 0
+        assert ch.factor(out["kkt"]) == -1
+        info = ch.info()
+        assert info["nnz_full"] == 2 * int(rp[-1]) - L.n and info["device_bytes"] > 0
+        assert info["nnz_factor"] >= int(rp[-1]) and info["factor_flops"] > info["nnz_factor"]
+        assert 1 <= info["max_col"] <= L.n
+
+
+def test_chol_rejects_bad_arguments(dev, acopf):
+    g = synth.workload_grid("30bus")
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        z = torch.zeros(m.nnz_kkt, dtype=torch.float64, device=dev)
+        with pytest.raises(acopf.AcopfError) as e:
+            ch.factor(z, pivot_tol=-1.0)
+        assert e.value.status == acopf.E_INVALID_ARG
+        with pytest.raises(acopf.AcopfError) as e:
+            ch.factor(None)
+        assert e.value.status == acopf.E_INVALID_ARG
+        with pytest.raises(acopf.AcopfError) as e:  # nothing factored yet
+            ch.solve(z, z)
+        assert e.value.status == acopf.E_INVALID_ARG
+
+
+def _symbolic_nnz(K):
+    """Entries of the Cholesky factor of the pattern of K (dense boolean
+    elimination: column j's pattern merges into every later column it
+    touches)."""
+    S = K != 0
+    n = S.shape[0]
+    nnz = 0
+    for j in range(n):
+        rows = np.flatnonzero(S[j + 1:, j]) + j + 1
+        nnz += 1 + rows.size
+        if rows.size:
+            S[np.ix_(rows, rows)] = True
+    return nnz
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2])
+def test_symbolic_counts_and_permutation(dev, acopf, idx):
+    """The order is a permutation, and nnz(L) of the library's symbolic count
+    equals a dense structural elimination of P M_cond P'."""
+    name, make = CASES[idx]
+    g = make()
+    L = oracle.layout(g)
+    kv = _oracle_kvals(g, 80 + idx, 0.0, 1e-4, 0.0)
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        p = ch.permutation()
+        assert np.array_equal(np.sort(p), np.arange(L.n))
+        K = oracle.condensed_matrix(g, np.ones_like(kv)).toarray()[np.ix_(p, p)]
+        info = ch.info()
+        assert info["nnz_factor"] == _symbolic_nnz(K), name
+        stats = acopf.chol_analyze(m)
+        assert stats == {k: info[k] for k in stats}
