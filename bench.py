@@ -508,13 +508,13 @@ def run_step_bench(args, local):
 
 
 def run_chol_bench(args, local):
-    """Sparse Cholesky of M_cond (acopf_chol_*) on the 10,000- and 80,000-bus
-    workloads, random and near-planar: the host symbolic phase once, then the
-    numeric factorization
-    (value gather, library factorization, pivot test, which returns to the
-    host) and the solve (permutation, two triangular solves, permutation
-    back), M_cond assembled by the library at a convex point (no constraint
-    multipliers, delta_w = 1e-4, so positive definite)."""
+    """Sparse Cholesky of M_cond (acopf_chol_*) on the near-planar 10,000- and
+    80,000-bus workloads: the host symbolic phase once, then the numeric
+    factorization (zeroing and assembly of the supernodal blocks, one launch
+    per level of the supernodal tree, the pivot test returned to the host)
+    and the solve (permutation, forward and backward level sweeps,
+    permutation back), M_cond assembled by the library at a convex point (no
+    constraint multipliers, delta_w = 1e-4: positive definite)."""
     import time
 
     import torch
@@ -524,7 +524,7 @@ def run_chol_bench(args, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {}
-    for name, factor in (("10kbus", True), ("10kbus-geo", True)):
+    for name in ("10kbus-geo", "80kbus-geo"):
         grid = synth.workload_grid(name)
         model = acopf.model_create(grid, local)
         n, m = model.n, model.m
@@ -544,21 +544,13 @@ def run_chol_bench(args, local):
                                 bufs["g"], bufs["c"], bufs["j"], bufs["h"], bufs["k"],
                                 stream=stream)
         stream.synchronize()
-        stats = acopf.chol_analyze(model)
-        if not factor:
-            # the library's analysis returns an error on this pattern (its
-            # random chords give separators of linear size): symbolic counts only
-            out[name] = {**stats, "factor_gflop": stats["factor_flops"] / 1e9,
-                         "factorized": False}
-            model.close()
-            continue
         t0 = time.perf_counter()
         ch = acopf.chol_create(model)
         create_s = time.perf_counter() - t0
         info = ch.info()
         for _ in range(3):
             assert ch.factor(bufs["k"], stream=stream) == -1
-        reps = 10
+        reps = 20
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -578,13 +570,14 @@ def run_chol_bench(args, local):
         solve_ms = e0.elapsed_time(e1) / 50
         ch.close()
         model.close()
-        out[name] = {"n": n, "nnz_lower": int(model.nnz_kkt), "nnz_factor": info["nnz_factor"],
-                     "factor_gflop": info["factor_flops"] / 1e9, "max_col": info["max_col"],
-                     "symbolic_s": create_s, "factor_ms": factor_ms,
+        out[name] = {**{k: info[k] for k in ("n", "nnz_factor", "max_col", "n_supernodes",
+                                             "n_levels", "storage")},
+                     "factor_gflop": info["factor_flops"] / 1e9, "symbolic_s": create_s,
+                     "factor_ms": factor_ms,
                      "factor_gflops": info["factor_flops"] / (factor_ms * 1e-3) / 1e9,
-                     "solve_ms": solve_ms,
-                     "solve_gbs_L_twice": 2 * 12 * info["nnz_factor"] / (solve_ms * 1e-3) / 1e9,
-                     "device_bytes": info["device_bytes"]}
+                     "solve_ms": solve_ms, "device_bytes": info["device_bytes"],
+                     "launches": {"factor": info["n_levels"] + 1,
+                                  "solve": 2 * info["n_levels"] + 2}}
     out["timing"] = ("factor: host wall clock per call (each call returns the pivot test to the "
                      "host); solve: CUDA events over 50 calls")
     return out

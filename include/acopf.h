@@ -280,61 +280,67 @@ acopf_status acopf_kkt_residual(acopf_model* model, const acopf_iterate* it, con
  * of the assembled matrix).  Sec. IV.C: M_aug has the inertia (n + m, 0, m)
  * exactly when M_cond is positive definite, so a factorization that meets a
  * non-positive pivot is the inertia test that raises (delta_w, delta_c);
- * Sec. V factorizes with an AMD order fixed once per pattern and refactors
- * numerically every iteration.
- * acopf_chol_create: host symbolic phase, once per model (the full
- * symmetric pattern of M_cond, its approximate-minimum-degree order, the
- * permuted pattern and the library's symbolic analysis); synchronises; the
- * object holds about 24 bytes per entry of the full pattern plus the
- * factor's storage (acopf_chol_info).  ACOPF_E_NO_DEVICE for a host-only
- * model.  The object refers to the model, which must outlive it.
+ * Sec. V factorizes with a fill-reducing order fixed once per pattern and
+ * refactors numerically every iteration.
+ *
+ * Symbolic phase (host, once per chol object): a minimum-degree order P of
+ * M_cond's pattern (exact degrees on the elimination graph), the
+ * elimination tree in postorder, fundamental supernodes (at most 64
+ * columns), the row structure of each supernode and its place in its
+ * parent's.  The numeric factorization (multifrontal: each supernode adds
+ * its children's update matrices, factors its panel and forms its own
+ * update matrix) and the solves are this library's kernels: one launch per
+ * level of the supernodal elimination tree (leaves first), one thread block
+ * per supernode, fixed summation order (bit-reproducible).
+ *
+ * acopf_chol_create: the symbolic phase and the device copies of its
+ * arrays plus the factor's storage (acopf_chol_info's device_bytes);
+ * synchronises.  ACOPF_E_NO_DEVICE for a host-only model; ACOPF_E_INVALID_ARG
+ * when the elimination graph outgrows 2^28 entries (a pattern whose fill
+ * is beyond a sparse factorization).  The object refers to the model,
+ * which must outlive it.
  * acopf_chol_factor: kvals is the DEVICE lower-CSR value array of M_cond
  * (acopf_eval_assemble's kvals, acopf_kkt_structure's order).  Factorizes
- * P M_cond P' = L L' on `stream` and applies the library's zero-pivot test
- * (a pivot that is negative or at most pivot_tol fails; the factorization
- * of an indefinite matrix runs to its end and records the first failure);
+ * P M_cond P' = L L' on `stream`; a pivot (the diagonal entry before its
+ * square root) that is not above pivot_tol, or is NaN, fails; the
+ * factorization continues past it with the pivot replaced by 1.
  * *first_bad_pivot (HOST) receives -1 when every pivot passes (M_cond
- * positive definite), else the position of the first failing pivot in the
- * library's factorization order (which may refine P).  Synchronises
- * `stream` to return the test.  pivot_tol finite and >= 0, else
- * ACOPF_E_INVALID_ARG.
+ * positive definite), else the smallest failing column in the order P.
+ * Synchronises `stream` to return the test.  pivot_tol finite and >= 0,
+ * else ACOPF_E_INVALID_ARG.
  * acopf_chol_solve: x = M_cond^-1 b with the last factorization (DEVICE b,
- * x of n doubles; b and x may not alias); asynchronous on `stream`;
+ * x of n doubles; they may alias); asynchronous on `stream`;
  * ACOPF_E_INVALID_ARG unless the last factorization passed the test.
- * Calls on one object use its scratch: they must not overlap on the GPU.
- * The factorization and the triangular solves are a library call
- * (cuSOLVER's sparse Cholesky), as in the paper; the value gather and the
- * permutations are this library's kernels. */
+ * Calls on one object use its scratch: they must not overlap on the GPU. */
 typedef struct acopf_chol acopf_chol;
 acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out);
 acopf_status acopf_chol_destroy(acopf_chol* chol);
 acopf_status acopf_chol_factor(acopf_chol* chol, const double* kvals, double pivot_tol,
                                int32_t* first_bad_pivot, acopf_stream stream);
 acopf_status acopf_chol_solve(acopf_chol* chol, const double* b, double* x, acopf_stream stream);
-/* Symbolic counts of the factorization of M_cond in the AMD order P, from
- * this library's symbolic phase (elimination tree and column counts of
- * P M_cond P'): nnz_full, the entries of the full symmetric pattern;
- * nnz_factor, the entries of L (diagonal included); max_col, the entries of
- * L's largest column; factor_flops, the flops of one numeric factorization
- * (per column with c off-diagonal entries: 1 square root, c divisions and
- * c (c + 1) / 2 multiply-adds).  The library that factorizes may reorder
- * further; its own storage is acopf_chol_info's device_bytes. */
+/* Counts of the symbolic phase: nnz_full, the entries of M_cond's full
+ * symmetric pattern; nnz_factor, the entries of L (diagonal included);
+ * max_col, the entries of L's largest column; factor_flops, the flops of
+ * one numeric factorization (per column with c off-diagonal entries: 1
+ * square root, c divisions and c (c + 1) / 2 multiply-adds); n_supernodes;
+ * n_levels of the supernodal tree (launches per factorization, and per
+ * direction of a solve); storage, the doubles of the supernodal blocks;
+ * update_storage, the doubles of the children's update matrices and
+ * vectors the multifrontal factorization and solves pass up the tree. */
 typedef struct {
   int64_t n, nnz_full, nnz_factor, max_col;
   double factor_flops;
+  int64_t n_supernodes, n_levels;
+  int64_t storage, update_storage;
 } acopf_chol_stats;
-/* stats and device_bytes (the library's storage for the factor plus its
- * workspace) may each be NULL. */
+/* stats and device_bytes (all device memory of the object) may be NULL. */
 acopf_status acopf_chol_info(const acopf_chol* chol, acopf_chol_stats* stats,
                              int64_t* device_bytes);
-/* The symbolic phase alone (host work; the ordering routine needs the
- * model's device to be usable): the counts of a factorization of the
- * model's M_cond without creating one.  ACOPF_E_NO_DEVICE for a host-only
- * model. */
-acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats);
-/* The fill-reducing order: perm (HOST, n entries) receives P as the list
- * of M_cond's rows in factorization order (row i of P M_cond P' is row
- * perm[i] of M_cond). */
+/* The symbolic phase alone, on the host (host-only models included): its
+ * counts and, when perm is not NULL, the order (HOST, n entries: row i of
+ * P M_cond P' is row perm[i] of M_cond). */
+acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats, int32_t* perm);
+/* The order of a chol object, as acopf_chol_analyze's perm. */
 acopf_status acopf_chol_permutation(const acopf_chol* chol, int32_t* perm);
 
 /* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of

@@ -185,14 +185,16 @@ _chol_solve = _sig("acopf_chol_solve", C.c_int32, _vp, _vp, _vp, _vp)
 
 class CholStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_full", C.c_int64), ("nnz_factor", C.c_int64),
-                ("max_col", C.c_int64), ("factor_flops", C.c_double)]
+                ("max_col", C.c_int64), ("factor_flops", C.c_double),
+                ("n_supernodes", C.c_int64), ("n_levels", C.c_int64), ("storage", C.c_int64),
+                ("update_storage", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _chol_info = _sig("acopf_chol_info", C.c_int32, _vp, C.POINTER(CholStats), C.POINTER(C.c_int64))
-_chol_analyze = _sig("acopf_chol_analyze", C.c_int32, _vp, C.POINTER(CholStats))
+_chol_analyze = _sig("acopf_chol_analyze", C.c_int32, _vp, C.POINTER(CholStats), _vp)
 _chol_permutation = _sig("acopf_chol_permutation", C.c_int32, _vp, _vp)
 
 # Exported symbols the header declares (checked by the CPU tests).
@@ -747,8 +749,8 @@ class Chol:
         _check(_chol_solve(self._h, _ptr(b), _ptr(x), _stream(stream)), "acopf_chol_solve")
 
     def info(self) -> dict:
-        """The symbolic counts (CholStats fields) and device_bytes (the
-        library's factor and workspace)."""
+        """The symbolic counts (CholStats fields) and device_bytes (all
+        device memory of the object)."""
         st, nbytes = CholStats(), C.c_int64(0)
         _check(_chol_info(self._h, C.byref(st), C.byref(nbytes)), "acopf_chol_info")
         return {**st.as_dict(), "device_bytes": nbytes.value}
@@ -781,8 +783,11 @@ def chol_create(model: Model) -> Chol:
     return Chol(model)
 
 
-def chol_analyze(model: Model) -> dict:
-    """Symbolic counts of a factorization of the model's M_cond."""
+def chol_analyze(model: Model, with_perm: bool = False):
+    """Symbolic counts of a factorization of the model's M_cond (a dict);
+    with_perm: also the order (dict, perm)."""
     st = CholStats()
-    _check(_chol_analyze(model.handle, C.byref(st)), "acopf_chol_analyze")
-    return st.as_dict()
+    perm = np.empty(model.n, dtype=np.int32) if with_perm else None
+    _check(_chol_analyze(model.handle, C.byref(st), None if perm is None else perm.ctypes.data),
+           "acopf_chol_analyze")
+    return (st.as_dict(), perm) if with_perm else st.as_dict()

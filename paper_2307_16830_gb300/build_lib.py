@@ -18,9 +18,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libacopf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "stepapi.cpp",
-           "cholapi.cpp", "kernels.cu", "step.cu", "chol.cu", "noalloc.cu"]
-# the sparse Cholesky factorization of M_cond is cuSOLVER's
-LIBS = ["-lcusolver", "-lcusparse"]
+           "cholapi.cpp", "symbolic.cpp", "kernels.cu", "step.cu", "chol.cu", "noalloc.cu"]
+LIBS: list[str] = []
 
 
 def nvcc() -> str:

@@ -202,11 +202,6 @@ cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const doubl
                            double* dzl_x, double* dzu_x, double* dzl_s, double* dzu_s,
                            cudaStream_t s);
 
-// Sparse Cholesky support (chol.cu): out[t] = in[idx[t]]; out[idx[t]] = in[t].
-cudaError_t launch_gather(double* out, const double* in, const int32_t* idx, int n,
-                          cudaStream_t s);
-cudaError_t launch_scatter(double* out, const double* in, const int32_t* idx, int n,
-                           cudaStream_t s);
 
 // Launchers (kernels.cu).  Each returns the CUDA error of its launches.
 // `mid`, when not null, is recorded between the two phases (phase 2 then

@@ -1,15 +1,30 @@
-// Kernels around the sparse Cholesky factorization of M_cond: the value
-// gather from the lower CSR of the assembled matrix into the permuted full
-// pattern the factorization reads, and the symmetric permutation of
-// right-hand sides and solutions.
-#include "acopf_internal.h"
+// Numeric sparse Cholesky factorization of M_cond and solves with it.
+//
+// The factor L of P M_cond P' is stored in supernodes (dense column-major
+// blocks, see symbolic.h).  The factorization is multifrontal and runs the
+// supernodal elimination tree level by level, leaves first: one block per
+// supernode of a level (1) adds its children's update matrices into its
+// panel and its own update matrix (extend-add, one child after the other),
+// (2) factors its panel: a dense Cholesky of the diagonal block and the
+// scaled rows below it, and (3) subtracts L21 L21' from its update matrix,
+// which its parent adds in turn.  A pivot that is not above the tolerance
+// (or is NaN) is recorded (the smallest column, so the result does not
+// depend on the schedule) and replaced by 1 so the arithmetic stays finite;
+// the factorization then counts as failed.  The forward solve passes update
+// vectors up the tree the same way; the backward solve runs the levels root
+// first, each supernode reading its ancestors' solved entries.  Every sum
+// has a fixed order: results are bit-reproducible.
+#include "chol_internal.h"
+
+#include <algorithm>
 
 namespace acopf {
 namespace {
 
+constexpr int kCholThreads = 256;
+constexpr int kMaxWidth = kCholMaxWidth;
 constexpr int kPermThreads = 256;
 
-// out[t] = in[idx[t]]
 __global__ void __launch_bounds__(kPermThreads) k_gather(double* __restrict__ out,
                                                          const double* __restrict__ in,
                                                          const int32_t* __restrict__ idx, int n) {
@@ -17,7 +32,6 @@ __global__ void __launch_bounds__(kPermThreads) k_gather(double* __restrict__ ou
     out[t] = in[__ldg(idx + t)];
 }
 
-// out[idx[t]] = in[t]  (idx a permutation)
 __global__ void __launch_bounds__(kPermThreads) k_scatter(double* __restrict__ out,
                                                           const double* __restrict__ in,
                                                           const int32_t* __restrict__ idx, int n) {
@@ -25,21 +39,331 @@ __global__ void __launch_bounds__(kPermThreads) k_scatter(double* __restrict__ o
     out[__ldg(idx + t)] = in[t];
 }
 
-int perm_grid(int n) { return n > 0 ? min(ceil_div(n, kPermThreads), 4096) : 0; }
+// Lx[amap[k]] = kvals[k] (Lx zeroed before)
+__global__ void __launch_bounds__(kPermThreads) k_chol_assemble(double* __restrict__ Lx,
+                                                                const int64_t* __restrict__ amap,
+                                                                const double* __restrict__ kvals,
+                                                                int64_t nnz) {
+  for (int64_t k = int64_t(blockIdx.x) * kPermThreads + threadIdx.x; k < nnz;
+       k += int64_t(gridDim.x) * kPermThreads)
+    Lx[__ldg(amap + k)] = kvals[k];
+}
+
+// A supernode is handled by a group of NT threads: a whole block (NT =
+// kCholThreads) for the large supernodes of a level, one warp (NT = 32) for
+// the small ones.
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NT == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+// The panel of supernode t after its children's contributions: column by
+// column (every thread takes the same pivot), P of leading dimension h.
+template <int NT>
+__device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int tid, double tol,
+                             int32_t* bad) {
+  for (int k = 0; k < w; ++k) {
+    double p = P[size_t(k) * h + k];
+    if (!(p > tol)) {
+      if (tid == 0) atomicMin(bad, f + k);
+      p = 1.0;
+    }
+    const double r = sqrt(p);
+    group_sync<NT>();
+    if (tid == 0) P[size_t(k) * h + k] = r;
+    for (int i = k + 1 + tid; i < h; i += NT) P[size_t(k) * h + i] /= r;
+    group_sync<NT>();
+    const int mm = h - k - 1, cc = w - k - 1;  // trailing rows k+1.., columns k+1..w-1
+    for (int idx = tid; idx < mm * cc; idx += NT) {
+      const int jj = idx / mm, ii = idx - jj * mm;
+      const int j = k + 1 + jj, i = k + 1 + ii;
+      if (i < j) continue;
+      P[size_t(j) * h + i] -= P[size_t(k) * h + i] * P[size_t(k) * h + j];
+    }
+    group_sync<NT>();
+  }
+}
+
+// Extend-add of t's children's update matrices, one child at a time: the
+// entries in t's columns go to the panel P (leading dimension h), the rest
+// to t's update matrix.
+template <int NT>
+__device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict__ P, int h,
+                           int w, double* __restrict__ Ut) {
+  const int m = h - w;
+  for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
+    const int c = __ldg(d.kid + q);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
+    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+    for (int idx = tid; idx < mc * mc; idx += NT) {
+      const int jj = idx / mc, ii = idx - jj * mc;
+      if (ii < jj) continue;
+      const double v = Uc[idx];
+      const int ri = __ldg(rel + ii), rj = __ldg(rel + jj);
+      if (rj < w)
+        P[size_t(rj) * h + ri] += v;
+      else
+        Ut[size_t(rj - w) * m + (ri - w)] += v;
+    }
+    group_sync<NT>();
+  }
+}
+
+// A small supernode, whole, by one warp: children, panel, own update matrix.
+__device__ void factor_small(const CholDev& d, int t, int lane, double tol) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+  double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
+  extend_add<32>(d, t, lane, Lt, h, w, Ut);
+  factor_panel<32>(Lt, h, w, f, lane, tol, d.bad);
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int j = idx / m, i = idx - j * m;
+    if (i < j) continue;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(Lt[size_t(k) * h + w + i], Lt[size_t(k) * h + w + j], acc);
+    Ut[idx] -= acc;
+  }
+}
+
+// A large supernode by a whole block: children and panel, the panel staged
+// in shared memory when it fits (`staged` doubles); its update matrix is
+// formed afterwards by k_chol_syrk.
+__device__ void factor_large(const CholDev& d, int t, double tol, double* __restrict__ sp,
+                             int staged) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t);
+  double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
+  const bool in_smem = h * w <= staged;
+  double* __restrict__ P = in_smem ? sp : Lt;
+  if (in_smem) {
+    for (int idx = threadIdx.x; idx < h * w; idx += kCholThreads) sp[idx] = Lt[idx];
+    __syncthreads();
+  }
+  extend_add<kCholThreads>(d, t, threadIdx.x, P, h, w, Ut);
+  factor_panel<kCholThreads>(P, h, w, f, threadIdx.x, tol, d.bad);
+  if (in_smem)
+    for (int idx = threadIdx.x; idx < h * w; idx += kCholThreads) Lt[idx] = sp[idx];
+}
+
+// Forward substitution of one supernode: the children's update vectors,
+// the diagonal block, then its own update vector z_t -= L21 y_t.
+template <int NT>
+__device__ void forward_supernode(const CholDev& d, int t, int tid, double* __restrict__ y) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
+  for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
+    const int c = __ldg(d.kid + q);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const double* __restrict__ zc = d.Zx + __ldg(d.z_off + c);
+    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+    for (int ii = tid; ii < mc; ii += NT) {
+      const int r = __ldg(rel + ii);
+      if (r < w)
+        y[f + r] += zc[ii];
+      else
+        zt[r - w] += zc[ii];
+    }
+    group_sync<NT>();
+  }
+  for (int k = 0; k < w; ++k) {
+    const double yk = y[f + k] / Lt[size_t(k) * h + k];
+    group_sync<NT>();
+    if (tid == 0) y[f + k] = yk;
+    for (int i = k + 1 + tid; i < w; i += NT) y[f + i] -= Lt[size_t(k) * h + i] * yk;
+    group_sync<NT>();
+  }
+  for (int i = tid; i < m; i += NT) {
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(Lt[size_t(k) * h + w + i], y[f + k], acc);
+    zt[i] -= acc;
+  }
+}
+
+// Backward substitution of one supernode: x_t -= L21' x(R_t below) (one
+// warp per column, a fixed reduction tree), then the transposed diagonal
+// block.
+template <int NT>
+__device__ void backward_supernode(const CholDev& d, int t, int tid, double* __restrict__ x) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  const int lane = tid & 31;
+  for (int k = tid >> 5; k < w; k += NT / 32) {
+    double acc = 0.0;
+    for (int i = w + lane; i < h; i += 32)
+      acc = fma(Lt[size_t(k) * h + i], x[__ldg(d.rowidx + r0 + i)], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[f + k] -= acc;
+  }
+  group_sync<NT>();
+  for (int k = w - 1; k >= 0; --k) {
+    const double xk = x[f + k] / Lt[size_t(k) * h + k];
+    group_sync<NT>();
+    if (tid == 0) x[f + k] = xk;
+    for (int i = tid; i < k; i += NT) x[f + i] -= Lt[size_t(i) * h + k] * xk;
+    group_sync<NT>();
+  }
+}
+
+// One level: blocks [0, n_large) take the level's first n_large supernodes
+// one per block; the remaining blocks take the rest one per warp.
+constexpr int kWarpsPerBlock = kCholThreads / 32;
+
+__device__ __forceinline__ int level_item(int n_large, int count, int& tid, bool& whole) {
+  if (int(blockIdx.x) < n_large) {
+    whole = true;
+    tid = threadIdx.x;
+    return blockIdx.x;
+  }
+  whole = false;
+  tid = threadIdx.x & 31;
+  const int q = n_large + (int(blockIdx.x) - n_large) * kWarpsPerBlock + int(threadIdx.x >> 5);
+  return q < count ? q : -1;
+}
+
+__global__ void __launch_bounds__(kCholThreads) k_chol_factor(CholDev d, int begin, int count,
+                                                               int n_large, double tol,
+                                                               int staged) {
+  extern __shared__ double sp[];
+  int tid;
+  bool whole;
+  const int q = level_item(n_large, count, tid, whole);
+  if (q < 0) return;
+  const int t = __ldg(d.level_sn + begin + q);
+  if (whole)
+    factor_large(d, t, tol, sp, staged);
+  else
+    factor_small(d, t, tid, tol);
+}
+
+// U_t -= L21 L21' for the large supernodes of a level, one 32 x 32 tile of
+// U_t per block: tiles[i] = {t, tile row, tile column, 0}, lower tiles only.
+constexpr int kTile = 32;
+__global__ void __launch_bounds__(kCholThreads) k_chol_syrk(CholDev d, const int4* __restrict__ tiles,
+                                                             int begin) {
+  __shared__ double A[kTile][kMaxWidth + 1], B[kTile][kMaxWidth + 1];
+  const int4 tl = __ldg(tiles + begin + blockIdx.x);
+  const int t = tl.x;
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+  const double* __restrict__ L21 = d.Lx + __ldg(d.sn_off + t) + w;  // column k at L21[k h]
+  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
+  const int i0 = tl.y * kTile, j0 = tl.z * kTile;
+  for (int idx = threadIdx.x; idx < kTile * w; idx += kCholThreads) {
+    const int r = idx % kTile, k = idx / kTile;
+    A[r][k] = i0 + r < m ? L21[size_t(k) * h + i0 + r] : 0.0;
+    B[r][k] = j0 + r < m ? L21[size_t(k) * h + j0 + r] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x % kTile, r0 = threadIdx.x / kTile;
+  const int j = j0 + c;
+  for (int r = r0; r < kTile; r += kCholThreads / kTile) {
+    const int i = i0 + r;
+    if (i >= m || j >= m || i < j) continue;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(A[r][k], B[c][k], acc);
+    Ut[size_t(j) * m + i] -= acc;
+  }
+}
+
+__global__ void __launch_bounds__(kCholThreads) k_chol_fwd(CholDev d, int begin, int count,
+                                                            int n_large, double* __restrict__ y) {
+  int tid;
+  bool whole;
+  const int q = level_item(n_large, count, tid, whole);
+  if (q < 0) return;
+  const int t = __ldg(d.level_sn + begin + q);
+  if (whole)
+    forward_supernode<kCholThreads>(d, t, tid, y);
+  else
+    forward_supernode<32>(d, t, tid, y);
+}
+
+__global__ void __launch_bounds__(kCholThreads) k_chol_bwd(CholDev d, int begin, int count,
+                                                            int n_large, double* __restrict__ x) {
+  int tid;
+  bool whole;
+  const int q = level_item(n_large, count, tid, whole);
+  if (q < 0) return;
+  const int t = __ldg(d.level_sn + begin + q);
+  if (whole)
+    backward_supernode<kCholThreads>(d, t, tid, x);
+  else
+    backward_supernode<32>(d, t, tid, x);
+}
+
+int level_blocks(int count, int n_large) {
+  return n_large + (count - n_large + kWarpsPerBlock - 1) / kWarpsPerBlock;
+}
+
+int grid_for(int64_t n, int threads) {
+  return n > 0 ? int(std::min<int64_t>((n + threads - 1) / threads, 4096)) : 0;
+}
 
 }  // namespace
 
 cudaError_t launch_gather(double* out, const double* in, const int32_t* idx, int n,
                           cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather<<<perm_grid(n), kPermThreads, 0, s>>>(out, in, idx, n);
+  k_gather<<<grid_for(n, kPermThreads), kPermThreads, 0, s>>>(out, in, idx, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(double* out, const double* in, const int32_t* idx, int n,
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_scatter<<<perm_grid(n), kPermThreads, 0, s>>>(out, in, idx, n);
+  k_scatter<<<grid_for(n, kPermThreads), kPermThreads, 0, s>>>(out, in, idx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_assemble(double* Lx, const int64_t* amap, const double* kvals,
+                                 int64_t nnz, cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  k_chol_assemble<<<grid_for(nnz, kPermThreads), kPermThreads, 0, s>>>(Lx, amap, kvals, nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_factor_level(const CholDev& d, int begin, int count, int n_large,
+                                     double tol, int staged, const int4* tiles, int tile_begin,
+                                     int n_tiles, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = size_t(staged) * sizeof(double);
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_chol_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_chol_factor<<<level_blocks(count, n_large), kCholThreads, smem, s>>>(d, begin, count, n_large,
+                                                                          tol, staged);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && n_tiles > 0) {
+    k_chol_syrk<<<n_tiles, kCholThreads, 0, s>>>(d, tiles, tile_begin);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_chol_fwd_level(const CholDev& d, int begin, int count, int n_large, double* y,
+                                  cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_chol_fwd<<<level_blocks(count, n_large), kCholThreads, 0, s>>>(d, begin, count, n_large, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_bwd_level(const CholDev& d, int begin, int count, int n_large, double* x,
+                                  cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_chol_bwd<<<level_blocks(count, n_large), kCholThreads, 0, s>>>(d, begin, count, n_large, x);
   return cudaGetLastError();
 }
 
