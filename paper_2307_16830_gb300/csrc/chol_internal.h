@@ -33,16 +33,30 @@ cudaError_t launch_scatter(double* out, const double* in, const int32_t* idx, in
                            cudaStream_t s);
 cudaError_t launch_chol_assemble(double* Lx, const int64_t* amap, const double* kvals,
                                  int64_t nnz, cudaStream_t s);
-// Supernodes have at most this many columns.
+// Supernodes have at most this many columns; a large supernode's panel
+// (and its update matrix, when both fit) is staged in at most this many
+// doubles of shared memory.
 constexpr int kCholMaxWidth = 64;
+constexpr int kCholPanelDoubles = 20480;
+// Small supernodes (one warp each): at most this many rows and columns.
+constexpr int kCholWarpRows = 32;
+constexpr int kCholWarpCols = 8;
+// A child's rows below its columns fit a row-map scratch of this size.
+constexpr int kCholMaxRelRows = 4096;
 
-// One level of the supernodal tree: level_sn[begin .. begin + count), the
-// first n_large of them handled by a whole block each (panel staged in
-// `staged` doubles of shared memory when it fits, update matrix by the
-// tiles[tile_begin .. + n_tiles) of a second launch), the rest by a warp.
+// Supernodes level_sn[begin .. begin + count): either all by a whole block
+// each (n_large == count), with `stage` doubles of shared memory (the
+// largest block staging), or all by a warp each (n_large == 0), with
+// `stage` doubles per warp (the largest panel plus update matrix of the
+// group); then the update-matrix tiles tiles[tile_begin .. + n_tiles) in a
+// second launch.
 cudaError_t launch_chol_factor_level(const CholDev& d, int begin, int count, int n_large,
-                                     double tol, int staged, const int4* tiles, int tile_begin,
+                                     double tol, int stage, const int4* tiles, int tile_begin,
                                      int n_tiles, cudaStream_t s);
+// Dynamic shared memory of such a launch, and the opt-in that lets the
+// factor kernel use `bytes` of it (set once, before any launch or capture).
+size_t chol_factor_smem_bytes(int count, int n_large, int stage);
+cudaError_t chol_allow_smem(size_t bytes);
 cudaError_t launch_chol_fwd_level(const CholDev& d, int begin, int count, int n_large, double* y,
                                   cudaStream_t s);
 cudaError_t launch_chol_bwd_level(const CholDev& d, int begin, int count, int n_large, double* x,

@@ -22,7 +22,12 @@
 #include "symbolic.h"
 
 static_assert(acopf::kMaxSupernodeWidth == acopf::kCholMaxWidth,
-              "the syrk tiles hold a supernode's full width");
+              "the syrk tiles and solve staging hold a supernode's full width");
+static_assert(acopf::kPanelSmemDoubles == acopf::kCholPanelDoubles &&
+                  acopf::kWarpMaxRows == acopf::kCholWarpRows &&
+                  acopf::kWarpMaxCols == acopf::kCholWarpCols &&
+                  acopf::kMaxRowsBelow == acopf::kCholMaxRelRows,
+              "host and kernels agree on what is staged in shared memory");
 
 using acopf::cuda_fail;
 using acopf::DeviceScope;
@@ -34,6 +39,7 @@ struct acopf_chol {
   int64_t nnz_low = 0;
   acopf_chol_stats stats{};
   std::vector<int32_t> perm_host, level_ptr, level_large, level_smem, tile_ptr;
+  std::vector<int32_t> level_big, level_smem_big, level_small_stage;
   const int4* tiles = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -44,11 +50,19 @@ struct acopf_chol {
   size_t u_doubles = 0, z_doubles = 0;  // update matrices / vectors
   int32_t* bad_host = nullptr;  // page-locked copy of dev.bad
   bool factored = false;
+  // the factorization's and the solve's launch sequences, captured as CUDA
+  // graphs for the last arguments they ran with
+  cudaGraphExec_t factor_exec = nullptr, solve_exec = nullptr;
+  const void* factor_key = nullptr;
+  double factor_tol = -1.0;
+  const void *solve_b = nullptr, *solve_x = nullptr;
 };
 
 namespace {
 
 void release(acopf_chol* c) {
+  if (c->factor_exec) cudaGraphExecDestroy(c->factor_exec);
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
   if (c->arena) cudaFree(c->arena);
   if (c->bad_host) cudaFreeHost(c->bad_host);
   delete c;
@@ -72,6 +86,75 @@ acopf_status run_symbolic(const acopf_model* model, acopf::CholSymbolic& sy, con
       acopf::chol_symbolic(model->hm.L.n, model->hm.krowptr, model->hm.kcolind, sy, err);
   if (st != ACOPF_OK) return fail(st, std::string(where) + ": " + err);
   return ACOPF_OK;
+}
+
+// The factorization's device work: zeroed blocks, the assembly of M_cond's
+// values, and per level the big, the other block-handled and the small
+// supernodes, then the update-matrix tiles.
+cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double tol,
+                          cudaStream_t s) {
+  const acopf::CholDev& d = chol->dev;
+  cudaError_t e = cudaMemsetAsync(d.Lx, 0, size_t(chol->stats.storage) * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.Ux, 0, chol->u_doubles * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.bad, 0x7f, sizeof(int32_t), s);  // 0x7f7f7f7f: none
+  if (e == cudaSuccess) e = acopf::launch_chol_assemble(d.Lx, chol->amap, kvals, chol->nnz_low, s);
+  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large, &tp = chol->tile_ptr;
+  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v) {
+    const int32_t nb = chol->level_big[v], nl = ll[v], cnt = lp[v + 1] - lp[v];
+    if (nb > 0)
+      e = acopf::launch_chol_factor_level(d, lp[v], nb, nb, tol, chol->level_smem_big[v],
+                                          chol->tiles, 0, 0, s);
+    if (e == cudaSuccess && nl > nb)
+      e = acopf::launch_chol_factor_level(d, lp[v] + nb, nl - nb, nl - nb, tol,
+                                          chol->level_smem[v], chol->tiles, 0, 0, s);
+    if (e == cudaSuccess)
+      e = acopf::launch_chol_factor_level(d, lp[v] + nl, cnt - nl, 0, tol,
+                                          chol->level_small_stage[v], chol->tiles, tp[v],
+                                          tp[v + 1] - tp[v], s);
+  }
+  return e;
+}
+
+// The solve's device work: permutation, forward levels, backward levels,
+// permutation back.
+cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cudaStream_t s) {
+  const acopf::CholDev& d = chol->dev;
+  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large;
+  cudaError_t e = acopf::launch_gather(chol->work, b, chol->perm, chol->n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.Zx, 0, chol->z_doubles * sizeof(double), s);
+  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v)
+    e = acopf::launch_chol_fwd_level(d, lp[v], lp[v + 1] - lp[v], ll[v], chol->work, s);
+  for (size_t v = lp.size() - 1; e == cudaSuccess && v > 0; --v)
+    e = acopf::launch_chol_bwd_level(d, lp[v - 1], lp[v] - lp[v - 1], ll[v - 1], chol->work, s);
+  if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
+  return e;
+}
+
+// Runs `record` on `s`: through a CUDA graph captured for the current
+// arguments (re-captured when they change), or directly on the legacy
+// default stream, which cannot be captured.
+template <typename Record>
+cudaError_t run_recorded(cudaGraphExec_t& exec, bool reuse, cudaStream_t s, Record record) {
+  if (s == nullptr || s == cudaStreamLegacy) return record(s);
+  if (!(reuse && exec)) {
+    if (exec) {
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t er = record(s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (er != cudaSuccess) e = er;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      exec = nullptr;
+      return e;
+    }
+  }
+  return cudaGraphLaunch(exec, s);
 }
 
 }  // namespace
@@ -111,6 +194,9 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     c->level_ptr = sy.level_ptr;
     c->level_large = sy.level_large;
     c->level_smem = sy.level_smem;
+    c->level_big = sy.level_big;
+    c->level_smem_big = sy.level_smem_big;
+    c->level_small_stage = sy.level_small_stage;
     c->tile_ptr = sy.tile_ptr;
   } catch (const std::bad_alloc&) {
     release(c);
@@ -159,6 +245,15 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_amap, sy.amap.data(), sy.amap.size() * 8);
   up(o_perm, sy.perm.data(), n * 4);
   if (e == cudaSuccess) e = cudaMallocHost(&c->bad_host, sizeof(int32_t));
+  size_t smem = 0;
+  for (size_t v = 0; v + 1 < sy.level_ptr.size(); ++v) {
+    const int32_t nb = sy.level_big[v], nl = sy.level_large[v];
+    const int32_t cnt = sy.level_ptr[v + 1] - sy.level_ptr[v];
+    smem = std::max({smem, acopf::chol_factor_smem_bytes(nb, nb, sy.level_smem_big[v]),
+                     acopf::chol_factor_smem_bytes(nl - nb, nl - nb, sy.level_smem[v]),
+                     acopf::chol_factor_smem_bytes(cnt - nl, 0, sy.level_small_stage[v])});
+  }
+  if (e == cudaSuccess) e = acopf::chol_allow_smem(smem);
   if (e != cudaSuccess) {
     release(c);
     return cuda_fail(e, "acopf_chol_create: upload");
@@ -207,16 +302,12 @@ acopf_status acopf_chol_factor(acopf_chol* chol, const double* kvals, double piv
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   chol->factored = false;
   const acopf::CholDev& d = chol->dev;
-  cudaError_t e = cudaMemsetAsync(d.Lx, 0, size_t(chol->stats.storage) * sizeof(double), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.Ux, 0, chol->u_doubles * sizeof(double), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.bad, 0x7f, sizeof(int32_t), s);  // 0x7f7f7f7f: none
-  if (e == cudaSuccess) e = acopf::launch_chol_assemble(d.Lx, chol->amap, kvals, chol->nnz_low, s);
-  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large;
-  const std::vector<int32_t>& tp = chol->tile_ptr;
-  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v)
-    e = acopf::launch_chol_factor_level(d, lp[v], lp[v + 1] - lp[v], ll[v], pivot_tol,
-                                        chol->level_smem[v], chol->tiles, tp[v],
-                                        tp[v + 1] - tp[v], s);
+  const bool reuse = chol->factor_key == kvals && chol->factor_tol == pivot_tol;
+  cudaError_t e = run_recorded(chol->factor_exec, reuse, s, [&](cudaStream_t st) {
+    return record_factor(chol, kvals, pivot_tol, st);
+  });
+  chol->factor_key = chol->factor_exec ? kvals : nullptr;
+  chol->factor_tol = pivot_tol;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(chol->bad_host, d.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -235,15 +326,12 @@ acopf_status acopf_chol_solve(acopf_chol* chol, const double* b, double* x, acop
   DeviceScope ds(chol->model->device);
   if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_chol_solve");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const acopf::CholDev& d = chol->dev;
-  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large;
-  cudaError_t e = acopf::launch_gather(chol->work, b, chol->perm, chol->n, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.Zx, 0, chol->z_doubles * sizeof(double), s);
-  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v)
-    e = acopf::launch_chol_fwd_level(d, lp[v], lp[v + 1] - lp[v], ll[v], chol->work, s);
-  for (size_t v = lp.size() - 1; e == cudaSuccess && v > 0; --v)
-    e = acopf::launch_chol_bwd_level(d, lp[v - 1], lp[v] - lp[v - 1], ll[v - 1], chol->work, s);
-  if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
+  const bool reuse = chol->solve_b == b && chol->solve_x == x;
+  const cudaError_t e = run_recorded(chol->solve_exec, reuse, s, [&](cudaStream_t st) {
+    return record_solve(chol, b, x, st);
+  });
+  chol->solve_b = chol->solve_exec ? b : nullptr;
+  chol->solve_x = chol->solve_exec ? x : nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_solve");
   return ACOPF_OK;
 }

@@ -263,6 +263,16 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
       }
     }
 
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t m = (sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)]) -
+                        (sy.sn_first[size_t(s) + 1] - sy.sn_first[size_t(s)]);
+      if (m > kMaxRowsBelow) {
+        err = "a supernode has " + std::to_string(m) + " rows below its columns (at most " +
+              std::to_string(kMaxRowsBelow) + " are supported)";
+        return ACOPF_E_INVALID_ARG;
+      }
+    }
+
     // --- storage: supernode s is an h x w column-major block -------------
     sy.sn_off.assign(size_t(ns) + 1, 0);
     for (int32_t s = 0; s < ns; ++s) {
@@ -368,25 +378,56 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     // within a level, the large supernodes (a whole block each) first, then
     // the small ones (a warp each), each group in ascending order
     sy.level_large.assign(size_t(nlev), 0);
+    sy.level_big.assign(size_t(nlev), 0);
     sy.level_smem.assign(size_t(nlev), 0);
+    sy.level_smem_big.assign(size_t(nlev), 0);
+    sy.level_small_stage.assign(size_t(nlev), 0);
     sy.tile_ptr.assign(size_t(nlev) + 1, 0);
     sy.tiles.clear();
+    auto dims = [&](int32_t s, int32_t& h, int32_t& w) {
+      h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
+      w = sy.sn_first[size_t(s) + 1] - sy.sn_first[size_t(s)];
+    };
+    // shared-memory doubles a block-handled supernode stages (kernel rule:
+    // panel and update matrix when both fit, else the panel when it fits)
+    auto staging = [&](int32_t s) {
+      int32_t h, w;
+      dims(s, h, w);
+      const int64_t pw = int64_t(h) * w, mm = int64_t(h - w) * (h - w);
+      return pw + mm <= kPanelSmemDoubles ? pw + mm : (pw <= kPanelSmemDoubles ? pw : 0);
+    };
+    auto is_big = [&](int32_t s) {
+      int32_t h, w;
+      dims(s, h, w);
+      return int64_t(h) * w > kPanelSmemDoubles || staging(s) > kMediumSmemDoubles;
+    };
     for (int32_t v = 0; v < nlev; ++v) {
       auto* first = sy.level_sn.data() + sy.level_ptr[size_t(v)];
       auto* last = sy.level_sn.data() + sy.level_ptr[size_t(v) + 1];
       auto* mid = std::stable_partition(first, last, [&](int32_t s) {
-        const int32_t h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
-        const int32_t w = sy.sn_first[size_t(s) + 1] - sy.sn_first[size_t(s)];
+        int32_t h, w;
+        dims(s, h, w);
         return h > kWarpMaxRows || w > kWarpMaxCols;
       });
+      auto* big_end = std::stable_partition(first, mid, is_big);
       sy.level_large[size_t(v)] = int32_t(mid - first);
+      sy.level_big[size_t(v)] = int32_t(big_end - first);
+      for (auto* it = mid; it != last; ++it) {
+        int32_t h, w;
+        dims(*it, h, w);
+        sy.level_small_stage[size_t(v)] =
+            std::max(sy.level_small_stage[size_t(v)], h * w + (h - w) * (h - w));
+      }
       for (auto* it = first; it != mid; ++it) {
         const int32_t s = *it;
-        const int32_t h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
-        const int32_t w = sy.sn_first[size_t(s) + 1] - sy.sn_first[size_t(s)];
-        if (h * w <= kPanelSmemDoubles)
-          sy.level_smem[size_t(v)] = std::max(sy.level_smem[size_t(v)], h * w);
-        const int32_t nt = (h - w + 31) / 32;
+        int32_t h, w;
+        dims(s, h, w);
+        const int32_t m = h - w;
+        const int64_t need = staging(s);
+        int32_t& slot = it < big_end ? sy.level_smem_big[size_t(v)] : sy.level_smem[size_t(v)];
+        slot = std::max<int32_t>(slot, int32_t(need));
+        if (int64_t(h) * w + int64_t(m) * m <= kPanelSmemDoubles) continue;  // formed with the panel
+        const int32_t nt = (m + 31) / 32;
         for (int32_t ti = 0; ti < nt; ++ti)
           for (int32_t tj = 0; tj <= ti; ++tj) sy.tiles.insert(sy.tiles.end(), {s, ti, tj, 0});
       }

@@ -164,3 +164,35 @@ def test_object_order_is_the_symbolic_order(dev, acopf):
         assert np.array_equal(ch.permutation(), p)
         info = ch.info()
         assert stats == {k: info[k] for k in stats}
+
+
+def test_graph_path_matches_direct_path(dev, acopf):
+    """On a created stream the factorization and the solve run as captured
+    CUDA graphs (re-captured when their arguments change); the results are
+    bit-identical to the direct launches on the default stream."""
+    g = synth.make_grid(3000, 4050, 600, seed=4, topology="geometric")
+    L = oracle.layout(g)
+    kv1 = _oracle_kvals(g, 90, 0.0, 1e-4, 0.0)
+    kv2 = _oracle_kvals(g, 91, 0.0, 1e-3, 0.0)
+    b = gu.t64(torch, np.random.default_rng(92).standard_normal(L.n), dev)
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        ref = []
+        for kv in (kv1, kv2):
+            assert ch.factor(gu.t64(torch, kv, dev)) == -1
+            x = torch.empty(L.n, dtype=torch.float64, device=dev)
+            ch.solve(b, x)
+            torch.cuda.synchronize()
+            ref.append(x.cpu().numpy())
+        st = torch.cuda.Stream(device=dev)
+        k1, k2 = gu.t64(torch, kv1, dev), gu.t64(torch, kv2, dev)
+        x = torch.empty(L.n, dtype=torch.float64, device=dev)
+        for rep in range(2):  # capture, then replay
+            for kd, r in ((k1, ref[0]), (k2, ref[1])):
+                assert ch.factor(kd, stream=st) == -1
+                ch.solve(b, x, stream=st)
+                st.synchronize()
+                assert np.array_equal(x.cpu().numpy().view(np.uint64), r.view(np.uint64)), rep
+        bad = k1.clone()
+        bad[0] = -1.0  # row 0's only entry is its diagonal
+        assert ch.factor(bad, stream=st) >= 0
+        assert ch.factor(k1, stream=st) == -1
