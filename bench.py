@@ -524,7 +524,9 @@ def run_chol_bench(args, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {}
-    for name in ("10kbus-geo", "80kbus-geo"):
+    reps = max(1, args.chol_reps)
+    warm = 3 if reps >= 10 else 1
+    for name in args.chol_workloads:
         grid = synth.workload_grid(name)
         model = acopf.model_create(grid, local)
         n, m = model.n, model.m
@@ -548,9 +550,8 @@ def run_chol_bench(args, local):
         ch = acopf.chol_create(model)
         create_s = time.perf_counter() - t0
         info = ch.info()
-        for _ in range(3):
+        for _ in range(warm):
             assert ch.factor(bufs["k"], stream=stream) == -1
-        reps = 20
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -559,15 +560,15 @@ def run_chol_bench(args, local):
         b = t(rng.standard_normal(n))
         x = torch.empty(n, dtype=torch.float64, device=dev)
         with torch.cuda.stream(stream):
-            for _ in range(5):
+            for _ in range(warm):
                 ch.solve(b, x, stream=stream)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(50):
+            for _ in range(reps):
                 ch.solve(b, x, stream=stream)
             e1.record(stream)
         stream.synchronize()
-        solve_ms = e0.elapsed_time(e1) / 50
+        solve_ms = e0.elapsed_time(e1) / reps
         ch.close()
         model.close()
         out[name] = {**{k: info[k] for k in ("n", "nnz_factor", "max_col", "n_supernodes",
@@ -578,8 +579,8 @@ def run_chol_bench(args, local):
                      "solve_ms": solve_ms, "device_bytes": info["device_bytes"],
                      "launches": {"factor": info["n_levels"] + 1,
                                   "solve": 2 * info["n_levels"] + 2}}
-    out["timing"] = ("factor: host wall clock per call (each call returns the pivot test to the "
-                     "host); solve: CUDA events over 50 calls")
+    out["timing"] = (f"factor: host wall clock per call over {reps} calls (each call returns the "
+                     f"pivot test to the host); solve: CUDA events over {reps} calls")
     return out
 
 
@@ -838,6 +839,9 @@ def main():
                     help="also time the condensation and step recovery (80k workload)")
     ap.add_argument("--chol", type=int, default=1, choices=[0, 1],
                     help="also time the sparse Cholesky of M_cond (10k and 80k workloads)")
+    ap.add_argument("--chol-workloads", nargs="+", default=["10kbus-geo", "80kbus-geo"],
+                    choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--chol-reps", type=int, default=20)
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)
