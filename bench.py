@@ -584,6 +584,37 @@ def run_chol_bench(args, local):
     return out
 
 
+def run_ipm_bench(args, local):
+    """The full condensed-space interior-point method (acopf_ipm_solve,
+    Algorithm 1) on the lightly loaded workloads: a complete solve of the
+    2,000-bus network (tol 1e-4), and the per-iteration cost on the
+    80,000-bus near-planar network (at most --ipm-iters iterations; the solve
+    may stop earlier with its status).  Host wall time of each call, the
+    symbolic phase of the factorization included."""
+    import torch
+
+    from paper_2307_16830_gb300 import acopf
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    names = {0: "converged", 1: "max_iter", 2: "line search failed", 3: "inertia correction failed"}
+    out = {}
+    for name, max_iter in (("30bus-opf", 200), ("2kbus-opf", 200), ("80kbus-geo-opf", args.ipm_iters)):
+        model = acopf.model_create(synth.workload_grid(name), local)
+        res, _, hist = acopf.ipm_solve(model, tol=1e-4, max_iter=max_iter, stream=stream)
+        model.close()
+        it = max(res["iterations"], 1)
+        out[name] = {"status": names.get(res["status"], res["status"]),
+                     "iterations": res["iterations"], "seconds": res["seconds"],
+                     "setup_seconds": res["setup_seconds"],
+                     "ms_per_iteration": 1e3 * (res["seconds"] - res["setup_seconds"]) / it,
+                     "factorizations": res["factorizations"], "trial_points": res["trial_points"],
+                     "objective": res["objective"], "residual": res["residual"]}
+    out["timing"] = ("host wall time of acopf_ipm_solve; ms_per_iteration excludes the setup "
+                     "(symbolic phase of the factorization, allocation, initial point)")
+    return out
+
+
 def _pinned(torch, a):
     """Page-locked host copy of a numpy array (numpy view, torch owner)."""
     t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -842,6 +873,9 @@ def main():
     ap.add_argument("--chol-workloads", nargs="+", default=["10kbus-geo", "80kbus-geo"],
                     choices=sorted(synth.WORKLOADS))
     ap.add_argument("--chol-reps", type=int, default=20)
+    ap.add_argument("--ipm", type=int, default=1, choices=[0, 1],
+                    help="also run the full interior-point method (2k solve, 80k iterations)")
+    ap.add_argument("--ipm-iters", type=int, default=20)
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)
@@ -862,6 +896,7 @@ def main():
     small = run_small_workloads(local) if args.small_workloads and world == 1 else None
     step = run_step_bench(args, local) if args.step and world == 1 else None
     chol = run_chol_bench(args, local) if args.chol and world == 1 else None
+    ipm = run_ipm_bench(args, local) if args.ipm and world == 1 else None
     batch = run_batch_bench(args, local) if args.batch and world == 1 else None
     serve = run_serve_bench(args, local) if args.serve and world == 1 else None
     if rank != 0:
@@ -931,7 +966,7 @@ def main():
         "graph": None if r["graph_ms"] is None else {
             "ms_per_call": r["graph_ms"], "calls_per_s": 1e3 / r["graph_ms"],
             "note": f"{GRAPH_CALLS} calls per CUDA graph, {args.graph_replays} replays"},
-        "small_workloads": small, "step": step, "chol": chol,
+        "small_workloads": small, "step": step, "chol": chol, "ipm": ipm,
         "gpu": r["gpu"], "batch": batch, "serve": serve,
     }
     print(json.dumps(line), flush=True)

@@ -343,6 +343,53 @@ acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats, int
 /* The order of a chol object, as acopf_chol_analyze's perm. */
 acopf_status acopf_chol_permutation(const acopf_chol* chol, int32_t* perm);
 
+/* The condensed-space interior-point method (Algorithm 1) on a model's
+ * AC-OPF problem, driven from the host over this library's kernels: the
+ * equality rows relaxed to [-tol, tol] and every finite constraint bound
+ * widened by tol max(1, |bound|) (Eq. relax, Sec. IV.A); per iteration the
+ * scaled residual of Eq. first (acopf_kkt_residual, the convergence test:
+ * below tol), the monotone barrier update, the Newton right-hand side,
+ * condensation, assembly and factorization of M_cond with the inertia
+ * correction on delta_w (delta_c = 0), solve and step recovery (the printed
+ * Delta y is minus the Newton step of y), the fraction-to-boundary step
+ * bounds and the filter line search of the interior-point reference the
+ * paper cites (its default constants; no second-order correction and no
+ * restoration phase: a step below the minimum ends the solve with
+ * ACOPF_IPM_LINE_SEARCH_FAILED).  Initial point: voltage angles 0,
+ * magnitudes 1, the rest at the middle of its bounds (0 when unbounded),
+ * pushed into the interior; slacks at g(x0) pushed into their bounds;
+ * y = 0; bound multipliers 1.
+ * options: tol > 0, max_iter >= 0, mu_init > 0 (else ACOPF_E_INVALID_ARG).
+ * x_out: HOST array of n doubles receiving the final x, or NULL.
+ * history: HOST array of (max_iter + 1) x ACOPF_IPM_HISTORY_FIELDS doubles
+ * (row k: f, residual, mu at iteration k's start, the constraint violation
+ * sum |g - s|, then the step alpha, alpha_z and delta_w taken; NaN where
+ * not reached), or NULL.  All work runs on `stream`; the call returns when
+ * the solve ends.  It allocates its own device memory and a sparse Cholesky
+ * object, and uses the model's scratch: no other call on the model may
+ * overlap it.  ACOPF_E_NO_DEVICE for a host-only model. */
+#define ACOPF_IPM_CONVERGED 0
+#define ACOPF_IPM_MAX_ITER 1
+#define ACOPF_IPM_LINE_SEARCH_FAILED 2
+#define ACOPF_IPM_INERTIA_FAILED 3
+#define ACOPF_IPM_HISTORY_FIELDS 7
+typedef struct {
+  double tol;
+  int32_t max_iter;
+  double mu_init;
+} acopf_ipm_options;
+typedef struct {
+  int32_t status, iterations;     /* status: ACOPF_IPM_*; iterations taken */
+  int32_t factorizations;         /* of M_cond, inertia retries included */
+  int32_t trial_points;           /* of the line searches */
+  double objective, residual, mu; /* at the final point */
+  double seconds;                 /* host wall time of the solve */
+  double setup_seconds;           /* of which before the first iteration (symbolic phase of
+                                     the factorization, allocation, initial point) */
+} acopf_ipm_result;
+acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* options, double* x_out,
+                             double* history, acopf_ipm_result* result, acopf_stream stream);
+
 /* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of
  * one model with HOST inputs and outputs, whose host-to-device copies,
  * kernels and device-to-host copies overlap (three streams, `depth` device

@@ -9,3 +9,4 @@ nothing from the library except the seeded data generator
 from .acopf import *  # noqa: F401,F403
 from .step import *  # noqa: F401,F403
 from .chol import *  # noqa: F401,F403
+from .ipm import *  # noqa: F401,F403

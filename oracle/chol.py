@@ -41,14 +41,27 @@ def solve_condensed(grid, kvals, b):
     return np.asarray(spla.spsolve(K, np.asarray(b, dtype=np.float64)), dtype=np.float64)
 
 
-def is_positive_definite(grid, kvals):
-    """True when M_cond has a Cholesky factorization (dense; small n only)."""
-    K = condensed_matrix(grid, kvals).toarray()
+def is_positive_definite(grid, kvals, dense_max=3000):
+    """True when M_cond is positive definite: a dense Cholesky up to
+    dense_max unknowns; above, a sparse LU in symmetric mode with diagonal
+    pivots only (a fill-reducing symmetric order, no row interchanges), whose
+    pivots are those of L D L' of the reordered matrix: all positive exactly
+    when the matrix is positive definite."""
+    K = condensed_matrix(grid, kvals)
+    if K.shape[0] <= dense_max:
+        try:
+            np.linalg.cholesky(K.toarray())
+        except np.linalg.LinAlgError:
+            return False
+        return True
     try:
-        np.linalg.cholesky(K)
-    except np.linalg.LinAlgError:
+        lu = spla.splu(K.tocsc(), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                       options=dict(SymmetricMode=True))
+    except RuntimeError:  # an exactly singular pivot
         return False
-    return True
+    if not np.array_equal(lu.perm_r, lu.perm_c):
+        raise RuntimeError("the sparse LU interchanged rows: the pivot test does not apply")
+    return bool(np.all(lu.U.diagonal() > 0.0))
 
 
 def backward_error(grid, kvals, x, b):

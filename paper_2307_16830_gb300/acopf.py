@@ -197,6 +197,21 @@ _chol_info = _sig("acopf_chol_info", C.c_int32, _vp, C.POINTER(CholStats), C.POI
 _chol_analyze = _sig("acopf_chol_analyze", C.c_int32, _vp, C.POINTER(CholStats), _vp)
 _chol_permutation = _sig("acopf_chol_permutation", C.c_int32, _vp, _vp)
 
+class IpmOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("mu_init", C.c_double)]
+
+
+class IpmResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("factorizations", C.c_int32),
+                ("trial_points", C.c_int32), ("objective", C.c_double), ("residual", C.c_double),
+                ("mu", C.c_double), ("seconds", C.c_double), ("setup_seconds", C.c_double)]
+
+
+IPM_CONVERGED, IPM_MAX_ITER, IPM_LINE_SEARCH_FAILED, IPM_INERTIA_FAILED = 0, 1, 2, 3
+IPM_HISTORY_FIELDS = ("f", "residual", "mu", "theta", "alpha", "alpha_z", "delta_w")
+_ipm_solve = _sig("acopf_ipm_solve", C.c_int32, _vp, C.POINTER(IpmOptions), _vp, _vp,
+                  C.POINTER(IpmResult), _vp)
+
 # Exported symbols the header declares (checked by the CPU tests).
 EXPORTED = [
     "acopf_status_string", "acopf_last_error", "acopf_model_create", "acopf_model_destroy",
@@ -215,7 +230,7 @@ EXPORTED = [
     "acopf_pipeline_create", "acopf_pipeline_destroy", "acopf_pipeline_submit",
     "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step", "acopf_kkt_residual",
     "acopf_chol_create", "acopf_chol_destroy", "acopf_chol_factor", "acopf_chol_solve",
-    "acopf_chol_info", "acopf_chol_permutation", "acopf_chol_analyze",
+    "acopf_chol_info", "acopf_chol_permutation", "acopf_chol_analyze", "acopf_ipm_solve",
 ]
 
 
@@ -791,3 +806,16 @@ def chol_analyze(model: Model, with_perm: bool = False):
     _check(_chol_analyze(model.handle, C.byref(st), None if perm is None else perm.ctypes.data),
            "acopf_chol_analyze")
     return (st.as_dict(), perm) if with_perm else st.as_dict()
+
+
+def ipm_solve(model: Model, tol: float = 1e-4, max_iter: int = 200, mu_init: float = 0.1,
+              stream=None):
+    """Algorithm 1 on the model (acopf_ipm_solve).  Returns (result dict,
+    final x, history array of shape (max_iter + 1, 7))."""
+    opts = IpmOptions(float(tol), int(max_iter), float(mu_init))
+    res = IpmResult()
+    x = np.empty(model.n, dtype=np.float64)
+    hist = np.empty((int(max_iter) + 1, len(IPM_HISTORY_FIELDS)), dtype=np.float64)
+    _check(_ipm_solve(model.handle, C.byref(opts), x.ctypes.data, hist.ctypes.data, C.byref(res),
+                      _stream(stream)), "acopf_ipm_solve")
+    return {k: getattr(res, k) for k, _ in res._fields_}, x, hist

@@ -108,6 +108,10 @@ void append_items(const Layout& L, int32_t inst, std::vector<int4>& p1, std::vec
 // Frees the model's condensation arena (stepapi.cpp).
 void free_step(acopf_model* m);
 
+// Builds the Jacobian's row and column lists and the row scratch of the
+// condensation (m->step), once (stepapi.cpp).
+acopf_status step_lists(acopf_model* m);
+
 // Validates the scalar arguments of an evaluation.
 acopf_status check_eval_scalars(double obj_weight, double delta_w, double delta_c);
 

@@ -1,0 +1,364 @@
+// The condensed-space interior-point method (Algorithm 1), driven from the
+// host over the library's device kernels (acopf_ipm_solve).
+//
+// Per iteration: the scaled residual of Eq. first (convergence test), the
+// monotone barrier update, the Newton right-hand side, the Hessian, the
+// condensation and the assembly of M_cond, its factorization with the
+// inertia correction on delta_w, the solve and the step recovery, the step
+// bounds, the filter line search over trial points (objective, constraints
+// and barrier terms evaluated on the device), the update of the iterate and
+// of the multipliers.  The scalar decisions (filter, step sizes, barrier
+// parameter, regularization) are taken on the host from a few reduced values
+// per step; every vector stays on the device.  The rules and constants are
+// those of the interior-point reference the paper cites for its line
+// search (no second-order correction, no restoration phase).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <limits>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "host_internal.h"
+#include "ipm_internal.h"
+
+using acopf::cuda_fail;
+using acopf::DeviceScope;
+using acopf::fail;
+
+namespace {
+
+// The reference's default constants (see the oracle for their roles).
+constexpr double kKappaEps = 10.0, kKappaMu = 0.2, kThetaMu = 1.5, kTauMin = 0.99;
+constexpr double kBoundPush = 1e-2, kBoundFrac = 1e-2;
+constexpr double kGammaTheta = 1e-5, kGammaPhi = 1e-8, kDelta = 1.0, kSTheta = 1.1, kSPhi = 2.3;
+constexpr double kEtaPhi = 1e-4, kAlphaMinFrac = 0.05, kKappaSigma = 1e10;
+constexpr double kDeltaW0 = 1e-4, kDeltaWMin = 1e-20, kDeltaWMax = 1e40;
+constexpr double kKappaWMinus = 1.0 / 3.0, kKappaWPlus = 8.0, kKappaWPlusBar = 100.0;
+constexpr int kMaxBacktracks = 60, kMaxInertiaTries = 200;
+
+// The reference's initial-point rule: at least min(k1 max(1,|b|), k2 (hi - lo))
+// inside each finite bound.
+double push_interior(double v, double lo, double hi) {
+  const bool fl = std::isfinite(lo), fh = std::isfinite(hi);
+  const double width = fl && fh ? hi - lo : std::numeric_limits<double>::infinity();
+  if (fl) v = std::max(v, lo + std::min(kBoundPush * std::max(1.0, std::fabs(lo)), kBoundFrac * width));
+  if (fh) v = std::min(v, hi - std::min(kBoundPush * std::max(1.0, std::fabs(hi)), kBoundFrac * width));
+  return v;
+}
+
+struct Buffers {
+  void* arena = nullptr;
+  acopf::IpmVec v{};
+  double *xl, *xu, *sl, *su, *sigma_x, *sigma_s, *q_s, *rhs, *hvals, *kvals;
+  double *f, *ft, *out, *part;  // out: 16 reduced scalars, part: per-block partials
+  ~Buffers() {
+    if (arena) cudaFree(arena);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* options, double* x_out,
+                             double* history, acopf_ipm_result* result, acopf_stream stream) {
+  if (!model || !options || !result)
+    return fail(ACOPF_E_INVALID_ARG, "acopf_ipm_solve: null pointer");
+  if (model->device < 0) return fail(ACOPF_E_NO_DEVICE, "acopf_ipm_solve: host-only model");
+  const double tol = options->tol, mu_init = options->mu_init;
+  const int32_t max_iter = options->max_iter;
+  if (!(tol > 0.0) || !std::isfinite(tol) || !(mu_init > 0.0) || !std::isfinite(mu_init) ||
+      max_iter < 0)
+    return fail(ACOPF_E_INVALID_ARG,
+                "acopf_ipm_solve: tol and mu_init must be finite and > 0, max_iter >= 0");
+  const auto t_start = std::chrono::steady_clock::now();
+  *result = acopf_ipm_result{};
+  DeviceScope ds(model->device);
+  if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_ipm_solve");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  acopf_stream as = stream;
+  const acopf::HostModel& hm = model->hm;
+  const acopf::Layout& L = hm.L;
+  const int32_t n = L.n, m = L.m;
+  acopf_status st = acopf::step_lists(model);
+  if (st != ACOPF_OK) return st;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, model->device);
+  const int blocks = acopf::ipm_blocks(std::max(sms, 1));
+
+  // ---- device buffers ------------------------------------------------------
+  Buffers B;
+  acopf::ArenaPlan p;
+  const size_t N = size_t(n), M = size_t(m);
+  enum { kVecN = 19, kVecM = 24 };
+  const size_t o_n = p.take<double>(kVecN * N), o_m = p.take<double>(kVecM * M);
+  const size_t o_j = p.take<double>(size_t(L.nnzj)), o_h = p.take<double>(size_t(L.nnzh));
+  const size_t o_k = p.take<double>(size_t(L.nnzk)), o_s = p.take<double>(32);
+  const size_t o_p = p.take<double>(4 * size_t(blocks));
+  cudaError_t e = cudaMalloc(&B.arena, p.off);
+  if (e != cudaSuccess) {
+    B.arena = nullptr;
+    return cuda_fail(e, "acopf_ipm_solve: allocation");
+  }
+  char* base = static_cast<char*>(B.arena);
+  double* vn = reinterpret_cast<double*>(base + o_n);
+  double* vm = reinterpret_cast<double*>(base + o_m);
+  auto nv = [&](int k) { return vn + size_t(k) * N; };
+  auto mv = [&](int k) { return vm + size_t(k) * M; };
+  acopf::IpmVec& v = B.v;
+  v.x = nv(0); v.xt = nv(1); B.xl = nv(2); B.xu = nv(3); v.zl_x = nv(4); v.zu_x = nv(5);
+  v.grad = nv(6); v.p_x = nv(7); v.p_zl_x = nv(8); v.p_zu_x = nv(9); B.sigma_x = nv(10);
+  B.rhs = nv(11); v.dx = nv(12); v.dzl_x = nv(13); v.dzu_x = nv(14);
+  v.s = mv(0); v.st = mv(1); B.sl = mv(2); B.su = mv(3); v.zl_s = mv(4); v.zu_s = mv(5);
+  v.y = mv(6); v.ym = mv(7); v.cons = mv(8); v.cons_t = mv(9); v.p_s = mv(10); v.p_y = mv(11);
+  v.p_zl_s = mv(12); v.p_zu_s = mv(13); B.sigma_s = mv(14); B.q_s = mv(15); v.ds = mv(16);
+  v.dy = mv(17); v.dzl_s = mv(18); v.dzu_s = mv(19);
+  v.xl = B.xl; v.xu = B.xu; v.sl = B.sl; v.su = B.su;
+  v.jvals = reinterpret_cast<double*>(base + o_j);
+  B.hvals = reinterpret_cast<double*>(base + o_h);
+  B.kvals = reinterpret_cast<double*>(base + o_k);
+  double* scal = reinterpret_cast<double*>(base + o_s);
+  B.f = scal; B.ft = scal + 1; B.out = scal + 8;
+  B.part = reinterpret_cast<double*>(base + o_p);
+
+  // ---- initial point (reading d8) -------------------------------------------
+  std::vector<double> hx(N, 0.0), hs(M), hsl(M), hsu(M), hzlx(N), hzux(N), hzls(M), hzus(M);
+  for (int32_t j = 0; j < n; ++j) {
+    const double lo = hm.xl[size_t(j)], hi = hm.xu[size_t(j)];
+    hx[size_t(j)] = std::isfinite(lo) && std::isfinite(hi) ? 0.5 * (lo + hi) : 0.0;
+  }
+  for (int32_t b = 0; b < L.nb; ++b) {
+    hx[size_t(b)] = 0.0;          // va
+    hx[size_t(L.nb + b)] = 1.0;   // vm
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    hx[size_t(j)] = push_interior(hx[size_t(j)], hm.xl[size_t(j)], hm.xu[size_t(j)]);
+    hzlx[size_t(j)] = std::isfinite(hm.xl[size_t(j)]) ? 1.0 : 0.0;
+    hzux[size_t(j)] = std::isfinite(hm.xu[size_t(j)]) ? 1.0 : 0.0;
+  }
+  for (int32_t r = 0; r < m; ++r) {  // Eq. relax: bounds widened by tol max(1, |b|)
+    const double lo = hm.gl[size_t(r)], hi = hm.gu[size_t(r)];
+    hsl[size_t(r)] = std::isfinite(lo) ? lo - tol * std::max(1.0, std::fabs(lo)) : -INFINITY;
+    hsu[size_t(r)] = std::isfinite(hi) ? hi + tol * std::max(1.0, std::fabs(hi)) : INFINITY;
+    hzls[size_t(r)] = std::isfinite(hsl[size_t(r)]) ? 1.0 : 0.0;
+    hzus[size_t(r)] = std::isfinite(hsu[size_t(r)]) ? 1.0 : 0.0;
+  }
+  auto up = [&](double* d, const std::vector<double>& h) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s);
+  };
+  up(v.x, hx); up(B.xl, hm.xl); up(B.xu, hm.xu); up(B.sl, hsl); up(B.su, hsu);
+  up(v.zl_x, hzlx); up(v.zu_x, hzux); up(v.zl_s, hzls); up(v.zu_s, hzus);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.y, 0, M * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.ym, 0, M * 8, s);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: upload");
+  st = acopf_eval_cons(model, v.x, v.cons, as);
+  if (st != ACOPF_OK) return st;
+  e = cudaMemcpyAsync(hs.data(), v.cons, M * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: initial constraints");
+  for (int32_t r = 0; r < m; ++r) {
+    const double lo = hsl[size_t(r)], hi = hsu[size_t(r)];
+    double sr = std::min(std::max(hs[size_t(r)], lo), hi);
+    hs[size_t(r)] = push_interior(sr, lo, hi);
+  }
+  up(v.s, hs);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: slacks");
+
+  acopf_chol* chol = nullptr;
+  st = acopf_chol_create(model, &chol);
+  if (st != ACOPF_OK) return st;
+  struct CholGuard {
+    acopf_chol* c;
+    ~CholGuard() { acopf_chol_destroy(c); }
+  } guard{chol};
+
+  // ---- helpers ---------------------------------------------------------------
+  acopf_iterate it{};
+  auto set_iterate = [&]() {
+    it = acopf_iterate{v.x,    v.s,    B.xl,     B.xu,     B.sl,     B.su,     v.zl_x,
+                       v.zu_x, v.zl_s, v.zu_s,   v.p_x,    v.p_s,    v.p_y,    v.p_zl_x,
+                       v.p_zu_x, v.p_zl_s, v.p_zu_s};
+  };
+  double hout[16];
+  auto fetch = [&](int count) -> cudaError_t {  // B.out[0..count) -> hout
+    cudaError_t err = cudaMemcpyAsync(hout, B.out, size_t(count) * 8, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    return err;
+  };
+  auto residual = [&](double mu, double& out_e) -> acopf_status {
+    acopf_status r = acopf_kkt_residual(model, &it, v.y, v.grad, v.cons, v.jvals, mu, B.out, as);
+    if (r != ACOPF_OK) return r;
+    const cudaError_t err = fetch(1);
+    if (err != cudaSuccess) return cuda_fail(err, "acopf_ipm_solve: residual");
+    out_e = hout[0];
+    return ACOPF_OK;
+  };
+  auto record = [&](int32_t k, int field, double value) {
+    if (history && k <= max_iter) history[size_t(k) * ACOPF_IPM_HISTORY_FIELDS + size_t(field)] = value;
+  };
+  if (history)
+    std::fill(history, history + size_t(max_iter + 1) * ACOPF_IPM_HISTORY_FIELDS,
+              std::numeric_limits<double>::quiet_NaN());
+
+  // ---- evaluation at the initial point ----------------------------------------
+  double f = 0.0;
+  st = acopf_eval_obj(model, v.x, B.f, as);
+  if (st == ACOPF_OK) st = acopf_eval_grad(model, v.x, v.grad, as);
+  if (st == ACOPF_OK) st = acopf_eval_jac_coo(model, v.x, v.jvals, as);
+  if (st != ACOPF_OK) return st;
+  e = acopf::launch_ipm_measure(v, v.x, v.s, v.cons, n, m, blocks, B.part, B.out + 2, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B.out, B.f, 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = fetch(4);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: initial point");
+  f = hout[0];
+  double theta = hout[2];
+  const double theta_max = 1e4 * std::max(1.0, theta), theta_min = 1e-4 * std::max(1.0, theta);
+  std::vector<std::pair<double, double>> filter{{theta_max, -INFINITY}};
+  double mu = mu_init, dw_last = 0.0, res0 = INFINITY;
+  result->setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  int32_t status = ACOPF_IPM_MAX_ITER, k = 0;
+
+  for (k = 0; k <= max_iter; ++k) {
+    set_iterate();
+    st = residual(0.0, res0);
+    if (st != ACOPF_OK) return st;
+    record(k, 0, f);
+    record(k, 1, res0);
+    record(k, 2, mu);
+    record(k, 3, theta);
+    if (res0 <= tol) {
+      status = ACOPF_IPM_CONVERGED;
+      break;
+    }
+    if (k == max_iter) break;
+    // monotone barrier update, possibly several times
+    while (mu > tol / 10.0) {
+      double emu = 0.0;
+      st = residual(mu, emu);
+      if (st != ACOPF_OK) return st;
+      if (emu > kKappaEps * mu) break;
+      mu = std::max(tol / 10.0, std::min(kKappaMu * mu, std::pow(mu, kThetaMu)));
+      filter.assign(1, {theta_max, -INFINITY});
+    }
+    const double tau = std::max(kTauMin, 1.0 - mu);
+    // Newton right-hand side, Hessian of f - y'g
+    e = acopf::launch_ipm_rhs(model->step, v, mu, blocks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: right-hand side");
+    st = acopf_eval_hess_coo(model, v.x, v.ym, 1.0, B.hvals, as);
+    if (st != ACOPF_OK) return st;
+    // inertia correction on delta_w
+    double dw = 0.0;
+    bool ok = false;
+    for (int tries = 0; tries < kMaxInertiaTries; ++tries) {
+      st = acopf_condense(model, &it, v.jvals, dw, 0.0, B.sigma_x, B.sigma_s, B.q_s, B.rhs, as);
+      if (st == ACOPF_OK)
+        st = acopf_assemble_condensed_kkt_csr(model, B.hvals, v.jvals, B.sigma_x, B.sigma_s, dw,
+                                              0.0, B.kvals, as);
+      int32_t bad = -1;
+      if (st == ACOPF_OK) st = acopf_chol_factor(chol, B.kvals, 0.0, &bad, as);
+      if (st != ACOPF_OK) return st;
+      result->factorizations++;
+      if (bad < 0) {
+        ok = true;
+        break;
+      }
+      if (dw == 0.0)
+        dw = dw_last == 0.0 ? kDeltaW0 : std::max(kDeltaWMin, kKappaWMinus * dw_last);
+      else
+        dw *= dw_last == 0.0 ? kKappaWPlusBar : kKappaWPlus;
+      if (dw > kDeltaWMax) break;
+    }
+    if (!ok) {
+      status = ACOPF_IPM_INERTIA_FAILED;
+      break;
+    }
+    if (dw > 0.0) dw_last = dw;
+    st = acopf_chol_solve(chol, B.rhs, v.dx, as);
+    if (st == ACOPF_OK)
+      st = acopf_recover_step(model, &it, v.jvals, dw, 0.0, B.sigma_s, B.q_s, v.dx, v.ds, v.dy,
+                              v.dzl_x, v.dzu_x, v.dzl_s, v.dzu_s, as);
+    if (st != ACOPF_OK) return st;
+    e = acopf::launch_ipm_dir(v, n, m, tau, mu, blocks, B.part, B.out, s);
+    if (e == cudaSuccess) e = fetch(4);
+    if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: step bounds");
+    const double a_max = hout[0], a_z = hout[1], gphi = hout[2];
+    const double phi = f - mu * hout[3];
+    double alpha_min = kGammaTheta;
+    if (gphi < 0.0)
+      alpha_min = std::min({alpha_min, kGammaPhi * theta / (-gphi),
+                            kDelta * std::pow(theta, kSTheta) / std::pow(-gphi, kSPhi)});
+    alpha_min *= kAlphaMinFrac;
+    // filter line search
+    double alpha = a_max, ft = 0.0, tht = 0.0, pht = 0.0;
+    int accepted = 0;  // 1: f-type, 2: h-type
+    for (int b = 0; b < kMaxBacktracks; ++b) {
+      e = acopf::launch_ipm_trial(v, n, m, alpha, blocks, s);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: trial point");
+      st = acopf_eval_obj(model, v.xt, B.ft, as);
+      if (st == ACOPF_OK) st = acopf_eval_cons(model, v.xt, v.cons_t, as);
+      if (st != ACOPF_OK) return st;
+      e = acopf::launch_ipm_measure(v, v.xt, v.st, v.cons_t, n, m, blocks, B.part, B.out + 2, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(B.out, B.ft, 8, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = fetch(4);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: trial measures");
+      result->trial_points++;
+      ft = hout[0];
+      tht = hout[2];
+      pht = ft - mu * hout[3];
+      bool in_filter = false;
+      for (const auto& fe : filter)
+        if (tht >= fe.first && pht >= fe.second) in_filter = true;
+      const bool switching =
+          gphi < 0.0 && alpha * std::pow(-gphi, kSPhi) > kDelta * std::pow(theta, kSTheta);
+      if (!in_filter) {
+        if (switching && theta <= theta_min) {
+          if (pht <= phi + kEtaPhi * alpha * gphi) {
+            accepted = 1;
+            break;
+          }
+        } else if (tht <= (1.0 - kGammaTheta) * theta || pht <= phi - kGammaPhi * theta) {
+          accepted = 2;
+          break;
+        }
+      }
+      alpha *= 0.5;
+      if (alpha < alpha_min) break;
+    }
+    if (!accepted) {
+      status = ACOPF_IPM_LINE_SEARCH_FAILED;
+      break;
+    }
+    if (accepted == 2)
+      filter.push_back({(1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta});
+    std::swap(v.x, v.xt);
+    std::swap(v.s, v.st);
+    std::swap(v.cons, v.cons_t);
+    f = ft;
+    theta = tht;
+    e = acopf::launch_ipm_accept(v, n, m, alpha, a_z, mu, kKappaSigma, blocks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: update");
+    st = acopf_eval_grad(model, v.x, v.grad, as);
+    if (st == ACOPF_OK) st = acopf_eval_jac_coo(model, v.x, v.jvals, as);
+    if (st != ACOPF_OK) return st;
+    record(k, 4, alpha);
+    record(k, 5, a_z);
+    record(k, 6, dw);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && x_out) e = cudaMemcpy(x_out, v.x, N * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: result");
+  result->status = status;
+  result->iterations = std::min(k, max_iter);
+  result->objective = f;
+  result->residual = res0;
+  result->mu = mu;
+  result->seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return ACOPF_OK;
+}
+
+}  // extern "C"

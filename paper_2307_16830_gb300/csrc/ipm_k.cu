@@ -1,0 +1,223 @@
+// Vector kernels of the condensed-space interior-point iteration (Algorithm
+// 1): the Newton right-hand side (minus the conditions of Eq. first), the
+// step-size bounds and the barrier terms of the line search, the trial
+// point, and the update of the multipliers.  Reductions run over a fixed
+// grid (4 blocks per SM): per-block partials in a fixed order, then one
+// block combining them in block order, so every result is reproducible.
+#include "ipm_internal.h"
+
+namespace acopf {
+namespace {
+
+constexpr int kIpmThreads = 256;
+
+__device__ __forceinline__ bool finite_bound(double v) { return isfinite(v); }
+
+// Block reduction of NV values, the first NMIN by min, the rest by sum, in a
+// fixed order; thread 0 writes them to out[NV * blockIdx.x ..].
+template <int NV, int NMIN>
+__device__ void block_reduce(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double sh[kIpmThreads / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const double u = __shfl_down_sync(0xffffffffu, v[q], o);
+      v[q] = q < NMIN ? fmin(v[q], u) : v[q] + u;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[warp][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) b[q] = sh[0][q];
+    for (int w = 1; w < kIpmThreads / 32; ++w)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) b[q] = q < NMIN ? fmin(b[q], sh[w][q]) : b[q] + sh[w][q];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[NV * blockIdx.x + q] = b[q];
+  }
+}
+
+// One block: combines nb partial records of NV values in block order.
+template <int NV, int NMIN>
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_final(const double* __restrict__ part,
+                                                            int nb, double* __restrict__ out) {
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = q < NMIN ? INFINITY : 0.0;
+  for (int b = threadIdx.x; b < nb; b += kIpmThreads)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const double u = part[NV * b + q];
+      v[q] = q < NMIN ? fmin(v[q], u) : v[q] + u;
+    }
+  __shared__ double tmp[NV];
+  // reuse block_reduce's tree with a single block's record
+  block_reduce<NV, NMIN>(v, tmp);
+  __syncthreads();
+  if (threadIdx.x < NV) out[threadIdx.x] = tmp[threadIdx.x];
+}
+
+// Newton right-hand side: minus the conditions of Eq. first at the iterate.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_rhs(DevStep st, IpmVec v, double mu) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < st.n; j += stride) {
+    double aty = 0.0;
+    for (int k = __ldg(st.jt_ptr + j), k1 = __ldg(st.jt_ptr + j + 1); k < k1; ++k)
+      aty = fma(v.jvals[__ldg(st.jt_slot + k)], v.y[__ldg(st.jt_row + k)], aty);
+    const double x = v.x[j], zl = v.zl_x[j], zu = v.zu_x[j], lo = v.xl[j], hi = v.xu[j];
+    v.p_x[j] = -(v.grad[j] - aty - zl + zu);
+    v.p_zl_x[j] = finite_bound(lo) ? mu - zl * (x - lo) : 0.0;
+    v.p_zu_x[j] = finite_bound(hi) ? mu - zu * (hi - x) : 0.0;
+  }
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < st.m; r += stride) {
+    const double s = v.s[r], zl = v.zl_s[r], zu = v.zu_s[r], lo = v.sl[r], hi = v.su[r];
+    v.p_s[r] = -(v.y[r] - zl + zu);
+    v.p_y[r] = -(v.cons[r] - s);
+    v.p_zl_s[r] = finite_bound(lo) ? mu - zl * (s - lo) : 0.0;
+    v.p_zu_s[r] = finite_bound(hi) ? mu - zu * (hi - s) : 0.0;
+  }
+}
+
+// Step bounds and barrier terms at the iterate, per block:
+// [primal fraction-to-boundary alpha, dual alpha, grad phi' d, sum log gaps].
+__device__ __forceinline__ void primal_terms(double v, double dv, double lo, double hi, double tau,
+                                             double mu, double (&a)[4]) {
+  if (finite_bound(lo)) {
+    const double gap = v - lo;
+    if (dv < 0.0) a[0] = fmin(a[0], -tau * gap / dv);
+    a[2] -= mu * dv / gap;
+    a[3] += log(gap);
+  }
+  if (finite_bound(hi)) {
+    const double gap = hi - v;
+    if (dv > 0.0) a[0] = fmin(a[0], tau * gap / dv);
+    a[2] += mu * dv / gap;
+    a[3] += log(gap);
+  }
+}
+
+__device__ __forceinline__ void dual_term(double z, double dz, double tau, double (&a)[4]) {
+  if (dz < 0.0) a[1] = fmin(a[1], -tau * z / dz);
+}
+
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_dir(IpmVec v, int n, int m, double tau,
+                                                          double mu, double* __restrict__ part) {
+  double a[4] = {1.0, 1.0, 0.0, 0.0};
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double dx = v.dx[j];
+    a[2] = fma(v.grad[j], dx, a[2]);
+    primal_terms(v.x[j], dx, v.xl[j], v.xu[j], tau, mu, a);
+    dual_term(v.zl_x[j], v.dzl_x[j], tau, a);
+    dual_term(v.zu_x[j], v.dzu_x[j], tau, a);
+  }
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
+    primal_terms(v.s[r], v.ds[r], v.sl[r], v.su[r], tau, mu, a);
+    dual_term(v.zl_s[r], v.dzl_s[r], tau, a);
+    dual_term(v.zu_s[r], v.dzu_s[r], tau, a);
+  }
+  block_reduce<4, 2>(a, part);
+}
+
+// Trial point x_t = x + alpha dx, s_t = s + alpha ds.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_trial(IpmVec v, int n, int m, double alpha) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride)
+    v.xt[j] = fma(alpha, v.dx[j], v.x[j]);
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride)
+    v.st[r] = fma(alpha, v.ds[r], v.s[r]);
+}
+
+// At a point (x, s) with its constraint values: [sum |g - s|, sum log gaps].
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_measure(IpmVec v, const double* __restrict__ x,
+                                                              const double* __restrict__ s,
+                                                              const double* __restrict__ cons,
+                                                              int n, int m,
+                                                              double* __restrict__ part) {
+  double a[2] = {0.0, 0.0};
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double lo = v.xl[j], hi = v.xu[j], xj = x[j];
+    if (finite_bound(lo)) a[1] += log(xj - lo);
+    if (finite_bound(hi)) a[1] += log(hi - xj);
+  }
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
+    const double lo = v.sl[r], hi = v.su[r], sr = s[r];
+    a[0] += fabs(cons[r] - sr);
+    if (finite_bound(lo)) a[1] += log(sr - lo);
+    if (finite_bound(hi)) a[1] += log(hi - sr);
+  }
+  block_reduce<2, 0>(a, part);
+}
+
+// Accepted step: y <- y - alpha dy (the printed system's Delta y is minus
+// the Newton step of y), z <- z + alpha_z dz, then the safeguard
+// z in [mu/(kappa gap), kappa mu/gap] at the new point (already in x, s).
+__device__ __forceinline__ double reset_z(double z, double gap, double mu, double kappa) {
+  return fmax(fmin(z, kappa * mu / gap), mu / (kappa * gap));
+}
+
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_accept(IpmVec v, int n, int m, double alpha,
+                                                             double alpha_z, double mu,
+                                                             double kappa) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double x = v.x[j], lo = v.xl[j], hi = v.xu[j];
+    if (finite_bound(lo)) v.zl_x[j] = reset_z(fma(alpha_z, v.dzl_x[j], v.zl_x[j]), x - lo, mu, kappa);
+    if (finite_bound(hi)) v.zu_x[j] = reset_z(fma(alpha_z, v.dzu_x[j], v.zu_x[j]), hi - x, mu, kappa);
+  }
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
+    const double s = v.s[r], lo = v.sl[r], hi = v.su[r];
+    const double yr = fma(-alpha, v.dy[r], v.y[r]);
+    v.y[r] = yr;
+    v.ym[r] = -yr;
+    if (finite_bound(lo)) v.zl_s[r] = reset_z(fma(alpha_z, v.dzl_s[r], v.zl_s[r]), s - lo, mu, kappa);
+    if (finite_bound(hi)) v.zu_s[r] = reset_z(fma(alpha_z, v.dzu_s[r], v.zu_s[r]), hi - s, mu, kappa);
+  }
+}
+
+}  // namespace
+
+int ipm_blocks(int sms) { return 4 * sms; }
+
+cudaError_t launch_ipm_rhs(const DevStep& st, const IpmVec& v, double mu, int blocks,
+                           cudaStream_t s) {
+  k_ipm_rhs<<<blocks, kIpmThreads, 0, s>>>(st, v, mu);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ipm_dir(const IpmVec& v, int n, int m, double tau, double mu, int blocks,
+                           double* part, double* out, cudaStream_t s) {
+  k_ipm_dir<<<blocks, kIpmThreads, 0, s>>>(v, n, m, tau, mu, part);
+  k_ipm_final<4, 2><<<1, kIpmThreads, 0, s>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ipm_trial(const IpmVec& v, int n, int m, double alpha, int blocks,
+                             cudaStream_t s) {
+  k_ipm_trial<<<blocks, kIpmThreads, 0, s>>>(v, n, m, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ipm_measure(const IpmVec& v, const double* x, const double* sv,
+                               const double* cons, int n, int m, int blocks, double* part,
+                               double* out, cudaStream_t s) {
+  k_ipm_measure<<<blocks, kIpmThreads, 0, s>>>(v, x, sv, cons, n, m, part);
+  k_ipm_final<2, 0><<<1, kIpmThreads, 0, s>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ipm_accept(const IpmVec& v, int n, int m, double alpha, double alpha_z,
+                              double mu, double kappa, int blocks, cudaStream_t s) {
+  k_ipm_accept<<<blocks, kIpmThreads, 0, s>>>(v, n, m, alpha, alpha_z, mu, kappa);
+  return cudaGetLastError();
+}
+
+}  // namespace acopf

@@ -97,6 +97,8 @@ acopf_status check_iterate(const acopf_iterate* it, acopf::StepIterate& out, con
 }  // namespace
 
 namespace acopf {
+
+acopf_status step_lists(acopf_model* m) { return ensure_step(m); }
 void free_step(acopf_model* m) {
   if (m->step_arena) cudaFree(m->step_arena);
   m->step_arena = nullptr;

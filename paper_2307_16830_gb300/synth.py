@@ -20,7 +20,8 @@ benchmarks (Section V.A), which are not available here:
 * branches: r ~ U(0.001, 0.05), x ~ U(0.01, 0.3), total charging b ~ U(0, 0.1),
   tap 1 except U(0.95, 1.05) on 10 % of branches, shift 0,
   rate_a ~ U(1, 5) p.u., angle-difference limits +-30 degrees;
-* buses: Pd ~ U(0, 1), Qd = 0.3 Pd, Gs = Bs = 0, Vm in [0.9, 1.1];
+* buses: Pd ~ U(0, 1) (times the workload's load scale, 1 unless stated),
+  Qd = 0.3 Pd, Gs = Bs = 0, Vm in [0.9, 1.1];
 * generators at distinct random buses: c2 ~ U(0, 0.1), c1 ~ U(10, 40), c0 = 0,
   Pg in [0, Pmax] with Pmax ~ U(1, 5), Qg in [-Pmax/2, Pmax/2];
   the bus of generator 0 is the (single) reference bus;
@@ -206,9 +207,11 @@ def _geometric_topology(rng: np.random.Generator, n_bus: int, n_branch: int):
 
 
 def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
-              name: str | None = None, topology: str = "random") -> Grid:
+              name: str | None = None, topology: str = "random",
+              load_scale: float = 1.0) -> Grid:
     """Synthetic grid with the recipe of the module docstring (topology
-    "random", or "geometric": see _geometric_topology)."""
+    "random", or "geometric": see _geometric_topology); load_scale scales
+    the drawn loads (the same draws)."""
     if not 1 <= n_gen <= n_bus:
         raise ValueError("need 1 <= n_gen <= n_bus")
     rng = np.random.default_rng(seed)
@@ -231,7 +234,7 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
     angmin = np.full(nl, -ang)
     angmax = np.full(nl, ang)
 
-    Pd = rng.uniform(0.0, 1.0, n_bus)
+    Pd = rng.uniform(0.0, 1.0, n_bus) * load_scale
     Qd = 0.3 * Pd
     Gs = np.zeros(n_bus)
     Bs = np.zeros(n_bus)
@@ -395,13 +398,21 @@ WORKLOADS = {
                        topology="geometric"),
     "80kbus-geo": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1012,
                        topology="geometric"),
+    # lightly loaded networks, solvable from the flat start: the workloads of
+    # the full interior-point method (at full load the recipe's networks
+    # have no feasible point the method finds)
+    "30bus-opf": dict(n_bus=30, n_branch=41, n_gen=6, seed=1000, load_scale=0.5),
+    "2kbus-opf": dict(n_bus=2000, n_branch=2700, n_gen=400, seed=1011, load_scale=0.1),
+    "80kbus-geo-opf": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1012,
+                           topology="geometric", load_scale=0.1),
 }
 
 
 def workload_grid(name: str) -> Grid:
     spec = WORKLOADS[name]
     return make_grid(spec["n_bus"], spec["n_branch"], spec["n_gen"], spec["seed"],
-                     name=f"synthetic-{name}", topology=spec.get("topology", "random"))
+                     name=f"synthetic-{name}", topology=spec.get("topology", "random"),
+                     load_scale=spec.get("load_scale", 1.0))
 
 
 def point_seed(grid_seed: int, call_index: int) -> int:

@@ -223,3 +223,11 @@ def test_chol_analyze_runs_on_host_only_models():
     with acopf.model_create(g, -1) as m:
         st = acopf.chol_analyze(m)
         assert st["n"] == m.n and st["nnz_factor"] >= st["n"]
+
+
+def test_ipm_solve_rejects_without_device_work():
+    g = synth.workload_grid("30bus-opf")
+    with acopf.model_create(g, -1) as m:
+        with pytest.raises(acopf.AcopfError) as ei:
+            acopf.ipm_solve(m)
+        assert ei.value.status == acopf.E_NO_DEVICE

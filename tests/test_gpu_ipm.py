@@ -1,0 +1,91 @@
+"""GPU interior-point method (acopf_ipm_solve) against the oracle's
+(oracle.ipm_solve): the same algorithm, the same decisions.
+
+At tol = 1e-4 (the paper's default for the condensed method) on networks
+both solve: the same status and iteration count, per-iteration objective,
+residual, barrier parameter, violation and step sizes within 1e-4
+relative, the final objective within 1e-8 relative and x within 1e-4; on a
+network where the line search fails, the same failure at the same
+iteration.  The 1e-4: the slack boxes of the equality rows are 2e-4 wide
+and the gaps shrink with mu, so Sigma reaches 1e8-1e10 late in a solve;
+M_cond's condition number times the double-precision unit roundoff then
+bounds the relative difference of two correct steps computed in different
+summation orders at 1e-6-1e-5 (measured up to 1.1e-5); the step sizes and
+the next iterates inherit it.  At tol = 1e-6 the equality rows' slack boxes are 2e-6 wide, so
+Sigma_s reaches 1e8 and M_cond's condition number amplifies rounding-level
+differences of the two implementations (a different summation order) into
+relative step differences of about 1e-4: there the two must converge to the
+same point (objective within 1e-7 relative, x within 1e-4) in iteration
+counts at most 2 apart."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_16830_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+def _half_load(g):
+    import dataclasses
+    return dataclasses.replace(g, Pd=g.Pd * 0.5, Qd=g.Qd * 0.5)
+
+
+STATUS = {"converged": 0, "max_iter": 1, "line search failed": 2, "inertia correction failed": 3}
+
+
+@pytest.fixture(scope="module")
+def acopf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_16830_gb300 import acopf as lib
+    return lib
+
+
+CASES = [("30bus-opf", lambda: synth.workload_grid("30bus-opf"), 1e-4),
+         ("edge7", lambda: _half_load(synth.make_edge_case_grid(7)), 1e-4),
+         ("random500", lambda: synth.make_grid(500, 675, 100, seed=21, load_scale=0.1), 1e-4),
+         ("geo300", lambda: synth.make_grid(300, 405, 60, seed=1011, topology="geometric",
+                                            load_scale=0.1), 1e-4),
+         ("30bus full load", lambda: synth.workload_grid("30bus"), 1e-4)]
+
+
+@pytest.mark.parametrize("idx", range(len(CASES)))
+def test_ipm_matches_oracle(acopf, idx):
+    name, make, tol = CASES[idx]
+    g = make()
+    ref = oracle.ipm_solve(g, oracle.IpmOptions(tol=tol))
+    with acopf.model_create(g, 0) as m:
+        res, x, hist = acopf.ipm_solve(m, tol=tol, max_iter=200)
+    assert res["status"] == STATUS[ref.status], (name, res, ref.status)
+    assert res["iterations"] == ref.iterations, (name, res["iterations"], ref.iterations)
+    for k, h in enumerate(ref.history):
+        for j, key in enumerate(("f", "residual", "mu", "theta", "alpha", "alpha_z", "delta_w")):
+            if key not in h:
+                continue
+            a, b = hist[k, j], h[key]
+            assert abs(a - b) <= 1e-4 * max(1.0, abs(b)), (name, k, key, a, b)
+    if ref.status == "converged":
+        assert abs(res["objective"] - ref.objective) <= 1e-8 * abs(ref.objective)
+        assert np.max(np.abs(x - ref.x)) <= 1e-4
+        assert res["residual"] <= tol
+
+
+def test_ipm_tight_tolerance_reaches_the_same_point(acopf):
+    g = synth.workload_grid("30bus-opf")
+    ref = oracle.ipm_solve(g, oracle.IpmOptions(tol=1e-6))
+    with acopf.model_create(g, 0) as m:
+        res, x, _ = acopf.ipm_solve(m, tol=1e-6, max_iter=200)
+    assert ref.status == "converged" and res["status"] == acopf.IPM_CONVERGED
+    assert abs(res["iterations"] - ref.iterations) <= 2
+    assert abs(res["objective"] - ref.objective) <= 1e-7 * abs(ref.objective)
+    assert np.max(np.abs(x - ref.x)) <= 1e-4
+
+
+def test_ipm_rejects_bad_arguments(acopf):
+    g = synth.workload_grid("30bus-opf")
+    with acopf.model_create(g, 0) as m:
+        for kw in (dict(tol=0.0), dict(mu_init=-1.0), dict(max_iter=-1)):
+            with pytest.raises(acopf.AcopfError) as e:
+                acopf.ipm_solve(m, **kw)
+            assert e.value.status == acopf.E_INVALID_ARG

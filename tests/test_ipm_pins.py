@@ -1,0 +1,125 @@
+"""Pins of the interior-point oracle (oracle/ipm.py, Algorithm 1).
+
+* The Newton step (condensation, solve, recovery, with the printed Delta y
+  taken as minus the Newton step of y: reading d7) solves the linearization
+  of Eq. first: F(v + eps d) = (1 - eps) F(v) to first order, checked by
+  evaluating the conditions of Eq. first from the callbacks alone; the
+  opposite reading of Delta y fails.
+* The solution on the half-loaded 30-bus network matches an independent
+  solver (scipy's SLSQP from the same start) and satisfies the bounds and
+  the relaxed constraints.
+* The initial-point and step-bound rules against hand values.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.ipm import IpmOptions, fraction_to_boundary, ipm_start, push_interior
+from paper_2307_16830_gb300 import synth
+
+
+def _conditions(g, b, x, s, y, z, mu):
+    """The left-hand sides of Eq. first (the complementarity rows at finite
+    bounds only)."""
+    grad = oracle.gradient(g, x)[0]
+    cons = oracle.constraints(g, x)[0]
+    A = oracle.acopf._jac_matrix(g, oracle.jacobian(g, x)[0])
+    fin = lambda bd, v: np.where(np.isfinite(bd), v, 0.0)  # noqa: E731
+    with np.errstate(invalid="ignore"):
+        return [grad - A.T @ y - z["zl_x"] + z["zu_x"], y - z["zl_s"] + z["zu_s"], cons - s,
+                fin(b["xl"], z["zl_x"] * (x - b["xl"]) - mu),
+                fin(b["xu"], z["zu_x"] * (b["xu"] - x) - mu),
+                fin(b["sl"], z["zl_s"] * (s - b["sl"]) - mu),
+                fin(b["su"], z["zu_s"] * (b["su"] - s) - mu)]
+
+
+def _newton_check(dy_sign):
+    g = synth.workload_grid("30bus-opf")
+    L = oracle.layout(g)
+    st = ipm_start(g, IpmOptions())
+    b = {k: st[k] for k in ("xl", "xu", "sl", "su")}
+    rng = np.random.default_rng(0)
+    x, s = st["x"], st["s"]
+    y = rng.standard_normal(L.m) * 0.1
+    z = {k: st[k] * (1 + rng.random(st[k].size)) for k in ("zl_x", "zu_x", "zl_s", "zu_s")}
+    mu = 0.1
+    F0 = _conditions(g, b, x, s, y, z, mu)
+    J = oracle.jacobian(g, x)[0]
+    it = oracle.Iterate(x=x, s=s, **b, **z, p_x=-F0[0], p_s=-F0[1], p_y=-F0[2], p_zl_x=-F0[3],
+                        p_zu_x=-F0[4], p_zl_s=-F0[5], p_zu_s=-F0[6])
+    H = oracle.hessian(g, x, -y, 1.0)[0]
+    c = oracle.condense(g, J, it, 0.0, 0.0)
+    kv, _ = oracle.condensed_kkt(g, H, J, c["sigma_x"][0], c["sigma_s"][0], 0.0, 0.0)
+    dx = oracle.solve_condensed(g, kv, c["rhs"][0])
+    r = oracle.recover(g, J, it, dx, 0.0, 0.0)
+    eps = 1e-7
+    z1 = {k: z[k] + eps * r["d" + k][0] for k in z}
+    F1 = _conditions(g, b, x + eps * dx, s + eps * r["ds"][0], y + dy_sign * eps * r["dy"][0],
+                     z1, mu)
+    return [np.max(np.abs(F1[i] - (1 - eps) * F0[i])) / (eps * np.max(np.abs(F0[i])))
+            for i in range(7)]
+
+
+def test_newton_step_solves_the_linearized_conditions():
+    err = _newton_check(-1.0)
+    assert max(err) < 1e-3, err
+
+
+def test_opposite_reading_of_delta_y_fails():
+    err = _newton_check(+1.0)
+    assert max(err[:2]) > 0.1, err
+
+
+def test_solution_matches_an_independent_solver():
+    """SLSQP (scipy) on the same problem from the same start; the oracle at
+    tol 1e-6 (its relaxation of the equality rows moves the optimum by
+    O(tol))."""
+    from scipy.optimize import minimize
+    g = synth.workload_grid("30bus-opf")
+    r = oracle.ipm_solve(g, IpmOptions(tol=1e-6))
+    assert r.status == "converged"
+    xl, xu, gl, gu = oracle.bounds(g)
+    x0 = ipm_start(g, IpmOptions())["x"]
+    A = lambda x: oracle.acopf._jac_matrix(g, oracle.jacobian(g, x)[0]).toarray()  # noqa: E731
+    eq = np.flatnonzero(gl == gu)
+    lo = np.flatnonzero(np.isfinite(gl) & (gl != gu))
+    hi = np.flatnonzero(np.isfinite(gu) & (gl != gu))
+    cons = [dict(type="eq", fun=lambda x: oracle.constraints(g, x)[0][eq], jac=lambda x: A(x)[eq]),
+            dict(type="ineq", fun=lambda x: oracle.constraints(g, x)[0][lo] - gl[lo],
+                 jac=lambda x: A(x)[lo]),
+            dict(type="ineq", fun=lambda x: gu[hi] - oracle.constraints(g, x)[0][hi],
+                 jac=lambda x: -A(x)[hi])]
+    bnds = [(a if np.isfinite(a) else None, b if np.isfinite(b) else None) for a, b in zip(xl, xu)]
+    s = minimize(lambda x: oracle.objective(g, x)[0], x0, jac=lambda x: oracle.gradient(g, x)[0],
+                 bounds=bnds, constraints=cons, method="SLSQP",
+                 options=dict(maxiter=1000, ftol=1e-12))
+    assert s.success
+    assert abs(r.objective - s.fun) <= 1e-4 * abs(s.fun), (r.objective, s.fun)
+
+
+def test_solution_is_interior_and_nearly_feasible():
+    g = synth.workload_grid("30bus-opf")
+    opts = IpmOptions()
+    r = oracle.ipm_solve(g, opts)
+    assert r.status == "converged" and r.residual <= opts.tol
+    xl, xu, gl, gu = oracle.bounds(g)
+    fx, fu = np.isfinite(xl), np.isfinite(xu)
+    assert np.all(r.x[fx] > xl[fx]) and np.all(r.x[fu] < xu[fu])
+    c = oracle.constraints(g, r.x)[0]
+    sl, su = oracle.relaxed_bounds(gl, gu, opts.tol)
+    viol = np.maximum(0.0, np.maximum(sl - c, c - su))
+    assert viol.max() <= opts.tol
+
+
+def test_initial_point_and_step_rules_by_hand():
+    # push: one-sided bound moves by k1 max(1,|b|); a narrow box by k2 of its width
+    assert push_interior(np.array([0.0]), np.array([0.0]), np.array([np.inf]), 1e-2, 1e-2)[0] == 1e-2
+    assert push_interior(np.array([5.0]), np.array([-np.inf]), np.array([2.0]), 1e-2, 1e-2)[0] == 2.0 - 2e-2
+    v = push_interior(np.array([0.0]), np.array([0.0]), np.array([1e-3]), 1e-2, 1e-2)[0]
+    assert v == 1e-5
+    # fraction to boundary: x = 1 in [0, 2], dx = -2, tau = 0.99 -> alpha = 0.495
+    a = fraction_to_boundary(np.array([1.0]), np.array([-2.0]), np.array([0.0]), np.array([2.0]),
+                             0.99)
+    assert abs(a - 0.495) < 1e-15
+    assert fraction_to_boundary(np.array([1.0]), np.array([0.1]), np.array([0.0]),
+                                np.array([2.0]), 0.99) == 1.0
