@@ -586,11 +586,11 @@ def run_chol_bench(args, local):
 
 def run_ipm_bench(args, local):
     """The full condensed-space interior-point method (acopf_ipm_solve,
-    Algorithm 1) on the lightly loaded workloads: a complete solve of the
-    2,000-bus network (tol 1e-4), and the per-iteration cost on the
-    80,000-bus near-planar network (at most --ipm-iters iterations; the solve
-    may stop earlier with its status).  Host wall time of each call, the
-    symbolic phase of the factorization included."""
+    Algorithm 1, tol 1e-4) on the lightly loaded workloads: the 30- and
+    2,000-bus random networks and the 10,000- and 80,000-bus near-planar
+    short-line networks (the last at most --ipm-iters iterations).  Host wall
+    time of each call, its setup (the symbolic phase of the factorization)
+    reported apart."""
     import torch
 
     from paper_2307_16830_gb300 import acopf
@@ -599,7 +599,8 @@ def run_ipm_bench(args, local):
     stream = torch.cuda.Stream(device=dev)
     names = {0: "converged", 1: "max_iter", 2: "line search failed", 3: "inertia correction failed"}
     out = {}
-    for name, max_iter in (("30bus-opf", 200), ("2kbus-opf", 200), ("80kbus-geo-opf", args.ipm_iters)):
+    for name, max_iter in (("30bus-opf", 200), ("2kbus-opf", 200), ("10kbus-geo-opf", 200),
+                           ("80kbus-geo-opf", args.ipm_iters)):
         model = acopf.model_create(synth.workload_grid(name), local)
         res, _, hist = acopf.ipm_solve(model, tol=1e-4, max_iter=max_iter, stream=stream)
         model.close()
@@ -875,7 +876,7 @@ def main():
     ap.add_argument("--chol-reps", type=int, default=20)
     ap.add_argument("--ipm", type=int, default=1, choices=[0, 1],
                     help="also run the full interior-point method (2k solve, 80k iterations)")
-    ap.add_argument("--ipm-iters", type=int, default=20)
+    ap.add_argument("--ipm-iters", type=int, default=200)
     ap.add_argument("--batch", type=int, default=1, choices=[0, 1],
                     help="also time the batched form (256 instances) against plain calls")
     ap.add_argument("--batch-steps", type=int, default=50)

@@ -17,7 +17,8 @@ benchmarks (Section V.A), which are not available here:
   and then by random pairs of near neighbours (real transmission networks
   are near-planar, with small separators; the random chords of the first
   recipe give separators of linear size);
-* branches: r ~ U(0.001, 0.05), x ~ U(0.01, 0.3), total charging b ~ U(0, 0.1),
+* branches: r ~ U(0.001, 0.05), x ~ U(0.01, 0.3), total charging b ~ U(0, 0.1)
+  (r, x and b times the workload's impedance and charging scales, 1 unless stated),
   tap 1 except U(0.95, 1.05) on 10 % of branches, shift 0,
   rate_a ~ U(1, 5) p.u., angle-difference limits +-30 degrees;
 * buses: Pd ~ U(0, 1) (times the workload's load scale, 1 unless stated),
@@ -208,10 +209,12 @@ def _geometric_topology(rng: np.random.Generator, n_bus: int, n_branch: int):
 
 def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
               name: str | None = None, topology: str = "random",
-              load_scale: float = 1.0) -> Grid:
+              load_scale: float = 1.0, impedance_scale: float = 1.0,
+              charging_scale: float = 1.0) -> Grid:
     """Synthetic grid with the recipe of the module docstring (topology
-    "random", or "geometric": see _geometric_topology); load_scale scales
-    the drawn loads (the same draws)."""
+    "random", or "geometric": see _geometric_topology); load_scale,
+    impedance_scale (r and x) and charging_scale (b) scale the drawn values
+    (the same draws)."""
     if not 1 <= n_gen <= n_bus:
         raise ValueError("need 1 <= n_gen <= n_bus")
     rng = np.random.default_rng(seed)
@@ -222,9 +225,9 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, seed: int,
     else:
         raise ValueError(f"unknown topology {topology!r}")
     nl = f.shape[0]
-    r = rng.uniform(0.001, 0.05, nl)
-    x = rng.uniform(0.01, 0.3, nl)
-    b = rng.uniform(0.0, 0.1, nl)
+    r = rng.uniform(0.001, 0.05, nl) * impedance_scale
+    x = rng.uniform(0.01, 0.3, nl) * impedance_scale
+    b = rng.uniform(0.0, 0.1, nl) * charging_scale
     tap = np.ones(nl)
     tapped = rng.random(nl) < 0.1
     tap[tapped] = rng.uniform(0.95, 1.05, int(tapped.sum()))
@@ -403,8 +406,15 @@ WORKLOADS = {
     # have no feasible point the method finds)
     "30bus-opf": dict(n_bus=30, n_branch=41, n_gen=6, seed=1000, load_scale=0.5),
     "2kbus-opf": dict(n_bus=2000, n_branch=2700, n_gen=400, seed=1011, load_scale=0.1),
+    # near-planar networks of short lines (impedance x0.3, charging x0.1):
+    # the recipe's draws make every local line electrically long, and those
+    # networks have no feasible point at these sizes
+    "10kbus-geo-opf": dict(n_bus=10_000, n_branch=13_500, n_gen=2_000, seed=1011,
+                           topology="geometric", load_scale=0.1, impedance_scale=0.3,
+                           charging_scale=0.1),
     "80kbus-geo-opf": dict(n_bus=80_000, n_branch=110_000, n_gen=12_000, seed=1012,
-                           topology="geometric", load_scale=0.1),
+                           topology="geometric", load_scale=0.1, impedance_scale=0.3,
+                           charging_scale=0.1),
 }
 
 
@@ -412,7 +422,9 @@ def workload_grid(name: str) -> Grid:
     spec = WORKLOADS[name]
     return make_grid(spec["n_bus"], spec["n_branch"], spec["n_gen"], spec["seed"],
                      name=f"synthetic-{name}", topology=spec.get("topology", "random"),
-                     load_scale=spec.get("load_scale", 1.0))
+                     load_scale=spec.get("load_scale", 1.0),
+                     impedance_scale=spec.get("impedance_scale", 1.0),
+                     charging_scale=spec.get("charging_scale", 1.0))
 
 
 def point_seed(grid_seed: int, call_index: int) -> int:

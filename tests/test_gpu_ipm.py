@@ -89,3 +89,37 @@ def test_ipm_rejects_bad_arguments(acopf):
             with pytest.raises(acopf.AcopfError) as e:
                 acopf.ipm_solve(m, **kw)
             assert e.value.status == acopf.E_INVALID_ARG
+
+
+def test_ipm_10k_near_planar_matches_oracle(acopf):
+    """The 10,000-bus near-planar short-line network: both converge to the
+    same point (objective within 1e-7 relative, x within 1e-4) in iteration
+    counts at most 2 apart."""
+    g = synth.workload_grid("10kbus-geo-opf")
+    ref = oracle.ipm_solve(g)
+    with acopf.model_create(g, 0) as m:
+        res, x, _ = acopf.ipm_solve(m)
+    assert ref.status == "converged" and res["status"] == acopf.IPM_CONVERGED, res
+    assert abs(res["iterations"] - ref.iterations) <= 2
+    assert abs(res["objective"] - ref.objective) <= 1e-7 * abs(ref.objective)
+    assert np.max(np.abs(x - ref.x)) <= 1e-4
+
+
+def test_ipm_80k_solution_properties(acopf):
+    """The 80,000-bus near-planar short-line network (too large for the
+    oracle's solve): the returned point is converged, strictly inside its
+    bounds, within tol of the relaxed constraints, and the oracle's objective
+    there equals the reported one."""
+    g = synth.workload_grid("80kbus-geo-opf")
+    tol = 1e-4
+    with acopf.model_create(g, 0) as m:
+        res, x, _ = acopf.ipm_solve(m, tol=tol)
+    assert res["status"] == acopf.IPM_CONVERGED and res["residual"] <= tol, res
+    xl, xu, gl, gu = oracle.bounds(g)
+    fx, fu = np.isfinite(xl), np.isfinite(xu)
+    assert np.all(x[fx] > xl[fx]) and np.all(x[fu] < xu[fu])
+    c = oracle.constraints(g, x)[0]
+    sl, su = oracle.relaxed_bounds(gl, gu, tol)
+    assert np.max(np.maximum(0.0, np.maximum(sl - c, c - su))) <= tol
+    f = oracle.objective(g, x)[0]
+    assert abs(f - res["objective"]) <= 1e-10 * abs(f)
