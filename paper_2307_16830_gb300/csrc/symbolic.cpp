@@ -10,9 +10,7 @@
 #include "symbolic.h"
 
 #include <algorithm>
-#include <functional>
 #include <new>
-#include <queue>
 #include <string>
 #include <utility>
 
@@ -20,31 +18,48 @@ namespace acopf {
 namespace {
 
 // Minimum-degree elimination order of the graph `adj` (sorted adjacency
-// lists without self loops); ties go to the smaller vertex.  Eliminating v
-// joins its neighbours into a clique.  Fails when the elimination graph
-// outgrows `max_entries` adjacency entries.
+// lists without self loops).  Eliminating v joins its neighbours into a
+// clique.  Vertices wait in buckets by degree (doubly linked lists, O(1)
+// moves); among vertices of the minimum degree the one most recently placed
+// in its bucket goes first (initially the largest index), a deterministic
+// rule.  Fails when the elimination graph outgrows `max_entries` adjacency
+// entries.
 bool minimum_degree(std::vector<std::vector<int32_t>>& adj, int64_t max_entries,
                     std::vector<int32_t>& order) {
   const int32_t n = int32_t(adj.size());
-  using Item = std::pair<int64_t, int32_t>;
-  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-  std::vector<char> alive(static_cast<size_t>(n), 1);
+  std::vector<int32_t> head(size_t(n) + 1, -1), next(size_t(n), -1), prev(size_t(n), -1);
+  std::vector<int32_t> deg(static_cast<size_t>(n));
+  auto insert = [&](int32_t v, int32_t d) {
+    deg[size_t(v)] = d;
+    prev[size_t(v)] = -1;
+    next[size_t(v)] = head[size_t(d)];
+    if (head[size_t(d)] >= 0) prev[size_t(head[size_t(d)])] = v;
+    head[size_t(d)] = v;
+  };
+  auto remove = [&](int32_t v) {
+    const int32_t d = deg[size_t(v)];
+    if (prev[size_t(v)] >= 0)
+      next[size_t(prev[size_t(v)])] = next[size_t(v)];
+    else
+      head[size_t(d)] = next[size_t(v)];
+    if (next[size_t(v)] >= 0) prev[size_t(next[size_t(v)])] = prev[size_t(v)];
+  };
   int64_t entries = 0;
   for (int32_t v = 0; v < n; ++v) {
-    heap.emplace(int64_t(adj[size_t(v)].size()), v);
+    insert(v, int32_t(adj[size_t(v)].size()));
     entries += int64_t(adj[size_t(v)].size());
   }
   order.clear();
   order.reserve(size_t(n));
-  std::vector<int32_t> merged;
-  while (!heap.empty()) {
-    const auto [deg, v] = heap.top();
-    heap.pop();
-    if (!alive[size_t(v)] || deg != int64_t(adj[size_t(v)].size())) continue;  // stale
-    alive[size_t(v)] = 0;
+  std::vector<int32_t> merged, nv;
+  int32_t mindeg = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    while (head[size_t(mindeg)] < 0) ++mindeg;
+    const int32_t v = head[size_t(mindeg)];
+    remove(v);
     order.push_back(v);
-    std::vector<int32_t> nv;
     nv.swap(adj[size_t(v)]);
+    adj[size_t(v)].clear();
     entries -= int64_t(nv.size());
     for (const int32_t u : nv) {
       std::vector<int32_t>& au = adj[size_t(u)];
@@ -65,7 +80,9 @@ bool minimum_degree(std::vector<std::vector<int32_t>>& adj, int64_t max_entries,
       }
       entries += int64_t(merged.size()) - int64_t(au.size());
       au.swap(merged);
-      heap.emplace(int64_t(au.size()), u);
+      remove(u);
+      insert(u, int32_t(au.size()));
+      if (deg[size_t(u)] < mindeg) mindeg = deg[size_t(u)];
     }
     if (entries > max_entries) return false;
   }
