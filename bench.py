@@ -323,11 +323,28 @@ def run_ours(args, rank, world, local):
         barrier()
         dt = reduce_max(time.perf_counter() - t0, world, dev)
         pipe.close()
+        h2d = 8 * (2 * model.n + 2 * model.m)
+        d2h = 8 * (1 + model.n + model.m + model.nnz_jac + model.nnz_hess + model.nnz_kkt)
         e2e = {"value": throughput(world, args.e2e_steps, 1e3 * dt), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * (2 * model.n + 2 * model.m),
-               "d2h_bytes_per_step": 8 * (1 + model.n + model.m + model.nnz_jac
-                                          + model.nnz_hess + model.nnz_kkt),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": f"acopf_pipeline_submit (depth {args.e2e_depth}), page-locked host buffers"}
+        # the host link's own rate for one call's outputs: a plain page-locked
+        # device-to-host copy of the same bytes, timed the same way
+        hbuf = torch.empty(d2h // 8, dtype=torch.float64).pin_memory()
+        dbuf = torch.empty(d2h // 8, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            hbuf.copy_(dbuf, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(20):
+            hbuf.copy_(dbuf, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        link = 20 * d2h / (time.perf_counter() - t0) / 1e9
+        per_rank = e2e["value"] / world
+        e2e["copy_bound"] = {"d2h_gbs_plain_copy": link,
+                             "d2h_gbs_achieved": per_rank * d2h / 1e9,
+                             "frac": per_rank * d2h / 1e9 / link}
+        del hbuf, dbuf
 
     fp64_rates = acopf.measure_fp64_rates(local)  # G lane-ops/s of fma, add, mul
     rp, _ = model.kkt_structure()
