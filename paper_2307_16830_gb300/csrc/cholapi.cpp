@@ -50,6 +50,10 @@ struct acopf_chol {
   size_t u_doubles = 0, z_doubles = 0;  // update matrices / vectors
   int32_t* bad_host = nullptr;  // page-locked copy of dev.bad
   bool factored = false;
+  // the groups of a level (big, other block-handled, small supernodes) are
+  // independent: two side streams run them beside the caller's stream
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   // the factorization's and the solve's launch sequences, captured as CUDA
   // graphs for the last arguments they ran with
   cudaGraphExec_t factor_exec = nullptr, solve_exec = nullptr;
@@ -61,6 +65,11 @@ struct acopf_chol {
 namespace {
 
 void release(acopf_chol* c) {
+  for (cudaStream_t st : c->side)
+    if (st) cudaStreamDestroy(st);
+  if (c->fork) cudaEventDestroy(c->fork);
+  for (cudaEvent_t ev : c->join)
+    if (ev) cudaEventDestroy(ev);
   if (c->factor_exec) cudaGraphExecDestroy(c->factor_exec);
   if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
   if (c->arena) cudaFree(c->arena);
@@ -90,7 +99,8 @@ acopf_status run_symbolic(const acopf_model* model, acopf::CholSymbolic& sy, con
 
 // The factorization's device work: zeroed blocks, the assembly of M_cond's
 // values, and per level the big, the other block-handled and the small
-// supernodes, then the update-matrix tiles.
+// supernodes (independent: on the caller's stream and two side streams that
+// fork from it and join back), then the update-matrix tiles.
 cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double tol,
                           cudaStream_t s) {
   const acopf::CholDev& d = chol->dev;
@@ -101,15 +111,42 @@ cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double to
   const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large, &tp = chol->tile_ptr;
   for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v) {
     const int32_t nb = chol->level_big[v], nl = ll[v], cnt = lp[v + 1] - lp[v];
-    if (nb > 0)
+    // the level's groups, each on its own stream when more than one is present
+    const bool groups[3] = {nb > 0, nl > nb, cnt > nl};
+    const int ngroups = int(groups[0]) + int(groups[1]) + int(groups[2]);
+    cudaStream_t gs[3] = {s, s, s};
+    if (ngroups > 1) {
+      e = cudaEventRecord(chol->fork, s);
+      int k = 0;
+      for (int g = 0; g < 3 && e == cudaSuccess; ++g) {
+        if (!groups[g]) continue;
+        if (k > 0) {
+          gs[g] = chol->side[k - 1];
+          e = cudaStreamWaitEvent(gs[g], chol->fork, 0);
+        }
+        ++k;
+      }
+    }
+    if (e == cudaSuccess && groups[0])
       e = acopf::launch_chol_factor_level(d, lp[v], nb, nb, tol, chol->level_smem_big[v],
-                                          chol->tiles, 0, 0, s);
-    if (e == cudaSuccess && nl > nb)
+                                          chol->tiles, 0, 0, gs[0]);
+    if (e == cudaSuccess && groups[1])
       e = acopf::launch_chol_factor_level(d, lp[v] + nb, nl - nb, nl - nb, tol,
-                                          chol->level_smem[v], chol->tiles, 0, 0, s);
-    if (e == cudaSuccess)
+                                          chol->level_smem[v], chol->tiles, 0, 0, gs[1]);
+    if (e == cudaSuccess && groups[2])
       e = acopf::launch_chol_factor_level(d, lp[v] + nl, cnt - nl, 0, tol,
-                                          chol->level_small_stage[v], chol->tiles, tp[v],
+                                          chol->level_small_stage[v], chol->tiles, 0, 0, gs[2]);
+    if (ngroups > 1) {  // join the side streams back
+      int k = 0;
+      for (int g = 0; g < 3 && e == cudaSuccess; ++g) {
+        if (!groups[g] || gs[g] == s) continue;
+        e = cudaEventRecord(chol->join[k], gs[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, chol->join[k], 0);
+        ++k;
+      }
+    }
+    if (e == cudaSuccess && tp[v + 1] > tp[v])
+      e = acopf::launch_chol_factor_level(d, lp[v], 0, 0, tol, 0, chol->tiles, tp[v],
                                           tp[v + 1] - tp[v], s);
   }
   return e;
@@ -245,6 +282,11 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_amap, sy.amap.data(), sy.amap.size() * 8);
   up(o_perm, sy.perm.data(), n * 4);
   if (e == cudaSuccess) e = cudaMallocHost(&c->bad_host, sizeof(int32_t));
+  for (cudaStream_t& st : c->side)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : c->join)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   size_t smem = 0;
   for (size_t v = 0; v + 1 < sy.level_ptr.size(); ++v) {
     const int32_t nb = sy.level_big[v], nl = sy.level_large[v];
