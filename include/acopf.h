@@ -309,8 +309,10 @@ acopf_status acopf_kkt_residual(acopf_model* model, const acopf_iterate* it, con
  * Synchronises `stream` to return the test.  pivot_tol finite and >= 0,
  * else ACOPF_E_INVALID_ARG.
  * acopf_chol_solve: x = M_cond^-1 b with the last factorization (DEVICE b,
- * x of n doubles; they may alias); asynchronous on `stream`;
- * ACOPF_E_INVALID_ARG unless the last factorization passed the test.
+ * x of n doubles; they may alias); asynchronous on `stream`, and may be
+ * captured into the caller's CUDA graph (the factorization, which returns
+ * its test to the host, may not); ACOPF_E_INVALID_ARG unless the last
+ * factorization passed the test.
  * Calls on one object use its scratch: they must not overlap on the GPU. */
 typedef struct acopf_chol acopf_chol;
 acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out);

@@ -169,10 +169,15 @@ cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cud
 
 // Runs `record` on `s`: through a CUDA graph captured for the current
 // arguments (re-captured when they change), or directly on the legacy
-// default stream, which cannot be captured.
+// default stream, which cannot be captured, and on a stream the caller is
+// capturing (the launches then become part of the caller's graph).
 template <typename Record>
 cudaError_t run_recorded(cudaGraphExec_t& exec, bool reuse, cudaStream_t s, Record record) {
   if (s == nullptr || s == cudaStreamLegacy) return record(s);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t qe = cudaStreamIsCapturing(s, &cap);
+  if (qe != cudaSuccess) return qe;
+  if (cap != cudaStreamCaptureStatusNone) return record(s);
   if (!(reuse && exec)) {
     if (exec) {
       cudaGraphExecDestroy(exec);

@@ -196,3 +196,25 @@ def test_graph_path_matches_direct_path(dev, acopf):
         bad[0] = -1.0  # row 0's only entry is its diagonal
         assert ch.factor(bad, stream=st) >= 0
         assert ch.factor(k1, stream=st) == -1
+
+
+def test_solve_captured_in_a_caller_graph(dev, acopf):
+    """A solve recorded inside the caller's own CUDA graph capture becomes part
+    of that graph; its replay gives the bits of a direct solve."""
+    g = synth.workload_grid("30bus")
+    L = oracle.layout(g)
+    kv = _oracle_kvals(g, 95, 0.0, 1e-4, 0.0)
+    with acopf.model_create(g, 0) as m, acopf.chol_create(m) as ch:
+        assert ch.factor(gu.t64(torch, kv, dev)) == -1
+        b = gu.t64(torch, np.random.default_rng(96).standard_normal(L.n), dev)
+        ref = torch.empty(L.n, dtype=torch.float64, device=dev)
+        ch.solve(b, ref)
+        torch.cuda.synchronize()
+        st = torch.cuda.Stream(device=dev)
+        x = torch.full((L.n,), float("nan"), dtype=torch.float64, device=dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=st):
+            ch.solve(b, x, stream=st)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(x.cpu().numpy().view(np.uint64), ref.cpu().numpy().view(np.uint64))
