@@ -20,7 +20,6 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "stepapi.cpp",
            "cholapi.cpp", "symbolic.cpp", "ipm.cpp", "kernels.cu", "step.cu", "chol.cu", "ipm_k.cu",
            "noalloc.cu"]
-LIBS: list[str] = []
 
 
 def nvcc() -> str:
@@ -48,7 +47,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, *LIBS]
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

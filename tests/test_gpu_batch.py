@@ -11,7 +11,6 @@ the scaled network.
 import numpy as np
 import pytest
 
-import oracle
 from paper_2307_16830_gb300 import synth
 
 import gpu_util as gu

@@ -11,7 +11,6 @@
 * The initial-point and step-bound rules against hand values.
 """
 import numpy as np
-import pytest
 
 import oracle
 from oracle.ipm import IpmOptions, fraction_to_boundary, ipm_start, push_interior
