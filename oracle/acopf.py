@@ -24,7 +24,7 @@ What it computes, and where the paper defines it:
   C = (delta_c Sigma_s + (1 + delta_c delta_w) I)^-1 and D = (Sigma_s + delta_w I) C.
 
 Every value comes with a magnitude ``M`` = the sum of the absolute values of
-the terms that make it up (sin and cos bounded by 1).  Parity tests accept a
+the terms that make it up (a trigonometric term u cos(th) counts |u cos(th)|).  Parity tests accept a
 GPU value v when |v - oracle| <= 1e-12 M + 1e-14, which is the stated
 "1e-12 relative, 1e-14 absolute floor" made well posed when Sigma spans 16
 orders of magnitude and terms cancel.
@@ -186,18 +186,19 @@ def _flow_value_and_derivs(form, vm_f, vm_t, c, s):
     V = vm_f * vm_t
     T = u * c + w * s
     T1 = -u * s + w * c
-    Tm = np.abs(u) + np.abs(w)                 # bound on |T|, |T'| term sums
+    TM = np.abs(u * c) + np.abs(w * s)         # sum of |terms| of T
+    T1M = np.abs(u * s) + np.abs(w * c)        # sum of |terms| of T'
     out = {
         "F": (a * vm_f ** 2 + d * vm_t ** 2 + V * T,
-              np.abs(a) * vm_f ** 2 + np.abs(d) * vm_t ** 2 + V * Tm),
-        "th": (V * T1, V * Tm),
-        "vmf": (2 * a * vm_f + vm_t * T, 2 * np.abs(a) * vm_f + vm_t * Tm),
-        "vmt": (2 * d * vm_t + vm_f * T, 2 * np.abs(d) * vm_t + vm_f * Tm),
-        "thth": (-V * T, V * Tm),
-        "thvmf": (vm_t * T1, vm_t * Tm),
-        "thvmt": (vm_f * T1, vm_f * Tm),
+              np.abs(a) * vm_f ** 2 + np.abs(d) * vm_t ** 2 + V * TM),
+        "th": (V * T1, V * T1M),
+        "vmf": (2 * a * vm_f + vm_t * T, 2 * np.abs(a) * vm_f + vm_t * TM),
+        "vmt": (2 * d * vm_t + vm_f * T, 2 * np.abs(d) * vm_t + vm_f * TM),
+        "thth": (-V * T, V * TM),
+        "thvmf": (vm_t * T1, vm_t * T1M),
+        "thvmt": (vm_f * T1, vm_f * T1M),
         "vmfvmf": (2 * a, 2 * np.abs(a)),
-        "vmfvmt": (T, Tm),
+        "vmfvmt": (T, TM),
         "vmtvmt": (2 * d, 2 * np.abs(d)),
     }
     return out
