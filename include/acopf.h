@@ -469,7 +469,8 @@ acopf_status acopf_measure_fp64_rates(int device, double* dfma, double* dadd, do
  * loading this library holds until the process exits; n_gen is limited to
  * 16777216 (2^24) and larger values return ACOPF_E_INVALID_ARG.  The first
  * call on a device resolves the array's device address (with that device
- * current), so make that first call before any stream capture.  All calls
+ * current; a lookup that fails returns ACOPF_E_CUDA and is tried again by the
+ * next call), so make that first call before any stream capture.  All calls
  * on a device share the array and it keeps the last call's contents: the
  * call clears the counter in stream order before its kernel, and calls that
  * overlap on the GPU (different streams without ordering) race.  The sum is

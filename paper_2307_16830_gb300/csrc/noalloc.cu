@@ -30,12 +30,13 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Device address of g_noalloc_scratch per device, taken once per device
-// with that device current.  In host code the symbol's name is only a
-// host-side handle, never a device address.
+// Device address of g_noalloc_scratch per device, taken with that device
+// current and kept once the lookup has succeeded (a failed lookup, such as
+// one that met an error left over from earlier work, is retried by the next
+// call).  In host code the symbol's name is only a host-side handle, never a
+// device address.
 NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu[kMaxDevices];
 
 // f = sum_g c2 pg^2 + c1 pg + c0: each thread sums its terms in index order
 // (grid stride), each block reduces in a fixed tree order, and the last
@@ -99,16 +100,23 @@ extern "C" acopf_status acopf_objective_noalloc(int64_t n_gen, const double* pg,
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(ACOPF_E_CUDA, "acopf_objective_noalloc: no usable current device");
-  // First call on this device: resolve the static array's device address.
-  std::call_once(g_scratch_once[dev], [dev] {
-    void* p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    g_scratch_addr[dev] = static_cast<NoAllocScratch*>(p);
-  });
-  if (g_scratch_err[dev] != cudaSuccess || !g_scratch_addr[dev])
-    return fail(ACOPF_E_CUDA, std::string("acopf_objective_noalloc: cudaGetSymbolAddress: ") +
-                                  cudaGetErrorString(g_scratch_err[dev]));
-  NoAllocScratch* scratch = g_scratch_addr[dev];
+  // First successful call on this device: resolve the static array's device
+  // address.
+  NoAllocScratch* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu[dev]);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
+        return fail(ACOPF_E_CUDA, std::string("acopf_objective_noalloc: cudaGetSymbolAddress: ") +
+                                      cudaGetErrorString(e));
+      }
+      g_scratch_addr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    scratch = g_scratch_addr[dev];
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // The arrival counter must start at zero; the array keeps what the last
   // call left, so clear it in stream order before the launch.
