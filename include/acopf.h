@@ -344,6 +344,20 @@ acopf_status acopf_chol_info(const acopf_chol* chol, acopf_chol_stats* stats,
 acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats, int32_t* perm);
 /* The order of a chol object, as acopf_chol_analyze's perm. */
 acopf_status acopf_chol_permutation(const acopf_chol* chol, int32_t* perm);
+/* Task trace (a profiling aid; the paper has no counterpart).  enable != 0
+ * allocates a device trace buffer (ACOPF_E_OOM when that fails) and every
+ * later factorization and solve records, per task of its task graph, six
+ * int64 words: the task's kind word and first argument (supernode or
+ * group), the GPU clock (ns) when a block took it, when its dependencies
+ * were met, when it finished, and the SM that ran it; enable == 0 frees the
+ * buffer.  acopf_chol_get_trace copies the last run of graph `which` (0 the
+ * factorization, 1 the forward, 2 the backward solve) into `out` (HOST,
+ * 6 * capacity int64; NULL when capacity is 0) and sets *n_tasks to the
+ * graph's task count; tasks
+ * beyond `capacity` are not copied.  Synchronises the device. */
+acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable);
+acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out, int64_t capacity,
+                                  int64_t* n_tasks);
 
 /* The condensed-space interior-point method (Algorithm 1) on a model's
  * AC-OPF problem, driven from the host over this library's kernels: the

@@ -196,6 +196,9 @@ class CholStats(C.Structure):
 _chol_info = _sig("acopf_chol_info", C.c_int32, _vp, C.POINTER(CholStats), C.POINTER(C.c_int64))
 _chol_analyze = _sig("acopf_chol_analyze", C.c_int32, _vp, C.POINTER(CholStats), _vp)
 _chol_permutation = _sig("acopf_chol_permutation", C.c_int32, _vp, _vp)
+_chol_set_trace = _sig("acopf_chol_set_trace", C.c_int32, _vp, C.c_int32)
+_chol_get_trace = _sig("acopf_chol_get_trace", C.c_int32, _vp, C.c_int32, _vp, C.c_int64,
+                       C.POINTER(C.c_int64))
 
 class IpmOptions(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("mu_init", C.c_double)]
@@ -231,6 +234,7 @@ EXPORTED = [
     "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step", "acopf_kkt_residual",
     "acopf_chol_create", "acopf_chol_destroy", "acopf_chol_factor", "acopf_chol_solve",
     "acopf_chol_info", "acopf_chol_permutation", "acopf_chol_analyze", "acopf_ipm_solve",
+    "acopf_chol_set_trace", "acopf_chol_get_trace",
 ]
 
 
@@ -769,6 +773,21 @@ class Chol:
         st, nbytes = CholStats(), C.c_int64(0)
         _check(_chol_info(self._h, C.byref(st), C.byref(nbytes)), "acopf_chol_info")
         return {**st.as_dict(), "device_bytes": nbytes.value}
+
+    def set_trace(self, enable: bool) -> None:
+        """Turns the per-task trace of later factorizations and solves on/off."""
+        _check(_chol_set_trace(self._h, 1 if enable else 0), "acopf_chol_set_trace")
+
+    def trace(self, which: int = 0) -> np.ndarray:
+        """The last run's trace of graph `which` (0 factorization, 1 forward,
+        2 backward solve): one row per task, (kind word, argument, taken ns,
+        ready ns, finished ns, SM)."""
+        n = C.c_int64(0)
+        _check(_chol_get_trace(self._h, int(which), None, 0, C.byref(n)), "acopf_chol_get_trace")
+        out = np.zeros((n.value, 6), dtype=np.int64)
+        _check(_chol_get_trace(self._h, int(which), out.ctypes.data, n.value, C.byref(n)),
+               "acopf_chol_get_trace")
+        return out
 
     def permutation(self) -> np.ndarray:
         """The fill-reducing order (row i of P M_cond P' is row perm[i])."""

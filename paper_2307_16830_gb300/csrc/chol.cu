@@ -1,35 +1,62 @@
 // Numeric sparse Cholesky factorization of M_cond and solves with it.
 //
 // The factor L of P M_cond P' is stored in supernodes (dense column-major
-// blocks, see symbolic.h).  The factorization is multifrontal and runs the
-// supernodal elimination tree level by level, leaves first: one block per
-// supernode of a level (1) adds its children's update matrices into its
-// panel and its own update matrix (extend-add, one child after the other),
-// (2) factors its panel: a dense Cholesky of the diagonal block and the
-// scaled rows below it, and (3) subtracts L21 L21' from its update matrix,
-// which its parent adds in turn.  A pivot that is not above the tolerance
-// (or is NaN) is recorded (the smallest column, so the result does not
-// depend on the schedule) and replaced by 1 so the arithmetic stays finite;
-// the factorization then counts as failed.  The forward solve passes update
-// vectors up the tree the same way; the backward solve runs the levels root
-// first, each supernode reading its ancestors' solved entries.  Every sum
-// has a fixed order: results are bit-reproducible.
+// blocks, see symbolic.h).  The factorization is multifrontal: a supernode
+// adds its children's update matrices into its panel and into its own
+// update matrix (extend-add), factors its panel (a dense Cholesky of the
+// diagonal block and the scaled rows below it) and subtracts L21 L21' from
+// its update matrix, which its parent adds in turn.
+//
+// All of it runs in ONE persistent kernel over the task graph of
+// chol_plan.h: each block takes the next task of the list (an atomic
+// counter), waits until the tasks it depends on have set their finished
+// flags, runs it, and sets its own flag.  The list is a topological order,
+// so the lowest unfinished task any running block holds has all its
+// dependencies finished: the blocks always progress, whether or not all of
+// them are resident.  Every wait is bounded (2 s of the GPU clock); a wait
+// that runs out sets the object's abort flag, every block then stops, and
+// the host reports a timeout.  Data another task wrote is read through L2
+// (ld.global.cg): L1 is not coherent across SMs.
+//
+// Task kinds: a group of small supernodes (one block, level by level, one
+// warp per supernode), one block supernode (panel and update matrix staged
+// in shared memory), and the tiles of a large supernode's front (32 x 32:
+// extend-add into a tile, Cholesky of a diagonal tile, triangular solve of
+// a tile below it, a tile minus a product of two such tiles).
+//
+// A pivot that is not above the tolerance (or is NaN) is recorded (the
+// smallest column, so the result does not depend on the schedule) and
+// replaced by 1 so the arithmetic stays finite; the factorization then
+// counts as failed.  The solves run the same way: the forward solve passes
+// update vectors up the tree, the backward solve reads the ancestors' solved
+// entries.  Every sum has a fixed order: results are bit-reproducible.
 #include "chol_internal.h"
+#include "chol_plan.h"
 
 #include <algorithm>
 
 namespace acopf {
 namespace {
 
-constexpr int kCholThreads = 256;
-constexpr int kMaxWidth = kCholMaxWidth;
-constexpr int kPanelDoubles = kCholPanelDoubles;
-// row-map scratch: a child's rows (a large supernode's children have at most
-// kRelScratch rows below their columns; a small one's at most kCholWarpRows)
-constexpr int kRelScratch = kCholMaxRelRows;
-static_assert(kRelScratch >= kCholWarpRows * (kCholThreads / 32), "warp row-map slices");
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int kPermThreads = 256;
+constexpr int T = kCholTile;
+static_assert(T == kCholTileEdge, "host plan and kernels agree on the tile edge");
+static_assert(kThreads == T * kWarps, "a tile column per warp, rows over the lanes");
+// per-warp staging of a small supernode: panel and update matrix,
+// h w + (h - w)^2 <= 32 + 31^2 for h <= 32
+constexpr int kSmallStage = 1024;
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kStageDoubles =
+    cmax(cmax(kWarps * kSmallStage, kCholBlockDoubles), cmax(3 * T * T + T, kCholMaxWidth * (kCholMaxWidth + 1)));
+constexpr int kRelInts = cmax(kWarps * kCholWarpRows, kCholBlockRows);
+constexpr int kSolveDoubles = kCholMaxWidth * (kCholMaxWidth + 1);
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// ---------------------------------------------------------------------------
+// plain kernels: permutation and assembly of M_cond into the blocks
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPermThreads) k_gather(double* __restrict__ out,
                                                          const double* __restrict__ in,
                                                          const int32_t* __restrict__ idx, int n) {
@@ -54,9 +81,95 @@ __global__ void __launch_bounds__(kPermThreads) k_chol_assemble(double* __restri
     Lx[__ldg(amap + k)] = kvals[k];
 }
 
-// A supernode is handled by a group of NT threads: a whole block (NT =
-// kCholThreads) for the large supernodes of a level, one warp (NT = 32) for
-// the small ones.
+// ---------------------------------------------------------------------------
+// task scheduling
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long gpu_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits until *flag is set; false when the abort flag is (or gets) set or
+// the wait runs past kWaitLimitNs (then it sets the abort flag).
+__device__ bool wait_done(const int32_t* flag, int32_t* abort) {
+  if (ld_acquire(flag)) return true;
+  const unsigned long long t0 = gpu_clock_ns();
+  for (unsigned it = 0;; ++it) {
+    __nanosleep(it < 32 ? 64 : 512);
+    if (ld_acquire(flag)) return true;
+    if ((it & 31) == 31) {
+      if (ld_acquire(abort)) return false;
+      if (gpu_clock_ns() - t0 > kWaitLimitNs) {
+        atomicExch(abort, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// The persistent loop: take the next task, wait for its dependencies (warp
+// 0's lanes each watch some of them), run it with the whole block, publish
+// its flag (fence, then a release store); with a trace buffer, record the
+// task's times.
+
+template <typename Run>
+__device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Run run) {
+  __shared__ int s_task, s_ok;
+  __shared__ unsigned long long s_t0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_task = ld_acquire(abort) ? g.n : atomicAdd(g.next, 1);
+      if (g.trace) s_t0 = gpu_clock_ns();
+    }
+    __syncthreads();
+    const int t = s_task;
+    if (t >= g.n) return;
+    if (threadIdx.x < 32) {
+      bool ok = true;
+      const int q1 = __ldg(g.dep_ptr + t + 1);
+      for (int q = __ldg(g.dep_ptr + t) + int(threadIdx.x); q < q1 && ok; q += 32)
+        ok = wait_done(g.done + __ldg(g.dep + q), abort);
+      ok = __all_sync(0xffffffffu, ok);
+      if (threadIdx.x == 0) s_ok = ok;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int4 tk = __ldg(g.task + t);
+    const unsigned long long t1 = g.trace && threadIdx.x == 0 ? gpu_clock_ns() : 0ull;
+    run(tk);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(g.done + t, 1);
+      if (g.trace) {
+        long long* r = g.trace + 6 * size_t(t);
+        r[0] = tk.x;
+        r[1] = tk.y;
+        r[2] = (long long)s_t0;
+        r[3] = (long long)t1;
+        r[4] = (long long)gpu_clock_ns();
+        r[5] = sm_id();
+      }
+    }
+  }
+}
+
 template <int NT>
 __device__ __forceinline__ void group_sync() {
   if constexpr (NT == 32)
@@ -65,24 +178,39 @@ __device__ __forceinline__ void group_sync() {
     __syncthreads();
 }
 
-// The panel of supernode t after its children's contributions: column by
-// column (every thread takes the same pivot and its reciprocal), P of
-// leading dimension h; the trailing columns go one per warp, rows over
-// the lanes.
+// ---------------------------------------------------------------------------
+// dense pieces of one supernode (panel P of leading dimension h, update
+// matrix U of leading dimension m = h - w, both in shared memory)
+// ---------------------------------------------------------------------------
+// Column by column: every thread takes the same pivot and its reciprocal;
+// the trailing columns go one per warp, rows over the lanes.
+// (FP64 is slow on this part: one warp instruction occupies a sub-partition
+// for 64 cycles however many lanes are active, so the pivot's reciprocal
+// square root, a 400-cycle chain, is computed by one warp and shared.)
 template <int NT>
 __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int tid, double tol,
                              int32_t* bad) {
   constexpr int NW = NT / 32;
   const int lane = tid & 31, warp = tid >> 5;
+  __shared__ double s_rinv;
   for (int k = 0; k < w; ++k) {
-    double p = P[size_t(k) * h + k];
-    if (!(p > tol)) {
-      if (tid == 0) atomicMin(bad, f + k);
-      p = 1.0;
+    double rinv = 0.0;
+    if (warp == 0) {  // nothing else reads the diagonal entry in this step
+      double p = P[size_t(k) * h + k];
+      if (!(p > tol)) {
+        if (tid == 0) atomicMin(bad, f + k);
+        p = 1.0;
+      }
+      rinv = rsqrt(p);
+      if (tid == 0) {
+        P[size_t(k) * h + k] = p * rinv;
+        if constexpr (NT > 32) s_rinv = rinv;
+      }
     }
-    const double r = sqrt(p), rinv = 1.0 / r;
     group_sync<NT>();
-    if (tid == 0) P[size_t(k) * h + k] = r;
+    if constexpr (NT > 32) {
+      if (warp != 0) rinv = s_rinv;
+    }
     for (int i = k + 1 + tid; i < h; i += NT) P[size_t(k) * h + i] *= rinv;
     group_sync<NT>();
     for (int j = k + 1 + warp; j < w; j += NW) {
@@ -93,8 +221,7 @@ __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int ti
   }
 }
 
-// U -= L21 L21' on the lower triangle (U of leading dimension m = h - w),
-// a column per warp, rows over the lanes.
+// U -= L21 L21' on the lower triangle, a column per warp, rows over the lanes.
 template <int NT>
 __device__ void form_update(const double* __restrict__ P, int h, int w, int tid,
                             double* __restrict__ U) {
@@ -109,10 +236,9 @@ __device__ void form_update(const double* __restrict__ P, int h, int w, int tid,
 }
 
 // Extend-add of t's children's update matrices, one child at a time: the
-// entries in t's columns go to the panel P (leading dimension h), the rest
-// to t's update matrix U (leading dimension h - w).  The child's row map is
-// staged in `srel` (a shared array of at least the child's row count) and
-// each thread keeps kBatch entries of the child's update matrix in flight.
+// entries in t's columns go to the panel P, the rest to the update matrix
+// U.  The child's row map is staged in `srel`; each thread keeps kBatch
+// entries of the child's update matrix in flight.
 template <int NT>
 __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict__ P, int h,
                            int w, double* __restrict__ U, int* __restrict__ srel) {
@@ -135,7 +261,7 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
         const int idx = base + u * NT;
         jj[u] = idx / mc;
         ii[u] = idx - jj[u] * mc;
-        v[u] = idx < total && ii[u] >= jj[u] ? Uc[idx] : 0.0;
+        v[u] = idx < total && ii[u] >= jj[u] ? __ldcg(Uc + idx) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
@@ -151,55 +277,459 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
   }
 }
 
-__device__ void factor_small(const CholDev& d, int t, int lane, double tol,
-                             double* __restrict__ ws, int* __restrict__ srel) {
+// A supernode staged in shared memory (ws: panel then update matrix) by a
+// group of NT threads: load, extend-add, factor, update matrix, store.
+template <int NT>
+__device__ void factor_staged(const CholDev& d, int t, int tid, double tol,
+                              double* __restrict__ ws, int* __restrict__ srel) {
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
   const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
   double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
   double* __restrict__ P = ws;
   double* __restrict__ U = ws + h * w;
-  for (int idx = lane; idx < h * w; idx += 32) P[idx] = Lt[idx];
-  for (int idx = lane; idx < m * m; idx += 32) U[idx] = 0.0;
-  __syncwarp();
-  extend_add<32>(d, t, lane, P, h, w, U, srel);
-  factor_panel<32>(P, h, w, f, lane, tol, d.bad);
-  form_update<32>(P, h, w, lane, U);
-  __syncwarp();
-  for (int idx = lane; idx < h * w; idx += 32) Lt[idx] = P[idx];
-  for (int idx = lane; idx < m * m; idx += 32) Ut[idx] = U[idx];
+  for (int idx = tid; idx < h * w; idx += NT) P[idx] = __ldcg(Lt + idx);
+  for (int idx = tid; idx < m * m; idx += NT) U[idx] = 0.0;
+  group_sync<NT>();
+  extend_add<NT>(d, t, tid, P, h, w, U, srel);
+  factor_panel<NT>(P, h, w, f, tid, tol, d.bad);
+  form_update<NT>(P, h, w, tid, U);
+  group_sync<NT>();
+  for (int idx = tid; idx < h * w; idx += NT) __stcg(Lt + idx, P[idx]);
+  for (int idx = tid; idx < m * m; idx += NT) __stcg(Ut + idx, U[idx]);
 }
 
-// A large supernode by a whole block: children and panel in shared memory
-// when the panel fits kPanelDoubles; when the panel and the update matrix
-// fit together, the update matrix too, and U_t -= L21 L21' is formed here;
-// otherwise k_chol_syrk forms it afterwards.
-__device__ void factor_large(const CholDev& d, int t, double tol, double* __restrict__ sp,
-                             int* __restrict__ srel) {
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
-  double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
-  const int pw = h * w;
-  const bool pan = pw <= kPanelDoubles, full = pw + m * m <= kPanelDoubles;
-  double* __restrict__ P = pan ? sp : Lt;
-  double* __restrict__ U = full ? sp + pw : Ut;
-  if (pan)
-    for (int idx = threadIdx.x; idx < pw; idx += kCholThreads) sp[idx] = Lt[idx];
-  if (full)
-    for (int idx = threadIdx.x; idx < m * m; idx += kCholThreads) U[idx] = 0.0;
-  __syncthreads();
-  extend_add<kCholThreads>(d, t, threadIdx.x, P, h, w, U, srel);
-  factor_panel<kCholThreads>(P, h, w, f, threadIdx.x, tol, d.bad);
-  if (full) {
-    form_update<kCholThreads>(P, h, w, threadIdx.x, U);
+// A group: its levels one after the other, a warp per supernode.
+__device__ void group_factor(const CholDev& d, int g, double tol, double* smem, int* srel) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lp = __ldg(d.grp_lptr + g), nlv = __ldg(d.grp_lptr + g + 1) - lp - 1;
+  double* ws = smem + warp * kSmallStage;
+  int* wr = srel + warp * kCholWarpRows;
+  for (int v = 0; v < nlv; ++v) {
+    const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
+    for (int q = a + warp; q < b; q += kWarps) factor_staged<32>(d, __ldg(d.grp_sn + q), lane, tol, ws, wr);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < m * m; idx += kCholThreads) Ut[idx] = U[idx];
   }
-  if (pan)
-    for (int idx = threadIdx.x; idx < pw; idx += kCholThreads) Lt[idx] = sp[idx];
 }
 
+// ---------------------------------------------------------------------------
+// tiles of a large supernode's front
+// ---------------------------------------------------------------------------
+struct Front {
+  double* L;  // panel, h x w, leading dimension h
+  double* U;  // update matrix, m x m, leading dimension m
+  int f, w, h, m, nbp;
+  __device__ Front(const CholDev& d, int s) {
+    f = __ldg(d.sn_first + s);
+    w = __ldg(d.sn_first + s + 1) - f;
+    h = __ldg(d.sn_rowptr + s + 1) - __ldg(d.sn_rowptr + s);
+    m = h - w;
+    nbp = (w + T - 1) / T;
+    L = d.Lx + __ldg(d.sn_off + s);
+    U = d.Ux + __ldg(d.u_off + s);
+  }
+  // first front row of tile row I and its row count (tiles do not straddle w)
+  __device__ void span(int I, int& r0, int& len) const {
+    if (I < nbp) {
+      r0 = I * T;
+      len = min(T, w - r0);
+    } else {
+      r0 = w + (I - nbp) * T;
+      len = min(T, h - r0);
+    }
+  }
+  // element (front row r, front column c), r >= c
+  __device__ double* at(int r, int c) const {
+    return c < w ? L + size_t(c) * h + r : U + size_t(c - w) * m + (r - w);
+  }
+  __device__ int ld(int c) const { return c < w ? h : m; }
+};
+
+// tile (rows r0.., cols c0..; nr x nc) of the front -> shared S (column-major,
+// leading dimension T): a row per lane, T / kWarps columns per warp, all
+// loads in flight together
+constexpr int kColsPerWarp = T / kWarps;
+__device__ __forceinline__ void tile_load(const Front& F, int r0, int nr, int c0, int nc,
+                                          double* __restrict__ S) {
+  const int lane = threadIdx.x & 31, w0 = threadIdx.x >> 5;
+  if (lane < nr) {
+    const double* src = F.at(r0 + lane, c0);
+    const size_t ld = F.ld(c0);
+    double v[kColsPerWarp];
+#pragma unroll
+    for (int u = 0; u < kColsPerWarp; ++u) {
+      const int c = w0 + u * kWarps;
+      v[u] = c < nc ? __ldcg(src + c * ld) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kColsPerWarp; ++u) S[(w0 + u * kWarps) * T + lane] = v[u];
+  }
+}
+__device__ __forceinline__ void tile_store(const Front& F, int r0, int nr, int c0, int nc,
+                                           const double* __restrict__ S) {
+  const int lane = threadIdx.x & 31, w0 = threadIdx.x >> 5;
+  if (lane < nr) {
+    double* dst = F.at(r0 + lane, c0);
+    const size_t ld = F.ld(c0);
+#pragma unroll
+    for (int u = 0; u < kColsPerWarp; ++u) {
+      const int c = w0 + u * kWarps;
+      if (c < nc) __stcg(dst + c * ld, S[c * T + lane]);
+    }
+  }
+}
+
+// Extend-add into tile (I, J): each child's update-matrix entries that land
+// in the tile, child after child.  The children's row maps ascend, so the
+// entries form one rectangle of the child's matrix: its rows [brk[I],
+// brk[I + 1]) and columns [brk[J], brk[J + 1]), brk being the child's row
+// positions at the parent's tile boundaries (computed on the host).
+__device__ void tile_asm(const CholDev& d, int s, int I, int J, double* smem) {
+  const Front F(d, s);
+  int r0, nr, c0, nc;
+  F.span(I, r0, nr);
+  F.span(J, c0, nc);
+  double* S = smem;
+  tile_load(F, r0, nr, c0, nc, S);
+  for (int q = __ldg(d.kid_ptr + s); q < __ldg(d.kid_ptr + s + 1); ++q) {
+    const int c = __ldg(d.kid + q);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const int32_t* rel = d.relmap + __ldg(d.rel_off + c);
+    const int32_t* brk = d.tile_brk + __ldg(d.brk_off + c);
+    const int ia = __ldg(brk + I), ni = __ldg(brk + I + 1) - ia;
+    const int ja = __ldg(brk + J), nj = __ldg(brk + J + 1) - ja;
+    const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
+    __syncthreads();  // the tile is loaded / the previous child's additions are done
+    for (int idx = threadIdx.x; idx < ni * nj; idx += kThreads) {
+      const int i = ia + idx % ni, j = ja + idx / ni;
+      if (i >= j) S[(__ldg(rel + j) - c0) * T + (__ldg(rel + i) - r0)] += __ldcg(Uc + size_t(j) * mc + i);
+    }
+  }
+  __syncthreads();
+  tile_store(F, r0, nr, c0, nc, S);
+}
+
+// Cholesky of diagonal tile k of the panel (pivot test as in factor_panel).
+__device__ void tile_potrf(const CholDev& d, int s, int k, double tol, double* smem) {
+  const Front F(d, s);
+  int r0, n;
+  F.span(k, r0, n);
+  double* A = smem;
+  tile_load(F, r0, n, r0, n, A);
+  __syncthreads();
+  __shared__ double s_rinv;
+  for (int c = 0; c < n; ++c) {
+    if (threadIdx.x < 32) {  // the pivot: one warp's reciprocal square root
+      double p = A[c * T + c];
+      if (!(p > tol)) {
+        if (threadIdx.x == 0) atomicMin(d.bad, F.f + r0 + c);
+        p = 1.0;
+      }
+      const double rinv = rsqrt(p);
+      if (threadIdx.x == 0) s_rinv = rinv;
+      __syncwarp();
+      if (threadIdx.x == 0) A[c * T + c] = p * rinv;
+    }
+    __syncthreads();
+    if (int(threadIdx.x) > c && int(threadIdx.x) < n) A[c * T + threadIdx.x] *= s_rinv;
+    __syncthreads();
+    // trailing lower triangle: column j = c + 1 + warp (+ kWarps ...), rows over the lanes
+    for (int j = c + 1 + int(threadIdx.x >> 5); j < n; j += kWarps) {
+      const int i = int(threadIdx.x & 31);
+      if (i >= j && i < n) A[j * T + i] -= A[c * T + i] * A[c * T + j];
+    }
+    __syncthreads();
+  }
+  tile_store(F, r0, n, r0, n, A);
+}
+
+// Tile (I, k) <- tile (I, k) L_kk^-T by four warps (one per sub-partition,
+// joined by a named barrier): a row of the tile per lane, column j held by
+// warp j mod 4 in registers.  Column c is scaled by its owner and shared;
+// every warp then subtracts its multiple from its later columns.
+constexpr int kTrsmWarps = 4;
+constexpr int kTrsmCols = T / kTrsmWarps;
+__device__ void tile_trsm(const CholDev& d, int s, int I, int k, double* smem) {
+  if (threadIdx.x >= 32 * kTrsmWarps) return;
+  const Front F(d, s);
+  int rk, n, r0, nr;
+  F.span(k, rk, n);
+  F.span(I, r0, nr);
+  double* Ls = smem;               // L_kk, column-major
+  double* rinv = smem + T * T;     // 1 / L_kk[c][c]
+  double* Xs = smem + T * T + T;   // the scaled column, two buffers
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  {  // L_kk: a row per lane, the warp's columns
+    const double* src = F.at(rk + lane, rk);
+    const size_t ld = F.ld(rk);
+#pragma unroll
+    for (int u = 0; u < kTrsmCols; ++u) {
+      const int c = wp + kTrsmWarps * u;
+      Ls[c * T + lane] = lane < n && c < n && c <= lane ? __ldcg(src + c * ld) : 0.0;
+    }
+  }
+  double b[kTrsmCols];
+  const double* src = F.at(r0 + (lane < nr ? lane : 0), rk);
+  const size_t ldb = F.ld(rk);
+#pragma unroll
+  for (int u = 0; u < kTrsmCols; ++u) {
+    const int c = wp + kTrsmWarps * u;
+    b[u] = lane < nr && c < n ? __ldcg(src + c * ldb) : 0.0;
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
+  if (wp == 0 && lane < n) rinv[lane] = 1.0 / Ls[lane * T + lane];
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
+#pragma unroll
+  for (int c = 0; c < T; ++c) {
+    if (c < n) {
+      if (wp == (c % kTrsmWarps)) {
+        const double x = b[c / kTrsmWarps] * rinv[c];
+        b[c / kTrsmWarps] = x;
+        Xs[(c & 1) * T + lane] = x;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
+      const double xc = Xs[(c & 1) * T + lane];
+#pragma unroll
+      for (int u = 0; u < kTrsmCols; ++u) {
+        const int j = wp + kTrsmWarps * u;
+        if (j > c && j < n) b[u] = fma(-xc, Ls[c * T + j], b[u]);
+      }
+    }
+  }
+  if (lane < nr) {
+    double* dst = F.at(r0 + lane, rk);
+#pragma unroll
+    for (int u = 0; u < kTrsmCols; ++u) {
+      const int c = wp + kTrsmWarps * u;
+      if (c < n) __stcg(dst + c * ldb, b[u]);
+    }
+  }
+}
+
+// Tile (I, J) -= tile (I, k) tile (J, k)' (lower part of a diagonal tile):
+// rows over the lanes, a column per warp and round.
+__device__ void tile_upd(const CholDev& d, int s, int I, int J, int k, double* smem) {
+  const Front F(d, s);
+  int rk, n, r0, nr, c0, nc;
+  F.span(k, rk, n);
+  F.span(I, r0, nr);
+  F.span(J, c0, nc);
+  double* As = smem;
+  double* Bs = smem + T * T;
+  tile_load(F, r0, nr, rk, n, As);
+  tile_load(F, c0, nc, rk, n, Bs);
+  __syncthreads();
+  const int i = int(threadIdx.x & 31);
+  if (i >= nr) return;
+  double* C = F.at(r0 + i, c0);
+  const int ld = F.ld(c0);
+  for (int j = int(threadIdx.x >> 5); j < nc; j += kWarps) {
+    if (I == J && i < j) continue;
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) acc = fma(As[q * T + i], Bs[q * T + j], acc);
+    __stcg(C + size_t(j) * ld, __ldcg(C + size_t(j) * ld) - acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// bottom levels: one thread per supernode (at most kCholBottomRows rows,
+// kCholBottomCols columns), its panel and the lower triangle of its update
+// matrix staged in shared memory, element e of thread t at [e * kBotThreads
+// + t] (so a warp's accesses fall on distinct banks)
+// ---------------------------------------------------------------------------
+constexpr int kBotThreads = 64;
+constexpr int kBotBatch = 16;   // global loads a thread keeps in flight
+// per-thread staging: the child's row map (kCholBottomRows ints, as doubles'
+// worth of space) then the panel and the packed lower update matrix
+constexpr int kBotMap = kCholBottomRows / 2;
+static_assert(kCholBottomRows == 16 && kCholBottomCols == 4, "staging is sized for 16 x 4");
+
+// `stage`: doubles of staging per thread for this level (at most kBotMap +
+// 142: h w + m (m + 1) / 2 <= 142 for h <= 16, w <= 4).
+__global__ void __launch_bounds__(kBotThreads) k_chol_bottom(CholDev d, const int32_t* __restrict__ list,
+                                                              int count, double tol) {
+  extern __shared__ double sb[];
+  const int q = blockIdx.x * kBotThreads + threadIdx.x;
+  if (q >= count) return;
+  int* __restrict__ R = reinterpret_cast<int*>(sb) + threadIdx.x;  // R[i * kBotThreads]
+  double* __restrict__ S = sb + kBotMap * kBotThreads + threadIdx.x;
+  const int s = __ldg(list + q);
+  const int f = __ldg(d.sn_first + s), w = __ldg(d.sn_first + s + 1) - f;
+  const int h = __ldg(d.sn_rowptr + s + 1) - __ldg(d.sn_rowptr + s), m = h - w, hw = h * w;
+  double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + s);
+  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + s);
+  // packed lower update matrix: column j at hw + j m - j (j - 1) / 2
+  auto uix = [&](int i, int j) { return hw + j * m - (j * (j - 1)) / 2 + (i - j); };
+  // the panel, kBotBatch loads in flight at a time
+  for (int e0 = 0; e0 < hw; e0 += kBotBatch) {
+    double v[kBotBatch];
+#pragma unroll
+    for (int u = 0; u < kBotBatch; ++u) v[u] = e0 + u < hw ? Lt[e0 + u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kBotBatch; ++u)
+      if (e0 + u < hw) S[(e0 + u) * kBotThreads] = v[u];
+  }
+  for (int e = hw; e < hw + m * (m + 1) / 2; ++e) S[e * kBotThreads] = 0.0;
+  for (int k = __ldg(d.kid_ptr + s); k < __ldg(d.kid_ptr + s + 1); ++k) {
+    const int c = __ldg(d.kid + k);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
+    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+    {  // the child's row map (at most kCholBottomRows - 1 rows below its columns)
+      int rv[kCholBottomRows];
+#pragma unroll
+      for (int u = 0; u < kCholBottomRows; ++u) rv[u] = u < mc ? __ldg(rel + u) : 0;
+#pragma unroll
+      for (int u = 0; u < kCholBottomRows; ++u) R[u * kBotThreads] = rv[u];
+    }
+    // its lower triangle, column by column, kBotBatch entries in flight at a time
+    int i = 0, j = 0;
+    const int nl = mc * (mc + 1) / 2;
+    for (int e0 = 0; e0 < nl; e0 += kBotBatch) {
+      double v[kBotBatch];
+      int ij[kBotBatch];
+#pragma unroll
+      for (int u = 0; u < kBotBatch; ++u) {
+        ij[u] = (j << 8) | i;
+        v[u] = e0 + u < nl ? Uc[size_t(j) * mc + i] : 0.0;
+        if (++i == mc) {
+          ++j;
+          i = j;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBotBatch; ++u) {
+        if (e0 + u >= nl) continue;
+        const int ri = R[(ij[u] & 0xff) * kBotThreads], rj = R[(ij[u] >> 8) * kBotThreads];
+        const int e = rj < w ? rj * h + ri : uix(ri - w, rj - w);
+        S[e * kBotThreads] += v[u];
+      }
+    }
+  }
+  for (int k = 0; k < w; ++k) {
+    double p = S[(k * h + k) * kBotThreads];
+    if (!(p > tol)) {
+      atomicMin(d.bad, f + k);
+      p = 1.0;
+    }
+    const double rinv = rsqrt(p), r = p * rinv;
+    S[(k * h + k) * kBotThreads] = r;
+    for (int i = k + 1; i < h; ++i) S[(k * h + i) * kBotThreads] *= rinv;
+    for (int j = k + 1; j < w; ++j) {
+      const double ljk = S[(k * h + j) * kBotThreads];
+      for (int i = j; i < h; ++i) S[(j * h + i) * kBotThreads] -= S[(k * h + i) * kBotThreads] * ljk;
+    }
+  }
+  for (int j = 0; j < m; ++j)
+    for (int i = j; i < m; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < w; ++k)
+        acc = fma(S[(k * h + w + i) * kBotThreads], S[(k * h + w + j) * kBotThreads], acc);
+      S[uix(i, j) * kBotThreads] -= acc;
+    }
+  for (int e = 0; e < hw; ++e) Lt[e] = S[e * kBotThreads];
+  for (int j = 0; j < m; ++j)
+    for (int i = j; i < m; ++i) Ut[size_t(j) * m + i] = S[uix(i, j) * kBotThreads];
+}
+
+// Forward substitution of the bottom supernodes of one level, a thread each.
+__global__ void __launch_bounds__(kThreads) k_chol_bottom_fwd(CholDev d, const int32_t* __restrict__ list,
+                                                               int count, double* __restrict__ y) {
+  const int q = blockIdx.x * kThreads + threadIdx.x;
+  if (q >= count) return;
+  const int s = __ldg(list + q);
+  const int f = __ldg(d.sn_first + s), w = __ldg(d.sn_first + s + 1) - f;
+  const int h = __ldg(d.sn_rowptr + s + 1) - __ldg(d.sn_rowptr + s), m = h - w;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + s);
+  double* __restrict__ zt = d.Zx + __ldg(d.z_off + s);
+  for (int k = __ldg(d.kid_ptr + s); k < __ldg(d.kid_ptr + s + 1); ++k) {
+    const int c = __ldg(d.kid + k);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const double* __restrict__ zc = d.Zx + __ldg(d.z_off + c);
+    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+    double v[kCholBottomRows];
+    int r[kCholBottomRows];
+#pragma unroll
+    for (int i = 0; i < kCholBottomRows; ++i) {
+      v[i] = i < mc ? zc[i] : 0.0;
+      r[i] = i < mc ? __ldg(rel + i) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kCholBottomRows; ++i) {
+      if (i >= mc) continue;
+      if (r[i] < w)
+        y[f + r[i]] += v[i];
+      else
+        zt[r[i] - w] += v[i];
+    }
+  }
+  double yv[kCholBottomCols];
+  for (int k = 0; k < w; ++k) {
+    const double yk = y[f + k] / Lt[size_t(k) * h + k];
+    y[f + k] = yk;
+    for (int i = k + 1; i < w; ++i) y[f + i] -= Lt[size_t(k) * h + i] * yk;
+  }
+#pragma unroll
+  for (int k = 0; k < kCholBottomCols; ++k) yv[k] = k < w ? y[f + k] : 0.0;
+  for (int i = 0; i < m; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kCholBottomCols; ++k)
+      if (k < w) acc = fma(Lt[size_t(k) * h + w + i], yv[k], acc);
+    zt[i] -= acc;
+  }
+}
+
+// Backward substitution of the bottom supernodes of one level, a thread each.
+__global__ void __launch_bounds__(kThreads) k_chol_bottom_bwd(CholDev d, const int32_t* __restrict__ list,
+                                                               int count, double* __restrict__ x) {
+  const int q = blockIdx.x * kThreads + threadIdx.x;
+  if (q >= count) return;
+  const int s = __ldg(list + q);
+  const int f = __ldg(d.sn_first + s), w = __ldg(d.sn_first + s + 1) - f;
+  const int r0 = __ldg(d.sn_rowptr + s), h = __ldg(d.sn_rowptr + s + 1) - r0;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + s);
+  double xb[kCholBottomRows];  // x at the rows below the supernode's columns
+#pragma unroll
+  for (int i = 0; i < kCholBottomRows; ++i) xb[i] = w + i < h ? x[__ldg(d.rowidx + r0 + w + i)] : 0.0;
+  for (int k = 0; k < w; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < kCholBottomRows; ++i)
+      if (w + i < h) acc = fma(Lt[size_t(k) * h + w + i], xb[i], acc);
+    x[f + k] -= acc;
+  }
+  for (int k = w - 1; k >= 0; --k) {
+    const double xk = x[f + k] / Lt[size_t(k) * h + k];
+    x[f + k] = xk;
+    for (int i = 0; i < k; ++i) x[f + i] -= Lt[size_t(i) * h + k] * xk;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_chol_factor_tasks(CholDev d, CholTasks g,
+                                                                    double tol) {
+  extern __shared__ double smem[];
+  int* srel = reinterpret_cast<int*>(smem + kStageDoubles);
+  task_loop(g, d.abort, [&](int4 tk) {
+    const int kind = tk.x & 0xff, k = tk.x >> 8;
+    switch (kind) {
+      case kTaskGroup: group_factor(d, tk.y, tol, smem, srel); break;
+      case kTaskBlock: factor_staged<kThreads>(d, tk.y, threadIdx.x, tol, smem, srel); break;
+      case kTaskAsm: tile_asm(d, tk.y, tk.z, tk.w, smem); break;
+      case kTaskPotrf: tile_potrf(d, tk.y, k, tol, smem); break;
+      case kTaskTrsm: tile_trsm(d, tk.y, tk.z, k, smem); break;
+      case kTaskUpd: tile_upd(d, tk.y, tk.z, tk.w, k, smem); break;
+      default: break;  // fin: no work
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------
+// solves
+// ---------------------------------------------------------------------------
 // The children's update vectors of t: entries in t's columns go to y, the
 // rest to t's update vector zt.
 template <int NT>
@@ -213,10 +743,8 @@ __device__ void add_children_z(const CholDev& d, int t, int tid, int f, int w,
     const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
     for (int ii = tid; ii < mc; ii += NT) {
       const int r = __ldg(rel + ii);
-      if (r < w)
-        y[f + r] += zc[ii];
-      else
-        zt[r - w] += zc[ii];
+      double* dst = r < w ? y + f + r : zt + (r - w);
+      __stcg(dst, __ldcg(dst) + __ldcg(zc + ii));
     }
     group_sync<NT>();
   }
@@ -232,16 +760,17 @@ __device__ void forward_small(const CholDev& d, int t, int lane, double* __restr
   double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
   add_children_z<32>(d, t, lane, f, w, y, zt);
   for (int k = 0; k < w; ++k) {
-    const double yk = y[f + k] / Lt[size_t(k) * h + k];
+    const double yk = __ldcg(y + f + k) / __ldcg(Lt + size_t(k) * h + k);
     __syncwarp();
-    if (lane == 0) y[f + k] = yk;
-    for (int i = k + 1 + lane; i < w; i += 32) y[f + i] -= Lt[size_t(k) * h + i] * yk;
+    if (lane == 0) __stcg(y + f + k, yk);
+    for (int i = k + 1 + lane; i < w; i += 32)
+      __stcg(y + f + i, __ldcg(y + f + i) - __ldcg(Lt + size_t(k) * h + i) * yk);
     __syncwarp();
   }
   for (int i = lane; i < m; i += 32) {
     double acc = 0.0;
-    for (int k = 0; k < w; ++k) acc = fma(Lt[size_t(k) * h + w + i], y[f + k], acc);
-    zt[i] -= acc;
+    for (int k = 0; k < w; ++k) acc = fma(__ldcg(Lt + size_t(k) * h + w + i), __ldcg(y + f + k), acc);
+    __stcg(zt + i, __ldcg(zt + i) - acc);
   }
 }
 
@@ -253,12 +782,12 @@ __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
   const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
-  add_children_z<kCholThreads>(d, t, threadIdx.x, f, w, y, zt);
-  for (int idx = threadIdx.x; idx < w * w; idx += kCholThreads) {
+  add_children_z<kThreads>(d, t, threadIdx.x, f, w, y, zt);
+  for (int idx = threadIdx.x; idx < w * w; idx += kThreads) {
     const int k = idx / w, i = idx - k * w;
-    sL[idx] = Lt[size_t(k) * h + i];
+    sL[idx] = __ldcg(Lt + size_t(k) * h + i);
   }
-  for (int k = threadIdx.x; k < w; k += kCholThreads) sy[k] = y[f + k];
+  for (int k = threadIdx.x; k < w; k += kThreads) sy[k] = __ldcg(y + f + k);
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -271,11 +800,11 @@ __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < w; k += kCholThreads) y[f + k] = sy[k];
-  for (int i = threadIdx.x; i < m; i += kCholThreads) {
+  for (int k = threadIdx.x; k < w; k += kThreads) __stcg(y + f + k, sy[k]);
+  for (int i = threadIdx.x; i < m; i += kThreads) {
     double acc = 0.0;
-    for (int k = 0; k < w; ++k) acc = fma(Lt[size_t(k) * h + w + i], sy[k], acc);
-    zt[i] -= acc;
+    for (int k = 0; k < w; ++k) acc = fma(__ldcg(Lt + size_t(k) * h + w + i), sy[k], acc);
+    __stcg(zt + i, __ldcg(zt + i) - acc);
   }
 }
 
@@ -289,16 +818,17 @@ __device__ void backward_small(const CholDev& d, int t, int lane, double* __rest
   for (int k = 0; k < w; ++k) {
     double acc = 0.0;
     for (int i = w + lane; i < h; i += 32)
-      acc = fma(Lt[size_t(k) * h + i], x[__ldg(d.rowidx + r0 + i)], acc);
+      acc = fma(__ldcg(Lt + size_t(k) * h + i), __ldcg(x + __ldg(d.rowidx + r0 + i)), acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[f + k] -= acc;
+    if (lane == 0) __stcg(x + f + k, __ldcg(x + f + k) - acc);
   }
   __syncwarp();
   for (int k = w - 1; k >= 0; --k) {
-    const double xk = x[f + k] / Lt[size_t(k) * h + k];
+    const double xk = __ldcg(x + f + k) / __ldcg(Lt + size_t(k) * h + k);
     __syncwarp();
-    if (lane == 0) x[f + k] = xk;
-    for (int i = lane; i < k; i += 32) x[f + i] -= Lt[size_t(i) * h + k] * xk;
+    if (lane == 0) __stcg(x + f + k, xk);
+    for (int i = lane; i < k; i += 32)
+      __stcg(x + f + i, __ldcg(x + f + i) - __ldcg(Lt + size_t(i) * h + k) * xk);
     __syncwarp();
   }
 }
@@ -309,16 +839,16 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
   const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   const int lane = threadIdx.x & 31;
-  for (int k = threadIdx.x >> 5; k < w; k += kCholThreads / 32) {
+  for (int k = threadIdx.x >> 5; k < w; k += kWarps) {
     double acc = 0.0;
     for (int i = w + lane; i < h; i += 32)
-      acc = fma(Lt[size_t(k) * h + i], x[__ldg(d.rowidx + r0 + i)], acc);
+      acc = fma(__ldcg(Lt + size_t(k) * h + i), __ldcg(x + __ldg(d.rowidx + r0 + i)), acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sx[k] = x[f + k] - acc;
+    if (lane == 0) sx[k] = __ldcg(x + f + k) - acc;
   }
-  for (int idx = threadIdx.x; idx < w * w; idx += kCholThreads) {
+  for (int idx = threadIdx.x; idx < w * w; idx += kThreads) {
     const int k = idx / w, i = idx - k * w;
-    sL[idx] = Lt[size_t(k) * h + i];
+    sL[idx] = __ldcg(Lt + size_t(k) * h + i);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -331,105 +861,43 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < w; k += kCholThreads) x[f + k] = sx[k];
+  for (int k = threadIdx.x; k < w; k += kThreads) __stcg(x + f + k, sx[k]);
 }
 
-// One level: blocks [0, n_large) take the level's first n_large supernodes
-// one per block; the remaining blocks take the rest one per warp.
-constexpr int kWarpsPerBlock = kCholThreads / 32;
-
-__device__ __forceinline__ int level_item(int n_large, int count, int& tid, bool& whole) {
-  if (int(blockIdx.x) < n_large) {
-    whole = true;
-    tid = threadIdx.x;
-    return blockIdx.x;
-  }
-  whole = false;
-  tid = threadIdx.x & 31;
-  const int q = n_large + (int(blockIdx.x) - n_large) * kWarpsPerBlock + int(threadIdx.x >> 5);
-  return q < count ? q : -1;
+__global__ void __launch_bounds__(kThreads, 4) k_chol_forward_tasks(CholDev d, CholTasks g,
+                                                                     double* __restrict__ y) {
+  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
+  task_loop(g, d.abort, [&](int4 tk) {
+    if ((tk.x & 0xff) == kTaskGroup) {
+      const int gi = tk.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
+      for (int v = 0; v < nlv; ++v) {
+        const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
+        for (int q = a + warp; q < b; q += kWarps) forward_small(d, __ldg(d.grp_sn + q), lane, y);
+        __syncthreads();
+      }
+    } else {
+      forward_large(d, tk.y, y, sL, sv);
+    }
+  });
 }
 
-// `stage`: doubles of shared memory per warp (small supernodes) or per
-// block (large ones) behind the row-map scratch.
-__global__ void __launch_bounds__(kCholThreads) k_chol_factor(CholDev d, int begin, int count,
-                                                               int n_large, double tol,
-                                                               int stage) {
-  extern __shared__ double sp[];
-  __shared__ int srel_all[kRelScratch];
-  int tid;
-  bool whole;
-  const int q = level_item(n_large, count, tid, whole);
-  if (q < 0) return;
-  const int t = __ldg(d.level_sn + begin + q);
-  if (whole) {
-    factor_large(d, t, tol, sp, srel_all);
-  } else {
-    const int warp = threadIdx.x >> 5;
-    factor_small(d, t, tid, tol, sp + warp * stage, srel_all + warp * kCholWarpRows);
-  }
-}
-
-// U_t -= L21 L21' for the large supernodes of a level, one 32 x 32 tile of
-// U_t per block: tiles[i] = {t, tile row, tile column, 0}, lower tiles only.
-constexpr int kTile = 32;
-__global__ void __launch_bounds__(kCholThreads) k_chol_syrk(CholDev d, const int4* __restrict__ tiles,
-                                                             int begin) {
-  __shared__ double A[kTile][kMaxWidth + 1], B[kTile][kMaxWidth + 1];
-  const int4 tl = __ldg(tiles + begin + blockIdx.x);
-  const int t = tl.x;
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
-  const double* __restrict__ L21 = d.Lx + __ldg(d.sn_off + t) + w;  // column k at L21[k h]
-  double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
-  const int i0 = tl.y * kTile, j0 = tl.z * kTile;
-  for (int idx = threadIdx.x; idx < kTile * w; idx += kCholThreads) {
-    const int r = idx % kTile, k = idx / kTile;
-    A[r][k] = i0 + r < m ? L21[size_t(k) * h + i0 + r] : 0.0;
-    B[r][k] = j0 + r < m ? L21[size_t(k) * h + j0 + r] : 0.0;
-  }
-  __syncthreads();
-  const int c = threadIdx.x % kTile, r0 = threadIdx.x / kTile;
-  const int j = j0 + c;
-  for (int r = r0; r < kTile; r += kCholThreads / kTile) {
-    const int i = i0 + r;
-    if (i >= m || j >= m || i < j) continue;
-    double acc = 0.0;
-    for (int k = 0; k < w; ++k) acc = fma(A[r][k], B[c][k], acc);
-    Ut[size_t(j) * m + i] -= acc;
-  }
-}
-
-__global__ void __launch_bounds__(kCholThreads) k_chol_fwd(CholDev d, int begin, int count,
-                                                            int n_large, double* __restrict__ y) {
-  __shared__ double sL[kMaxWidth * kMaxWidth], sy[kMaxWidth];
-  int tid;
-  bool whole;
-  const int q = level_item(n_large, count, tid, whole);
-  if (q < 0) return;
-  const int t = __ldg(d.level_sn + begin + q);
-  if (whole)
-    forward_large(d, t, y, sL, sy);
-  else
-    forward_small(d, t, tid, y);
-}
-
-__global__ void __launch_bounds__(kCholThreads) k_chol_bwd(CholDev d, int begin, int count,
-                                                            int n_large, double* __restrict__ x) {
-  __shared__ double sL[kMaxWidth * kMaxWidth], sx[kMaxWidth];
-  int tid;
-  bool whole;
-  const int q = level_item(n_large, count, tid, whole);
-  if (q < 0) return;
-  const int t = __ldg(d.level_sn + begin + q);
-  if (whole)
-    backward_large(d, t, x, sL, sx);
-  else
-    backward_small(d, t, tid, x);
-}
-
-int level_blocks(int count, int n_large) {
-  return n_large + (count - n_large + kWarpsPerBlock - 1) / kWarpsPerBlock;
+__global__ void __launch_bounds__(kThreads, 4) k_chol_backward_tasks(CholDev d, CholTasks g,
+                                                                      double* __restrict__ x) {
+  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
+  task_loop(g, d.abort, [&](int4 tk) {
+    if ((tk.x & 0xff) == kTaskGroup) {  // levels root side first
+      const int gi = tk.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
+      for (int v = nlv - 1; v >= 0; --v) {
+        const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
+        for (int q = a + warp; q < b; q += kWarps) backward_small(d, __ldg(d.grp_sn + q), lane, x);
+        __syncthreads();
+      }
+    } else {
+      backward_large(d, tk.y, x, sL, sv);
+    }
+  });
 }
 
 int grid_for(int64_t n, int threads) {
@@ -459,44 +927,69 @@ cudaError_t launch_chol_assemble(double* Lx, const int64_t* amap, const double* 
   return cudaGetLastError();
 }
 
-size_t chol_factor_smem_bytes(int count, int n_large, int stage) {
-  return size_t(n_large > 0 || count == 0 ? stage : kWarpsPerBlock * stage) * sizeof(double);
+size_t chol_bottom_smem_bytes(int stage) {
+  return size_t(kBotMap + stage) * kBotThreads * sizeof(double);
 }
 
-cudaError_t chol_allow_smem(size_t bytes) {
-  if (bytes + kRelScratch * sizeof(int) <= 48 * 1024) return cudaSuccess;  // the default
-  return cudaFuncSetAttribute(k_chol_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(bytes));
-}
-
-cudaError_t launch_chol_factor_level(const CholDev& d, int begin, int count, int n_large,
-                                     double tol, int stage, const int4* tiles, int tile_begin,
-                                     int n_tiles, cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  if (count > 0) {
-    const size_t smem = chol_factor_smem_bytes(count, n_large, stage);
-    k_chol_factor<<<level_blocks(count, n_large), kCholThreads, smem, s>>>(d, begin, count,
-                                                                            n_large, tol, stage);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess && n_tiles > 0) {
-    k_chol_syrk<<<n_tiles, kCholThreads, 0, s>>>(d, tiles, tile_begin);
-    e = cudaGetLastError();
-  }
-  return e;
-}
-
-cudaError_t launch_chol_fwd_level(const CholDev& d, int begin, int count, int n_large, double* y,
-                                  cudaStream_t s) {
+cudaError_t launch_chol_bottom(const CholDev& d, const int32_t* list, int count, int stage,
+                               double tol, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_chol_fwd<<<level_blocks(count, n_large), kCholThreads, 0, s>>>(d, begin, count, n_large, y);
+  k_chol_bottom<<<(count + kBotThreads - 1) / kBotThreads, kBotThreads,
+                  chol_bottom_smem_bytes(stage), s>>>(d, list, count, tol);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_bwd_level(const CholDev& d, int begin, int count, int n_large, double* x,
-                                  cudaStream_t s) {
+cudaError_t launch_chol_bottom_fwd(const CholDev& d, const int32_t* list, int count, double* y,
+                                   cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_chol_bwd<<<level_blocks(count, n_large), kCholThreads, 0, s>>>(d, begin, count, n_large, x);
+  k_chol_bottom_fwd<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(d, list, count, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_bottom_bwd(const CholDev& d, const int32_t* list, int count, double* x,
+                                   cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_chol_bottom_bwd<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(d, list, count, x);
+  return cudaGetLastError();
+}
+
+size_t chol_task_smem_bytes() {
+  return size_t(kStageDoubles) * sizeof(double) + size_t(kRelInts) * sizeof(int);
+}
+
+cudaError_t chol_task_setup(int* blocks_per_sm) {
+  const size_t bytes = chol_task_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_chol_factor_tasks,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_factor_tasks, kThreads, bytes);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(chol_bottom_smem_bytes(kCholBottomStage)));
+  if (e == cudaSuccess) *blocks_per_sm = std::min(per_sm, 2);
+  return e;
+}
+
+cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
+                                     cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  k_chol_factor_tasks<<<std::min(blocks, t.n), kThreads, chol_task_smem_bytes(), s>>>(d, t, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,
+                                      cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  k_chol_forward_tasks<<<std::min(blocks, t.n), kThreads, 0, s>>>(d, t, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
+                                       cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  k_chol_backward_tasks<<<std::min(blocks, t.n), kThreads, 0, s>>>(d, t, x);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
-// Device view of the supernodal factor and the launchers of chol.cu.
+// Device view of the supernodal factor, its task graphs, and the launchers
+// of chol.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,7 +8,37 @@
 
 namespace acopf {
 
-// Device copies of the symbolic arrays (see symbolic.h) and the factor.
+// Supernodes have at most this many columns (the solves stage a
+// supernode's diagonal block in shared memory).
+constexpr int kCholMaxWidth = 64;
+// Small supernodes (one warp each, inside group tasks): at most this many
+// rows and columns.
+constexpr int kCholWarpRows = 32;
+constexpr int kCholWarpCols = 8;
+// A child's rows below its columns fit a row-map scratch of this size.
+constexpr int kCholMaxRelRows = 4096;
+// Block tasks: panel plus update matrix staged in at most this many doubles,
+// and at most this many rows.
+constexpr int kCholBlockDoubles = 11264;
+constexpr int kCholBlockRows = 512;
+// Tiles of the tiled supernodes' fronts.
+constexpr int kCholTile = 32;
+
+// One task graph on the device: tasks (x = kind | k << 8, y, z, w), their
+// dependencies in CSR form, a finished flag per task and the counter the
+// blocks take tasks from (both zeroed before each run).
+struct CholTasks {
+  const int4* task;
+  const int32_t* dep_ptr;
+  const int32_t* dep;
+  int32_t* done;
+  int32_t* next;
+  long long* trace;  // NULL, or 6 words per task (kind, argument, taken, ready, finished, SM)
+  int32_t n;
+};
+
+// Device copies of the symbolic arrays (see symbolic.h, chol_plan.h) and
+// the factor.
 struct CholDev {
   int32_t n;
   const int32_t* sn_first;   // ns + 1
@@ -20,11 +51,17 @@ struct CholDev {
   const int32_t* relmap;
   const int64_t* u_off;      // ns + 1
   const int64_t* z_off;      // ns + 1
-  const int32_t* level_sn;   // ns
+  const int32_t* grp_ptr;    // groups + 1
+  const int32_t* grp_sn;
+  const int32_t* grp_lptr;   // groups + 1
+  const int32_t* grp_lev;
+  const int32_t* brk_off;    // ns: a tiled supernode's child's breakpoints in tile_brk
+  const int32_t* tile_brk;
   double* Lx;                // the supernodal blocks
   double* Ux;                // the update matrices
   double* Zx;                // the update vectors of a solve
   int32_t* bad;              // smallest failed pivot column (>= n: none)
+  int32_t* abort;            // nonzero: a task gave up waiting (the run failed)
 };
 
 cudaError_t launch_gather(double* out, const double* in, const int32_t* idx, int n,
@@ -33,33 +70,30 @@ cudaError_t launch_scatter(double* out, const double* in, const int32_t* idx, in
                            cudaStream_t s);
 cudaError_t launch_chol_assemble(double* Lx, const int64_t* amap, const double* kvals,
                                  int64_t nnz, cudaStream_t s);
-// Supernodes have at most this many columns; a large supernode's panel
-// (and its update matrix, when both fit) is staged in at most this many
-// doubles of shared memory.
-constexpr int kCholMaxWidth = 64;
-constexpr int kCholPanelDoubles = 20480;
-// Small supernodes (one warp each): at most this many rows and columns.
-constexpr int kCholWarpRows = 32;
-constexpr int kCholWarpCols = 8;
-// A child's rows below its columns fit a row-map scratch of this size.
-constexpr int kCholMaxRelRows = 4096;
 
-// Supernodes level_sn[begin .. begin + count): either all by a whole block
-// each (n_large == count), with `stage` doubles of shared memory (the
-// largest block staging), or all by a warp each (n_large == 0), with
-// `stage` doubles per warp (the largest panel plus update matrix of the
-// group); then the update-matrix tiles tiles[tile_begin .. + n_tiles) in a
-// second launch.
-cudaError_t launch_chol_factor_level(const CholDev& d, int begin, int count, int n_large,
-                                     double tol, int stage, const int4* tiles, int tile_begin,
-                                     int n_tiles, cudaStream_t s);
-// Dynamic shared memory of such a launch, and the opt-in that lets the
-// factor kernel use `bytes` of it (set once, before any launch or capture).
-size_t chol_factor_smem_bytes(int count, int n_large, int stage);
-cudaError_t chol_allow_smem(size_t bytes);
-cudaError_t launch_chol_fwd_level(const CholDev& d, int begin, int count, int n_large, double* y,
-                                  cudaStream_t s);
-cudaError_t launch_chol_bwd_level(const CholDev& d, int begin, int count, int n_large, double* x,
-                                  cudaStream_t s);
+// One bottom level (list: its count supernodes, device): the factorization,
+// forward and backward substitution, one thread per supernode.
+// `stage`: the level's largest h w + m (m + 1) / 2 (at most kCholBottomStage).
+constexpr int kCholBottomStage = 142;
+size_t chol_bottom_smem_bytes(int stage);
+cudaError_t launch_chol_bottom(const CholDev& d, const int32_t* list, int count, int stage,
+                               double tol, cudaStream_t s);
+cudaError_t launch_chol_bottom_fwd(const CholDev& d, const int32_t* list, int count, double* y,
+                                   cudaStream_t s);
+cudaError_t launch_chol_bottom_bwd(const CholDev& d, const int32_t* list, int count, double* x,
+                                   cudaStream_t s);
+// Dynamic shared memory of the task kernels, and the opt-in that lets them
+// use it (set once per device, before any launch or capture); blocks per SM
+// the kernels are launched with.
+size_t chol_task_smem_bytes();
+cudaError_t chol_task_setup(int* blocks_per_sm);
+// The factorization, forward and backward solve task kernels with `blocks`
+// persistent blocks (tasks, done flags and counter as described above).
+cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
+                                     cudaStream_t s);
+cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,
+                                      cudaStream_t s);
+cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
+                                       cudaStream_t s);
 
 }  // namespace acopf

@@ -6,10 +6,11 @@
 // fill-reducing order fixed once per pattern and refactors numerically every
 // iteration.
 //
-// Here: the symbolic phase (symbolic.cpp) runs on the host once per chol
-// object; the numeric factorization (multifrontal), its pivot test and the
-// solves are the supernodal kernels of chol.cu, one launch per level of the
-// supernodal elimination tree.
+// Here: the symbolic phase (symbolic.cpp) and the task graphs (chol_plan.cpp)
+// are built on the host once per chol object; the numeric factorization
+// (multifrontal), its pivot test and the solves are the persistent task
+// kernels of chol.cu: one launch for the factorization, one per direction of
+// a solve.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -18,16 +19,22 @@
 #include <vector>
 
 #include "chol_internal.h"
+#include "chol_plan.h"
 #include "host_internal.h"
 #include "symbolic.h"
 
 static_assert(acopf::kMaxSupernodeWidth == acopf::kCholMaxWidth,
-              "the syrk tiles and solve staging hold a supernode's full width");
-static_assert(acopf::kPanelSmemDoubles == acopf::kCholPanelDoubles &&
-                  acopf::kWarpMaxRows == acopf::kCholWarpRows &&
-                  acopf::kWarpMaxCols == acopf::kCholWarpCols &&
-                  acopf::kMaxRowsBelow == acopf::kCholMaxRelRows,
-              "host and kernels agree on what is staged in shared memory");
+              "the solves stage a supernode's diagonal block in shared memory");
+static_assert(acopf::kCholBottomRows * acopf::kCholBottomCols +
+                      (acopf::kCholBottomRows - acopf::kCholBottomCols) *
+                          (acopf::kCholBottomRows - acopf::kCholBottomCols + 1) / 2 <=
+                  acopf::kCholBottomStage,
+              "a bottom supernode's staging fits the kernel's bound");
+static_assert(acopf::kMaxRowsBelow == acopf::kCholMaxRelRows &&
+                  acopf::kCholBlockStage == acopf::kCholBlockDoubles &&
+                  acopf::kCholBlockMaxRows == acopf::kCholBlockRows &&
+                  acopf::kCholTileEdge == acopf::kCholTile,
+              "the plan and the kernels agree on what a task stages");
 
 using acopf::cuda_fail;
 using acopf::DeviceScope;
@@ -38,22 +45,22 @@ struct acopf_chol {
   int32_t n = 0;
   int64_t nnz_low = 0;
   acopf_chol_stats stats{};
-  std::vector<int32_t> perm_host, level_ptr, level_large, level_smem, tile_ptr;
-  std::vector<int32_t> level_big, level_smem_big, level_small_stage;
-  const int4* tiles = nullptr;
+  std::vector<int32_t> perm_host, bot_ptr, bot_stage;  // the bottom levels (chol_plan.h)
+  const int32_t* bot_sn = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
   acopf::CholDev dev{};
+  acopf::CholTasks tf{}, tfw{}, tbw{};  // factorization, forward and backward solve
+  int32_t* flags = nullptr;             // the three graphs' done flags and counters
+  size_t flag_ints = 0;
+  int blocks = 0, solve_blocks = 0;     // persistent blocks of the task kernels
   const int64_t* amap = nullptr;
   const int32_t* perm = nullptr;
   double* work = nullptr;       // n: the permuted right-hand side / solution
   size_t u_doubles = 0, z_doubles = 0;  // update matrices / vectors
-  int32_t* bad_host = nullptr;  // page-locked copy of dev.bad
+  int32_t* status_host = nullptr;       // page-locked copy of {bad, abort}
+  long long* trace = nullptr;           // task trace of the three graphs (NULL: off)
   bool factored = false;
-  // the groups of a level (big, other block-handled, small supernodes) are
-  // independent: two side streams run them beside the caller's stream
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   // the factorization's and the solve's launch sequences, captured as CUDA
   // graphs for the last arguments they ran with
   cudaGraphExec_t factor_exec = nullptr, solve_exec = nullptr;
@@ -65,15 +72,11 @@ struct acopf_chol {
 namespace {
 
 void release(acopf_chol* c) {
-  for (cudaStream_t st : c->side)
-    if (st) cudaStreamDestroy(st);
-  if (c->fork) cudaEventDestroy(c->fork);
-  for (cudaEvent_t ev : c->join)
-    if (ev) cudaEventDestroy(ev);
   if (c->factor_exec) cudaGraphExecDestroy(c->factor_exec);
   if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
   if (c->arena) cudaFree(c->arena);
-  if (c->bad_host) cudaFreeHost(c->bad_host);
+  if (c->trace) cudaFree(c->trace);
+  if (c->status_host) cudaFreeHost(c->status_host);
   delete c;
 }
 
@@ -97,72 +100,44 @@ acopf_status run_symbolic(const acopf_model* model, acopf::CholSymbolic& sy, con
   return ACOPF_OK;
 }
 
-// The factorization's device work: zeroed blocks, the assembly of M_cond's
-// values, and per level the big, the other block-handled and the small
-// supernodes (independent: on the caller's stream and two side streams that
-// fork from it and join back), then the update-matrix tiles.
+// The factorization's device work: zeroed blocks, update matrices, flags
+// and counter, the pivot marker, the assembly of M_cond's values, then the
+// task kernel.
 cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double tol,
                           cudaStream_t s) {
   const acopf::CholDev& d = chol->dev;
   cudaError_t e = cudaMemsetAsync(d.Lx, 0, size_t(chol->stats.storage) * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.Ux, 0, chol->u_doubles * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.bad, 0x7f, sizeof(int32_t), s);  // 0x7f7f7f7f: none
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(chol->tf.done, 0, (size_t(chol->tf.n) + 1) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = acopf::launch_chol_assemble(d.Lx, chol->amap, kvals, chol->nnz_low, s);
-  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large, &tp = chol->tile_ptr;
-  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v) {
-    const int32_t nb = chol->level_big[v], nl = ll[v], cnt = lp[v + 1] - lp[v];
-    // the level's groups, each on its own stream when more than one is present
-    const bool groups[3] = {nb > 0, nl > nb, cnt > nl};
-    const int ngroups = int(groups[0]) + int(groups[1]) + int(groups[2]);
-    cudaStream_t gs[3] = {s, s, s};
-    if (ngroups > 1) {
-      e = cudaEventRecord(chol->fork, s);
-      int k = 0;
-      for (int g = 0; g < 3 && e == cudaSuccess; ++g) {
-        if (!groups[g]) continue;
-        if (k > 0) {
-          gs[g] = chol->side[k - 1];
-          e = cudaStreamWaitEvent(gs[g], chol->fork, 0);
-        }
-        ++k;
-      }
-    }
-    if (e == cudaSuccess && groups[0])
-      e = acopf::launch_chol_factor_level(d, lp[v], nb, nb, tol, chol->level_smem_big[v],
-                                          chol->tiles, 0, 0, gs[0]);
-    if (e == cudaSuccess && groups[1])
-      e = acopf::launch_chol_factor_level(d, lp[v] + nb, nl - nb, nl - nb, tol,
-                                          chol->level_smem[v], chol->tiles, 0, 0, gs[1]);
-    if (e == cudaSuccess && groups[2])
-      e = acopf::launch_chol_factor_level(d, lp[v] + nl, cnt - nl, 0, tol,
-                                          chol->level_small_stage[v], chol->tiles, 0, 0, gs[2]);
-    if (ngroups > 1) {  // join the side streams back
-      int k = 0;
-      for (int g = 0; g < 3 && e == cudaSuccess; ++g) {
-        if (!groups[g] || gs[g] == s) continue;
-        e = cudaEventRecord(chol->join[k], gs[g]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, chol->join[k], 0);
-        ++k;
-      }
-    }
-    if (e == cudaSuccess && tp[v + 1] > tp[v])
-      e = acopf::launch_chol_factor_level(d, lp[v], 0, 0, tol, 0, chol->tiles, tp[v],
-                                          tp[v + 1] - tp[v], s);
-  }
+  const std::vector<int32_t>& bp = chol->bot_ptr;
+  for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
+    e = acopf::launch_chol_bottom(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->bot_stage[v],
+                                  tol, s);
+  if (e == cudaSuccess) e = acopf::launch_chol_factor_tasks(d, chol->tf, tol, chol->blocks, s);
   return e;
 }
 
-// The solve's device work: permutation, forward levels, backward levels,
+// The solve's device work: permutation, forward tasks, backward tasks,
 // permutation back.
 cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cudaStream_t s) {
   const acopf::CholDev& d = chol->dev;
-  const std::vector<int32_t>&lp = chol->level_ptr, &ll = chol->level_large;
   cudaError_t e = acopf::launch_gather(chol->work, b, chol->perm, chol->n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.Zx, 0, chol->z_doubles * sizeof(double), s);
-  for (size_t v = 0; e == cudaSuccess && v + 1 < lp.size(); ++v)
-    e = acopf::launch_chol_fwd_level(d, lp[v], lp[v + 1] - lp[v], ll[v], chol->work, s);
-  for (size_t v = lp.size() - 1; e == cudaSuccess && v > 0; --v)
-    e = acopf::launch_chol_bwd_level(d, lp[v - 1], lp[v] - lp[v - 1], ll[v - 1], chol->work, s);
+  if (e == cudaSuccess)  // forward and backward flags and counters are adjacent
+    e = cudaMemsetAsync(chol->tfw.done, 0,
+                        (size_t(chol->tfw.n) + size_t(chol->tbw.n) + 2) * sizeof(int32_t), s);
+  const std::vector<int32_t>& bp = chol->bot_ptr;
+  for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
+    e = acopf::launch_chol_bottom_fwd(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->work, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_forward_tasks(d, chol->tfw, chol->work, chol->solve_blocks, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_backward_tasks(d, chol->tbw, chol->work, chol->solve_blocks, s);
+  for (size_t v = bp.size() - 1; e == cudaSuccess && v > 0; --v)
+    e = acopf::launch_chol_bottom_bwd(d, chol->bot_sn + bp[v - 1], bp[v] - bp[v - 1], chol->work, s);
   if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
   return e;
 }
@@ -225,6 +200,12 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   acopf::CholSymbolic sy;
   st = run_symbolic(model, sy, "acopf_chol_create");
   if (st != ACOPF_OK) return st;
+  acopf::CholPlan plan;
+  {
+    std::string err;
+    st = acopf::chol_plan(sy, acopf::CholPlanParams{}, plan, err);
+    if (st != ACOPF_OK) return fail(st, "acopf_chol_create: " + err);
+  }
   acopf_chol* c = new (std::nothrow) acopf_chol;
   if (!c) return fail(ACOPF_E_OOM, "host allocation failed");
   c->model = model;
@@ -233,27 +214,38 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   c->stats = sy.stats;
   try {
     c->perm_host = sy.perm;
-    c->level_ptr = sy.level_ptr;
-    c->level_large = sy.level_large;
-    c->level_smem = sy.level_smem;
-    c->level_big = sy.level_big;
-    c->level_smem_big = sy.level_smem_big;
-    c->level_small_stage = sy.level_small_stage;
-    c->tile_ptr = sy.tile_ptr;
+    c->bot_ptr = plan.bot_ptr;
+    c->bot_stage = plan.bot_stage;
   } catch (const std::bad_alloc&) {
     release(c);
     return fail(ACOPF_E_OOM, "host allocation failed");
   }
-  const size_t ns = size_t(sy.ns), n = size_t(sy.n);
+  const size_t ns = size_t(sy.ns), n = size_t(sy.n), ng = plan.grp_ptr.size() - 1;
+  const acopf::CholGraph* graphs[3] = {&plan.factor, &plan.forward, &plan.backward};
   acopf::ArenaPlan p;
   const size_t o_first = p.take<int32_t>(ns + 1), o_rowptr = p.take<int32_t>(ns + 1);
   const size_t o_rowidx = p.take<int32_t>(sy.rowidx.size()), o_off = p.take<int64_t>(ns + 1);
   const size_t o_kptr = p.take<int32_t>(ns + 1), o_kid = p.take<int32_t>(sy.kid.size());
   const size_t o_roff = p.take<int32_t>(ns), o_rel = p.take<int32_t>(sy.relmap.size());
   const size_t o_uoff = p.take<int64_t>(ns + 1), o_zoff = p.take<int64_t>(ns + 1);
-  const size_t o_lev = p.take<int32_t>(ns), o_tiles = p.take<int32_t>(sy.tiles.size());
+  const size_t o_gptr = p.take<int32_t>(ng + 1), o_gsn = p.take<int32_t>(plan.grp_sn.size());
+  const size_t o_glp = p.take<int32_t>(ng + 1), o_glev = p.take<int32_t>(plan.grp_lev.size());
+  const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
+  const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
+  size_t o_task[3], o_dptr[3], o_dep[3];
+  for (int k = 0; k < 3; ++k) {
+    o_task[k] = p.take<int32_t>(graphs[k]->task.size());
+    o_dptr[k] = p.take<int32_t>(graphs[k]->dep_ptr.size());
+    o_dep[k] = p.take<int32_t>(graphs[k]->dep.size() + 1);
+  }
+  // done flags and counters: factor [n_f flags, counter], forward [n_fw, counter],
+  // backward [n_bw, counter] (forward and backward adjacent)
+  const size_t nf = size_t(plan.factor.n_tasks()), nfw = size_t(plan.forward.n_tasks()),
+               nbw = size_t(plan.backward.n_tasks());
+  c->flag_ints = nf + 1 + nfw + 1 + nbw + 1;
+  const size_t o_flags = p.take<int32_t>(c->flag_ints);
   const size_t o_amap = p.take<int64_t>(sy.amap.size()), o_perm = p.take<int32_t>(n);
-  const size_t o_work = p.take<double>(n), o_bad = p.take<int32_t>(1);
+  const size_t o_work = p.take<double>(n), o_status = p.take<int32_t>(2);
   const size_t o_lx = p.take<double>(size_t(sy.stats.storage));
   const size_t o_ux = p.take<double>(size_t(sy.u_off[ns]) + 1);
   const size_t o_zx = p.take<double>(size_t(sy.z_off[ns]) + 1);
@@ -282,29 +274,31 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_rel, sy.relmap.data(), sy.relmap.size() * 4);
   up(o_uoff, sy.u_off.data(), (ns + 1) * 8);
   up(o_zoff, sy.z_off.data(), (ns + 1) * 8);
-  up(o_lev, sy.level_sn.data(), ns * 4);
-  up(o_tiles, sy.tiles.data(), sy.tiles.size() * 4);
+  up(o_gptr, plan.grp_ptr.data(), (ng + 1) * 4);
+  up(o_gsn, plan.grp_sn.data(), plan.grp_sn.size() * 4);
+  up(o_glp, plan.grp_lptr.data(), (ng + 1) * 4);
+  up(o_glev, plan.grp_lev.data(), plan.grp_lev.size() * 4);
+  up(o_bot, plan.bot_sn.data(), plan.bot_sn.size() * 4);
+  up(o_boff, plan.brk_off.data(), ns * 4);
+  up(o_brk, plan.tile_brk.data(), plan.tile_brk.size() * 4);
+  for (int k = 0; k < 3; ++k) {
+    up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
+    up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
+    up(o_dep[k], graphs[k]->dep.data(), graphs[k]->dep.size() * 4);
+  }
   up(o_amap, sy.amap.data(), sy.amap.size() * 8);
   up(o_perm, sy.perm.data(), n * 4);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->bad_host, sizeof(int32_t));
-  for (cudaStream_t& st : c->side)
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
-  for (cudaEvent_t& ev : c->join)
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  size_t smem = 0;
-  for (size_t v = 0; v + 1 < sy.level_ptr.size(); ++v) {
-    const int32_t nb = sy.level_big[v], nl = sy.level_large[v];
-    const int32_t cnt = sy.level_ptr[v + 1] - sy.level_ptr[v];
-    smem = std::max({smem, acopf::chol_factor_smem_bytes(nb, nb, sy.level_smem_big[v]),
-                     acopf::chol_factor_smem_bytes(nl - nb, nl - nb, sy.level_smem[v]),
-                     acopf::chol_factor_smem_bytes(cnt - nl, 0, sy.level_small_stage[v])});
-  }
-  if (e == cudaSuccess) e = acopf::chol_allow_smem(smem);
+  if (e == cudaSuccess) e = cudaMemset(base + o_status, 0, 2 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->status_host, 2 * sizeof(int32_t));
+  int per_sm = 0, sms = 0;
+  if (e == cudaSuccess) e = acopf::chol_task_setup(&per_sm);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, model->device);
   if (e != cudaSuccess) {
     release(c);
     return cuda_fail(e, "acopf_chol_create: upload");
   }
+  c->blocks = per_sm * sms;
+  c->solve_blocks = 4 * sms;
   acopf::CholDev& d = c->dev;
   d.n = sy.n;
   d.sn_first = reinterpret_cast<const int32_t*>(base + o_first);
@@ -317,15 +311,33 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.relmap = reinterpret_cast<const int32_t*>(base + o_rel);
   d.u_off = reinterpret_cast<const int64_t*>(base + o_uoff);
   d.z_off = reinterpret_cast<const int64_t*>(base + o_zoff);
-  d.level_sn = reinterpret_cast<const int32_t*>(base + o_lev);
+  d.grp_ptr = reinterpret_cast<const int32_t*>(base + o_gptr);
+  d.grp_sn = reinterpret_cast<const int32_t*>(base + o_gsn);
+  d.grp_lptr = reinterpret_cast<const int32_t*>(base + o_glp);
+  d.grp_lev = reinterpret_cast<const int32_t*>(base + o_glev);
+  d.brk_off = reinterpret_cast<const int32_t*>(base + o_boff);
+  d.tile_brk = reinterpret_cast<const int32_t*>(base + o_brk);
   d.Lx = reinterpret_cast<double*>(base + o_lx);
   d.Ux = reinterpret_cast<double*>(base + o_ux);
   d.Zx = reinterpret_cast<double*>(base + o_zx);
-  d.bad = reinterpret_cast<int32_t*>(base + o_bad);
+  d.bad = reinterpret_cast<int32_t*>(base + o_status);
+  d.abort = d.bad + 1;
+  c->flags = reinterpret_cast<int32_t*>(base + o_flags);
+  acopf::CholTasks* tk[3] = {&c->tf, &c->tfw, &c->tbw};
+  int32_t* fl = c->flags;
+  for (int k = 0; k < 3; ++k) {
+    tk[k]->task = reinterpret_cast<const int4*>(base + o_task[k]);
+    tk[k]->dep_ptr = reinterpret_cast<const int32_t*>(base + o_dptr[k]);
+    tk[k]->dep = reinterpret_cast<const int32_t*>(base + o_dep[k]);
+    tk[k]->n = graphs[k]->n_tasks();
+    tk[k]->done = fl;
+    tk[k]->next = fl + tk[k]->n;
+    fl += tk[k]->n + 1;
+  }
+  c->bot_sn = reinterpret_cast<const int32_t*>(base + o_bot);
   c->amap = reinterpret_cast<const int64_t*>(base + o_amap);
   c->perm = reinterpret_cast<const int32_t*>(base + o_perm);
   c->work = reinterpret_cast<double*>(base + o_work);
-  c->tiles = reinterpret_cast<const int4*>(base + o_tiles);
   *out = c;
   return ACOPF_OK;
 }
@@ -356,10 +368,14 @@ acopf_status acopf_chol_factor(acopf_chol* chol, const double* kvals, double piv
   chol->factor_key = chol->factor_exec ? kvals : nullptr;
   chol->factor_tol = pivot_tol;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(chol->bad_host, d.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(chol->status_host, d.bad, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_factor");
-  const int32_t bad = *chol->bad_host;
+  if (chol->status_host[1] != 0)
+    return fail(ACOPF_E_TIMEOUT,
+                "acopf_chol_factor: a task of the factorization or of an earlier solve waited "
+                "past its limit; the object is unusable");
+  const int32_t bad = chol->status_host[0];
   *first_bad_pivot = bad < chol->n ? bad : -1;
   chol->factored = bad >= chol->n;
   return ACOPF_OK;
@@ -388,6 +404,58 @@ acopf_status acopf_chol_info(const acopf_chol* chol, acopf_chol_stats* stats,
   if (!chol) return fail(ACOPF_E_INVALID_ARG, "acopf_chol_info: null pointer");
   if (stats) *stats = chol->stats;
   if (device_bytes) *device_bytes = int64_t(chol->arena_bytes);
+  return ACOPF_OK;
+}
+
+acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable) {
+  if (!chol) return fail(ACOPF_E_INVALID_ARG, "acopf_chol_set_trace: null pointer");
+  DeviceScope ds(chol->model->device);
+  if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_chol_set_trace");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_set_trace");
+  acopf::CholTasks* tk[3] = {&chol->tf, &chol->tfw, &chol->tbw};
+  if (chol->trace) {
+    cudaFree(chol->trace);
+    chol->trace = nullptr;
+  }
+  if (enable) {
+    const size_t words = 6 * (size_t(tk[0]->n) + size_t(tk[1]->n) + size_t(tk[2]->n));
+    e = cudaMalloc(&chol->trace, words * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(chol->trace, 0, words * sizeof(long long));
+    if (e != cudaSuccess) {
+      if (chol->trace) cudaFree(chol->trace);
+      chol->trace = nullptr;
+      for (auto* t : tk) t->trace = nullptr;
+      return fail(ACOPF_E_OOM, "acopf_chol_set_trace: trace buffer");
+    }
+  }
+  long long* p = chol->trace;
+  for (auto* t : tk) {
+    t->trace = p;
+    if (p) p += 6 * size_t(t->n);
+  }
+  // the captured graphs hold the old kernel arguments
+  if (chol->factor_exec) cudaGraphExecDestroy(chol->factor_exec);
+  if (chol->solve_exec) cudaGraphExecDestroy(chol->solve_exec);
+  chol->factor_exec = chol->solve_exec = nullptr;
+  chol->factor_key = chol->solve_b = chol->solve_x = nullptr;
+  return ACOPF_OK;
+}
+
+acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out, int64_t capacity,
+                                  int64_t* n_tasks) {
+  if (!chol || !n_tasks || which < 0 || which > 2 || capacity < 0 || (!out && capacity > 0))
+    return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: bad argument");
+  const acopf::CholTasks* tk[3] = {&chol->tf, &chol->tfw, &chol->tbw};
+  *n_tasks = tk[which]->n;
+  if (!tk[which]->trace) return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: trace is off");
+  DeviceScope ds(chol->model->device);
+  cudaError_t e = ds.error();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  const size_t cnt = size_t(std::min<int64_t>(capacity, tk[which]->n));
+  if (e == cudaSuccess && cnt)
+    e = cudaMemcpy(out, tk[which]->trace, 6 * cnt * sizeof(long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_get_trace");
   return ACOPF_OK;
 }
 

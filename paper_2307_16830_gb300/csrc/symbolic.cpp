@@ -374,7 +374,7 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
       }
     }
 
-    // --- levels of the supernodal tree (leaves first) ---------------------
+    // --- depth of the supernodal tree (a statistic) -------------------------
     std::vector<int32_t> level(static_cast<size_t>(ns), 0);
     int32_t nlev = ns > 0 ? 1 : 0;
     for (int32_t s = 0; s < ns; ++s) {
@@ -383,72 +383,6 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
         level[size_t(p)] = std::max(level[size_t(p)], level[size_t(s)] + 1);
         nlev = std::max(nlev, level[size_t(p)] + 1);
       }
-    }
-    sy.level_ptr.assign(size_t(nlev) + 1, 0);
-    for (int32_t s = 0; s < ns; ++s) sy.level_ptr[size_t(level[size_t(s)]) + 1]++;
-    for (int32_t v = 0; v < nlev; ++v) sy.level_ptr[size_t(v) + 1] += sy.level_ptr[size_t(v)];
-    sy.level_sn.resize(size_t(ns));
-    {
-      std::vector<int32_t> nx(sy.level_ptr.begin(), sy.level_ptr.end() - 1);
-      for (int32_t s = 0; s < ns; ++s) sy.level_sn[size_t(nx[size_t(level[size_t(s)])]++)] = s;
-    }
-    // within a level, the large supernodes (a whole block each) first, then
-    // the small ones (a warp each), each group in ascending order
-    sy.level_large.assign(size_t(nlev), 0);
-    sy.level_big.assign(size_t(nlev), 0);
-    sy.level_smem.assign(size_t(nlev), 0);
-    sy.level_smem_big.assign(size_t(nlev), 0);
-    sy.level_small_stage.assign(size_t(nlev), 0);
-    sy.tile_ptr.assign(size_t(nlev) + 1, 0);
-    sy.tiles.clear();
-    auto dims = [&](int32_t s, int32_t& h, int32_t& w) {
-      h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
-      w = sy.sn_first[size_t(s) + 1] - sy.sn_first[size_t(s)];
-    };
-    // shared-memory doubles a block-handled supernode stages (kernel rule:
-    // panel and update matrix when both fit, else the panel when it fits)
-    auto staging = [&](int32_t s) {
-      int32_t h, w;
-      dims(s, h, w);
-      const int64_t pw = int64_t(h) * w, mm = int64_t(h - w) * (h - w);
-      return pw + mm <= kPanelSmemDoubles ? pw + mm : (pw <= kPanelSmemDoubles ? pw : 0);
-    };
-    auto is_big = [&](int32_t s) {
-      int32_t h, w;
-      dims(s, h, w);
-      return int64_t(h) * w > kPanelSmemDoubles || staging(s) > kMediumSmemDoubles;
-    };
-    for (int32_t v = 0; v < nlev; ++v) {
-      auto* first = sy.level_sn.data() + sy.level_ptr[size_t(v)];
-      auto* last = sy.level_sn.data() + sy.level_ptr[size_t(v) + 1];
-      auto* mid = std::stable_partition(first, last, [&](int32_t s) {
-        int32_t h, w;
-        dims(s, h, w);
-        return h > kWarpMaxRows || w > kWarpMaxCols;
-      });
-      auto* big_end = std::stable_partition(first, mid, is_big);
-      sy.level_large[size_t(v)] = int32_t(mid - first);
-      sy.level_big[size_t(v)] = int32_t(big_end - first);
-      for (auto* it = mid; it != last; ++it) {
-        int32_t h, w;
-        dims(*it, h, w);
-        sy.level_small_stage[size_t(v)] =
-            std::max(sy.level_small_stage[size_t(v)], h * w + (h - w) * (h - w));
-      }
-      for (auto* it = first; it != mid; ++it) {
-        const int32_t s = *it;
-        int32_t h, w;
-        dims(s, h, w);
-        const int32_t m = h - w;
-        const int64_t need = staging(s);
-        int32_t& slot = it < big_end ? sy.level_smem_big[size_t(v)] : sy.level_smem[size_t(v)];
-        slot = std::max<int32_t>(slot, int32_t(need));
-        if (int64_t(h) * w + int64_t(m) * m <= kPanelSmemDoubles) continue;  // formed with the panel
-        const int32_t nt = (m + 31) / 32;
-        for (int32_t ti = 0; ti < nt; ++ti)
-          for (int32_t tj = 0; tj <= ti; ++tj) sy.tiles.insert(sy.tiles.end(), {s, ti, tj, 0});
-      }
-      sy.tile_ptr[size_t(v) + 1] = int32_t(sy.tiles.size() / 4);
     }
 
     // --- counts -------------------------------------------------------------
