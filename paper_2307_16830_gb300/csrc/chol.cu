@@ -47,6 +47,8 @@ static_assert(kThreads == T * kWarps, "a tile column per warp, rows over the lan
 // per-warp staging of a small supernode: panel and update matrix,
 // h w + (h - w)^2 <= 32 + 31^2 for h <= 32
 constexpr int kSmallStage = 1024;
+constexpr int kSmallPanel = kCholWarpRows * kCholWarpCols;  // a small supernode's panel
+static_assert(kWarps * kSmallPanel <= kCholMaxWidth * kCholMaxWidth, "solve staging holds a group");
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kStageDoubles =
     cmax(cmax(kWarps * kSmallStage, kCholBlockDoubles), cmax(3 * T * T + T, kCholMaxWidth * (kCholMaxWidth + 1)));
@@ -189,7 +191,7 @@ __device__ __forceinline__ void group_sync() {
 // square root, a 400-cycle chain, is computed by one warp and shared.)
 template <int NT>
 __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int tid, double tol,
-                             int32_t* bad) {
+                             int32_t* bad, double* __restrict__ dinv) {
   constexpr int NW = NT / 32;
   const int lane = tid & 31, warp = tid >> 5;
   __shared__ double s_rinv;
@@ -204,6 +206,7 @@ __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int ti
       rinv = rsqrt(p);
       if (tid == 0) {
         P[size_t(k) * h + k] = p * rinv;
+        dinv[f + k] = rinv;
         if constexpr (NT > 32) s_rinv = rinv;
       }
     }
@@ -221,28 +224,59 @@ __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int ti
   }
 }
 
-// U -= L21 L21' on the lower triangle, a column per warp, rows over the lanes.
+// U -= L21 L21' on the lower triangle.  A block: a column per warp, rows
+// over the lanes.  A warp: the lower triangle's entries column by column,
+// 32 consecutive ones per round, so every lane has an entry.
 template <int NT>
 __device__ void form_update(const double* __restrict__ P, int h, int w, int tid,
                             double* __restrict__ U) {
   constexpr int NW = NT / 32;
   const int lane = tid & 31, m = h - w;
-  for (int j = tid >> 5; j < m; j += NW)
-    for (int i = j + lane; i < m; i += 32) {
+  if constexpr (NT == 32) {
+    const int total = m * (m + 1) / 2;
+    int i = lane, j = 0;  // entry `lane` of the triangle: column j, row i
+    while (j < m && i >= m) {
+      i -= m - j - 1;
+      ++j;
+    }
+    for (int e = lane; e < total; e += 32) {
       double acc = 0.0;
       for (int k = 0; k < w; ++k) acc = fma(P[size_t(k) * h + w + i], P[size_t(k) * h + w + j], acc);
       U[size_t(j) * m + i] -= acc;
+      i += 32;  // the entry 32 further on
+      while (j < m && i >= m) {
+        i -= m - j - 1;
+        ++j;
+      }
     }
+  } else {
+    for (int j = tid >> 5; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) {
+        double acc = 0.0;
+        for (int k = 0; k < w; ++k) acc = fma(P[size_t(k) * h + w + i], P[size_t(k) * h + w + j], acc);
+        U[size_t(j) * m + i] -= acc;
+      }
+  }
+}
+
+// (i, j) -> the entry `step` positions further on in the column-by-column
+// enumeration of an m x m lower triangle (rows j..m-1 of column j)
+__device__ __forceinline__ void tri_advance(int& i, int& j, int m, int step) {
+  i += step;
+  while (j < m && i >= m) {
+    i -= m - j - 1;
+    ++j;
+  }
 }
 
 // Extend-add of t's children's update matrices, one child at a time: the
 // entries in t's columns go to the panel P, the rest to the update matrix
-// U.  The child's row map is staged in `srel`; each thread keeps kBatch
-// entries of the child's update matrix in flight.
+// U.  The child's row map is staged in `srel`; the lower triangle of its
+// update matrix is read NT entries per round, kBatch rounds in flight.
 template <int NT>
 __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict__ P, int h,
                            int w, double* __restrict__ U, int* __restrict__ srel) {
-  constexpr int kBatch = 4;
+  constexpr int kBatch = 8;
   const int m = h - w;
   for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
     const int c = __ldg(d.kid + q);
@@ -252,20 +286,22 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
     const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
     for (int i = tid; i < mc; i += NT) srel[i] = __ldg(rel + i);
     group_sync<NT>();
-    const int total = mc * mc;
-    for (int base = tid; base < total; base += kBatch * NT) {
+    const int nl = mc * (mc + 1) / 2;
+    int i = 0, j = 0;
+    tri_advance(i, j, mc, tid);
+    for (int e0 = 0; e0 < nl; e0 += kBatch * NT) {
       double v[kBatch];
-      int jj[kBatch], ii[kBatch];
+      int ii[kBatch], jj[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        const int idx = base + u * NT;
-        jj[u] = idx / mc;
-        ii[u] = idx - jj[u] * mc;
-        v[u] = idx < total && ii[u] >= jj[u] ? __ldcg(Uc + idx) : 0.0;
+        ii[u] = i;
+        jj[u] = j;
+        v[u] = e0 + u * NT + tid < nl ? __ldcg(Uc + size_t(j) * mc + i) : 0.0;
+        tri_advance(i, j, mc, NT);
       }
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        if (base + u * NT >= total || ii[u] < jj[u]) continue;
+        if (e0 + u * NT + tid >= nl) continue;
         const int ri = srel[ii[u]], rj = srel[jj[u]];
         if (rj < w)
           P[size_t(rj) * h + ri] += v[u];
@@ -282,17 +318,26 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
 template <int NT>
 __device__ void factor_staged(const CholDev& d, int t, int tid, double tol,
                               double* __restrict__ ws, int* __restrict__ srel) {
+  constexpr int kBatch = 8;
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
   const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
   double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   double* __restrict__ Ut = d.Ux + __ldg(d.u_off + t);
   double* __restrict__ P = ws;
   double* __restrict__ U = ws + h * w;
-  for (int idx = tid; idx < h * w; idx += NT) P[idx] = __ldcg(Lt + idx);
+  const int hw = h * w;
+  for (int base = tid; base < hw; base += kBatch * NT) {  // kBatch loads in flight
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) v[u] = base + u * NT < hw ? __ldcg(Lt + base + u * NT) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (base + u * NT < hw) P[base + u * NT] = v[u];
+  }
   for (int idx = tid; idx < m * m; idx += NT) U[idx] = 0.0;
   group_sync<NT>();
   extend_add<NT>(d, t, tid, P, h, w, U, srel);
-  factor_panel<NT>(P, h, w, f, tid, tol, d.bad);
+  factor_panel<NT>(P, h, w, f, tid, tol, d.bad, d.Dinv);
   form_update<NT>(P, h, w, tid, U);
   group_sync<NT>();
   for (int idx = tid; idx < h * w; idx += NT) __stcg(Lt + idx, P[idx]);
@@ -427,7 +472,10 @@ __device__ void tile_potrf(const CholDev& d, int s, int k, double tol, double* s
         p = 1.0;
       }
       const double rinv = rsqrt(p);
-      if (threadIdx.x == 0) s_rinv = rinv;
+      if (threadIdx.x == 0) {
+        s_rinv = rinv;
+        d.Dinv[F.f + r0 + c] = rinv;
+      }
       __syncwarp();
       if (threadIdx.x == 0) A[c * T + c] = p * rinv;
     }
@@ -616,6 +664,7 @@ __global__ void __launch_bounds__(kBotThreads) k_chol_bottom(CholDev d, const in
     }
     const double rinv = rsqrt(p), r = p * rinv;
     S[(k * h + k) * kBotThreads] = r;
+    d.Dinv[f + k] = rinv;
     for (int i = k + 1; i < h; ++i) S[(k * h + i) * kBotThreads] *= rinv;
     for (int j = k + 1; j < w; ++j) {
       const double ljk = S[(k * h + j) * kBotThreads];
@@ -668,7 +717,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_bottom_fwd(CholDev d, const i
   }
   double yv[kCholBottomCols];
   for (int k = 0; k < w; ++k) {
-    const double yk = y[f + k] / Lt[size_t(k) * h + k];
+    const double yk = y[f + k] * d.Dinv[f + k];
     y[f + k] = yk;
     for (int i = k + 1; i < w; ++i) y[f + i] -= Lt[size_t(k) * h + i] * yk;
   }
@@ -703,7 +752,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_bottom_bwd(CholDev d, const i
     x[f + k] -= acc;
   }
   for (int k = w - 1; k >= 0; --k) {
-    const double xk = x[f + k] / Lt[size_t(k) * h + k];
+    const double xk = x[f + k] * d.Dinv[f + k];
     x[f + k] = xk;
     for (int i = 0; i < k; ++i) x[f + i] -= Lt[size_t(i) * h + k] * xk;
   }
@@ -750,28 +799,43 @@ __device__ void add_children_z(const CholDev& d, int t, int tid, int f, int w,
   }
 }
 
-// Forward substitution of one supernode by one warp (small supernodes):
-// the children's update vectors, the diagonal block, then its own update
-// vector z_t -= L21 y_t.
-__device__ void forward_small(const CholDev& d, int t, int lane, double* __restrict__ y) {
+// Forward substitution of one supernode by one warp (small supernodes): the
+// children's update vectors, the diagonal block (y_t in the lanes, pivots
+// as stored reciprocals), then its own update vector z_t -= L21 y_t.  The
+// panel is staged in the warp's slice `ws` of shared memory with all its
+// loads in flight.
+__device__ void forward_small(const CholDev& d, int t, int lane, double* __restrict__ y,
+                              double* __restrict__ ws) {
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
   const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
-  add_children_z<32>(d, t, lane, f, w, y, zt);
+  {
+    double v[kSmallPanel / 32];
+#pragma unroll
+    for (int u = 0; u < kSmallPanel / 32; ++u) {
+      const int e = lane + 32 * u;
+      v[u] = e < h * w ? __ldcg(Lt + e) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
+  }
+  add_children_z<32>(d, t, lane, f, w, y, zt);  // ends with a warp barrier
+  double yv = lane < w ? __ldcg(y + f + lane) : 0.0;
+  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
   for (int k = 0; k < w; ++k) {
-    const double yk = __ldcg(y + f + k) / __ldcg(Lt + size_t(k) * h + k);
-    __syncwarp();
-    if (lane == 0) __stcg(y + f + k, yk);
-    for (int i = k + 1 + lane; i < w; i += 32)
-      __stcg(y + f + i, __ldcg(y + f + i) - __ldcg(Lt + size_t(k) * h + i) * yk);
-    __syncwarp();
+    const double yk = __shfl_sync(0xffffffffu, yv * di, k);
+    if (lane == k) yv = yk;
+    if (lane > k && lane < w) yv = fma(-ws[k * h + lane], yk, yv);
   }
-  for (int i = lane; i < m; i += 32) {
-    double acc = 0.0;
-    for (int k = 0; k < w; ++k) acc = fma(__ldcg(Lt + size_t(k) * h + w + i), __ldcg(y + f + k), acc);
-    __stcg(zt + i, __ldcg(zt + i) - acc);
+  if (lane < w) __stcg(y + f + lane, yv);
+  double acc = 0.0;
+  for (int k = 0; k < w; ++k) {
+    const double yk = __shfl_sync(0xffffffffu, yv, k);
+    if (lane < m) acc = fma(ws[k * h + w + lane], yk, acc);
   }
+  if (lane < m) __stcg(zt + lane, __ldcg(zt + lane) - acc);
+  __syncwarp();  // the slice is reused by the warp's next supernode
 }
 
 // The same by a whole block, the diagonal block and y_t staged in shared
@@ -792,7 +856,7 @@ __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int k = 0; k < w; ++k) {
-      const double yk = sy[k] / sL[k * w + k];
+      const double yk = sy[k] * __ldcg(d.Dinv + f + k);
       __syncwarp();
       if (lane == 0) sy[k] = yk;
       for (int i = k + 1 + lane; i < w; i += 32) sy[i] -= sL[k * w + i] * yk;
@@ -808,29 +872,40 @@ __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
   }
 }
 
-// Backward substitution of one supernode: x_t -= L21' x(R_t below) (one
-// warp per column, a fixed reduction tree), then the transposed diagonal
-// block (by a warp; from shared memory in the block form).
-__device__ void backward_small(const CholDev& d, int t, int lane, double* __restrict__ x) {
+// Backward substitution of one supernode by one warp (small supernodes):
+// x_t -= L21' x(R_t below) (fixed reduction trees), then the transposed
+// diagonal block (x_t in the lanes).  Panel staged as in forward_small.
+__device__ void backward_small(const CholDev& d, int t, int lane, double* __restrict__ x,
+                               double* __restrict__ ws) {
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0;
+  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0, m = h - w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  for (int k = 0; k < w; ++k) {
-    double acc = 0.0;
-    for (int i = w + lane; i < h; i += 32)
-      acc = fma(__ldcg(Lt + size_t(k) * h + i), __ldcg(x + __ldg(d.rowidx + r0 + i)), acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) __stcg(x + f + k, __ldcg(x + f + k) - acc);
+  {
+    double v[kSmallPanel / 32];
+#pragma unroll
+    for (int u = 0; u < kSmallPanel / 32; ++u) {
+      const int e = lane + 32 * u;
+      v[u] = e < h * w ? __ldcg(Lt + e) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
   }
+  const double xb = lane < m ? __ldcg(x + __ldg(d.rowidx + r0 + w + lane)) : 0.0;
+  double xv = lane < w ? __ldcg(x + f + lane) : 0.0;
+  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
   __syncwarp();
-  for (int k = w - 1; k >= 0; --k) {
-    const double xk = __ldcg(x + f + k) / __ldcg(Lt + size_t(k) * h + k);
-    __syncwarp();
-    if (lane == 0) __stcg(x + f + k, xk);
-    for (int i = lane; i < k; i += 32)
-      __stcg(x + f + i, __ldcg(x + f + i) - __ldcg(Lt + size_t(i) * h + k) * xk);
-    __syncwarp();
+  for (int k = 0; k < w; ++k) {
+    double acc = lane < m ? ws[k * h + w + lane] * xb : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == k) xv -= acc;
   }
+  for (int k = w - 1; k >= 0; --k) {
+    const double xk = __shfl_sync(0xffffffffu, xv * di, k);
+    if (lane == k) xv = xk;
+    if (lane < k) xv = fma(-ws[lane * h + k], xk, xv);
+  }
+  if (lane < w) __stcg(x + f + lane, xv);
+  __syncwarp();
 }
 
 __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
@@ -853,7 +928,7 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
   __syncthreads();
   if (threadIdx.x < 32) {
     for (int k = w - 1; k >= 0; --k) {
-      const double xk = sx[k] / sL[k * w + k];
+      const double xk = sx[k] * __ldcg(d.Dinv + f + k);
       __syncwarp();
       if (lane == 0) sx[k] = xk;
       for (int i = lane; i < k; i += 32) sx[i] -= sL[i * w + k] * xk;
@@ -873,7 +948,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_chol_forward_tasks(CholDev d, C
       const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
       for (int v = 0; v < nlv; ++v) {
         const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
-        for (int q = a + warp; q < b; q += kWarps) forward_small(d, __ldg(d.grp_sn + q), lane, y);
+        for (int q = a + warp; q < b; q += kWarps)
+          forward_small(d, __ldg(d.grp_sn + q), lane, y, sL + warp * kSmallPanel);
         __syncthreads();
       }
     } else {
@@ -891,7 +967,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_chol_backward_tasks(CholDev d, 
       const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
       for (int v = nlv - 1; v >= 0; --v) {
         const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
-        for (int q = a + warp; q < b; q += kWarps) backward_small(d, __ldg(d.grp_sn + q), lane, x);
+        for (int q = a + warp; q < b; q += kWarps)
+          backward_small(d, __ldg(d.grp_sn + q), lane, x, sL + warp * kSmallPanel);
         __syncthreads();
       }
     } else {

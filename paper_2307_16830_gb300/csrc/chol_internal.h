@@ -60,6 +60,7 @@ struct CholDev {
   double* Lx;                // the supernodal blocks
   double* Ux;                // the update matrices
   double* Zx;                // the update vectors of a solve
+  double* Dinv;              // n: 1 / L[j][j] of the last factorization (the solves multiply)
   int32_t* bad;              // smallest failed pivot column (>= n: none)
   int32_t* abort;            // nonzero: a task gave up waiting (the run failed)
 };

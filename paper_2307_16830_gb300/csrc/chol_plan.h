@@ -52,7 +52,7 @@ enum CholSnClass : int8_t { kSnSmall = 0, kSnBlock = 1, kSnTiled = 2, kSnBottom 
 // one length): the pivots of 32 supernodes share each FP64 instruction.
 constexpr int32_t kCholBottomRows = 16;
 constexpr int32_t kCholBottomCols = 4;
-constexpr int32_t kCholBottomMinCount = 4096;
+constexpr int32_t kCholBottomMinCount = 32768;
 
 // Tile edge of the tiled supernodes' fronts.
 constexpr int32_t kCholTileEdge = 32;

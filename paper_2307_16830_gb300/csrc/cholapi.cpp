@@ -246,6 +246,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_flags = p.take<int32_t>(c->flag_ints);
   const size_t o_amap = p.take<int64_t>(sy.amap.size()), o_perm = p.take<int32_t>(n);
   const size_t o_work = p.take<double>(n), o_status = p.take<int32_t>(2);
+  const size_t o_dinv = p.take<double>(n);
   const size_t o_lx = p.take<double>(size_t(sy.stats.storage));
   const size_t o_ux = p.take<double>(size_t(sy.u_off[ns]) + 1);
   const size_t o_zx = p.take<double>(size_t(sy.z_off[ns]) + 1);
@@ -320,6 +321,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.Lx = reinterpret_cast<double*>(base + o_lx);
   d.Ux = reinterpret_cast<double*>(base + o_ux);
   d.Zx = reinterpret_cast<double*>(base + o_zx);
+  d.Dinv = reinterpret_cast<double*>(base + o_dinv);
   d.bad = reinterpret_cast<int32_t*>(base + o_status);
   d.abort = d.bad + 1;
   c->flags = reinterpret_cast<int32_t*>(base + o_flags);
