@@ -351,7 +351,8 @@ acopf_status acopf_chol_permutation(const acopf_chol* chol, int32_t* perm);
  * group), the GPU clock (ns) when a block took it, when its dependencies
  * were met, when it finished, and the SM that ran it; enable == 0 frees the
  * buffer.  acopf_chol_get_trace copies the last run of graph `which` (0 the
- * factorization, 1 the forward, 2 the backward solve) into `out` (HOST,
+ * factorization; the solves' block tasks: 1 forward, 2 backward; their
+ * warp tasks: 3 forward, 4 backward) into `out` (HOST,
  * 6 * capacity int64; NULL when capacity is 0) and sets *n_tasks to the
  * graph's task count; tasks
  * beyond `capacity` are not copied.  Synchronises the device. */

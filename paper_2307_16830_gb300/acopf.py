@@ -779,9 +779,10 @@ class Chol:
         _check(_chol_set_trace(self._h, 1 if enable else 0), "acopf_chol_set_trace")
 
     def trace(self, which: int = 0) -> np.ndarray:
-        """The last run's trace of graph `which` (0 factorization, 1 forward,
-        2 backward solve): one row per task, (kind word, argument, taken ns,
-        ready ns, finished ns, SM)."""
+        """The last run's trace of graph `which` (0 factorization; solve block
+        tasks 1 forward, 2 backward; solve warp tasks 3 forward, 4 backward):
+        one row per task, (kind word, argument, taken ns, ready ns, finished
+        ns, SM)."""
         n = C.c_int64(0)
         _check(_chol_get_trace(self._h, int(which), None, 0, C.byref(n)), "acopf_chol_get_trace")
         out = np.zeros((n.value, 6), dtype=np.int64)

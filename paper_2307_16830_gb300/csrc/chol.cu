@@ -799,17 +799,21 @@ __device__ void add_children_z(const CholDev& d, int t, int tid, int f, int w,
   }
 }
 
-// Forward substitution of one supernode by one warp (small supernodes): the
-// children's update vectors, the diagonal block (y_t in the lanes, pivots
-// as stored reciprocals), then its own update vector z_t -= L21 y_t.  The
-// panel is staged in the warp's slice `ws` of shared memory with all its
-// loads in flight.
+// Forward substitution of one supernode by one warp (small supernodes).
+// The front's right-hand side (y_t, then the update vector z_t, which no
+// one else writes and which starts at zero) is gathered in shared memory:
+// y_t, then the children's update vectors one child after the other (each
+// child's loads issued before the previous child is added).  Then the
+// diagonal block (y_t in the lanes, pivots as stored reciprocals) and
+// z_t = (gathered) - L21 y_t, each stored once.  The panel is staged in
+// the warp's slice `ws` with all its loads in flight.
 __device__ void forward_small(const CholDev& d, int t, int lane, double* __restrict__ y,
                               double* __restrict__ ws) {
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
   const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
   double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
+  double* __restrict__ acc = ws + kSmallPanel;  // h entries: y_t then z_t
   {
     double v[kSmallPanel / 32];
 #pragma unroll
@@ -817,11 +821,31 @@ __device__ void forward_small(const CholDev& d, int t, int lane, double* __restr
       const int e = lane + 32 * u;
       v[u] = e < h * w ? __ldcg(Lt + e) : 0.0;
     }
+    const double y0 = lane < w ? __ldcg(y + f + lane) : 0.0;
 #pragma unroll
     for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
+    if (lane < h) acc[lane] = y0;  // rows >= w: 0
   }
-  add_children_z<32>(d, t, lane, f, w, y, zt);  // ends with a warp barrier
-  double yv = lane < w ? __ldcg(y + f + lane) : 0.0;
+  const int k0 = __ldg(d.kid_ptr + t), k1 = __ldg(d.kid_ptr + t + 1);
+  int r = 0;
+  double zv = 0.0;
+  auto fetch = [&](int k) {  // lane's entry of child k's update vector and its row
+    const int c = __ldg(d.kid + k);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    r = lane < mc ? __ldg(d.relmap + __ldg(d.rel_off + c) + lane) : -1;
+    zv = lane < mc ? __ldcg(d.Zx + __ldg(d.z_off + c) + lane) : 0.0;
+  };
+  if (k0 < k1) fetch(k0);
+  __syncwarp();
+  for (int k = k0; k < k1; ++k) {
+    const int rr = r;
+    const double vv = zv;
+    if (k + 1 < k1) fetch(k + 1);
+    if (rr >= 0) acc[rr] += vv;  // a child's rows are distinct
+    __syncwarp();
+  }
+  double yv = lane < w ? acc[lane] : 0.0;
   const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
   for (int k = 0; k < w; ++k) {
     const double yk = __shfl_sync(0xffffffffu, yv * di, k);
@@ -829,12 +853,12 @@ __device__ void forward_small(const CholDev& d, int t, int lane, double* __restr
     if (lane > k && lane < w) yv = fma(-ws[k * h + lane], yk, yv);
   }
   if (lane < w) __stcg(y + f + lane, yv);
-  double acc = 0.0;
+  double z = lane < m ? acc[w + lane] : 0.0;
   for (int k = 0; k < w; ++k) {
     const double yk = __shfl_sync(0xffffffffu, yv, k);
-    if (lane < m) acc = fma(ws[k * h + w + lane], yk, acc);
+    if (lane < m) z = fma(-ws[k * h + w + lane], yk, z);
   }
-  if (lane < m) __stcg(zt + lane, __ldcg(zt + lane) - acc);
+  if (lane < m) __stcg(zt + lane, z);
   __syncwarp();  // the slice is reused by the warp's next supernode
 }
 
@@ -880,6 +904,9 @@ __device__ void backward_small(const CholDev& d, int t, int lane, double* __rest
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
   const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0, m = h - w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  const int ri = lane < m ? __ldg(d.rowidx + r0 + w + lane) : 0;
+  double xv = lane < w ? __ldcg(x + f + lane) : 0.0;
+  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
   {
     double v[kSmallPanel / 32];
 #pragma unroll
@@ -890,9 +917,7 @@ __device__ void backward_small(const CholDev& d, int t, int lane, double* __rest
 #pragma unroll
     for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
   }
-  const double xb = lane < m ? __ldcg(x + __ldg(d.rowidx + r0 + w + lane)) : 0.0;
-  double xv = lane < w ? __ldcg(x + f + lane) : 0.0;
-  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
+  const double xb = lane < m ? __ldcg(x + ri) : 0.0;
   __syncwarp();
   for (int k = 0; k < w; ++k) {
     double acc = lane < m ? ws[k * h + w + lane] * xb : 0.0;
@@ -942,39 +967,63 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
 __global__ void __launch_bounds__(kThreads, 4) k_chol_forward_tasks(CholDev d, CholTasks g,
                                                                      double* __restrict__ y) {
   __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
-  task_loop(g, d.abort, [&](int4 tk) {
-    if ((tk.x & 0xff) == kTaskGroup) {
-      const int gi = tk.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
-      for (int v = 0; v < nlv; ++v) {
-        const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
-        for (int q = a + warp; q < b; q += kWarps)
-          forward_small(d, __ldg(d.grp_sn + q), lane, y, sL + warp * kSmallPanel);
-        __syncthreads();
-      }
-    } else {
-      forward_large(d, tk.y, y, sL, sv);
-    }
-  });
+  task_loop(g, d.abort, [&](int4 tk) { forward_large(d, tk.y, y, sL, sv); });
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_chol_backward_tasks(CholDev d, CholTasks g,
                                                                       double* __restrict__ x) {
   __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
-  task_loop(g, d.abort, [&](int4 tk) {
-    if ((tk.x & 0xff) == kTaskGroup) {  // levels root side first
-      const int gi = tk.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      const int lp = __ldg(d.grp_lptr + gi), nlv = __ldg(d.grp_lptr + gi + 1) - lp - 1;
-      for (int v = nlv - 1; v >= 0; --v) {
-        const int a = __ldg(d.grp_lev + lp + v), b = __ldg(d.grp_lev + lp + v + 1);
-        for (int q = a + warp; q < b; q += kWarps)
-          backward_small(d, __ldg(d.grp_sn + q), lane, x, sL + warp * kSmallPanel);
-        __syncthreads();
-      }
-    } else {
-      backward_large(d, tk.y, x, sL, sv);
+  task_loop(g, d.abort, [&](int4 tk) { backward_large(d, tk.y, x, sL, sv); });
+}
+
+// The solves' warp tasks: each warp takes the next small supernode of the
+// list, waits (bounded) for the tasks it depends on, solves it and sets its
+// flag; the same progress argument as task_loop, with warps for blocks.
+template <bool kForward>
+__global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTasks g,
+                                                                double* __restrict__ v) {
+  __shared__ double ws_all[kWarps * (kSmallPanel + kCholWarpRows)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* ws = ws_all + warp * (kSmallPanel + kCholWarpRows);
+  for (;;) {
+    int t = 0;
+    unsigned long long t0 = 0ull;
+    if (lane == 0) {
+      t = ld_acquire(d.abort) ? g.n : atomicAdd(g.next, 1);
+      if (g.trace) t0 = gpu_clock_ns();
     }
-  });
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= g.n) return;
+    int ok = 1;
+    if (lane == 0) {
+      const int q1 = __ldg(g.dep_ptr + t + 1);
+      for (int q = __ldg(g.dep_ptr + t); q < q1 && ok; ++q) ok = wait_done(g.done + __ldg(g.dep + q), d.abort);
+      __threadfence();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    if (!ok) return;
+    const int4 tk = __ldg(g.task + t);
+    const unsigned long long t1 = g.trace && lane == 0 ? gpu_clock_ns() : 0ull;
+    if constexpr (kForward)
+      forward_small(d, tk.y, lane, v, ws);
+    else
+      backward_small(d, tk.y, lane, v, ws);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      st_release(g.done + t, 1);
+      if (g.trace) {
+        long long* r = g.trace + 6 * size_t(t);
+        r[0] = tk.x;
+        r[1] = tk.y;
+        r[2] = (long long)t0;
+        r[3] = (long long)t1;
+        r[4] = (long long)gpu_clock_ns();
+        r[5] = sm_id();
+      }
+    }
+  }
 }
 
 int grid_for(int64_t n, int threads) {
@@ -1067,6 +1116,17 @@ cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, dou
                                        cudaStream_t s) {
   if (t.n <= 0) return cudaSuccess;
   k_chol_backward_tasks<<<std::min(blocks, t.n), kThreads, 0, s>>>(d, t, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_solve_warps(const CholDev& d, const CholTasks& t, double* v, bool forward,
+                                    int blocks, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  const int grid = std::min(blocks, (t.n + kWarps - 1) / kWarps);
+  if (forward)
+    k_chol_solve_warps<true><<<grid, kThreads, 0, s>>>(d, t, v);
+  else
+    k_chol_solve_warps<false><<<grid, kThreads, 0, s>>>(d, t, v);
   return cudaGetLastError();
 }
 

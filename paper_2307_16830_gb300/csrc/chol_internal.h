@@ -96,5 +96,8 @@ cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, doub
                                       cudaStream_t s);
 cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
                                        cudaStream_t s);
+// The solves' warp tasks (one small supernode per warp) with `blocks` blocks.
+cudaError_t launch_chol_solve_warps(const CholDev& d, const CholTasks& t, double* v, bool forward,
+                                    int blocks, cudaStream_t s);
 
 }  // namespace acopf

@@ -400,28 +400,55 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
     }
     schedule(B.task, deps, B.dur, prm.workers, plan.factor, &plan.est_factor_us,
              &plan.est_critical_us, plan.est_critical_by_kind);
-    // --- the solves: groups, and one task per other supernode ----------------
-    Builder F;
-    std::vector<std::vector<int32_t>> fdeps;
-    std::vector<int32_t> fcomp(static_cast<size_t>(ns), -1);
-    for (int32_t g = 0; g < ng; ++g) {
-      F.add(kTaskGroup, g, 0, 0, grp_solve_us[size_t(g)]);
-      fdeps.emplace_back();
-    }
+    // --- the solves -------------------------------------------------------------
+    // Warp tasks: small supernodes whose descendants are all small (or
+    // bottom), one task each, in ascending (forward) or descending
+    // (backward) order; the rest are block tasks, run after the warp tasks
+    // in the forward solve and before them in the backward solve.
+    std::vector<char> wsmall(static_cast<size_t>(ns), 0);
     for (int32_t s = 0; s < ns; ++s) {
-      if (plan.sn_class[size_t(s)] == kSnBottom) continue;  // before (forward) / after (backward)
-      if (grp[size_t(s)] >= 0) {
-        fcomp[size_t(s)] = grp[size_t(s)];
-      } else {
+      if (plan.sn_class[size_t(s)] != kSnSmall) continue;
+      bool ok = true;
+      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1] && ok; ++q) {
+        const int32_t k = sy.kid[size_t(q)];
+        ok = wsmall[size_t(k)] || plan.sn_class[size_t(k)] == kSnBottom;
+      }
+      wsmall[size_t(s)] = ok;
+    }
+    std::vector<int32_t> widx(static_cast<size_t>(ns), -1), wsn;
+    for (int32_t s = 0; s < ns; ++s)
+      if (wsmall[size_t(s)]) {
+        widx[size_t(s)] = int32_t(wsn.size());
+        wsn.push_back(s);
+      }
+    const int32_t nw = int32_t(wsn.size());
+    {  // both directions ordered by a list schedule on the warps
+      std::vector<int32_t> wtask;
+      std::vector<double> wdur;
+      std::vector<std::vector<int32_t>> wf(static_cast<size_t>(nw)), wb(static_cast<size_t>(nw));
+      for (int32_t k = 0; k < nw; ++k) {
+        const int32_t s = wsn[size_t(k)];
+        wtask.insert(wtask.end(), {kTaskBlock, s, 0, 0});
+        wdur.push_back(6.0);
+        const int32_t p = sy.sn_parent[size_t(s)];
+        if (p >= 0 && widx[size_t(p)] >= 0) {
+          wf[size_t(widx[size_t(p)])].push_back(k);
+          wb[size_t(k)].push_back(widx[size_t(p)]);
+        }
+      }
+      schedule(wtask, wf, wdur, prm.warps, plan.forward_warp, nullptr, nullptr);
+      schedule(wtask, wb, wdur, prm.warps, plan.backward_warp, nullptr, nullptr);
+    }
+    Builder F;
+    std::vector<int32_t> fcomp(static_cast<size_t>(ns), -1);
+    for (int32_t s = 0; s < ns; ++s)
+      if (plan.sn_class[size_t(s)] != kSnBottom && !wsmall[size_t(s)])
         fcomp[size_t(s)] = F.add(kTaskBlock, s, 0, 0,
                                  2.0 + double(H[size_t(s)]) * W[size_t(s)] / 2000.0);
-        fdeps.emplace_back();
-      }
-    }
-    std::vector<std::vector<int32_t>> bdeps(fdeps.size());
+    std::vector<std::vector<int32_t>> fdeps(F.dur.size()), bdeps(F.dur.size());
     for (int32_t s = 0; s < ns; ++s) {
       const int32_t p = sy.sn_parent[size_t(s)];
-      if (p < 0 || fcomp[size_t(s)] < 0 || fcomp[size_t(p)] == fcomp[size_t(s)]) continue;
+      if (p < 0 || fcomp[size_t(s)] < 0) continue;
       // s's task needs s's children (forward); s's task needs its parent's (backward)
       fdeps[size_t(fcomp[size_t(p)])].push_back(fcomp[size_t(s)]);
       bdeps[size_t(fcomp[size_t(s)])].push_back(fcomp[size_t(p)]);

@@ -16,7 +16,8 @@
 //           it times the inverse transpose of that factor), upd (one tile
 //           minus the product of two trsm tiles) and fin (no work; done
 //           once the supernode's update matrix is complete).
-// The solves use the same groups, and one task per other supernode.
+// The solves take the small supernodes whose subtrees hold only small
+// supernodes one per warp, and the others one per block.
 #pragma once
 
 #include <cstdint>
@@ -88,7 +89,10 @@ struct CholPlan {
   std::vector<int8_t> sn_class;
   std::vector<int32_t> bot_ptr, bot_sn, bot_stage, brk_off, tile_brk;
   std::vector<int32_t> grp_ptr, grp_sn, grp_lptr, grp_lev;
-  CholGraph factor, forward, backward;
+  // factorization; solves: warp tasks (forward_warp, backward_warp: one
+  // small supernode each, every dependency earlier in the list) and block
+  // tasks (forward, backward: the other supernodes)
+  CholGraph factor, forward, backward, forward_warp, backward_warp;
   // the list schedule's estimates: makespan, critical path, and the
   // critical path's time by task kind
   double est_factor_us = 0.0, est_critical_us = 0.0, est_critical_by_kind[8] = {};
@@ -100,6 +104,7 @@ struct CholPlanParams {
   int32_t group_members = 64;
   double tile_fma = 150000.0;  // supernodes above this work are tiled
   int32_t workers = 304;       // concurrent blocks the list schedule assumes
+  int32_t warps = 4864;        // concurrent warps of the solves' warp tasks
 };
 
 // Builds the plan for the symbolic factorization sy (its supernodes, row

@@ -50,7 +50,10 @@ struct acopf_chol {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   acopf::CholDev dev{};
-  acopf::CholTasks tf{}, tfw{}, tbw{};  // factorization, forward and backward solve
+  // the task graphs: factorization, forward warp tasks, forward block tasks,
+  // backward block tasks, backward warp tasks (flags and counters in this
+  // order, the four of the solves adjacent)
+  acopf::CholTasks tg[5] = {};
   int32_t* flags = nullptr;             // the three graphs' done flags and counters
   size_t flag_ints = 0;
   int blocks = 0, solve_blocks = 0;     // persistent blocks of the task kernels
@@ -110,13 +113,13 @@ cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double to
   if (e == cudaSuccess) e = cudaMemsetAsync(d.Ux, 0, chol->u_doubles * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.bad, 0x7f, sizeof(int32_t), s);  // 0x7f7f7f7f: none
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(chol->tf.done, 0, (size_t(chol->tf.n) + 1) * sizeof(int32_t), s);
+    e = cudaMemsetAsync(chol->tg[0].done, 0, (size_t(chol->tg[0].n) + 1) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = acopf::launch_chol_assemble(d.Lx, chol->amap, kvals, chol->nnz_low, s);
   const std::vector<int32_t>& bp = chol->bot_ptr;
   for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
     e = acopf::launch_chol_bottom(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->bot_stage[v],
                                   tol, s);
-  if (e == cudaSuccess) e = acopf::launch_chol_factor_tasks(d, chol->tf, tol, chol->blocks, s);
+  if (e == cudaSuccess) e = acopf::launch_chol_factor_tasks(d, chol->tg[0], tol, chol->blocks, s);
   return e;
 }
 
@@ -126,16 +129,22 @@ cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cud
   const acopf::CholDev& d = chol->dev;
   cudaError_t e = acopf::launch_gather(chol->work, b, chol->perm, chol->n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.Zx, 0, chol->z_doubles * sizeof(double), s);
-  if (e == cudaSuccess)  // forward and backward flags and counters are adjacent
-    e = cudaMemsetAsync(chol->tfw.done, 0,
-                        (size_t(chol->tfw.n) + size_t(chol->tbw.n) + 2) * sizeof(int32_t), s);
+  if (e == cudaSuccess) {  // the solve graphs' flags and counters are adjacent
+    size_t words = 0;
+    for (int k = 1; k < 5; ++k) words += size_t(chol->tg[k].n) + 1;
+    e = cudaMemsetAsync(chol->tg[1].done, 0, words * sizeof(int32_t), s);
+  }
   const std::vector<int32_t>& bp = chol->bot_ptr;
   for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
     e = acopf::launch_chol_bottom_fwd(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->work, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_forward_tasks(d, chol->tfw, chol->work, chol->solve_blocks, s);
+    e = acopf::launch_chol_solve_warps(d, chol->tg[1], chol->work, true, chol->solve_blocks, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_backward_tasks(d, chol->tbw, chol->work, chol->solve_blocks, s);
+    e = acopf::launch_chol_forward_tasks(d, chol->tg[2], chol->work, chol->solve_blocks, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_backward_tasks(d, chol->tg[3], chol->work, chol->solve_blocks, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_solve_warps(d, chol->tg[4], chol->work, false, chol->solve_blocks, s);
   for (size_t v = bp.size() - 1; e == cudaSuccess && v > 0; --v)
     e = acopf::launch_chol_bottom_bwd(d, chol->bot_sn + bp[v - 1], bp[v] - bp[v - 1], chol->work, s);
   if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
@@ -221,7 +230,8 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     return fail(ACOPF_E_OOM, "host allocation failed");
   }
   const size_t ns = size_t(sy.ns), n = size_t(sy.n), ng = plan.grp_ptr.size() - 1;
-  const acopf::CholGraph* graphs[3] = {&plan.factor, &plan.forward, &plan.backward};
+  const acopf::CholGraph* graphs[5] = {&plan.factor, &plan.forward_warp, &plan.forward,
+                                       &plan.backward, &plan.backward_warp};
   acopf::ArenaPlan p;
   const size_t o_first = p.take<int32_t>(ns + 1), o_rowptr = p.take<int32_t>(ns + 1);
   const size_t o_rowidx = p.take<int32_t>(sy.rowidx.size()), o_off = p.take<int64_t>(ns + 1);
@@ -232,17 +242,15 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_glp = p.take<int32_t>(ng + 1), o_glev = p.take<int32_t>(plan.grp_lev.size());
   const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
   const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
-  size_t o_task[3], o_dptr[3], o_dep[3];
-  for (int k = 0; k < 3; ++k) {
+  size_t o_task[5], o_dptr[5], o_dep[5];
+  for (int k = 0; k < 5; ++k) {
     o_task[k] = p.take<int32_t>(graphs[k]->task.size());
     o_dptr[k] = p.take<int32_t>(graphs[k]->dep_ptr.size());
     o_dep[k] = p.take<int32_t>(graphs[k]->dep.size() + 1);
   }
-  // done flags and counters: factor [n_f flags, counter], forward [n_fw, counter],
-  // backward [n_bw, counter] (forward and backward adjacent)
-  const size_t nf = size_t(plan.factor.n_tasks()), nfw = size_t(plan.forward.n_tasks()),
-               nbw = size_t(plan.backward.n_tasks());
-  c->flag_ints = nf + 1 + nfw + 1 + nbw + 1;
+  // done flags and counters: per graph [its n flags, its counter]
+  c->flag_ints = 0;
+  for (int k = 0; k < 5; ++k) c->flag_ints += size_t(graphs[k]->n_tasks()) + 1;
   const size_t o_flags = p.take<int32_t>(c->flag_ints);
   const size_t o_amap = p.take<int64_t>(sy.amap.size()), o_perm = p.take<int32_t>(n);
   const size_t o_work = p.take<double>(n), o_status = p.take<int32_t>(2);
@@ -282,7 +290,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_bot, plan.bot_sn.data(), plan.bot_sn.size() * 4);
   up(o_boff, plan.brk_off.data(), ns * 4);
   up(o_brk, plan.tile_brk.data(), plan.tile_brk.size() * 4);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 5; ++k) {
     up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
     up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
     up(o_dep[k], graphs[k]->dep.data(), graphs[k]->dep.size() * 4);
@@ -325,9 +333,9 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.bad = reinterpret_cast<int32_t*>(base + o_status);
   d.abort = d.bad + 1;
   c->flags = reinterpret_cast<int32_t*>(base + o_flags);
-  acopf::CholTasks* tk[3] = {&c->tf, &c->tfw, &c->tbw};
   int32_t* fl = c->flags;
-  for (int k = 0; k < 3; ++k) {
+  acopf::CholTasks* tk[5] = {&c->tg[0], &c->tg[1], &c->tg[2], &c->tg[3], &c->tg[4]};
+  for (int k = 0; k < 5; ++k) {
     tk[k]->task = reinterpret_cast<const int4*>(base + o_task[k]);
     tk[k]->dep_ptr = reinterpret_cast<const int32_t*>(base + o_dptr[k]);
     tk[k]->dep = reinterpret_cast<const int32_t*>(base + o_dep[k]);
@@ -415,13 +423,14 @@ acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable) {
   if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_chol_set_trace");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_set_trace");
-  acopf::CholTasks* tk[3] = {&chol->tf, &chol->tfw, &chol->tbw};
+  acopf::CholTasks* tk[5] = {&chol->tg[0], &chol->tg[1], &chol->tg[2], &chol->tg[3], &chol->tg[4]};
   if (chol->trace) {
     cudaFree(chol->trace);
     chol->trace = nullptr;
   }
   if (enable) {
-    const size_t words = 6 * (size_t(tk[0]->n) + size_t(tk[1]->n) + size_t(tk[2]->n));
+    size_t words = 0;
+    for (auto* t : tk) words += 6 * size_t(t->n);
     e = cudaMalloc(&chol->trace, words * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(chol->trace, 0, words * sizeof(long long));
     if (e != cudaSuccess) {
@@ -446,9 +455,10 @@ acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable) {
 
 acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out, int64_t capacity,
                                   int64_t* n_tasks) {
-  if (!chol || !n_tasks || which < 0 || which > 2 || capacity < 0 || (!out && capacity > 0))
+  if (!chol || !n_tasks || which < 0 || which > 4 || capacity < 0 || (!out && capacity > 0))
     return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: bad argument");
-  const acopf::CholTasks* tk[3] = {&chol->tf, &chol->tfw, &chol->tbw};
+  const acopf::CholTasks* tk[5] = {&chol->tg[0], &chol->tg[2], &chol->tg[3], &chol->tg[1],
+                                   &chol->tg[4]};
   *n_tasks = tk[which]->n;
   if (!tk[which]->trace) return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: trace is off");
   DeviceScope ds(chol->model->device);
