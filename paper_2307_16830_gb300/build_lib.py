@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libacopf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["model.cpp", "capi.cpp", "batch.cpp", "server.cpp", "pipeline.cpp", "stepapi.cpp",
-           "cholapi.cpp", "symbolic.cpp", "chol_plan.cpp", "ipm.cpp", "kernels.cu", "step.cu",
+           "cholapi.cpp", "symbolic.cpp", "amd.cpp", "chol_plan.cpp", "ipm.cpp", "kernels.cu", "step.cu",
            "chol.cu", "ipm_k.cu", "noalloc.cu"]
 
 

@@ -5,8 +5,8 @@
 //
 // Sec. V factorizes M_cond with a fill-reducing order fixed once per
 // pattern and refactors numerically every iteration; this is the once-per-
-// pattern part.  The order is minimum degree on the explicit elimination
-// graph (the exact degrees that approximate minimum degree estimates).
+// pattern part.  The order is approximate minimum degree (amd.cpp), the
+// order family the paper's solvers use.
 #include "symbolic.h"
 
 #include <algorithm>
@@ -17,78 +17,6 @@
 namespace acopf {
 namespace {
 
-// Minimum-degree elimination order of the graph `adj` (sorted adjacency
-// lists without self loops).  Eliminating v joins its neighbours into a
-// clique.  Vertices wait in buckets by degree (doubly linked lists, O(1)
-// moves); among vertices of the minimum degree the one most recently placed
-// in its bucket goes first (initially the largest index), a deterministic
-// rule.  Fails when the elimination graph outgrows `max_entries` adjacency
-// entries.
-bool minimum_degree(std::vector<std::vector<int32_t>>& adj, int64_t max_entries,
-                    std::vector<int32_t>& order) {
-  const int32_t n = int32_t(adj.size());
-  std::vector<int32_t> head(size_t(n) + 1, -1), next(size_t(n), -1), prev(size_t(n), -1);
-  std::vector<int32_t> deg(static_cast<size_t>(n));
-  auto insert = [&](int32_t v, int32_t d) {
-    deg[size_t(v)] = d;
-    prev[size_t(v)] = -1;
-    next[size_t(v)] = head[size_t(d)];
-    if (head[size_t(d)] >= 0) prev[size_t(head[size_t(d)])] = v;
-    head[size_t(d)] = v;
-  };
-  auto remove = [&](int32_t v) {
-    const int32_t d = deg[size_t(v)];
-    if (prev[size_t(v)] >= 0)
-      next[size_t(prev[size_t(v)])] = next[size_t(v)];
-    else
-      head[size_t(d)] = next[size_t(v)];
-    if (next[size_t(v)] >= 0) prev[size_t(next[size_t(v)])] = prev[size_t(v)];
-  };
-  int64_t entries = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    insert(v, int32_t(adj[size_t(v)].size()));
-    entries += int64_t(adj[size_t(v)].size());
-  }
-  order.clear();
-  order.reserve(size_t(n));
-  std::vector<int32_t> merged, nv;
-  int32_t mindeg = 0;
-  for (int32_t k = 0; k < n; ++k) {
-    while (head[size_t(mindeg)] < 0) ++mindeg;
-    const int32_t v = head[size_t(mindeg)];
-    remove(v);
-    order.push_back(v);
-    nv.swap(adj[size_t(v)]);
-    adj[size_t(v)].clear();
-    entries -= int64_t(nv.size());
-    for (const int32_t u : nv) {
-      std::vector<int32_t>& au = adj[size_t(u)];
-      merged.clear();
-      merged.reserve(au.size() + nv.size());
-      size_t p = 0, q = 0;
-      while (p < au.size() || q < nv.size()) {
-        int32_t x;
-        if (q == nv.size() || (p < au.size() && au[p] < nv[q])) {
-          x = au[p++];
-        } else if (p == au.size() || nv[q] < au[p]) {
-          x = nv[q++];
-        } else {
-          x = au[p++];
-          ++q;
-        }
-        if (x != u && x != v) merged.push_back(x);
-      }
-      entries += int64_t(merged.size()) - int64_t(au.size());
-      au.swap(merged);
-      remove(u);
-      insert(u, int32_t(au.size()));
-      if (deg[size_t(u)] < mindeg) mindeg = deg[size_t(u)];
-    }
-    if (entries > max_entries) return false;
-  }
-  return true;
-}
-
 }  // namespace
 
 acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
@@ -97,21 +25,32 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     sy = CholSymbolic{};
     sy.n = n;
     const int64_t nnz_low = rp[size_t(n)];
-    // --- fill-reducing order --------------------------------------------
-    std::vector<std::vector<int32_t>> adj(static_cast<size_t>(n));
+    // --- fill-reducing order: approximate minimum degree (amd.cpp) -------
+    std::vector<int32_t> ap(size_t(n) + 1, 0), ai;
     for (int32_t i = 0; i < n; ++i)
-      for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
-        const int32_t j = ci[size_t(k)];
-        if (j == i) continue;
-        adj[size_t(i)].push_back(j);  // rows ascend, so every list stays sorted
-        adj[size_t(j)].push_back(i);
-      }
+      for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
+        if (ci[size_t(k)] != i) {
+          ap[size_t(i) + 1]++;
+          ap[size_t(ci[size_t(k)]) + 1]++;
+        }
+    for (int32_t i = 0; i < n; ++i) ap[size_t(i) + 1] += ap[size_t(i)];
+    ai.resize(size_t(ap[size_t(n)]));
+    {
+      std::vector<int32_t> nx(ap.begin(), ap.end() - 1);
+      for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
+          const int32_t j = ci[size_t(k)];
+          if (j == i) continue;
+          ai[size_t(nx[size_t(i)]++)] = j;
+          ai[size_t(nx[size_t(j)]++)] = i;
+        }
+    }
     std::vector<int32_t> md;
-    if (!minimum_degree(adj, kMaxGraphEntries, md)) {
-      err = "the elimination graph of M_cond exceeds " + std::to_string(kMaxGraphEntries) +
-            " entries (fill too large for a sparse factorization)";
+    if (!approximate_minimum_degree(n, ap, ai, md)) {
+      err = "the fill-reducing order failed";
       return ACOPF_E_INVALID_ARG;
     }
+    std::vector<int32_t>().swap(ai);
     std::vector<int32_t> ipmd(static_cast<size_t>(n));
     for (int32_t k = 0; k < n; ++k) ipmd[size_t(md[size_t(k)])] = k;
 
@@ -299,21 +238,42 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     }
 
     // --- assembly map: lower entry k of M -> its place in the blocks -----
+    // (entries grouped by their column in the order, then one supernode at a
+    // time with the positions of its rows in a scatter map)
     sy.amap.resize(size_t(nnz_low));
-    for (int32_t i = 0; i < n; ++i)
-      for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
-        const int32_t a = ip[size_t(i)], b = ip[size_t(ci[size_t(k)])];
-        const int32_t r = std::max(a, b), c = std::min(a, b), s = sn_of[size_t(c)];
+    {
+      std::vector<int32_t> cptr(size_t(n) + 1, 0), ck(static_cast<size_t>(nnz_low));
+      for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
+          cptr[size_t(std::min(ip[size_t(i)], ip[size_t(ci[size_t(k)])])) + 1]++;
+      for (int32_t c = 0; c < n; ++c) cptr[size_t(c) + 1] += cptr[size_t(c)];
+      std::vector<int32_t> nx(cptr.begin(), cptr.end() - 1);
+      for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
+          ck[size_t(nx[size_t(std::min(ip[size_t(i)], ip[size_t(ci[size_t(k)])]))]++)] = k;
+      std::vector<int32_t> rowpos(static_cast<size_t>(n), -1);
+      std::vector<int32_t> krow(static_cast<size_t>(nnz_low));  // entry k's row of M
+      for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) krow[size_t(k)] = i;
+      for (int32_t s = 0; s < ns; ++s) {
+        const int32_t f = sy.sn_first[size_t(s)], l = sy.sn_first[size_t(s) + 1];
         const int32_t* R = sy.rowidx.data() + sy.sn_rowptr[size_t(s)];
         const int32_t h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
-        const int32_t pos = int32_t(std::lower_bound(R, R + h, r) - R);
-        if (pos >= h || R[pos] != r) {
-          err = "symbolic phase: an entry of M_cond is missing from the factor's structure";
-          return ACOPF_E_INVALID_ARG;
-        }
-        sy.amap[size_t(k)] =
-            sy.sn_off[size_t(s)] + int64_t(c - sy.sn_first[size_t(s)]) * h + pos;
+        for (int32_t q = 0; q < h; ++q) rowpos[size_t(R[q])] = q;
+        for (int32_t c = f; c < l; ++c)
+          for (int32_t t = cptr[size_t(c)]; t < cptr[size_t(c) + 1]; ++t) {
+            const int32_t k = ck[size_t(t)];
+            const int32_t r = std::max(ip[size_t(krow[size_t(k)])], ip[size_t(ci[size_t(k)])]);
+            const int32_t pos = rowpos[size_t(r)];
+            if (pos < 0 || R[pos] != r) {
+              err = "symbolic phase: an entry of M_cond is missing from the factor's structure";
+              return ACOPF_E_INVALID_ARG;
+            }
+            sy.amap[size_t(k)] = sy.sn_off[size_t(s)] + int64_t(c - f) * h + pos;
+          }
+        for (int32_t q = 0; q < h; ++q) rowpos[size_t(R[q])] = -1;
       }
+    }
 
     // --- multifrontal links: each supernode's children (ascending), the
     // positions of a child's rows below its columns within its parent's rows,

@@ -35,6 +35,12 @@ struct CholSymbolic {
   acopf_chol_stats stats{};
 };
 
+// Approximate minimum degree order (amd.cpp) of the symmetric pattern whose
+// adjacency (no diagonal, both triangles) is ai[ap[i] .. ap[i+1]): `order`
+// lists the nodes in elimination order.  False if the order is incomplete.
+bool approximate_minimum_degree(int32_t n, const std::vector<int32_t>& ap,
+                                const std::vector<int32_t>& ai, std::vector<int32_t>& order);
+
 // Builds the symbolic factorization of the symmetric matrix whose lower
 // triangle has the CSR pattern (rp, ci) (columns ascending, diagonal last
 // in every row).  On failure returns a status and sets `err`.
