@@ -148,71 +148,119 @@ int blocks_for(int count) { return (count + kStepThreads - 1) / kStepThreads; }
 // count of finite bounds (sums in a fixed order for the fixed grid; maxima
 // are order-free) for k_residual_final, which writes
 // out = [E, max|r_d|, max|r_p|, max|r_c|, ||y||_1, ||z||_1, n_z, s_d, s_c].
+// Maxima of absolute values are taken on the bit patterns (a non-negative
+// double orders like its bits as an unsigned integer; NaN bits exceed every
+// number's, so a NaN propagates) and counts are integers: both off the FP64
+// pipe, which the sums and products keep busy.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffULL;
+}
+
 __global__ void __launch_bounds__(kStepThreads) k_kkt_residual(
     DevStep st, StepIterate it, const double* __restrict__ y, const double* __restrict__ grad,
     const double* __restrict__ cons, const double* __restrict__ J, double mu) {
-  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // dmax, pmax, cmax, ysum, zsum, nz
+  unsigned long long mx[3] = {0ull, 0ull, 0ull};  // max |r_d|, |r_p|, |r_c| (bits)
+  double ysum = 0.0, zsum = 0.0;
+  long long nz = 0;
   const int stride = gridDim.x * kStepThreads;
   for (int j = blockIdx.x * kStepThreads + threadIdx.x; j < st.n; j += stride) {
+    // A'y over the variable's Jacobian entries in slot order, four in flight
     double aty = 0.0;
-    for (int k = __ldg(st.jt_ptr + j), k1 = __ldg(st.jt_ptr + j + 1); k < k1; ++k)
-      aty = fma(ldg(J + __ldg(st.jt_slot + k)), ldg(y + __ldg(st.jt_row + k)), aty);
+    int k = __ldg(st.jt_ptr + j);
+    const int k1 = __ldg(st.jt_ptr + j + 1);
+    for (; k + 4 <= k1; k += 4) {
+      int sl[4], rw[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sl[u] = __ldg(st.jt_slot + k + u);
+        rw[u] = __ldg(st.jt_row + k + u);
+      }
+      double jv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        jv[u] = ldg(J + sl[u]);
+        yv[u] = ldg(y + rw[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) aty = fma(jv[u], yv[u], aty);
+    }
+    for (; k < k1; ++k) aty = fma(ldg(J + __ldg(st.jt_slot + k)), ldg(y + __ldg(st.jt_row + k)), aty);
     const double zl = ldg(it.zl_x + j), zu = ldg(it.zu_x + j), x = ldg(it.x + j);
-    v[0] = fmax(v[0], fabs(ldg(grad + j) - aty - zl + zu));
+    mx[0] = max(mx[0], abs_bits(ldg(grad + j) - aty - zl + zu));
     const double lo = ldg(it.xl + j), hi = ldg(it.xu + j);
     if (is_finite_bits(lo)) {
-      v[2] = fmax(v[2], fabs(fma(zl, x - lo, -mu)));
-      v[4] += fabs(zl);
-      v[5] += 1.0;
+      mx[2] = max(mx[2], abs_bits(fma(zl, x - lo, -mu)));
+      zsum += fabs(zl);
+      ++nz;
     }
     if (is_finite_bits(hi)) {
-      v[2] = fmax(v[2], fabs(fma(zu, hi - x, -mu)));
-      v[4] += fabs(zu);
-      v[5] += 1.0;
+      mx[2] = max(mx[2], abs_bits(fma(zu, hi - x, -mu)));
+      zsum += fabs(zu);
+      ++nz;
     }
   }
   for (int r = blockIdx.x * kStepThreads + threadIdx.x; r < st.m; r += stride) {
     const double yr = ldg(y + r), zl = ldg(it.zl_s + r), zu = ldg(it.zu_s + r);
     const double sr = ldg(it.s + r);
-    v[0] = fmax(v[0], fabs(yr - zl + zu));
-    v[1] = fmax(v[1], fabs(ldg(cons + r) - sr));
-    v[3] += fabs(yr);
+    mx[0] = max(mx[0], abs_bits(yr - zl + zu));
+    mx[1] = max(mx[1], abs_bits(ldg(cons + r) - sr));
+    ysum += fabs(yr);
     const double lo = ldg(it.sl + r), hi = ldg(it.su + r);
     if (is_finite_bits(lo)) {
-      v[2] = fmax(v[2], fabs(fma(zl, sr - lo, -mu)));
-      v[4] += fabs(zl);
-      v[5] += 1.0;
+      mx[2] = max(mx[2], abs_bits(fma(zl, sr - lo, -mu)));
+      zsum += fabs(zl);
+      ++nz;
     }
     if (is_finite_bits(hi)) {
-      v[2] = fmax(v[2], fabs(fma(zu, hi - sr, -mu)));
-      v[4] += fabs(zu);
-      v[5] += 1.0;
+      mx[2] = max(mx[2], abs_bits(fma(zu, hi - sr, -mu)));
+      zsum += fabs(zu);
+      ++nz;
     }
   }
   // Block reduction: shuffle trees (fixed order), then the warps in order.
-  __shared__ double sh[kStepThreads / 32][6];
+  __shared__ unsigned long long shm[kStepThreads / 32][3];
+  __shared__ double shs[kStepThreads / 32][2];
+  __shared__ long long shn[kStepThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-#pragma unroll
-    for (int q = 3; q < 6; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    for (int q = 0; q < 3; ++q) mx[q] = max(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
+    ysum += __shfl_down_sync(0xffffffffu, ysum, o);
+    zsum += __shfl_down_sync(0xffffffffu, zsum, o);
+    nz += __shfl_down_sync(0xffffffffu, nz, o);
   }
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sh[warp][q] = v[q];
+    for (int q = 0; q < 3; ++q) shm[warp][q] = mx[q];
+    shs[warp][0] = ysum;
+    shs[warp][1] = zsum;
+    shn[warp] = nz;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    unsigned long long bm[3] = {0ull, 0ull, 0ull};
+    double bs[2] = {0.0, 0.0};
+    long long bn = 0;
     for (int w = 0; w < kStepThreads / 32; ++w) {
-      for (int q = 0; q < 3; ++q) b[q] = fmax(b[q], sh[w][q]);
-      for (int q = 3; q < 6; ++q) b[q] += sh[w][q];
+      for (int q = 0; q < 3; ++q) bm[q] = max(bm[q], shm[w][q]);
+      bs[0] += shs[w][0];
+      bs[1] += shs[w][1];
+      bn += shn[w];
     }
-    for (int q = 0; q < 6; ++q) st.res_part[6 * blockIdx.x + q] = b[q];
+    double* out = st.res_part + 6 * blockIdx.x;
+    for (int q = 0; q < 3; ++q) out[q] = __longlong_as_double(static_cast<long long>(bm[q]));
+    out[3] = bs[0];
+    out[4] = bs[1];
+    out[5] = static_cast<double>(bn);  // exact below 2^53
   }
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// The larger of two non-negative doubles (or NaN), compared as bits.
+__device__ __forceinline__ double max_bits(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
 }
 
 // One block: the blocks' parts in a fixed order (each thread a strided
@@ -233,7 +281,7 @@ __global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int
 #pragma unroll
     for (int u = 0; u < U; ++u) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], t[u][q]);
+      for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], t[u][q]);
 #pragma unroll
       for (int q = 3; q < 6; ++q) c[q] += t[u][q];
     }
@@ -243,7 +291,7 @@ __global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], __shfl_down_sync(0xffffffffu, c[q], o));
+    for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], __shfl_down_sync(0xffffffffu, c[q], o));
 #pragma unroll
     for (int q = 3; q < 6; ++q) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
   }
@@ -255,7 +303,7 @@ __global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int
   if (threadIdx.x == 0) {
     for (int q = 0; q < 6; ++q) c[q] = sh[0][q];
     for (int w = 1; w < kStepThreads / 32; ++w) {
-      for (int q = 0; q < 3; ++q) c[q] = fmax(c[q], sh[w][q]);
+      for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], sh[w][q]);
       for (int q = 3; q < 6; ++q) c[q] += sh[w][q];
     }
     const double smax = 100.0;  // s_max of the scaling
