@@ -527,11 +527,12 @@ def run_step_bench(args, local):
 def run_chol_bench(args, local):
     """Sparse Cholesky of M_cond (acopf_chol_*) on the near-planar 10,000- and
     80,000-bus workloads: the host symbolic phase once, then the numeric
-    factorization (zeroing and assembly of the supernodal blocks, one launch
-    per level of the supernodal tree, the pivot test returned to the host)
-    and the solve (permutation, forward and backward level sweeps,
-    permutation back), M_cond assembled by the library at a convex point (no
-    constraint multipliers, delta_w = 1e-4: positive definite)."""
+    factorization (zeroing and assembly of the supernodal blocks, the bottom
+    levels one thread per supernode, then one persistent task-graph launch;
+    the pivot test returned to the host) and the solve (permutation, bottom
+    levels, warp and block task launches each way, permutation back), M_cond
+    assembled by the library at a convex point (no constraint multipliers,
+    delta_w = 1e-4: positive definite)."""
     import time
 
     import torch
@@ -594,8 +595,9 @@ def run_chol_bench(args, local):
                      "factor_ms": factor_ms,
                      "factor_gflops": info["factor_flops"] / (factor_ms * 1e-3) / 1e9,
                      "solve_ms": solve_ms, "device_bytes": info["device_bytes"],
-                     "launches": {"factor": info["n_levels"] + 1,
-                                  "solve": 2 * info["n_levels"] + 2}}
+                     "factor_tasks": info["factor_tasks"],
+                     "launches": {"factor": info["factor_launches"],
+                                  "solve": info["solve_launches"]}}
     out["timing"] = (f"factor: host wall clock per call over {reps} calls (each call returns the "
                      f"pivot test to the host); solve: CUDA events over {reps} calls")
     return out

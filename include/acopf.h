@@ -325,15 +325,18 @@ acopf_status acopf_chol_solve(acopf_chol* chol, const double* b, double* x, acop
  * max_col, the entries of L's largest column; factor_flops, the flops of
  * one numeric factorization (per column with c off-diagonal entries: 1
  * square root, c divisions and c (c + 1) / 2 multiply-adds); n_supernodes;
- * n_levels of the supernodal tree (launches per factorization, and per
- * direction of a solve); storage, the doubles of the supernodal blocks;
- * update_storage, the doubles of the children's update matrices and
- * vectors the multifrontal factorization and solves pass up the tree. */
+ * n_levels, the depth of the supernodal tree; storage, the doubles of the
+ * supernodal blocks; update_storage, the doubles of the children's update
+ * matrices and vectors the multifrontal factorization and solves pass up
+ * the tree; factor_tasks, the tasks of the factorization's task graph;
+ * factor_launches and solve_launches, the kernel launches of one
+ * factorization and of one solve. */
 typedef struct {
   int64_t n, nnz_full, nnz_factor, max_col;
   double factor_flops;
   int64_t n_supernodes, n_levels;
   int64_t storage, update_storage;
+  int64_t factor_tasks, factor_launches, solve_launches;
 } acopf_chol_stats;
 /* stats and device_bytes (all device memory of the object) may be NULL. */
 acopf_status acopf_chol_info(const acopf_chol* chol, acopf_chol_stats* stats,

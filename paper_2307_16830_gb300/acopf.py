@@ -187,7 +187,8 @@ class CholStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_full", C.c_int64), ("nnz_factor", C.c_int64),
                 ("max_col", C.c_int64), ("factor_flops", C.c_double),
                 ("n_supernodes", C.c_int64), ("n_levels", C.c_int64), ("storage", C.c_int64),
-                ("update_storage", C.c_int64)]
+                ("update_storage", C.c_int64), ("factor_tasks", C.c_int64),
+                ("factor_launches", C.c_int64), ("solve_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

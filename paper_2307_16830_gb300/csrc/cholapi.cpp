@@ -95,6 +95,17 @@ acopf_status check_model(const acopf_model* model, const char* where) {
   return ACOPF_OK;
 }
 
+// The plan's counts: tasks of the factorization, and the launches of one
+// factorization (assembly, the bottom levels, the task kernel) and of one
+// solve (permutation, bottom levels, warp and block tasks per direction,
+// bottom levels, permutation back).
+void plan_stats(const acopf::CholPlan& plan, acopf_chol_stats& st) {
+  const int64_t nbl = int64_t(plan.bot_ptr.size()) - 1;
+  st.factor_tasks = plan.factor.n_tasks();
+  st.factor_launches = 2 + nbl;
+  st.solve_launches = 6 + 2 * nbl;
+}
+
 acopf_status run_symbolic(const acopf_model* model, acopf::CholSymbolic& sy, const char* where) {
   std::string err;
   const acopf_status st =
@@ -195,6 +206,13 @@ acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats,
   acopf::CholSymbolic sy;
   st = run_symbolic(model, sy, "acopf_chol_analyze");
   if (st != ACOPF_OK) return st;
+  acopf::CholPlan plan;
+  {
+    std::string err;
+    st = acopf::chol_plan(sy, acopf::CholPlanParams{}, plan, err);
+    if (st != ACOPF_OK) return fail(st, "acopf_chol_analyze: " + err);
+  }
+  plan_stats(plan, sy.stats);
   *stats = sy.stats;
   if (perm) std::copy(sy.perm.begin(), sy.perm.end(), perm);
   return ACOPF_OK;
@@ -221,6 +239,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   c->n = sy.n;
   c->nnz_low = int64_t(sy.amap.size());
   c->stats = sy.stats;
+  plan_stats(plan, c->stats);
   try {
     c->perm_host = sy.perm;
     c->bot_ptr = plan.bot_ptr;

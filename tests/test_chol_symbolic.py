@@ -84,3 +84,6 @@ def test_geometric_workload_has_a_small_factor():
         st = acopf.chol_analyze(m)
     assert st["nnz_factor"] < 2 * st["nnz_full"]
     assert st["n_levels"] < 200
+    # the task plan: one persistent launch after the bottom levels
+    assert st["factor_tasks"] >= 1
+    assert st["factor_launches"] >= 2 and st["solve_launches"] == 2 * st["factor_launches"] + 2
