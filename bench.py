@@ -616,7 +616,8 @@ def run_ipm_bench(args, local):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    names = {0: "converged", 1: "max_iter", 2: "line search failed", 3: "inertia correction failed"}
+    names = {0: "converged", 1: "max_iter", 2: "line search failed", 3: "inertia correction failed",
+             4: "infeasible"}
     out = {}
     for name, max_iter in (("30bus-opf", 200), ("2kbus-opf", 200), ("10kbus-geo-opf", 200),
                            ("80kbus-geo-opf", args.ipm_iters)):

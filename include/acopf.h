@@ -373,9 +373,17 @@ acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out,
  * correction on delta_w (delta_c = 0), solve and step recovery (the printed
  * Delta y is minus the Newton step of y), the fraction-to-boundary step
  * bounds and the filter line search of the interior-point reference the
- * paper cites (its default constants; no second-order correction and no
- * restoration phase: a step below the minimum ends the solve with
- * ACOPF_IPM_LINE_SEARCH_FAILED).  Initial point: voltage angles 0,
+ * paper cites (its default constants; no second-order correction).  A step
+ * below the line search's minimum enters a feasibility restoration: Gauss-
+ * Newton steps on 1/2 ||g(x) - clip(g(x))||^2 (slacks following g, clipped
+ * onto their box pushed inside) plus a log barrier on x's bounds and a
+ * proximal term, factored on M_cond's pattern; it returns to the iteration
+ * at the first point the filter accepts with at most 0.9 times the
+ * violation (1e-3 times when the iteration came back to the restoration
+ * without getting below the violation of its last exit), or ends the solve
+ * with ACOPF_IPM_INFEASIBLE when the violation
+ * stops decreasing (a point of local infeasibility).  (The status
+ * ACOPF_IPM_LINE_SEARCH_FAILED is no longer produced.)  Initial point: voltage angles 0,
  * magnitudes 1, the rest at the middle of its bounds (0 when unbounded),
  * pushed into the interior; slacks at g(x0) pushed into their bounds;
  * y = 0; bound multipliers 1.
@@ -383,8 +391,9 @@ acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out,
  * x_out: HOST array of n doubles receiving the final x, or NULL.
  * history: HOST array of (max_iter + 1) x ACOPF_IPM_HISTORY_FIELDS doubles
  * (row k: f, residual, mu at iteration k's start, the constraint violation
- * sum |g - s|, then the step alpha, alpha_z and delta_w taken; NaN where
- * not reached), or NULL.  All work runs on `stream`; the call returns when
+ * sum |g - s|, then the step alpha, alpha_z and delta_w taken, alpha = 0
+ * for an iteration that ran the restoration; NaN where not reached), or
+ * NULL.  All work runs on `stream`; the call returns when
  * the solve ends.  It allocates its own device memory and a sparse Cholesky
  * object, and uses the model's scratch: no other call on the model may
  * overlap it.  ACOPF_E_NO_DEVICE for a host-only model. */
@@ -392,6 +401,7 @@ acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out,
 #define ACOPF_IPM_MAX_ITER 1
 #define ACOPF_IPM_LINE_SEARCH_FAILED 2
 #define ACOPF_IPM_INERTIA_FAILED 3
+#define ACOPF_IPM_INFEASIBLE 4
 #define ACOPF_IPM_HISTORY_FIELDS 7
 typedef struct {
   double tol;

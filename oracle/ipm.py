@@ -17,12 +17,14 @@ description, with its default constants: the fraction-to-boundary rule with
 tau = max(tau_min, 1 - mu); the filter line search (switching condition,
 Armijo condition on the barrier objective, sufficient decrease in the
 constraint violation or the barrier objective, filter acceptance; no
-second-order correction and no restoration phase: a step size below the
-minimum ends the solve with status "line search failed"); the monotone
+second-order correction); the monotone
 barrier update mu <- max(eps/10, min(kappa_mu mu, mu^theta_mu)) when the
 barrier problem's error is below kappa_eps mu; the inertia correction on
 delta_w (delta_c = 0); the safeguard of the bound multipliers
-(kappa_sigma); the initial point pushed into the interior of the bounds.
+(kappa_sigma); the initial point pushed into the interior of the bounds;
+when the line search fails, a feasibility restoration (reading d10,
+`restoration`) that either returns a point the filter accepts or ends the
+solve with status "infeasible".
 
 Readings:
 * (d7) Eq. first uses the Lagrangian f - y'(g - s) (its first row carries
@@ -48,7 +50,7 @@ from .chol import is_positive_definite, solve_condensed
 from .step import Iterate, condense, kkt_residual, recover
 
 __all__ = ["IpmOptions", "IpmResult", "ipm_start", "ipm_solve", "relaxed_bounds",
-           "push_interior", "fraction_to_boundary", "barrier_objective"]
+           "push_interior", "fraction_to_boundary", "barrier_objective", "restoration"]
 
 
 @dataclasses.dataclass
@@ -77,6 +79,11 @@ class IpmOptions:
     kappa_w_plus: float = 8.0
     kappa_w_plus_bar: float = 100.0
     max_backtracks: int = 60
+    resto_max_iter: int = 200     # restoration iterations at most
+    resto_stall: int = 10         # ... and without a 1 % decrease of the violation for this many
+    resto_mu_min: float = 1e-9    # the restoration's barrier parameter at least
+    resto_reduction: float = 0.9  # restoration ends below this fraction of the violation
+    resto_reduction_repeat: float = 1e-3  # ... when re-entered without progress since its last exit
 
 
 @dataclasses.dataclass
@@ -190,6 +197,92 @@ def _reset_z(z, gap, mu, kappa):
     return out
 
 
+def restoration(grid, x, b, mu, accept, opts: IpmOptions):
+    """Feasibility restoration (reading d10), entered when the line search
+    fails: minimise over x inside its bounds
+
+        psi(x) = 1/2 ||v(x)||^2 - mu_R sum(log gaps of x) + zeta/2 ||x - x_R||^2,
+        v(x) = g(x) - P(g(x)),
+
+    P clipping onto the slack box pushed inside as for the initial point
+    (the slacks follow g), zeta = sqrt(mu_R), x_R the current point (so the
+    proximal term damps each step, Levenberg-Marquardt fashion), mu_R
+    starting at the main barrier parameter and divided by 10 whenever the
+    violation stalls.  Each step is a Gauss-Newton step,
+    (A' W A + Sigma + zeta I) dx = -grad psi with W the 0/1 diagonal of the
+    rows outside the box and Sigma the barrier's curvature: M_cond's pattern
+    with no Hessian and D = W.  Step sizes: fraction to the boundary
+    (tau = 0.99), then halving until psi decreases by 1e-4 alpha grad psi'dx.
+    Returns ("ok", x, s) as soon as accept(x, s) holds (the main filter
+    accepts the point, whose violation is at most resto_reduction times the
+    one where the line search failed), else ("infeasible", x, s) when the violation stops
+    decreasing with mu_R at resto_mu_min (less than 1 % over resto_stall
+    iterations, or a step below 1e-12), or after resto_max_iter iterations:
+    a point of local infeasibility."""
+    L = layout(grid)
+    xl, xu, sl, su = b["xl"], b["xu"], b["sl"], b["su"]
+    lo_s = push_interior(np.full(L.m, -np.inf), sl, su, opts.bound_push, opts.bound_frac)
+    hi_s = push_interior(np.full(L.m, np.inf), sl, su, opts.bound_push, opts.bound_frac)
+    lo_s = np.where(np.isfinite(sl), lo_s, -np.inf)
+    hi_s = np.where(np.isfinite(su), hi_s, np.inf)
+    mu_r = mu  # the restoration's own barrier parameter
+    x_r = x.copy()
+    fl, fu = np.isfinite(xl), np.isfinite(xu)
+
+    def parts(xv):
+        g = constraints(grid, xv)[0]
+        sv = np.clip(g, lo_s, hi_s)
+        return g, sv, g - sv
+
+    def psi(xv, v):
+        return (0.5 * float(v @ v) - mu_r * _log_gaps(xv, xl, xu)
+                + 0.5 * np.sqrt(mu_r) * float((xv - x_r) @ (xv - x_r)))
+
+    g, s, v = parts(x)
+    best, since = float(np.sum(np.abs(v))), 0
+    for _ in range(opts.resto_max_iter):
+        if accept(x, s):
+            return "ok", x, s
+        J = jacobian(grid, x)[0]
+        w = (v != 0.0).astype(np.float64)
+        with np.errstate(divide="ignore"):
+            gl_ = np.where(fl, 1.0 / (x - np.where(fl, xl, 0.0)), 0.0)
+            gu_ = np.where(fu, 1.0 / (np.where(fu, xu, 0.0) - x), 0.0)
+        zeta = np.sqrt(mu_r)
+        grad = J_T(grid, J, w * v) + mu_r * (gu_ - gl_) + zeta * (x - x_r)
+        sig = mu_r * (gl_ * gl_ + gu_ * gu_) + zeta
+        kv, _ = condensed_kkt(grid, np.zeros(hessian(grid, x, np.zeros(L.m), 0.0)[0].size), J,
+                              sig, w, 0.0, 0.0)
+        dx = solve_condensed(grid, kv, -grad)
+        alpha = fraction_to_boundary(x, dx, xl, xu, 0.99)
+        p0, slope = psi(x, v), float(grad @ dx)
+        while True:
+            xt = x + alpha * dx
+            gt, st_, vt = parts(xt)
+            if psi(xt, vt) <= p0 + 1e-4 * alpha * slope:
+                break
+            alpha *= 0.5
+            if alpha < 1e-12:
+                break
+        if alpha < 1e-12:  # no decrease along the step: a smaller barrier, else infeasible
+            if mu_r <= opts.resto_mu_min:
+                return "infeasible", x, s
+            mu_r, since = 0.1 * mu_r, 0
+            continue
+        x, g, s, v = xt, gt, st_, vt
+        x_r = x.copy()  # the proximal term damps each step (Levenberg-Marquardt)
+        th = float(np.sum(np.abs(v)))
+        if th < 0.99 * best:
+            best, since = th, 0
+        else:
+            since += 1
+            if since >= opts.resto_stall:  # stalled: a smaller barrier, else local infeasibility
+                if mu_r <= opts.resto_mu_min:
+                    return "infeasible", x, s
+                mu_r, since = 0.1 * mu_r, 0
+    return ("ok", x, s) if accept(x, s) else ("infeasible", x, s)
+
+
 def ipm_solve(grid, opts: IpmOptions | None = None, factor_check=None) -> IpmResult:
     """Algorithm 1 on the AC-OPF model of `grid`.  factor_check(kvals) may
     replace the dense positive-definiteness test (the default)."""
@@ -219,6 +312,7 @@ def ipm_solve(grid, opts: IpmOptions | None = None, factor_check=None) -> IpmRes
     status = "max_iter"
     it_count = 0
     res0 = None
+    resto_exit = None  # the violation where the last restoration ended
     for it_count in range(opts.max_iter + 1):
         it = Iterate(x=x, s=s, xl=b["xl"], xu=b["xu"], sl=b["sl"], su=b["su"], zl_x=zl_x,
                      zu_x=zu_x, zl_s=zl_s, zu_s=zu_s, p_x=np.zeros(L.n), p_s=np.zeros(L.m),
@@ -310,8 +404,38 @@ def ipm_solve(grid, opts: IpmOptions | None = None, factor_check=None) -> IpmRes
             if alpha < alpha_min:
                 break
         if accepted is None:
-            status = "line search failed"
-            break
+            # feasibility restoration: a point the filter (augmented with the
+            # current one) accepts with a sufficiently smaller violation
+            filt.append(((1 - opts.gamma_theta) * theta, phi - opts.gamma_phi * theta))
+
+            # back without getting below the last restoration's exit: demand
+            # (nearly) feasibility this time, which an infeasible network cannot give
+            red = (opts.resto_reduction_repeat
+                   if resto_exit is not None and theta >= resto_exit else opts.resto_reduction)
+
+            def accept(xv, sv, theta=theta, mu=mu, red=red):
+                fv, cv = objective(grid, xv)[0], constraints(grid, xv)[0]
+                tv = theta_of(cv, sv)
+                pv = barrier_objective(fv, xv, sv, b, mu)
+                return tv <= red * theta and not any(
+                    tv >= fth and pv >= fph for fth, fph in filt)
+
+            rstat, x, s = restoration(grid, x, b, mu, accept, opts)
+            f, cons = objective(grid, x)[0], constraints(grid, x)[0]
+            resto_exit = theta_of(cons, s)
+            grad, J = gradient(grid, x)[0], jacobian(grid, x)[0]
+            history[-1].update(alpha=0.0, alpha_z=0.0, delta_w=dw, restoration=True)
+            if rstat != "ok":
+                status = "infeasible"
+                break
+            # multipliers restart: y = 0, bound duals on the central path
+            y = np.zeros(L.m)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                zl_x = np.where(np.isfinite(b["xl"]), mu / (x - b["xl"]), 0.0)
+                zu_x = np.where(np.isfinite(b["xu"]), mu / (b["xu"] - x), 0.0)
+                zl_s = np.where(np.isfinite(b["sl"]), mu / (s - b["sl"]), 0.0)
+                zu_s = np.where(np.isfinite(b["su"]), mu / (b["su"] - s), 0.0)
+            continue
         kind, x, s, f, cons = accepted
         if kind == "h":
             filt.append(((1 - opts.gamma_theta) * theta, phi - opts.gamma_phi * theta))

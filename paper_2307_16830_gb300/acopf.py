@@ -212,6 +212,7 @@ class IpmResult(C.Structure):
 
 
 IPM_CONVERGED, IPM_MAX_ITER, IPM_LINE_SEARCH_FAILED, IPM_INERTIA_FAILED = 0, 1, 2, 3
+IPM_INFEASIBLE = 4
 IPM_HISTORY_FIELDS = ("f", "residual", "mu", "theta", "alpha", "alpha_z", "delta_w")
 _ipm_solve = _sig("acopf_ipm_solve", C.c_int32, _vp, C.POINTER(IpmOptions), _vp, _vp,
                   C.POINTER(IpmResult), _vp)

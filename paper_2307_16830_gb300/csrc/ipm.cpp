@@ -11,7 +11,9 @@
 // parameter, regularization) are taken on the host from a few reduced values
 // per step; every vector stays on the device.  The rules and constants are
 // those of the interior-point reference the paper cites for its line
-// search (no second-order correction, no restoration phase).
+// search (no second-order correction); a failed line search enters a
+// feasibility restoration (reading d10) that returns to the iteration or
+// ends the solve as infeasible.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -38,6 +40,10 @@ constexpr double kEtaPhi = 1e-4, kAlphaMinFrac = 0.05, kKappaSigma = 1e10;
 constexpr double kDeltaW0 = 1e-4, kDeltaWMin = 1e-20, kDeltaWMax = 1e40;
 constexpr double kKappaWMinus = 1.0 / 3.0, kKappaWPlus = 8.0, kKappaWPlusBar = 100.0;
 constexpr int kMaxBacktracks = 60, kMaxInertiaTries = 200;
+// feasibility restoration (reading d10): iterations at most, stall window,
+// smallest barrier parameter, required reduction of the violation
+constexpr int kRestoMaxIter = 200, kRestoStall = 10;
+constexpr double kRestoMuMin = 1e-9, kRestoReduction = 0.9, kRestoReductionRepeat = 1e-3;
 
 // The reference's initial-point rule: at least min(k1 max(1,|b|), k2 (hi - lo))
 // inside each finite bound.
@@ -53,6 +59,7 @@ struct Buffers {
   void* arena = nullptr;
   acopf::IpmVec v{};
   double *xl, *xu, *sl, *su, *sigma_x, *sigma_s, *q_s, *rhs, *hvals, *kvals;
+  double *xr, *lo_s, *hi_s, *r;  // restoration: proximal centre, pushed slack box, violation
   double *f, *ft, *out, *part;  // out: 16 reduced scalars, part: per-block partials
   ~Buffers() {
     if (arena) cudaFree(arena);
@@ -93,7 +100,7 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   Buffers B;
   acopf::ArenaPlan p;
   const size_t N = size_t(n), M = size_t(m);
-  enum { kVecN = 19, kVecM = 24 };
+  enum { kVecN = 20, kVecM = 27 };
   const size_t o_n = p.take<double>(kVecN * N), o_m = p.take<double>(kVecM * M);
   const size_t o_j = p.take<double>(size_t(L.nnzj)), o_h = p.take<double>(size_t(L.nnzh));
   const size_t o_k = p.take<double>(size_t(L.nnzk)), o_s = p.take<double>(32);
@@ -116,6 +123,7 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   v.y = mv(6); v.ym = mv(7); v.cons = mv(8); v.cons_t = mv(9); v.p_s = mv(10); v.p_y = mv(11);
   v.p_zl_s = mv(12); v.p_zu_s = mv(13); B.sigma_s = mv(14); B.q_s = mv(15); v.ds = mv(16);
   v.dy = mv(17); v.dzl_s = mv(18); v.dzu_s = mv(19);
+  B.xr = nv(15); B.lo_s = mv(20); B.hi_s = mv(21); B.r = mv(22);
   v.xl = B.xl; v.xu = B.xu; v.sl = B.sl; v.su = B.su;
   v.jvals = reinterpret_cast<double*>(base + o_j);
   B.hvals = reinterpret_cast<double*>(base + o_h);
@@ -126,6 +134,7 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
 
   // ---- initial point (reading d8) -------------------------------------------
   std::vector<double> hx(N, 0.0), hs(M), hsl(M), hsu(M), hzlx(N), hzux(N), hzls(M), hzus(M);
+  std::vector<double> hlos(M), hhis(M);
   for (int32_t j = 0; j < n; ++j) {
     const double lo = hm.xl[size_t(j)], hi = hm.xu[size_t(j)];
     hx[size_t(j)] = std::isfinite(lo) && std::isfinite(hi) ? 0.5 * (lo + hi) : 0.0;
@@ -145,12 +154,18 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
     hsu[size_t(r)] = std::isfinite(hi) ? hi + tol * std::max(1.0, std::fabs(hi)) : INFINITY;
     hzls[size_t(r)] = std::isfinite(hsl[size_t(r)]) ? 1.0 : 0.0;
     hzus[size_t(r)] = std::isfinite(hsu[size_t(r)]) ? 1.0 : 0.0;
+    // the restoration's slack box: the slack bounds pushed inside as for the initial point
+    hlos[size_t(r)] = std::isfinite(hsl[size_t(r)]) ? push_interior(-INFINITY, hsl[size_t(r)], hsu[size_t(r)])
+                                                    : -INFINITY;
+    hhis[size_t(r)] = std::isfinite(hsu[size_t(r)]) ? push_interior(INFINITY, hsl[size_t(r)], hsu[size_t(r)])
+                                                    : INFINITY;
   }
   auto up = [&](double* d, const std::vector<double>& h) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s);
   };
   up(v.x, hx); up(B.xl, hm.xl); up(B.xu, hm.xu); up(B.sl, hsl); up(B.su, hsu);
   up(v.zl_x, hzlx); up(v.zu_x, hzux); up(v.zl_s, hzls); up(v.zu_s, hzus);
+  up(B.lo_s, hlos); up(B.hi_s, hhis);
   if (e == cudaSuccess) e = cudaMemsetAsync(v.y, 0, M * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(v.ym, 0, M * 8, s);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: upload");
@@ -218,9 +233,133 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   const double theta_max = 1e4 * std::max(1.0, theta), theta_min = 1e-4 * std::max(1.0, theta);
   std::vector<std::pair<double, double>> filter{{theta_max, -INFINITY}};
   double mu = mu_init, dw_last = 0.0, res0 = INFINITY;
+  double resto_exit = -1.0;  // the violation where the last restoration ended (-1: none yet)
   result->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   int32_t status = ACOPF_IPM_MAX_ITER, k = 0;
+
+  // Feasibility restoration (reading d10, the oracle's `restoration`): from
+  // x, minimise 1/2 ||r||^2 - mu_R sum log gaps(x) + zeta/2 ||x - x_R||^2,
+  // r = g(x) - clip(g(x)), by Gauss-Newton steps on M_cond's pattern (no
+  // Hessian, D the 0/1 rows outside the box), until the filter accepts a
+  // point with at most `reduction` times theta_k (returns 1) or the
+  // violation stalls at the smallest barrier (returns 0: infeasible).  On
+  // return x, s, cons, f and theta are those of the last point.
+  auto restoration = [&](double mu, double theta_k, double reduction, int& code) -> acopf_status {
+    double mu_r = mu;
+    code = 0;
+    auto slack = [&](const double* cons, double* sv, double* rv, double* wv) -> cudaError_t {
+      cudaError_t err = acopf::launch_resto_slack(cons, B.lo_s, B.hi_s, m, sv, rv, wv, blocks,
+                                                  B.part, B.out, s);
+      if (err == cudaSuccess) err = fetch(2);
+      return err;
+    };
+    e = slack(v.cons, v.s, B.r, B.sigma_s);
+    if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration");
+    double th = hout[0], rr = hout[1];
+    double best = th;
+    int since = 0;
+    e = cudaMemcpyAsync(B.xr, v.x, N * 8, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration");
+    auto accepted = [&](bool& ok) -> acopf_status {  // the main filter's test at (x, s)
+      acopf_status r = acopf_eval_obj(model, v.x, B.f, as);
+      if (r != ACOPF_OK) return r;
+      cudaError_t err =
+          acopf::launch_ipm_measure(v, v.x, v.s, v.cons, n, m, blocks, B.part, B.out + 2, s);
+      if (err == cudaSuccess) err = cudaMemcpyAsync(B.out, B.f, 8, cudaMemcpyDeviceToDevice, s);
+      if (err == cudaSuccess) err = fetch(4);
+      if (err != cudaSuccess) return cuda_fail(err, "acopf_ipm_solve: restoration");
+      f = hout[0];
+      theta = hout[2];
+      const double pv = f - mu * hout[3];
+      bool dominated = false;
+      for (const auto& fe : filter)
+        if (theta >= fe.first && pv >= fe.second) dominated = true;
+      ok = theta <= reduction * theta_k && !dominated;
+      return ACOPF_OK;
+    };
+    for (int it_r = 0; it_r < kRestoMaxIter; ++it_r) {
+      bool ok = false;
+      acopf_status r = accepted(ok);
+      if (r != ACOPF_OK) return r;
+      if (ok) {
+        code = 1;
+        return ACOPF_OK;
+      }
+      // Gauss-Newton step
+      r = acopf_eval_jac_coo(model, v.x, v.jvals, as);
+      if (r != ACOPF_OK) return r;
+      const double zeta = std::sqrt(mu_r);
+      e = acopf::launch_resto_grad(model->step, v.jvals, B.r, v.x, B.xr, B.xl, B.xu, mu_r, zeta,
+                                   B.rhs, B.sigma_x, blocks, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(B.hvals, 0, size_t(L.nnzh) * 8, s);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration step");
+      r = acopf_assemble_condensed_kkt_csr(model, B.hvals, v.jvals, B.sigma_x, B.sigma_s, 0.0,
+                                           0.0, B.kvals, as);
+      int32_t bad = -1;
+      if (r == ACOPF_OK) r = acopf_chol_factor(chol, B.kvals, 0.0, &bad, as);
+      if (r != ACOPF_OK) return r;
+      result->factorizations++;
+      if (bad >= 0) break;  // (positive definite by construction; a failure ends as infeasible)
+      r = acopf_chol_solve(chol, B.rhs, v.dx, as);
+      if (r != ACOPF_OK) return r;
+      e = acopf::launch_resto_dir(v.x, v.dx, B.rhs, B.xr, B.xl, B.xu, n, 0.99, blocks, B.part,
+                                  B.out, s);
+      if (e == cudaSuccess) e = fetch(4);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration step");
+      double alpha = hout[0];
+      const double slope = hout[1];
+      const double psi0 = 0.5 * rr - mu_r * hout[2] + 0.5 * zeta * hout[3];
+      double rt = 0.0, tht = 0.0;
+      bool step_ok = false;
+      while (true) {
+        e = acopf::launch_resto_trial(v.x, v.dx, B.xr, B.xl, B.xu, n, alpha, v.xt, blocks, B.part,
+                                      B.out, s);
+        if (e == cudaSuccess) e = fetch(2);
+        if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration trial");
+        const double lg = hout[0], pr = hout[1];
+        r = acopf_eval_cons(model, v.xt, v.cons_t, as);
+        if (r != ACOPF_OK) return r;
+        e = slack(v.cons_t, v.st, nullptr, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration trial");
+        result->trial_points++;
+        tht = hout[0];
+        rt = hout[1];
+        if (0.5 * rt - mu_r * lg + 0.5 * zeta * pr <= psi0 + 1e-4 * alpha * slope) {
+          step_ok = true;
+          break;
+        }
+        alpha *= 0.5;
+        if (alpha < 1e-12) break;
+      }
+      if (!step_ok) {  // no decrease along the step: a smaller barrier, else infeasible
+        if (mu_r <= kRestoMuMin) return ACOPF_OK;
+        mu_r *= 0.1;
+        since = 0;
+        continue;
+      }
+      std::swap(v.x, v.xt);
+      std::swap(v.s, v.st);
+      std::swap(v.cons, v.cons_t);
+      rr = rt;
+      e = slack(v.cons, v.s, B.r, B.sigma_s);  // the violation and its rows at the new point
+      if (e == cudaSuccess) e = cudaMemcpyAsync(B.xr, v.x, N * 8, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration update");
+      if (tht < 0.99 * best) {
+        best = tht;
+        since = 0;
+      } else if (++since >= kRestoStall) {  // stalled: a smaller barrier, else infeasible
+        if (mu_r <= kRestoMuMin) return ACOPF_OK;
+        mu_r *= 0.1;
+        since = 0;
+      }
+    }
+    bool ok = false;
+    const acopf_status r = accepted(ok);
+    if (r != ACOPF_OK) return r;
+    code = ok ? 1 : 0;
+    return ACOPF_OK;
+  };
 
   for (k = 0; k <= max_iter; ++k) {
     set_iterate();
@@ -328,9 +467,30 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
       alpha *= 0.5;
       if (alpha < alpha_min) break;
     }
-    if (!accepted) {
-      status = ACOPF_IPM_LINE_SEARCH_FAILED;
-      break;
+    if (!accepted) {  // feasibility restoration from the current point
+      filter.push_back({(1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta});
+      // back without getting below the last restoration's exit: demand
+      // (nearly) feasibility this time, which an infeasible network cannot give
+      const double red =
+          resto_exit >= 0.0 && theta >= resto_exit ? kRestoReductionRepeat : kRestoReduction;
+      int code = 0;
+      st = restoration(mu, theta, red, code);
+      if (st != ACOPF_OK) return st;
+      resto_exit = theta;
+      record(k, 4, 0.0);
+      record(k, 5, 0.0);
+      record(k, 6, dw);
+      if (code == 0) {
+        status = ACOPF_IPM_INFEASIBLE;
+        break;
+      }
+      // multipliers restart: y = 0, bound duals on the central path
+      e = acopf::launch_resto_duals(v, n, m, mu, blocks, s);
+      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: restoration duals");
+      st = acopf_eval_grad(model, v.x, v.grad, as);
+      if (st == ACOPF_OK) st = acopf_eval_jac_coo(model, v.x, v.jvals, as);
+      if (st != ACOPF_OK) return st;
+      continue;
     }
     if (accepted == 2)
       filter.push_back({(1.0 - kGammaTheta) * theta, phi - kGammaPhi * theta});

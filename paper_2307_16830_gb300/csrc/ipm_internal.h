@@ -35,4 +35,28 @@ cudaError_t launch_ipm_measure(const IpmVec& v, const double* x, const double* s
 cudaError_t launch_ipm_accept(const IpmVec& v, int n, int m, double alpha, double alpha_z,
                               double mu, double kappa, int blocks, cudaStream_t s);
 
+// Feasibility restoration.  s = clip(cons, lo_s, hi_s), r = cons - s, w = 1
+// where r != 0 (r, w may be NULL); out[0..1] = sum |r|, sum r^2.
+cudaError_t launch_resto_slack(const double* cons, const double* lo_s, const double* hi_s, int m,
+                               double* s, double* r, double* w, int blocks, double* part,
+                               double* out, cudaStream_t st);
+// rhs = -(A'r + mu_r (1/(u-x) - 1/(x-l)) + zeta (x - xr)), sigma the
+// barrier's curvature + zeta.
+cudaError_t launch_resto_grad(const DevStep& step, const double* jvals, const double* r,
+                              const double* x, const double* xr, const double* xl,
+                              const double* xu, double mu_r, double zeta, double* rhs,
+                              double* sigma, int blocks, cudaStream_t s);
+// out[0..3] = fraction-to-boundary step, -rhs'dx, sum log gaps of x, ||x - xr||^2.
+cudaError_t launch_resto_dir(const double* x, const double* dx, const double* rhs,
+                             const double* xr, const double* xl, const double* xu, int n,
+                             double tau, int blocks, double* part, double* out, cudaStream_t s);
+// xt = x + alpha dx; out[0..1] = sum log gaps of xt, ||xt - xr||^2.
+cudaError_t launch_resto_trial(const double* x, const double* dx, const double* xr,
+                               const double* xl, const double* xu, int n, double alpha,
+                               double* xt, int blocks, double* part, double* out,
+                               cudaStream_t s);
+// y = 0 and z = mu / gap at the finite bounds of the iterate.
+cudaError_t launch_resto_duals(const IpmVec& v, int n, int m, double mu, int blocks,
+                               cudaStream_t s);
+
 }  // namespace acopf

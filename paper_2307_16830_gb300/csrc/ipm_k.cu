@@ -1,7 +1,8 @@
 // Vector kernels of the condensed-space interior-point iteration (Algorithm
 // 1): the Newton right-hand side (minus the conditions of Eq. first), the
 // step-size bounds and the barrier terms of the line search, the trial
-// point, and the update of the multipliers.  Reductions run over a fixed
+// point, the update of the multipliers, and the feasibility restoration's
+// slack projection, Gauss-Newton right-hand side, step bound and trials.  Reductions run over a fixed
 // grid (4 blocks per SM): per-block partials in a fixed order, then one
 // block combining them in block order, so every result is reproducible.
 #include "ipm_internal.h"
@@ -183,9 +184,167 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_accept(IpmVec v, int n, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// feasibility restoration (the oracle's `restoration`, reading d10)
+// ---------------------------------------------------------------------------
+// At x with its constraint values g: the slacks follow g clipped onto the
+// pushed slack box [lo_s, hi_s] (s = clip(g)), the violation is
+// r = g - s, w = 1 where r != 0 (the assembly's D), and per block
+// [sum |r|, sum r^2].
+__global__ void __launch_bounds__(kIpmThreads) k_resto_slack(
+    const double* __restrict__ cons, const double* __restrict__ lo_s,
+    const double* __restrict__ hi_s, int m, double* __restrict__ s, double* __restrict__ r,
+    double* __restrict__ w, double* __restrict__ part) {
+  double a[2] = {0.0, 0.0};
+  const int stride = gridDim.x * kIpmThreads;
+  for (int k = blockIdx.x * kIpmThreads + threadIdx.x; k < m; k += stride) {
+    const double g = cons[k];
+    const double sk = fmin(fmax(g, lo_s[k]), hi_s[k]);
+    const double rk = g - sk;
+    s[k] = sk;
+    if (r) r[k] = rk;
+    if (w) w[k] = rk != 0.0 ? 1.0 : 0.0;
+    a[0] += fabs(rk);
+    a[1] = fma(rk, rk, a[1]);
+  }
+  block_reduce<2, 0>(a, part);
+}
+
+// The gradient of the restoration merit psi at x, minus (the solve's
+// right-hand side), and the diagonal sigma = mu_R (1/(x-l)^2 + 1/(u-x)^2)
+// + zeta: -(A'(w r) + mu_R (1/(u-x) - 1/(x-l)) + zeta (x - x_R)).  A'(w r)
+// is gathered per variable in slot order (w r = r: r is 0 where w is).
+__global__ void __launch_bounds__(kIpmThreads) k_resto_grad(
+    DevStep st, const double* __restrict__ jvals, const double* __restrict__ r,
+    const double* __restrict__ x, const double* __restrict__ xr, const double* __restrict__ xl,
+    const double* __restrict__ xu, double mu_r, double zeta, double* __restrict__ rhs,
+    double* __restrict__ sigma) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < st.n; j += stride) {
+    double atr = 0.0;
+    for (int k = __ldg(st.jt_ptr + j), k1 = __ldg(st.jt_ptr + j + 1); k < k1; ++k)
+      atr = fma(jvals[__ldg(st.jt_slot + k)], r[__ldg(st.jt_row + k)], atr);
+    const double xj = x[j], lo = xl[j], hi = xu[j];
+    double g = fma(zeta, xj - xr[j], atr), sg = zeta;
+    if (finite_bound(lo)) {
+      const double il = 1.0 / (xj - lo);
+      g -= mu_r * il;
+      sg = fma(mu_r * il, il, sg);
+    }
+    if (finite_bound(hi)) {
+      const double iu = 1.0 / (hi - xj);
+      g += mu_r * iu;
+      sg = fma(mu_r * iu, iu, sg);
+    }
+    rhs[j] = -g;
+    sigma[j] = sg;
+  }
+}
+
+// Per block: [fraction-to-boundary step of x along dx (tau), -rhs' dx (the
+// merit's slope), sum of log gaps of x, ||x - x_R||^2].
+__global__ void __launch_bounds__(kIpmThreads) k_resto_dir(
+    const double* __restrict__ x, const double* __restrict__ dx, const double* __restrict__ rhs,
+    const double* __restrict__ xr, const double* __restrict__ xl, const double* __restrict__ xu,
+    int n, double tau, double* __restrict__ part) {
+  double a[4] = {1.0, 0.0, 0.0, 0.0};
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double xj = x[j], d = dx[j], lo = xl[j], hi = xu[j];
+    a[1] = fma(-rhs[j], d, a[1]);
+    if (finite_bound(lo)) {
+      if (d < 0.0) a[0] = fmin(a[0], -tau * (xj - lo) / d);
+      a[2] += log(xj - lo);
+    }
+    if (finite_bound(hi)) {
+      if (d > 0.0) a[0] = fmin(a[0], tau * (hi - xj) / d);
+      a[2] += log(hi - xj);
+    }
+    const double e = xj - xr[j];
+    a[3] = fma(e, e, a[3]);
+  }
+  block_reduce<4, 1>(a, part);
+}
+
+// x_t = x + alpha dx, and per block [sum log gaps of x_t, ||x_t - x_R||^2].
+__global__ void __launch_bounds__(kIpmThreads) k_resto_trial(
+    const double* __restrict__ x, const double* __restrict__ dx, const double* __restrict__ xr,
+    const double* __restrict__ xl, const double* __restrict__ xu, int n, double alpha,
+    double* __restrict__ xt, double* __restrict__ part) {
+  double a[2] = {0.0, 0.0};
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double v = fma(alpha, dx[j], x[j]), lo = xl[j], hi = xu[j];
+    xt[j] = v;
+    if (finite_bound(lo)) a[0] += log(v - lo);
+    if (finite_bound(hi)) a[0] += log(hi - v);
+    const double e = v - xr[j];
+    a[1] = fma(e, e, a[1]);
+  }
+  block_reduce<2, 0>(a, part);
+}
+
+// After restoration: y = 0 and the bound multipliers on the central path,
+// z = mu / gap at every finite bound of (x, s).
+__global__ void __launch_bounds__(kIpmThreads) k_resto_duals(IpmVec v, int n, int m, double mu) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
+    const double x = v.x[j], lo = v.xl[j], hi = v.xu[j];
+    v.zl_x[j] = finite_bound(lo) ? mu / (x - lo) : 0.0;
+    v.zu_x[j] = finite_bound(hi) ? mu / (hi - x) : 0.0;
+  }
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
+    const double s = v.s[r], lo = v.sl[r], hi = v.su[r];
+    v.y[r] = 0.0;
+    v.ym[r] = 0.0;
+    v.zl_s[r] = finite_bound(lo) ? mu / (s - lo) : 0.0;
+    v.zu_s[r] = finite_bound(hi) ? mu / (hi - s) : 0.0;
+  }
+}
+
 }  // namespace
 
 int ipm_blocks(int sms) { return 4 * sms; }
+
+cudaError_t launch_resto_slack(const double* cons, const double* lo_s, const double* hi_s, int m,
+                               double* s, double* r, double* w, int blocks, double* part,
+                               double* out, cudaStream_t st) {
+  k_resto_slack<<<blocks, kIpmThreads, 0, st>>>(cons, lo_s, hi_s, m, s, r, w, part);
+  k_ipm_final<2, 0><<<1, kIpmThreads, 0, st>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resto_grad(const DevStep& step, const double* jvals, const double* r,
+                              const double* x, const double* xr, const double* xl,
+                              const double* xu, double mu_r, double zeta, double* rhs,
+                              double* sigma, int blocks, cudaStream_t s) {
+  k_resto_grad<<<blocks, kIpmThreads, 0, s>>>(step, jvals, r, x, xr, xl, xu, mu_r, zeta, rhs,
+                                              sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resto_dir(const double* x, const double* dx, const double* rhs,
+                             const double* xr, const double* xl, const double* xu, int n,
+                             double tau, int blocks, double* part, double* out, cudaStream_t s) {
+  k_resto_dir<<<blocks, kIpmThreads, 0, s>>>(x, dx, rhs, xr, xl, xu, n, tau, part);
+  k_ipm_final<4, 1><<<1, kIpmThreads, 0, s>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resto_trial(const double* x, const double* dx, const double* xr,
+                               const double* xl, const double* xu, int n, double alpha,
+                               double* xt, int blocks, double* part, double* out,
+                               cudaStream_t s) {
+  k_resto_trial<<<blocks, kIpmThreads, 0, s>>>(x, dx, xr, xl, xu, n, alpha, xt, part);
+  k_ipm_final<2, 0><<<1, kIpmThreads, 0, s>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resto_duals(const IpmVec& v, int n, int m, double mu, int blocks,
+                               cudaStream_t s) {
+  k_resto_duals<<<blocks, kIpmThreads, 0, s>>>(v, n, m, mu);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ipm_rhs(const DevStep& st, const IpmVec& v, double mu, int blocks,
                            cudaStream_t s) {

@@ -4,9 +4,10 @@
 At tol = 1e-4 (the paper's default for the condensed method) on networks
 both solve: the same status and iteration count, per-iteration objective,
 residual, barrier parameter, violation and step sizes within 1e-4
-relative, the final objective within 1e-8 relative and x within 1e-4; on a
-network where the line search fails, the same failure at the same
-iteration.  The 1e-4: the slack boxes of the equality rows are 2e-4 wide
+relative, the final objective within 1e-8 relative and x within 1e-4; on
+networks without a feasible point (the 30-bus network at 0.8 and 1.0 times
+its loads), the same restorations and the same "infeasible" stop at the same
+iteration, at a point of the same violation.  The 1e-4: the slack boxes of the equality rows are 2e-4 wide
 and the gaps shrink with mu, so Sigma reaches 1e8-1e10 late in a solve;
 M_cond's condition number times the double-precision unit roundoff then
 bounds the relative difference of two correct steps computed in different
@@ -26,12 +27,17 @@ from paper_2307_16830_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-def _half_load(g):
+def _scaled(g, scale):
     import dataclasses
-    return dataclasses.replace(g, Pd=g.Pd * 0.5, Qd=g.Qd * 0.5)
+    return dataclasses.replace(g, Pd=g.Pd * scale, Qd=g.Qd * scale)
 
 
-STATUS = {"converged": 0, "max_iter": 1, "line search failed": 2, "inertia correction failed": 3}
+def _half_load(g):
+    return _scaled(g, 0.5)
+
+
+STATUS = {"converged": 0, "max_iter": 1, "line search failed": 2, "inertia correction failed": 3,
+          "infeasible": 4}
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +53,7 @@ CASES = [("30bus-opf", lambda: synth.workload_grid("30bus-opf"), 1e-4),
          ("random500", lambda: synth.make_grid(500, 675, 100, seed=21, load_scale=0.1), 1e-4),
          ("geo300", lambda: synth.make_grid(300, 405, 60, seed=1011, topology="geometric",
                                             load_scale=0.1), 1e-4),
+         ("30bus 0.8 load", lambda: _scaled(synth.workload_grid("30bus"), 0.8), 1e-4),
          ("30bus full load", lambda: synth.workload_grid("30bus"), 1e-4)]
 
 
@@ -69,6 +76,13 @@ def test_ipm_matches_oracle(acopf, idx):
         assert abs(res["objective"] - ref.objective) <= 1e-8 * abs(ref.objective)
         assert np.max(np.abs(x - ref.x)) <= 1e-4
         assert res["residual"] <= tol
+    if ref.status == "infeasible":  # stopped at a point of the same violation
+        from oracle.ipm import relaxed_bounds
+        _, _, gl, gu = oracle.bounds(g)
+        sl, su = relaxed_bounds(gl, gu, tol)
+        viol = lambda v: float(np.sum(np.abs(v - np.clip(v, sl, su))))  # noqa: E731
+        a, b = viol(oracle.constraints(g, x)[0]), viol(oracle.constraints(g, ref.x)[0])
+        assert abs(a - b) <= 1e-3 * b, (name, a, b)
 
 
 def test_ipm_tight_tolerance_reaches_the_same_point(acopf):

@@ -9,8 +9,17 @@
   solver (scipy's SLSQP from the same start) and satisfies the bounds and
   the relaxed constraints.
 * The initial-point and step-bound rules against hand values.
+* The feasibility restoration (reading d10): on the 30-bus network at 0.8
+  and 1.0 times its loads, which have no feasible point, the solve stops as
+  infeasible at a point whose violation equals the smallest one an
+  independent least-squares solver (scipy's trust-region reflective method
+  from random starts) finds; at 0.6 times the loads (feasible) it converges.
 """
+import dataclasses
+
 import numpy as np
+import pytest
+import scipy.sparse as sp
 
 import oracle
 from oracle.ipm import IpmOptions, fraction_to_boundary, ipm_start, push_interior
@@ -122,3 +131,82 @@ def test_initial_point_and_step_rules_by_hand():
     assert abs(a - 0.495) < 1e-15
     assert fraction_to_boundary(np.array([1.0]), np.array([0.1]), np.array([0.0]),
                                 np.array([2.0]), 0.99) == 1.0
+
+
+def _scaled_30bus(scale):
+    g = synth.workload_grid("30bus")
+    return dataclasses.replace(g, Pd=g.Pd * scale, Qd=g.Qd * scale)
+
+
+def _violation_l1(g, x, tol=1e-4):
+    from oracle.ipm import relaxed_bounds
+    _, _, gl, gu = oracle.bounds(g)
+    sl, su = relaxed_bounds(gl, gu, tol)
+    c = oracle.constraints(g, x)[0]
+    return float(np.sum(np.abs(c - np.clip(c, sl, su))))
+
+
+def _least_violation(g, starts=2, tol=1e-4):
+    """The smallest L1 constraint violation (against the relaxed bounds, x
+    within its bounds) scipy's least_squares reaches from random starts."""
+    from scipy.optimize import least_squares
+
+    from oracle.ipm import relaxed_bounds
+    L = oracle.layout(g)
+    xl, xu, gl, gu = oracle.bounds(g)
+    sl, su = relaxed_bounds(gl, gu, tol)
+    jr, jc = oracle.jac_structure(g)
+
+    def resid(x):
+        c = oracle.constraints(g, x)[0]
+        return c - np.clip(c, sl, su)
+
+    def jac(x):
+        c = oracle.constraints(g, x)[0]
+        outside = ((c < sl) | (c > su)).astype(float)
+        A = sp.csr_matrix((oracle.jacobian(g, x)[0], (jr, jc)), shape=(L.m, L.n))
+        return (sp.diags(outside) @ A).toarray()
+
+    lb = np.where(np.isfinite(xl), xl, -np.inf)
+    ub = np.where(np.isfinite(xu), xu, np.inf)
+    best = np.inf
+    for t in range(starts):
+        x0 = np.clip(synth.make_point(g, 200 + t).x, lb + 1e-9, ub - 1e-9)
+        r = least_squares(resid, x0, jac=jac, bounds=(lb, ub), method="trf", max_nfev=500,
+                          xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        best = min(best, float(np.sum(np.abs(resid(r.x)))))
+    return best
+
+
+@pytest.mark.parametrize("scale", [0.8, 1.0])
+def test_restoration_stops_at_the_least_violation_when_infeasible(scale):
+    g = _scaled_30bus(scale)
+    r = oracle.ipm_solve(g, IpmOptions())
+    assert r.status == "infeasible", r.status
+    assert any(h.get("restoration") for h in r.history)
+    least = _least_violation(g)
+    assert least > 0.1  # no feasible point: the pin's premise
+    assert abs(_violation_l1(g, r.x) - least) <= 5e-3 * least, (_violation_l1(g, r.x), least)
+
+
+def test_feasible_load_converges():
+    g = _scaled_30bus(0.6)
+    assert _least_violation(g, starts=1) < 1e-8  # a feasible point exists
+    r = oracle.ipm_solve(g, IpmOptions())
+    assert r.status == "converged"
+
+
+def test_pin_catches_restoration_that_gives_up_early(monkeypatch):
+    """A restoration stopping at its first stall (no smaller barrier) leaves
+    a larger violation than the least one: the pin above fails."""
+    import oracle.ipm as ipm_mod
+    real = ipm_mod.restoration
+
+    def early(grid, x, b, mu, accept, opts):
+        return real(grid, x, b, mu, accept, dataclasses.replace(opts, resto_mu_min=1e30))
+
+    monkeypatch.setattr(ipm_mod, "restoration", early)
+    g = _scaled_30bus(1.0)
+    r = oracle.ipm_solve(g, IpmOptions())
+    least = _least_violation(g)
+    assert r.status != "infeasible" or abs(_violation_l1(g, r.x) - least) > 5e-3 * least
