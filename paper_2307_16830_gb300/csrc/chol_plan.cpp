@@ -127,6 +127,94 @@ void schedule(const std::vector<int32_t>& task, const std::vector<std::vector<in
   }
 }
 
+// The list schedule of a forest of tasks of equal duration on `workers`
+// workers, in rounds: up to `workers` ready tasks start together and finish
+// together; ready tasks with the longest remaining chain start first (ties:
+// the most recently released; released tasks wait for the next round).  up[k] is task k's parent (-1: a root; parents
+// have larger numbers than their children); `forward`: a task needs its
+// children, else its parent.  False if `up` is not such a forest.
+bool schedule_forest(const std::vector<int32_t>& task, const std::vector<int32_t>& up,
+                     bool forward, int32_t workers, CholGraph& g) {
+  const int32_t nt = int32_t(up.size());
+  for (int32_t k = 0; k < nt; ++k)
+    if (up[size_t(k)] >= nt || (up[size_t(k)] >= 0 && up[size_t(k)] <= k)) return false;
+  std::vector<int32_t> kp(size_t(nt) + 1, 0), kids;  // children of each task
+  for (int32_t k = 0; k < nt; ++k)
+    if (up[size_t(k)] >= 0) kp[size_t(up[size_t(k)]) + 1]++;
+  for (int32_t k = 0; k < nt; ++k) kp[size_t(k) + 1] += kp[size_t(k)];
+  kids.resize(size_t(kp[size_t(nt)]));
+  {
+    std::vector<int32_t> nx(kp.begin(), kp.end() - 1);
+    for (int32_t k = 0; k < nt; ++k)
+      if (up[size_t(k)] >= 0) kids[size_t(nx[size_t(up[size_t(k)])]++)] = k;
+  }
+  // remaining chain length: forward, the path to the root; backward, the
+  // longest path to a leaf
+  std::vector<int32_t> bl(static_cast<size_t>(nt), 1);
+  int32_t top = 0;
+  if (forward) {
+    for (int32_t k = nt - 1; k >= 0; --k)
+      if (up[size_t(k)] >= 0) bl[size_t(k)] = bl[size_t(up[size_t(k)])] + 1;
+  } else {
+    for (int32_t k = 0; k < nt; ++k)
+      if (up[size_t(k)] >= 0)
+        bl[size_t(up[size_t(k)])] = std::max(bl[size_t(up[size_t(k)])], bl[size_t(k)] + 1);
+  }
+  for (int32_t k = 0; k < nt; ++k) top = std::max(top, bl[size_t(k)]);
+  std::vector<std::vector<int32_t>> bucket(size_t(top) + 1);
+  std::vector<int32_t> wait(static_cast<size_t>(nt));
+  for (int32_t k = 0; k < nt; ++k) {
+    wait[size_t(k)] = forward ? kp[size_t(k) + 1] - kp[size_t(k)] : (up[size_t(k)] >= 0 ? 1 : 0);
+    if (wait[size_t(k)] == 0) bucket[size_t(bl[size_t(k)])].push_back(k);
+  }
+  std::vector<int32_t> order, round;
+  order.reserve(size_t(nt));
+  while (int32_t(order.size()) < nt) {
+    round.clear();
+    for (int32_t b = top; b >= 1 && int32_t(round.size()) < workers;) {
+      if (bucket[size_t(b)].empty()) {
+        top = --b;
+        continue;
+      }
+      round.push_back(bucket[size_t(b)].back());
+      bucket[size_t(b)].pop_back();
+    }
+    if (round.empty()) return false;
+    order.insert(order.end(), round.begin(), round.end());
+    auto release = [&](int32_t t) {
+      bucket[size_t(bl[size_t(t)])].push_back(t);
+      top = std::max(top, bl[size_t(t)]);
+    };
+    for (const int32_t k : round) {
+      if (forward) {
+        const int32_t p = up[size_t(k)];
+        if (p >= 0 && --wait[size_t(p)] == 0) release(p);
+      } else {
+        for (int32_t q = kp[size_t(k)]; q < kp[size_t(k) + 1]; ++q) release(kids[size_t(q)]);
+      }
+    }
+  }
+  std::vector<int32_t> pos(static_cast<size_t>(nt));
+  for (int32_t k = 0; k < nt; ++k) pos[size_t(order[size_t(k)])] = k;
+  g.task.resize(size_t(nt) * 4);
+  g.dep_ptr.assign(size_t(nt) + 1, 0);
+  g.dep.clear();
+  g.dep.reserve(size_t(kp[size_t(nt)]));
+  for (int32_t k = 0; k < nt; ++k) {
+    const int32_t t = order[size_t(k)];
+    std::copy(task.begin() + 4 * t, task.begin() + 4 * t + 4, g.task.begin() + 4 * k);
+    const size_t d0 = g.dep.size();
+    if (forward) {
+      for (int32_t q = kp[size_t(t)]; q < kp[size_t(t) + 1]; ++q) g.dep.push_back(pos[size_t(kids[size_t(q)])]);
+    } else if (up[size_t(t)] >= 0) {
+      g.dep.push_back(pos[size_t(up[size_t(t)])]);
+    }
+    std::sort(g.dep.begin() + d0, g.dep.end());
+    g.dep_ptr[size_t(k) + 1] = int32_t(g.dep.size());
+  }
+  return true;
+}
+
 }  // namespace
 
 acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPlan& plan,
@@ -423,21 +511,19 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
       }
     const int32_t nw = int32_t(wsn.size());
     {  // both directions ordered by a list schedule on the warps
-      std::vector<int32_t> wtask;
-      std::vector<double> wdur;
-      std::vector<std::vector<int32_t>> wf(static_cast<size_t>(nw)), wb(static_cast<size_t>(nw));
+      std::vector<int32_t> wtask(size_t(nw) * 4), wup(static_cast<size_t>(nw));
       for (int32_t k = 0; k < nw; ++k) {
-        const int32_t s = wsn[size_t(k)];
-        wtask.insert(wtask.end(), {kTaskBlock, s, 0, 0});
-        wdur.push_back(6.0);
-        const int32_t p = sy.sn_parent[size_t(s)];
-        if (p >= 0 && widx[size_t(p)] >= 0) {
-          wf[size_t(widx[size_t(p)])].push_back(k);
-          wb[size_t(k)].push_back(widx[size_t(p)]);
-        }
+        const int32_t s = wsn[size_t(k)], p = sy.sn_parent[size_t(s)];
+        wtask[4 * size_t(k)] = kTaskBlock;
+        wtask[4 * size_t(k) + 1] = s;
+        wtask[4 * size_t(k) + 2] = wtask[4 * size_t(k) + 3] = 0;
+        wup[size_t(k)] = p >= 0 ? widx[size_t(p)] : -1;
       }
-      schedule(wtask, wf, wdur, prm.warps, plan.forward_warp, nullptr, nullptr);
-      schedule(wtask, wb, wdur, prm.warps, plan.backward_warp, nullptr, nullptr);
+      if (!schedule_forest(wtask, wup, true, prm.warps, plan.forward_warp) ||
+          !schedule_forest(wtask, wup, false, prm.warps, plan.backward_warp)) {
+        err = "task plan: the supernodal tree is not a forest in postorder";
+        return ACOPF_E_INVALID_ARG;
+      }
     }
     Builder F;
     std::vector<int32_t> fcomp(static_cast<size_t>(ns), -1);

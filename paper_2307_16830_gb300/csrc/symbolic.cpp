@@ -10,12 +10,18 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <utility>
 
 namespace acopf {
 namespace {
+
+// Host threads of the parallel passes.
+constexpr int32_t kSymbolicThreads = 8;
 
 }  // namespace
 
@@ -25,57 +31,99 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     sy = CholSymbolic{};
     sy.n = n;
     const int64_t nnz_low = rp[size_t(n)];
-    // --- fill-reducing order: approximate minimum degree (amd.cpp) -------
-    std::vector<int32_t> ap(size_t(n) + 1, 0), ai;
-    for (int32_t i = 0; i < n; ++i)
-      for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
-        if (ci[size_t(k)] != i) {
-          ap[size_t(i) + 1]++;
-          ap[size_t(ci[size_t(k)]) + 1]++;
-        }
-    for (int32_t i = 0; i < n; ++i) ap[size_t(i) + 1] += ap[size_t(i)];
-    ai.resize(size_t(ap[size_t(n)]));
+    // --- the symmetric pattern without its diagonal (both triangles) ------
+    std::vector<int32_t> gp(size_t(n) + 1, 0), gi;
     {
-      std::vector<int32_t> nx(ap.begin(), ap.end() - 1);
+      std::vector<int32_t> ap(size_t(n) + 1, 0), ai;
       for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
-          const int32_t j = ci[size_t(k)];
-          if (j == i) continue;
-          ai[size_t(nx[size_t(i)]++)] = j;
-          ai[size_t(nx[size_t(j)]++)] = i;
+        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
+          if (ci[size_t(k)] != i) {
+            ap[size_t(i) + 1]++;
+            ap[size_t(ci[size_t(k)]) + 1]++;
+          }
+      for (int32_t i = 0; i < n; ++i) ap[size_t(i) + 1] += ap[size_t(i)];
+      ai.resize(size_t(ap[size_t(n)]));
+      {
+        std::vector<int32_t> nx(ap.begin(), ap.end() - 1);
+        for (int32_t i = 0; i < n; ++i)
+          for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
+            const int32_t j = ci[size_t(k)];
+            if (j == i) continue;
+            ai[size_t(nx[size_t(i)]++)] = j;
+            ai[size_t(nx[size_t(j)]++)] = i;
+          }
+      }
+      // --- locality: the nodes renumbered breadth first (each component
+      // from its lowest unvisited node), so that the order and the passes
+      // after it, which walk the graph, find neighbours near each other in
+      // memory.  bfs[v] is the input node numbered v, nid its inverse.
+      std::vector<int32_t> bfs, nid(static_cast<size_t>(n), -1);
+      bfs.reserve(size_t(n));
+      for (int32_t r = 0; r < n; ++r) {
+        if (nid[size_t(r)] >= 0) continue;
+        nid[size_t(r)] = int32_t(bfs.size());
+        bfs.push_back(r);
+        for (size_t h = bfs.size() - 1; h < bfs.size(); ++h) {
+          const int32_t v = bfs[h];
+          for (int32_t k = ap[size_t(v)]; k < ap[size_t(v) + 1]; ++k) {
+            const int32_t u = ai[size_t(k)];
+            if (nid[size_t(u)] < 0) {
+              nid[size_t(u)] = int32_t(bfs.size());
+              bfs.push_back(u);
+            }
+          }
         }
+      }
+      gi.resize(ai.size());
+      for (int32_t v = 0; v < n; ++v) {
+        const int32_t o = bfs[size_t(v)];
+        int32_t t = gp[size_t(v)];
+        for (int32_t k = ap[size_t(o)]; k < ap[size_t(o) + 1]; ++k) gi[size_t(t++)] = nid[size_t(ai[size_t(k)])];
+        gp[size_t(v) + 1] = t;
+      }
+      sy.perm.swap(bfs);  // (for now: the renumbering)
     }
-    std::vector<int32_t> md;
-    if (!approximate_minimum_degree(n, ap, ai, md)) {
+    // --- fill-reducing order: approximate minimum degree (amd.cpp) -------
+    std::vector<int32_t> md;  // md[k]: the (renumbered) node eliminated k-th
+    if (!approximate_minimum_degree(n, gp, gi, md)) {
       err = "the fill-reducing order failed";
       return ACOPF_E_INVALID_ARG;
     }
-    std::vector<int32_t>().swap(ai);
-    std::vector<int32_t> ipmd(static_cast<size_t>(n));
-    for (int32_t k = 0; k < n; ++k) ipmd[size_t(md[size_t(k)])] = k;
+    // lower rows of the matrix in an order (ord[k]: the node at position k,
+    // ipos its inverse), gathered row by row from the adjacency; with
+    // `upper`, the entries above the diagonal by rows too (= the lower
+    // triangle by columns)
+    auto gather_rows = [&](const std::vector<int32_t>& ord, const std::vector<int32_t>& ipos,
+                           std::vector<int32_t>& lrp, std::vector<int32_t>& lci,
+                           std::vector<int32_t>* urp, std::vector<int32_t>* uci) {
+      lrp.assign(size_t(n) + 1, 0);
+      lci.clear();
+      lci.reserve(gi.size() / 2);
+      if (urp) {
+        urp->assign(size_t(n) + 1, 0);
+        uci->clear();
+        uci->reserve(gi.size() / 2);
+      }
+      for (int32_t k = 0; k < n; ++k) {
+        const int32_t v = ord[size_t(k)];
+        for (int32_t q = gp[size_t(v)]; q < gp[size_t(v) + 1]; ++q) {
+          const int32_t a = ipos[size_t(gi[size_t(q)])];
+          if (a < k)
+            lci.push_back(a);
+          else if (urp)
+            uci->push_back(a);
+        }
+        lrp[size_t(k) + 1] = int32_t(lci.size());
+        if (urp) (*urp)[size_t(k) + 1] = int32_t(uci->size());
+      }
+    };
 
     // --- elimination tree of the reordered matrix (Liu) ----------------
-    // lower rows of B = P M P': for each row r the columns c < r
-    auto lower_rows = [&](const std::vector<int32_t>& ip, std::vector<int32_t>& brp,
-                          std::vector<int32_t>& bci) {
-      brp.assign(size_t(n) + 1, 0);
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
-          const int32_t a = ip[size_t(i)], b = ip[size_t(ci[size_t(k)])];
-          if (a != b) brp[size_t(std::max(a, b)) + 1]++;
-        }
-      for (int32_t i = 0; i < n; ++i) brp[size_t(i) + 1] += brp[size_t(i)];
-      bci.resize(size_t(brp[size_t(n)]));
-      std::vector<int32_t> nx(brp.begin(), brp.end() - 1);
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
-          const int32_t a = ip[size_t(i)], b = ip[size_t(ci[size_t(k)])];
-          if (a != b) bci[size_t(nx[size_t(std::max(a, b))]++)] = std::min(a, b);
-        }
-    };
-    auto etree = [&](const std::vector<int32_t>& brp, const std::vector<int32_t>& bci,
-                     std::vector<int32_t>& parent) {
-      parent.assign(static_cast<size_t>(n), -1);
+    std::vector<int32_t> brp, bci, parent(static_cast<size_t>(n), -1);
+    {
+      std::vector<int32_t> ipmd(static_cast<size_t>(n));
+      for (int32_t k = 0; k < n; ++k) ipmd[size_t(md[size_t(k)])] = k;
+      gather_rows(md, ipmd, brp, bci, nullptr, nullptr);
       std::vector<int32_t> anc(static_cast<size_t>(n), -1);
       for (int32_t i = 0; i < n; ++i)
         for (int32_t k = brp[size_t(i)]; k < brp[size_t(i) + 1]; ++k) {
@@ -90,44 +138,57 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
             parent[size_t(r)] = i;
           }
         }
-    };
-    std::vector<int32_t> brp, bci, parent;
-    lower_rows(ipmd, brp, bci);
-    etree(brp, bci, parent);
+    }
 
     // --- postorder (children in ascending order, depth first) -----------
-    std::vector<int32_t> head(static_cast<size_t>(n), -1), next(static_cast<size_t>(n), -1), post;
-    post.reserve(size_t(n));
-    for (int32_t v = n - 1; v >= 0; --v)
-      if (parent[size_t(v)] >= 0) {
-        next[size_t(v)] = head[size_t(parent[size_t(v)])];
-        head[size_t(parent[size_t(v)])] = v;
-      }
-    std::vector<int32_t> stack;
-    for (int32_t root = 0; root < n; ++root) {
-      if (parent[size_t(root)] != -1) continue;
-      stack.push_back(root);
-      while (!stack.empty()) {
-        const int32_t v = stack.back();
-        const int32_t c = head[size_t(v)];
-        if (c == -1) {
-          post.push_back(v);
-          stack.pop_back();
-        } else {
-          head[size_t(v)] = next[size_t(c)];
-          stack.push_back(c);
+    std::vector<int32_t> post;
+    {
+      std::vector<int32_t> head(static_cast<size_t>(n), -1), next(static_cast<size_t>(n), -1);
+      post.reserve(size_t(n));
+      for (int32_t v = n - 1; v >= 0; --v)
+        if (parent[size_t(v)] >= 0) {
+          next[size_t(v)] = head[size_t(parent[size_t(v)])];
+          head[size_t(parent[size_t(v)])] = v;
+        }
+      std::vector<int32_t> stack;
+      for (int32_t root = 0; root < n; ++root) {
+        if (parent[size_t(root)] != -1) continue;
+        stack.push_back(root);
+        while (!stack.empty()) {
+          const int32_t v = stack.back();
+          const int32_t c = head[size_t(v)];
+          if (c == -1) {
+            post.push_back(v);
+            stack.pop_back();
+          } else {
+            head[size_t(v)] = next[size_t(c)];
+            stack.push_back(c);
+          }
         }
       }
     }
-    // final order: position k holds M's row md[post[k]]
-    sy.perm.resize(size_t(n));
-    std::vector<int32_t> ip(static_cast<size_t>(n));
-    for (int32_t k = 0; k < n; ++k) {
-      sy.perm[size_t(k)] = md[size_t(post[size_t(k)])];
-      ip[size_t(sy.perm[size_t(k)])] = k;
+    // final order: position k holds the renumbered node ordf[k] = md[post[k]],
+    // the input node perm[k].  A postorder of the elimination tree is an
+    // equivalent order: the tree of the reordered matrix is the same tree,
+    // relabelled.
+    std::vector<int32_t> ordf(static_cast<size_t>(n)), ipf(static_cast<size_t>(n));
+    {
+      std::vector<int32_t> fpos(static_cast<size_t>(n)), par(static_cast<size_t>(n));
+      for (int32_t k = 0; k < n; ++k) fpos[size_t(post[size_t(k)])] = k;
+      for (int32_t k = 0; k < n; ++k) {
+        const int32_t p = parent[size_t(post[size_t(k)])];
+        par[size_t(k)] = p < 0 ? -1 : fpos[size_t(p)];
+        ordf[size_t(k)] = md[size_t(post[size_t(k)])];
+        ipf[size_t(ordf[size_t(k)])] = k;
+      }
+      parent.swap(par);
+      std::vector<int32_t> perm(static_cast<size_t>(n));
+      for (int32_t k = 0; k < n; ++k) perm[size_t(k)] = sy.perm[size_t(ordf[size_t(k)])];
+      sy.perm.swap(perm);
     }
-    lower_rows(ip, brp, bci);
-    etree(brp, bci, parent);
+    std::vector<int32_t> crp, cri;  // the lower triangle by columns
+    gather_rows(ordf, ipf, brp, bci, &crp, &cri);
+    std::vector<int32_t>().swap(gi);
 
     // --- column counts (row subtrees) -----------------------------------
     std::vector<int64_t> cnt(static_cast<size_t>(n), 0);
@@ -165,22 +226,21 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
       sy.sn_parent[size_t(s)] = p < 0 ? -1 : sn_of[size_t(p)];
     }
 
-    // --- row structures: own columns, the lower entries of B's columns in
-    // the supernode, and the children's rows below their columns
-    std::vector<int32_t> crp(static_cast<size_t>(n) + 1, 0), cri;  // lower B by columns
-    for (int32_t i = 0; i < n; ++i)
-      for (int32_t k = brp[size_t(i)]; k < brp[size_t(i) + 1]; ++k) crp[size_t(bci[size_t(k)]) + 1]++;
-    for (int32_t j = 0; j < n; ++j) crp[size_t(j) + 1] += crp[size_t(j)];
-    cri.resize(size_t(crp[size_t(n)]));
+    // --- children of each supernode (ascending) --------------------------
+    sy.kid_ptr.assign(size_t(ns) + 1, 0);
+    for (int32_t c = 0; c < ns; ++c)
+      if (sy.sn_parent[size_t(c)] >= 0) sy.kid_ptr[size_t(sy.sn_parent[size_t(c)]) + 1]++;
+    for (int32_t t = 0; t < ns; ++t) sy.kid_ptr[size_t(t) + 1] += sy.kid_ptr[size_t(t)];
+    sy.kid.resize(size_t(sy.kid_ptr[size_t(ns)]));
     {
-      std::vector<int32_t> nx(crp.begin(), crp.end() - 1);
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = brp[size_t(i)]; k < brp[size_t(i) + 1]; ++k)
-          cri[size_t(nx[size_t(bci[size_t(k)])]++)] = i;
+      std::vector<int32_t> nx(sy.kid_ptr.begin(), sy.kid_ptr.end() - 1);
+      for (int32_t c = 0; c < ns; ++c)
+        if (sy.sn_parent[size_t(c)] >= 0) sy.kid[size_t(nx[size_t(sy.sn_parent[size_t(c)])]++)] = c;
     }
-    std::vector<std::vector<int32_t>> kids(static_cast<size_t>(ns));
-    for (int32_t s = 0; s < ns; ++s)
-      if (sy.sn_parent[size_t(s)] >= 0) kids[size_t(sy.sn_parent[size_t(s)])].push_back(s);
+
+    // --- row structures: own columns, the lower entries of the reordered
+    // matrix's columns in the supernode, and the children's rows below
+    // their columns
     sy.sn_rowptr.assign(size_t(ns) + 1, 0);
     sy.rowidx.clear();
     std::fill(mark.begin(), mark.end(), -1);
@@ -200,7 +260,8 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
             rows.push_back(r);
           }
         }
-      for (const int32_t c : kids[size_t(s)]) {
+      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q) {
+        const int32_t c = sy.kid[size_t(q)];
         const int32_t wc = sy.sn_first[size_t(c) + 1] - sy.sn_first[size_t(c)];
         for (int32_t p = sy.sn_rowptr[size_t(c)] + wc; p < sy.sn_rowptr[size_t(c) + 1]; ++p) {
           const int32_t r = sy.rowidx[size_t(p)];
@@ -238,56 +299,56 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     }
 
     // --- assembly map: lower entry k of M -> its place in the blocks -----
-    // (entries grouped by their column in the order, then one supernode at a
-    // time with the positions of its rows in a scatter map)
+    // (entry (i, j) lands in column c = min(pos i, pos j) of its supernode, at
+    // row r = max(...): a row among the supernode's own columns directly, one
+    // below them by binary search; the input's rows visited in the order, in
+    // parallel slices)
     sy.amap.resize(size_t(nnz_low));
     {
-      std::vector<int32_t> cptr(size_t(n) + 1, 0), ck(static_cast<size_t>(nnz_low));
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
-          cptr[size_t(std::min(ip[size_t(i)], ip[size_t(ci[size_t(k)])])) + 1]++;
-      for (int32_t c = 0; c < n; ++c) cptr[size_t(c) + 1] += cptr[size_t(c)];
-      std::vector<int32_t> nx(cptr.begin(), cptr.end() - 1);
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
-          ck[size_t(nx[size_t(std::min(ip[size_t(i)], ip[size_t(ci[size_t(k)])]))]++)] = k;
-      std::vector<int32_t> rowpos(static_cast<size_t>(n), -1);
-      std::vector<int32_t> krow(static_cast<size_t>(nnz_low));  // entry k's row of M
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) krow[size_t(k)] = i;
-      for (int32_t s = 0; s < ns; ++s) {
-        const int32_t f = sy.sn_first[size_t(s)], l = sy.sn_first[size_t(s) + 1];
-        const int32_t* R = sy.rowidx.data() + sy.sn_rowptr[size_t(s)];
-        const int32_t h = sy.sn_rowptr[size_t(s) + 1] - sy.sn_rowptr[size_t(s)];
-        for (int32_t q = 0; q < h; ++q) rowpos[size_t(R[q])] = q;
-        for (int32_t c = f; c < l; ++c)
-          for (int32_t t = cptr[size_t(c)]; t < cptr[size_t(c) + 1]; ++t) {
-            const int32_t k = ck[size_t(t)];
-            const int32_t r = std::max(ip[size_t(krow[size_t(k)])], ip[size_t(ci[size_t(k)])]);
-            const int32_t pos = rowpos[size_t(r)];
-            if (pos < 0 || R[pos] != r) {
-              err = "symbolic phase: an entry of M_cond is missing from the factor's structure";
-              return ACOPF_E_INVALID_ARG;
+      std::vector<int32_t> ipin(static_cast<size_t>(n));  // input node -> position
+      for (int32_t k = 0; k < n; ++k) ipin[size_t(sy.perm[size_t(k)])] = k;
+      std::atomic<bool> missing{false};
+      auto slice = [&](int32_t a0, int32_t a1) {  // the input's rows at positions [a0, a1)
+        for (int32_t a = a0; a < a1; ++a) {
+          const int32_t i = sy.perm[size_t(a)];
+          for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
+            const int32_t b = ipin[size_t(ci[size_t(k)])];
+            const int32_t c = std::min(a, b), r = std::max(a, b), sn = sn_of[size_t(c)];
+            const int32_t f = sy.sn_first[size_t(sn)], w = sy.sn_first[size_t(sn) + 1] - f;
+            const int32_t* R = sy.rowidx.data() + sy.sn_rowptr[size_t(sn)];
+            const int32_t h = sy.sn_rowptr[size_t(sn) + 1] - sy.sn_rowptr[size_t(sn)];
+            int32_t pos = r - f;
+            if (pos >= w) {
+              pos = int32_t(std::lower_bound(R + w, R + h, r) - R);
+              if (pos == h || R[pos] != r) {
+                missing = true;
+                return;
+              }
             }
-            sy.amap[size_t(k)] = sy.sn_off[size_t(s)] + int64_t(c - f) * h + pos;
+            sy.amap[size_t(k)] = sy.sn_off[size_t(sn)] + int64_t(c - f) * h + pos;
           }
-        for (int32_t q = 0; q < h; ++q) rowpos[size_t(R[q])] = -1;
+        }
+      };
+      const int32_t nth = int32_t(std::min<int64_t>(kSymbolicThreads, 1 + nnz_low / 262144));
+      auto lo = [&](int32_t t) { return int32_t(int64_t(n) * t / nth); };
+      std::vector<std::thread> pool;
+      int32_t t = 1;
+      try {
+        for (; t < nth; ++t) pool.emplace_back(slice, lo(t), lo(t + 1));
+      } catch (const std::system_error&) {  // no thread: the slice runs here
+      }
+      for (int32_t u = t; u < nth; ++u) slice(lo(u), lo(u + 1));
+      slice(lo(0), lo(1));
+      for (auto& th : pool) th.join();
+      if (missing) {
+        err = "symbolic phase: an entry of M_cond is missing from the factor's structure";
+        return ACOPF_E_INVALID_ARG;
       }
     }
 
-    // --- multifrontal links: each supernode's children (ascending), the
-    // positions of a child's rows below its columns within its parent's rows,
-    // and the offsets of the update matrices (m x m, m = h - w) and vectors
-    sy.kid_ptr.assign(size_t(ns) + 1, 0);
-    for (int32_t c = 0; c < ns; ++c)
-      if (sy.sn_parent[size_t(c)] >= 0) sy.kid_ptr[size_t(sy.sn_parent[size_t(c)]) + 1]++;
-    for (int32_t t = 0; t < ns; ++t) sy.kid_ptr[size_t(t) + 1] += sy.kid_ptr[size_t(t)];
-    sy.kid.resize(size_t(sy.kid_ptr[size_t(ns)]));
-    {
-      std::vector<int32_t> nx(sy.kid_ptr.begin(), sy.kid_ptr.end() - 1);
-      for (int32_t c = 0; c < ns; ++c)
-        if (sy.sn_parent[size_t(c)] >= 0) sy.kid[size_t(nx[size_t(sy.sn_parent[size_t(c)])]++)] = c;
-    }
+    // --- multifrontal links: the positions of a child's rows below its
+    // columns within its parent's rows, and the offsets of the update
+    // matrices (m x m, m = h - w) and vectors
     sy.rel_off.assign(size_t(ns), 0);
     sy.u_off.assign(size_t(ns) + 1, 0);
     sy.z_off.assign(size_t(ns) + 1, 0);
