@@ -328,7 +328,8 @@ acopf_status acopf_chol_solve(acopf_chol* chol, const double* b, double* x, acop
  * n_levels, the depth of the supernodal tree; storage, the doubles of the
  * supernodal blocks; update_storage, the doubles of the children's update
  * matrices and vectors the multifrontal factorization and solves pass up
- * the tree; factor_tasks, the tasks of the factorization's task graph;
+ * the tree; factor_tasks, the tasks of the factorization's warp-task and
+ * block-task graphs;
  * factor_launches and solve_launches, the kernel launches of one
  * factorization and of one solve. */
 typedef struct {
@@ -354,8 +355,9 @@ acopf_status acopf_chol_permutation(const acopf_chol* chol, int32_t* perm);
  * group), the GPU clock (ns) when a block took it, when its dependencies
  * were met, when it finished, and the SM that ran it; enable == 0 frees the
  * buffer.  acopf_chol_get_trace copies the last run of graph `which` (0 the
- * factorization; the solves' block tasks: 1 forward, 2 backward; their
- * warp tasks: 3 forward, 4 backward) into `out` (HOST,
+ * factorization's block tasks; the solves' block tasks: 1 forward,
+ * 2 backward; their warp tasks: 3 forward, 4 backward; 5 the
+ * factorization's warp tasks) into `out` (HOST,
  * 6 * capacity int64; NULL when capacity is 0) and sets *n_tasks to the
  * graph's task count; tasks
  * beyond `capacity` are not copied.  Synchronises the device. */

@@ -781,8 +781,9 @@ class Chol:
         _check(_chol_set_trace(self._h, 1 if enable else 0), "acopf_chol_set_trace")
 
     def trace(self, which: int = 0) -> np.ndarray:
-        """The last run's trace of graph `which` (0 factorization; solve block
-        tasks 1 forward, 2 backward; solve warp tasks 3 forward, 4 backward):
+        """The last run's trace of graph `which` (0 factorization block tasks;
+        solve block tasks 1 forward, 2 backward; solve warp tasks 3 forward,
+        4 backward; 5 factorization warp tasks):
         one row per task, (kind word, argument, taken ns, ready ns, finished
         ns, SM)."""
         n = C.c_int64(0)

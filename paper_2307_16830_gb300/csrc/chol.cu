@@ -124,10 +124,10 @@ __device__ __forceinline__ unsigned sm_id() {
   return r;
 }
 
-// The persistent loop: take the next task, wait for its dependencies (warp
-// 0's lanes each watch some of them), run it with the whole block, publish
-// its flag (fence, then a release store); with a trace buffer, record the
-// task's times.
+// The persistent loop: take the next task, wait for its dependencies and
+// those in the other graph (warp 0's lanes each watch some of them), run it
+// with the whole block, publish its flag (fence, then a release store);
+// with a trace buffer, record the task's times.
 
 template <typename Run>
 __device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Run run) {
@@ -146,6 +146,11 @@ __device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Ru
       const int q1 = __ldg(g.dep_ptr + t + 1);
       for (int q = __ldg(g.dep_ptr + t) + int(threadIdx.x); q < q1 && ok; q += 32)
         ok = wait_done(g.done + __ldg(g.dep + q), abort);
+      if (g.xdep_ptr) {
+        const int x1 = __ldg(g.xdep_ptr + t + 1);
+        for (int q = __ldg(g.xdep_ptr + t) + int(threadIdx.x); q < x1 && ok; q += 32)
+          ok = wait_done(g.xdone + __ldg(g.xdep + q), abort);
+      }
       ok = __all_sync(0xffffffffu, ok);
       if (threadIdx.x == 0) s_ok = ok;
       __threadfence();
@@ -284,8 +289,6 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
                    (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
     const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
     const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
-    for (int i = tid; i < mc; i += NT) srel[i] = __ldg(rel + i);
-    group_sync<NT>();
     const int nl = mc * (mc + 1) / 2;
     int i = 0, j = 0;
     tri_advance(i, j, mc, tid);
@@ -298,6 +301,10 @@ __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict_
         jj[u] = j;
         v[u] = e0 + u * NT + tid < nl ? __ldcg(Uc + size_t(j) * mc + i) : 0.0;
         tri_advance(i, j, mc, NT);
+      }
+      if (e0 == 0) {  // the row map, staged while the first batch is in flight
+        for (int r = tid; r < mc; r += NT) srel[r] = __ldg(rel + r);
+        group_sync<NT>();
       }
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
@@ -455,49 +462,21 @@ __device__ void tile_asm(const CholDev& d, int s, int I, int J, double* smem) {
   tile_store(F, r0, nr, c0, nc, S);
 }
 
-// Cholesky of diagonal tile k of the panel (pivot test as in factor_panel).
-__device__ void tile_potrf(const CholDev& d, int s, int k, double tol, double* smem) {
-  const Front F(d, s);
-  int r0, n;
-  F.span(k, r0, n);
-  double* A = smem;
-  tile_load(F, r0, n, r0, n, A);
-  __syncthreads();
-  __shared__ double s_rinv;
-  for (int c = 0; c < n; ++c) {
-    if (threadIdx.x < 32) {  // the pivot: one warp's reciprocal square root
-      double p = A[c * T + c];
-      if (!(p > tol)) {
-        if (threadIdx.x == 0) atomicMin(d.bad, F.f + r0 + c);
-        p = 1.0;
-      }
-      const double rinv = rsqrt(p);
-      if (threadIdx.x == 0) {
-        s_rinv = rinv;
-        d.Dinv[F.f + r0 + c] = rinv;
-      }
-      __syncwarp();
-      if (threadIdx.x == 0) A[c * T + c] = p * rinv;
-    }
-    __syncthreads();
-    if (int(threadIdx.x) > c && int(threadIdx.x) < n) A[c * T + threadIdx.x] *= s_rinv;
-    __syncthreads();
-    // trailing lower triangle: column j = c + 1 + warp (+ kWarps ...), rows over the lanes
-    for (int j = c + 1 + int(threadIdx.x >> 5); j < n; j += kWarps) {
-      const int i = int(threadIdx.x & 31);
-      if (i >= j && i < n) A[j * T + i] -= A[c * T + i] * A[c * T + j];
-    }
-    __syncthreads();
-  }
-  tile_store(F, r0, n, r0, n, A);
-}
-
-// Tile (I, k) <- tile (I, k) L_kk^-T by four warps (one per sub-partition,
-// joined by a named barrier): a row of the tile per lane, column j held by
-// warp j mod 4 in registers.  Column c is scaled by its owner and shared;
-// every warp then subtracts its multiple from its later columns.
+// Tile (I, k) <- tile (I, k) L_kk^-T by four warps (one per sub-partition):
+// a row of the tile per lane, column j held by warp j mod 4 in registers.
+// Step c: every warp subtracts the solved column c's multiple from its later
+// columns; the owner of column c + 1 updates that column first, solves it
+// (times 1 / L_kk[c+1][c+1]) into the ring buffer c + 1 mod 4 and announces
+// it with a non-waiting arrival, the others wait for it (named barriers as
+// in tile_potrf below).
 constexpr int kTrsmWarps = 4;
 constexpr int kTrsmCols = T / kTrsmWarps;
+__device__ __forceinline__ void named_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(32 * kTrsmWarps) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(32 * kTrsmWarps) : "memory");
+}
 __device__ void tile_trsm(const CholDev& d, int s, int I, int k, double* smem) {
   if (threadIdx.x >= 32 * kTrsmWarps) return;
   const Front F(d, s);
@@ -506,7 +485,7 @@ __device__ void tile_trsm(const CholDev& d, int s, int I, int k, double* smem) {
   F.span(I, r0, nr);
   double* Ls = smem;               // L_kk, column-major
   double* rinv = smem + T * T;     // 1 / L_kk[c][c]
-  double* Xs = smem + T * T + T;   // the scaled column, two buffers
+  double* Xs = smem + T * T + T;   // the solved columns, a ring of four
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   {  // L_kk: a row per lane, the warp's columns
     const double* src = F.at(rk + lane, rk);
@@ -525,24 +504,36 @@ __device__ void tile_trsm(const CholDev& d, int s, int I, int k, double* smem) {
     const int c = wp + kTrsmWarps * u;
     b[u] = lane < nr && c < n ? __ldcg(src + c * ldb) : 0.0;
   }
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
+  named_sync(1);
   if (wp == 0 && lane < n) rinv[lane] = 1.0 / Ls[lane * T + lane];
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
+  named_sync(1);
+  if (wp == 0) {  // column 0 needs no update
+    b[0] *= rinv[0];
+    Xs[lane] = b[0];
+  }
+  named_sync(2);
 #pragma unroll
   for (int c = 0; c < T; ++c) {
     if (c < n) {
-      if (wp == (c % kTrsmWarps)) {
-        const double x = b[c / kTrsmWarps] * rinv[c];
-        b[c / kTrsmWarps] = x;
-        Xs[(c & 1) * T + lane] = x;
+      const double* X = Xs + (c & 3) * T;
+      const double xc = X[lane];
+      const bool producer = c + 1 < n && wp == (c + 1) % kTrsmWarps;
+      if (producer) {
+        const int u1 = (c + 1) / kTrsmWarps;  // (a constant: c is unrolled)
+#pragma unroll
+        for (int u = 0; u < kTrsmCols; ++u)
+          if (u == u1) {
+            b[u] = fma(-xc, Ls[c * T + c + 1], b[u]) * rinv[c + 1];
+            Xs[((c + 1) & 3) * T + lane] = b[u];
+          }
+        named_arrive(1 + (c & 1));
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * kTrsmWarps) : "memory");
-      const double xc = Xs[(c & 1) * T + lane];
 #pragma unroll
       for (int u = 0; u < kTrsmCols; ++u) {
         const int j = wp + kTrsmWarps * u;
-        if (j > c && j < n) b[u] = fma(-xc, Ls[c * T + j], b[u]);
+        if (j > c + 1 && j < n) b[u] = fma(-xc, Ls[c * T + j], b[u]);
       }
+      if (!producer) named_sync(1 + (c & 1));
     }
   }
   if (lane < nr) {
@@ -551,6 +542,83 @@ __device__ void tile_trsm(const CholDev& d, int s, int I, int k, double* smem) {
     for (int u = 0; u < kTrsmCols; ++u) {
       const int c = wp + kTrsmWarps * u;
       if (c < n) __stcg(dst + c * ldb, b[u]);
+    }
+  }
+}
+
+// Cholesky of diagonal tile k of the panel by four warps (one per
+// sub-partition; pivot test as in factor_panel): a row of the tile per
+// lane, column j held by warp j mod 4 in registers.  Step c: every warp
+// subtracts column c's multiple from its later columns.  The owner of column
+// c + 1 updates that column first, takes its pivot (reciprocal square root,
+// scaled column into the ring buffer c + 1 mod 4) and announces it with a
+// non-waiting arrival; the others wait for it at the step's barrier (named
+// barriers 1 and 2 alternate, so a warp that arrives early cannot be counted
+// in the previous step's barrier).  The chain of dependent work per column
+// is one update, one reciprocal square root and one barrier.
+__device__ void tile_potrf(const CholDev& d, int s, int k, double tol, double* smem) {
+  if (threadIdx.x >= 32 * kTrsmWarps) return;
+  const Front F(d, s);
+  int r0, n;
+  F.span(k, r0, n);
+  double* Xs = smem;  // the scaled columns, a ring of four
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const size_t ld = F.ld(r0);
+  double a[kTrsmCols];
+  {
+    const double* src = F.at(r0 + (lane < n ? lane : 0), r0);
+#pragma unroll
+    for (int u = 0; u < kTrsmCols; ++u) {
+      const int c = wp + kTrsmWarps * u;
+      a[u] = lane < n && c < n && c <= lane ? __ldcg(src + c * ld) : 0.0;
+    }
+  }
+  // column c's pivot by its owner (register a[u]): L[c][c] and L[i][c]
+  // (i > c) into a[u] and ring buffer c & 3
+  auto pivot = [&](int c, int u) {
+    double p = __shfl_sync(0xffffffffu, a[u], c);
+    if (!(p > tol)) {
+      if (lane == 0) atomicMin(d.bad, F.f + r0 + c);
+      p = 1.0;
+    }
+    const double rinv = rsqrt(p);
+    const double x = lane == c ? p * rinv : (lane > c ? a[u] * rinv : 0.0);
+    a[u] = x;
+    Xs[(c & 3) * T + lane] = x;
+    if (lane == 0) d.Dinv[F.f + r0 + c] = rinv;
+  };
+  if (wp == 0 && n > 0) pivot(0, 0);
+  named_sync(2);
+#pragma unroll
+  for (int c = 0; c < T; ++c) {
+    if (c < n) {
+      const double* X = Xs + (c & 3) * T;
+      const double xi = X[lane];
+      const bool producer = c + 1 < n && wp == (c + 1) % kTrsmWarps;
+      if (producer) {  // the next column, its pivot, the announcement
+        const int u1 = (c + 1) / kTrsmWarps;  // (a constant: c is unrolled)
+#pragma unroll
+        for (int u = 0; u < kTrsmCols; ++u)
+          if (u == u1) {
+            a[u] = fma(-xi, X[c + 1], a[u]);
+            pivot(c + 1, u);
+          }
+        named_arrive(1 + (c & 1));
+      }
+#pragma unroll
+      for (int u = 0; u < kTrsmCols; ++u) {
+        const int j = wp + kTrsmWarps * u;
+        if (j > c + 1 && j < n) a[u] = fma(-xi, X[j], a[u]);
+      }
+      if (!producer) named_sync(1 + (c & 1));
+    }
+  }
+  if (lane < n) {
+    double* dst = F.at(r0 + lane, r0);
+#pragma unroll
+    for (int u = 0; u < kTrsmCols; ++u) {
+      const int c = wp + kTrsmWarps * u;
+      if (c < n && c <= lane) __stcg(dst + c * ld, a[u]);
     }
   }
 }
@@ -976,39 +1044,33 @@ __global__ void __launch_bounds__(kThreads, 4) k_chol_backward_tasks(CholDev d, 
   task_loop(g, d.abort, [&](int4 tk) { backward_large(d, tk.y, x, sL, sv); });
 }
 
-// The solves' warp tasks: each warp takes the next small supernode of the
-// list, waits (bounded) for the tasks it depends on, solves it and sets its
-// flag; the same progress argument as task_loop, with warps for blocks.
-template <bool kForward>
-__global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTasks g,
-                                                                double* __restrict__ v) {
-  __shared__ double ws_all[kWarps * (kSmallPanel + kCholWarpRows)];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* ws = ws_all + warp * (kSmallPanel + kCholWarpRows);
+// Warp tasks: each warp takes the next task of the list, waits (bounded)
+// for the tasks it depends on, runs it and sets its flag; the same progress
+// argument as task_loop, with warps for blocks.
+template <typename Run>
+__device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abort, Run run) {
+  const int lane = threadIdx.x & 31;
   for (;;) {
     int t = 0;
     unsigned long long t0 = 0ull;
     if (lane == 0) {
-      t = ld_acquire(d.abort) ? g.n : atomicAdd(g.next, 1);
+      t = ld_acquire(abort) ? g.n : atomicAdd(g.next, 1);
       if (g.trace) t0 = gpu_clock_ns();
     }
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= g.n) return;
-    int ok = 1;
-    if (lane == 0) {
+    bool ok = true;  // the lanes watch the dependencies together
+    {
       const int q1 = __ldg(g.dep_ptr + t + 1);
-      for (int q = __ldg(g.dep_ptr + t); q < q1 && ok; ++q) ok = wait_done(g.done + __ldg(g.dep + q), d.abort);
+      for (int q = __ldg(g.dep_ptr + t) + lane; q < q1 && ok; q += 32)
+        ok = wait_done(g.done + __ldg(g.dep + q), abort);
       __threadfence();
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
+    ok = __all_sync(0xffffffffu, ok);
     if (!ok) return;
     const int4 tk = __ldg(g.task + t);
     const unsigned long long t1 = g.trace && lane == 0 ? gpu_clock_ns() : 0ull;
-    if constexpr (kForward)
-      forward_small(d, tk.y, lane, v, ws);
-    else
-      backward_small(d, tk.y, lane, v, ws);
+    run(tk);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
@@ -1025,6 +1087,40 @@ __global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTa
     }
   }
 }
+
+// The solves' warp tasks: one small supernode per warp.
+template <bool kForward>
+__global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTasks g,
+                                                                double* __restrict__ v) {
+  __shared__ double ws_all[kWarps * (kSmallPanel + kCholWarpRows)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* ws = ws_all + warp * (kSmallPanel + kCholWarpRows);
+  warp_task_loop(g, d.abort, [&](int4 tk) {
+    if constexpr (kForward)
+      forward_small(d, tk.y, lane, v, ws);
+    else
+      backward_small(d, tk.y, lane, v, ws);
+  });
+}
+
+// The factorization's warp tasks: one warp-small supernode per warp, staged
+// in the warp's slice of shared memory (kSmallStage doubles, then its row
+// map scratch).
+__global__ void __launch_bounds__(kThreads) k_chol_factor_warps(CholDev d, CholTasks g,
+                                                                 double tol) {
+  // the task kernel after this one may start now: its blocks take SMs as
+  // this kernel's blocks leave, and wait for this kernel's flags
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* ws = smem + warp * kSmallStage;
+  int* wr = reinterpret_cast<int*>(smem + kWarps * kSmallStage) + warp * kCholWarpRows;
+  warp_task_loop(g, d.abort,
+                 [&](int4 tk) { factor_staged<32>(d, tk.y, lane, tol, ws, wr); });
+}
+
+constexpr size_t kFactorWarpSmem =
+    size_t(kWarps) * kSmallStage * sizeof(double) + size_t(kWarps) * kCholWarpRows * sizeof(int);
 
 int grid_for(int64_t n, int threads) {
   return n > 0 ? int(std::min<int64_t>((n + threads - 1) / threads, 4096)) : 0;
@@ -1083,7 +1179,7 @@ size_t chol_task_smem_bytes() {
   return size_t(kStageDoubles) * sizeof(double) + size_t(kRelInts) * sizeof(int);
 }
 
-cudaError_t chol_task_setup(int* blocks_per_sm) {
+cudaError_t chol_task_setup(int* blocks_per_sm, int* warp_blocks_per_sm) {
   const size_t bytes = chol_task_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(k_chol_factor_tasks,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -1095,14 +1191,39 @@ cudaError_t chol_task_setup(int* blocks_per_sm) {
     e = cudaFuncSetAttribute(k_chol_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(chol_bottom_smem_bytes(kCholBottomStage)));
   if (e == cudaSuccess) *blocks_per_sm = std::min(per_sm, 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol_factor_warps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kFactorWarpSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_factor_warps, kThreads,
+                                                      kFactorWarpSmem);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess) *warp_blocks_per_sm = per_sm;
   return e;
 }
 
-cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
+cudaError_t launch_chol_factor_warps(const CholDev& d, const CholTasks& t, double tol, int blocks,
                                      cudaStream_t s) {
   if (t.n <= 0) return cudaSuccess;
-  k_chol_factor_tasks<<<std::min(blocks, t.n), kThreads, chol_task_smem_bytes(), s>>>(d, t, tol);
+  const int grid = std::min(blocks, (t.n + kWarps - 1) / kWarps);
+  k_chol_factor_warps<<<grid, kThreads, kFactorWarpSmem, s>>>(d, t, tol);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
+                                     bool early, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(std::min(blocks, t.n)));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = chol_task_smem_bytes();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = early ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_chol_factor_tasks, d, t, tol);
 }
 
 cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,

@@ -26,7 +26,9 @@ constexpr int kCholTile = 32;
 
 // One task graph on the device: tasks (x = kind | k << 8, y, z, w), their
 // dependencies in CSR form, a finished flag per task and the counter the
-// blocks take tasks from (both zeroed before each run).
+// blocks take tasks from (both zeroed before each run); optionally the
+// tasks of another graph each task also waits for (xdep, CSR, as indices
+// into that graph's flags xdone; xdep_ptr NULL: none).
 struct CholTasks {
   const int4* task;
   const int32_t* dep_ptr;
@@ -35,6 +37,9 @@ struct CholTasks {
   int32_t* next;
   long long* trace;  // NULL, or 6 words per task (kind, argument, taken, ready, finished, SM)
   int32_t n;
+  const int32_t* xdep_ptr;
+  const int32_t* xdep;
+  const int32_t* xdone;
 };
 
 // Device copies of the symbolic arrays (see symbolic.h, chol_plan.h) and
@@ -85,17 +90,25 @@ cudaError_t launch_chol_bottom_bwd(const CholDev& d, const int32_t* list, int co
                                    cudaStream_t s);
 // Dynamic shared memory of the task kernels, and the opt-in that lets them
 // use it (set once per device, before any launch or capture); blocks per SM
-// the kernels are launched with.
+// the block-task and the factorization's warp-task kernels are launched
+// with.
 size_t chol_task_smem_bytes();
-cudaError_t chol_task_setup(int* blocks_per_sm);
+cudaError_t chol_task_setup(int* blocks_per_sm, int* warp_blocks_per_sm);
 // The factorization, forward and backward solve task kernels with `blocks`
 // persistent blocks (tasks, done flags and counter as described above).
+// `early`: the factorization's task kernel is launched as a programmatic
+// dependent of the warp-task kernel before it, whose flags its tasks wait
+// for (xdep).
 cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
-                                     cudaStream_t s);
+                                     bool early, cudaStream_t s);
 cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,
                                       cudaStream_t s);
 cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
                                        cudaStream_t s);
+// The factorization's warp tasks (one warp-small supernode per warp, after
+// the bottom levels and before the block-task kernel) with `blocks` blocks.
+cudaError_t launch_chol_factor_warps(const CholDev& d, const CholTasks& t, double tol, int blocks,
+                                     cudaStream_t s);
 // The solves' warp tasks (one small supernode per warp) with `blocks` blocks.
 cudaError_t launch_chol_solve_warps(const CholDev& d, const CholTasks& t, double* v, bool forward,
                                     int blocks, cudaStream_t s);

@@ -34,7 +34,8 @@ struct Builder {
 // on `workers` concurrent workers; fills g and the estimates.
 void schedule(const std::vector<int32_t>& task, const std::vector<std::vector<int32_t>>& deps,
               const std::vector<double>& dur, int32_t workers, CholGraph& g, double* makespan,
-              double* critical, double* crit_by_kind = nullptr) {
+              double* critical, double* crit_by_kind = nullptr,
+              const std::vector<std::vector<int32_t>>* xdeps = nullptr) {
   const int32_t nt = int32_t(dur.size());
   std::vector<std::vector<int32_t>> succ(static_cast<size_t>(nt));
   std::vector<int32_t> indeg(static_cast<size_t>(nt), 0);
@@ -101,6 +102,8 @@ void schedule(const std::vector<int32_t>& task, const std::vector<std::vector<in
   g.task.resize(size_t(nt) * 4);
   g.dep_ptr.assign(size_t(nt) + 1, 0);
   g.dep.clear();
+  g.xdep_ptr.assign(size_t(nt) + 1, 0);
+  g.xdep.clear();
   for (int32_t k = 0; k < nt; ++k) {
     const int32_t t = order[size_t(k)];
     std::copy(task.begin() + 4 * t, task.begin() + 4 * t + 4, g.task.begin() + 4 * k);
@@ -110,6 +113,13 @@ void schedule(const std::vector<int32_t>& task, const std::vector<std::vector<in
     ds.erase(std::unique(ds.begin(), ds.end()), ds.end());
     g.dep.insert(g.dep.end(), ds.begin(), ds.end());
     g.dep_ptr[size_t(k) + 1] = int32_t(g.dep.size());
+    if (xdeps) {
+      ds = (*xdeps)[size_t(t)];
+      std::sort(ds.begin(), ds.end());
+      ds.erase(std::unique(ds.begin(), ds.end()), ds.end());
+      g.xdep.insert(g.xdep.end(), ds.begin(), ds.end());
+    }
+    g.xdep_ptr[size_t(k) + 1] = int32_t(g.xdep.size());
   }
   if (makespan) *makespan = now;
   if (critical) *critical = crit;
@@ -200,6 +210,8 @@ bool schedule_forest(const std::vector<int32_t>& task, const std::vector<int32_t
   g.dep_ptr.assign(size_t(nt) + 1, 0);
   g.dep.clear();
   g.dep.reserve(size_t(kp[size_t(nt)]));
+  g.xdep_ptr.assign(size_t(nt) + 1, 0);
+  g.xdep.clear();
   for (int32_t k = 0; k < nt; ++k) {
     const int32_t t = order[size_t(k)];
     std::copy(task.begin() + 4 * t, task.begin() + 4 * t + 4, g.task.begin() + 4 * k);
@@ -297,7 +309,23 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
                                   std::make_pair(W[size_t(b)], H[size_t(b)]);
                          });
     }
-    const auto small = [&](int32_t s) { return plan.sn_class[size_t(s)] == kSnSmall; };
+    // --- warp-small supernodes: small ones whose descendants are all small
+    // or bottom supernodes; the factorization's warp tasks (before the task
+    // kernel) and the solves' warp tasks
+    std::vector<char> wsmall(static_cast<size_t>(ns), 0);
+    for (int32_t s = 0; s < ns; ++s) {
+      if (plan.sn_class[size_t(s)] != kSnSmall) continue;
+      bool ok = true;
+      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1] && ok; ++q) {
+        const int32_t k = sy.kid[size_t(q)];
+        ok = wsmall[size_t(k)] || plan.sn_class[size_t(k)] == kSnBottom;
+      }
+      wsmall[size_t(s)] = ok;
+    }
+    // the other small supernodes go into group tasks
+    const auto small = [&](int32_t s) {
+      return plan.sn_class[size_t(s)] == kSnSmall && !wsmall[size_t(s)];
+    };
     // --- groups: cut the small forest into connected sets of bounded work ---
     std::vector<double> open_cost(static_cast<size_t>(ns), 0.0);
     std::vector<int32_t> open_cnt(static_cast<size_t>(ns), 0);
@@ -393,9 +421,39 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
       grp_us[size_t(g)] = us;
       grp_solve_us[size_t(g)] = 1.0 + 1.5 * nlv;
     }
+    // --- the warp tasks: both directions ordered by a list schedule on the
+    // warps; wpos: a warp-small supernode's position in the forward list
+    std::vector<int32_t> widx(static_cast<size_t>(ns), -1), wsn;
+    for (int32_t s = 0; s < ns; ++s)
+      if (wsmall[size_t(s)]) {
+        widx[size_t(s)] = int32_t(wsn.size());
+        wsn.push_back(s);
+      }
+    const int32_t nw = int32_t(wsn.size());
+    {
+      std::vector<int32_t> wtask(size_t(nw) * 4), wup(static_cast<size_t>(nw));
+      for (int32_t k = 0; k < nw; ++k) {
+        const int32_t s = wsn[size_t(k)], p = sy.sn_parent[size_t(s)];
+        wtask[4 * size_t(k)] = kTaskBlock;
+        wtask[4 * size_t(k) + 1] = s;
+        wtask[4 * size_t(k) + 2] = wtask[4 * size_t(k) + 3] = 0;
+        wup[size_t(k)] = p >= 0 ? widx[size_t(p)] : -1;
+      }
+      if (!schedule_forest(wtask, wup, true, prm.warps, plan.forward_warp) ||
+          !schedule_forest(wtask, wup, false, prm.warps, plan.backward_warp)) {
+        err = "task plan: the supernodal tree is not a forest in postorder";
+        return ACOPF_E_INVALID_ARG;
+      }
+    }
+    std::vector<int32_t> wpos(static_cast<size_t>(ns), -1);
+    for (int32_t k = 0; k < nw; ++k) wpos[size_t(plan.forward_warp.task[4 * size_t(k) + 1])] = k;
     // --- the factorization's tasks -------------------------------------------
     Builder B;
-    std::vector<std::vector<int32_t>> deps;
+    std::vector<std::vector<int32_t>> deps, xdeps;  // xdeps: warp tasks (wpos)
+    auto xd = [&](int32_t t) -> std::vector<int32_t>& {  // task t's warp tasks
+      if (int32_t(xdeps.size()) <= t) xdeps.resize(size_t(t) + 1);
+      return xdeps[size_t(t)];
+    };
     std::vector<int32_t> comp(static_cast<size_t>(ns), -1);
     std::vector<int32_t> grp_task(static_cast<size_t>(ng));
     for (int32_t g = 0; g < ng; ++g) {
@@ -404,9 +462,13 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
     }
     for (int32_t s = 0; s < ns; ++s)
       if (grp[size_t(s)] >= 0) comp[size_t(s)] = grp_task[size_t(grp[size_t(s)])];
-    auto child_comps = [&](int32_t s, std::vector<int32_t>& out) {  // bottom children: done before
+    auto child_comps = [&](int32_t s, std::vector<int32_t>& out) {  // bottom: done before
       for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q)
         if (comp[size_t(sy.kid[size_t(q)])] >= 0) out.push_back(comp[size_t(sy.kid[size_t(q)])]);
+    };
+    auto child_warps = [&](int32_t s, std::vector<int32_t>& out) {
+      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q)
+        if (wpos[size_t(sy.kid[size_t(q)])] >= 0) out.push_back(wpos[size_t(sy.kid[size_t(q)])]);
     };
     const double ut = double(T) * T * T;
     plan.brk_off.assign(static_cast<size_t>(ns), 0);
@@ -418,6 +480,7 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
         comp[size_t(s)] = B.add(kTaskBlock, s, 0, 0, 3.0 + cost[size_t(s)] / 2000.0);
         deps.emplace_back();
         child_comps(s, deps.back());
+        child_warps(s, xd(comp[size_t(s)]));
         continue;
       }
       const int32_t w = W[size_t(s)], m = H[size_t(s)] - w;
@@ -434,13 +497,15 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
       }
       std::vector<int32_t> last(size_t(nb) * size_t(nb), -1);
       auto L = [&](int32_t i, int32_t j) -> int32_t& { return last[size_t(i) * size_t(nb) + size_t(j)]; };
-      std::vector<int32_t> kc;
+      std::vector<int32_t> kc, kw;
       child_comps(s, kc);
+      child_warps(s, kw);
       if (has_kids)
         for (int32_t i = 0; i < nb; ++i)
           for (int32_t j = 0; j <= i; ++j) {
             L(i, j) = B.add(kTaskAsm, s, i, j, 2.0);
             deps.push_back(kc);
+            xd(L(i, j)) = kw;
           }
       std::vector<int32_t> trsm(static_cast<size_t>(nb), -1);
       for (int32_t k = 0; k < nbp; ++k) {
@@ -484,47 +549,17 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
           const int32_t k = sy.kid[size_t(q)];
           if (grp[size_t(k)] != g && comp[size_t(k)] >= 0) d.push_back(comp[size_t(k)]);
         }
+        child_warps(s, xd(grp_task[size_t(g)]));
       }
     }
+    xdeps.resize(deps.size());
     schedule(B.task, deps, B.dur, prm.workers, plan.factor, &plan.est_factor_us,
-             &plan.est_critical_us, plan.est_critical_by_kind);
+             &plan.est_critical_us, plan.est_critical_by_kind, &xdeps);
     // --- the solves -------------------------------------------------------------
-    // Warp tasks: small supernodes whose descendants are all small (or
-    // bottom), one task each, in ascending (forward) or descending
-    // (backward) order; the rest are block tasks, run after the warp tasks
-    // in the forward solve and before them in the backward solve.
-    std::vector<char> wsmall(static_cast<size_t>(ns), 0);
-    for (int32_t s = 0; s < ns; ++s) {
-      if (plan.sn_class[size_t(s)] != kSnSmall) continue;
-      bool ok = true;
-      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1] && ok; ++q) {
-        const int32_t k = sy.kid[size_t(q)];
-        ok = wsmall[size_t(k)] || plan.sn_class[size_t(k)] == kSnBottom;
-      }
-      wsmall[size_t(s)] = ok;
-    }
-    std::vector<int32_t> widx(static_cast<size_t>(ns), -1), wsn;
-    for (int32_t s = 0; s < ns; ++s)
-      if (wsmall[size_t(s)]) {
-        widx[size_t(s)] = int32_t(wsn.size());
-        wsn.push_back(s);
-      }
-    const int32_t nw = int32_t(wsn.size());
-    {  // both directions ordered by a list schedule on the warps
-      std::vector<int32_t> wtask(size_t(nw) * 4), wup(static_cast<size_t>(nw));
-      for (int32_t k = 0; k < nw; ++k) {
-        const int32_t s = wsn[size_t(k)], p = sy.sn_parent[size_t(s)];
-        wtask[4 * size_t(k)] = kTaskBlock;
-        wtask[4 * size_t(k) + 1] = s;
-        wtask[4 * size_t(k) + 2] = wtask[4 * size_t(k) + 3] = 0;
-        wup[size_t(k)] = p >= 0 ? widx[size_t(p)] : -1;
-      }
-      if (!schedule_forest(wtask, wup, true, prm.warps, plan.forward_warp) ||
-          !schedule_forest(wtask, wup, false, prm.warps, plan.backward_warp)) {
-        err = "task plan: the supernodal tree is not a forest in postorder";
-        return ACOPF_E_INVALID_ARG;
-      }
-    }
+    // Warp tasks: the warp-small supernodes, one task each, in ascending
+    // (forward) or descending (backward) order; the rest are block tasks, run
+    // after the warp tasks in the forward solve and before them in the
+    // backward solve.
     Builder F;
     std::vector<int32_t> fcomp(static_cast<size_t>(ns), -1);
     for (int32_t s = 0; s < ns; ++s)

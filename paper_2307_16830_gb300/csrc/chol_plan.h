@@ -16,8 +16,13 @@
 //           it times the inverse transpose of that factor), upd (one tile
 //           minus the product of two trsm tiles) and fin (no work; done
 //           once the supernode's update matrix is complete).
-// The solves take the small supernodes whose subtrees hold only small
-// supernodes one per warp, and the others one per block.
+// The small supernodes whose descendants are all small or bottom ones
+// (warp-small) are factored by a kernel of warp tasks, one supernode per
+// warp, in the forward solve's warp list (the same dependencies: children
+// first), launched before the task kernel, which may start while it runs:
+// a task that needs a warp-small child waits for that warp task's flag.
+// The group tasks hold the other small supernodes.  The solves take the warp-small supernodes one per warp and
+// the others (but the bottom ones) one per block.
 #pragma once
 
 #include <cstdint>
@@ -69,9 +74,11 @@ constexpr int32_t kCholBlockMaxRows = 512;
 // supernode, b = tile row, c = tile column; potrf: a = supernode, b = c =
 // k; upd: a = supernode, b = tile row, c = tile column, k the panel tile
 // column of the product), its dependencies dep[dep_ptr[t] .. dep_ptr[t+1])
-// (all earlier in the list).
+// (all earlier in the list) and, for the factorization's block tasks, the
+// warp tasks it needs xdep[xdep_ptr[t] .. xdep_ptr[t+1]) (positions in
+// forward_warp's list; empty otherwise).
 struct CholGraph {
-  std::vector<int32_t> task, dep_ptr, dep;
+  std::vector<int32_t> task, dep_ptr, dep, xdep_ptr, xdep;
   int32_t n_tasks() const { return int32_t(task.size() / 4); }
 };
 
@@ -89,9 +96,10 @@ struct CholPlan {
   std::vector<int8_t> sn_class;
   std::vector<int32_t> bot_ptr, bot_sn, bot_stage, brk_off, tile_brk;
   std::vector<int32_t> grp_ptr, grp_sn, grp_lptr, grp_lev;
-  // factorization; solves: warp tasks (forward_warp, backward_warp: one
-  // small supernode each, every dependency earlier in the list) and block
-  // tasks (forward, backward: the other supernodes)
+  // factorization's task kernel; warp tasks (forward_warp, backward_warp:
+  // one warp-small supernode each, every dependency earlier in the list;
+  // forward_warp also orders the factorization's warp tasks) and block
+  // tasks of the solves (forward, backward: the other supernodes)
   CholGraph factor, forward, backward, forward_warp, backward_warp;
   // the list schedule's estimates: makespan, critical path, and the
   // critical path's time by task kind
@@ -102,9 +110,9 @@ struct CholPlan {
 struct CholPlanParams {
   double group_fma = 20000.0;  // work of one group task at most
   int32_t group_members = 64;
-  double tile_fma = 150000.0;  // supernodes above this work are tiled
+  double tile_fma = 60000.0;  // supernodes above this work are tiled
   int32_t workers = 304;       // concurrent blocks the list schedule assumes
-  int32_t warps = 4864;        // concurrent warps of the solves' warp tasks
+  int32_t warps = 4864;        // concurrent warps of the warp tasks
 };
 
 // Builds the plan for the symbolic factorization sy (its supernodes, row

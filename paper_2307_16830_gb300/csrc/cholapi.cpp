@@ -50,19 +50,21 @@ struct acopf_chol {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   acopf::CholDev dev{};
-  // the task graphs: factorization, forward warp tasks, forward block tasks,
-  // backward block tasks, backward warp tasks (flags and counters in this
-  // order, the four of the solves adjacent)
-  acopf::CholTasks tg[5] = {};
-  int32_t* flags = nullptr;             // the three graphs' done flags and counters
+  // the task graphs: factorization (block tasks), forward warp tasks,
+  // forward block tasks, backward block tasks, backward warp tasks, the
+  // factorization's warp tasks (the forward warp list with flags of its
+  // own); flags and counters in the order 0, 5, 1, 2, 3, 4, the four of the
+  // solves adjacent
+  acopf::CholTasks tg[6] = {};
+  int32_t* flags = nullptr;             // the graphs' done flags and counters
   size_t flag_ints = 0;
-  int blocks = 0, solve_blocks = 0;     // persistent blocks of the task kernels
+  int blocks = 0, warp_blocks = 0, solve_blocks = 0;  // persistent blocks of the task kernels
   const int64_t* amap = nullptr;
   const int32_t* perm = nullptr;
   double* work = nullptr;       // n: the permuted right-hand side / solution
   size_t u_doubles = 0, z_doubles = 0;  // update matrices / vectors
   int32_t* status_host = nullptr;       // page-locked copy of {bad, abort}
-  long long* trace = nullptr;           // task trace of the three graphs (NULL: off)
+  long long* trace = nullptr;           // task trace of the graphs (NULL: off)
   bool factored = false;
   // the factorization's and the solve's launch sequences, captured as CUDA
   // graphs for the last arguments they ran with
@@ -101,8 +103,8 @@ acopf_status check_model(const acopf_model* model, const char* where) {
 // bottom levels, permutation back).
 void plan_stats(const acopf::CholPlan& plan, acopf_chol_stats& st) {
   const int64_t nbl = int64_t(plan.bot_ptr.size()) - 1;
-  st.factor_tasks = plan.factor.n_tasks();
-  st.factor_launches = 2 + nbl;
+  st.factor_tasks = plan.factor.n_tasks() + plan.forward_warp.n_tasks();
+  st.factor_launches = 3 + nbl;
   st.solve_launches = 6 + 2 * nbl;
 }
 
@@ -115,22 +117,26 @@ acopf_status run_symbolic(const acopf_model* model, acopf::CholSymbolic& sy, con
 }
 
 // The factorization's device work: zeroed blocks, update matrices, flags
-// and counter, the pivot marker, the assembly of M_cond's values, then the
-// task kernel.
+// and counters, the pivot marker, the assembly of M_cond's values, the
+// bottom levels, the warp tasks, then the block-task kernel.
 cudaError_t record_factor(const acopf_chol* chol, const double* kvals, double tol,
                           cudaStream_t s) {
   const acopf::CholDev& d = chol->dev;
   cudaError_t e = cudaMemsetAsync(d.Lx, 0, size_t(chol->stats.storage) * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.Ux, 0, chol->u_doubles * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.bad, 0x7f, sizeof(int32_t), s);  // 0x7f7f7f7f: none
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(chol->tg[0].done, 0, (size_t(chol->tg[0].n) + 1) * sizeof(int32_t), s);
+  if (e == cudaSuccess)  // graphs 0 and 5: adjacent
+    e = cudaMemsetAsync(chol->tg[0].done, 0,
+                        (size_t(chol->tg[0].n) + size_t(chol->tg[5].n) + 2) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = acopf::launch_chol_assemble(d.Lx, chol->amap, kvals, chol->nnz_low, s);
   const std::vector<int32_t>& bp = chol->bot_ptr;
   for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
     e = acopf::launch_chol_bottom(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->bot_stage[v],
                                   tol, s);
-  if (e == cudaSuccess) e = acopf::launch_chol_factor_tasks(d, chol->tg[0], tol, chol->blocks, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_factor_warps(d, chol->tg[5], tol, chol->warp_blocks, s);
+  if (e == cudaSuccess)
+    e = acopf::launch_chol_factor_tasks(d, chol->tg[0], tol, chol->blocks, chol->tg[5].n > 0, s);
   return e;
 }
 
@@ -267,8 +273,10 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     o_dptr[k] = p.take<int32_t>(graphs[k]->dep_ptr.size());
     o_dep[k] = p.take<int32_t>(graphs[k]->dep.size() + 1);
   }
+  const size_t o_xptr = p.take<int32_t>(plan.factor.xdep_ptr.size());
+  const size_t o_xdep = p.take<int32_t>(plan.factor.xdep.size() + 1);
   // done flags and counters: per graph [its n flags, its counter]
-  c->flag_ints = 0;
+  c->flag_ints = size_t(plan.forward_warp.n_tasks()) + 1;  // graph 5
   for (int k = 0; k < 5; ++k) c->flag_ints += size_t(graphs[k]->n_tasks()) + 1;
   const size_t o_flags = p.take<int32_t>(c->flag_ints);
   const size_t o_amap = p.take<int64_t>(sy.amap.size()), o_perm = p.take<int32_t>(n);
@@ -314,18 +322,21 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
     up(o_dep[k], graphs[k]->dep.data(), graphs[k]->dep.size() * 4);
   }
+  up(o_xptr, plan.factor.xdep_ptr.data(), plan.factor.xdep_ptr.size() * 4);
+  up(o_xdep, plan.factor.xdep.data(), plan.factor.xdep.size() * 4);
   up(o_amap, sy.amap.data(), sy.amap.size() * 8);
   up(o_perm, sy.perm.data(), n * 4);
   if (e == cudaSuccess) e = cudaMemset(base + o_status, 0, 2 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&c->status_host, 2 * sizeof(int32_t));
-  int per_sm = 0, sms = 0;
-  if (e == cudaSuccess) e = acopf::chol_task_setup(&per_sm);
+  int per_sm = 0, warp_per_sm = 0, sms = 0;
+  if (e == cudaSuccess) e = acopf::chol_task_setup(&per_sm, &warp_per_sm);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, model->device);
   if (e != cudaSuccess) {
     release(c);
     return cuda_fail(e, "acopf_chol_create: upload");
   }
   c->blocks = per_sm * sms;
+  c->warp_blocks = warp_per_sm * sms;
   c->solve_blocks = 4 * sms;
   acopf::CholDev& d = c->dev;
   d.n = sy.n;
@@ -353,16 +364,21 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.abort = d.bad + 1;
   c->flags = reinterpret_cast<int32_t*>(base + o_flags);
   int32_t* fl = c->flags;
-  acopf::CholTasks* tk[5] = {&c->tg[0], &c->tg[1], &c->tg[2], &c->tg[3], &c->tg[4]};
-  for (int k = 0; k < 5; ++k) {
-    tk[k]->task = reinterpret_cast<const int4*>(base + o_task[k]);
-    tk[k]->dep_ptr = reinterpret_cast<const int32_t*>(base + o_dptr[k]);
-    tk[k]->dep = reinterpret_cast<const int32_t*>(base + o_dep[k]);
-    tk[k]->n = graphs[k]->n_tasks();
-    tk[k]->done = fl;
-    tk[k]->next = fl + tk[k]->n;
-    fl += tk[k]->n + 1;
+  for (const int k : {0, 5, 1, 2, 3, 4}) {
+    acopf::CholTasks& t = c->tg[k];
+    const int src = k == 5 ? 1 : k;  // graph 5 runs graph 1's list
+    t.task = reinterpret_cast<const int4*>(base + o_task[src]);
+    t.dep_ptr = reinterpret_cast<const int32_t*>(base + o_dptr[src]);
+    t.dep = reinterpret_cast<const int32_t*>(base + o_dep[src]);
+    t.n = graphs[src]->n_tasks();
+    t.done = fl;
+    t.next = fl + t.n;
+    fl += t.n + 1;
   }
+  // the factorization's block tasks also wait for its warp tasks
+  c->tg[0].xdep_ptr = reinterpret_cast<const int32_t*>(base + o_xptr);
+  c->tg[0].xdep = reinterpret_cast<const int32_t*>(base + o_xdep);
+  c->tg[0].xdone = c->tg[5].done;
   c->bot_sn = reinterpret_cast<const int32_t*>(base + o_bot);
   c->amap = reinterpret_cast<const int64_t*>(base + o_amap);
   c->perm = reinterpret_cast<const int32_t*>(base + o_perm);
@@ -442,7 +458,8 @@ acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable) {
   if (ds.error() != cudaSuccess) return cuda_fail(ds.error(), "acopf_chol_set_trace");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "acopf_chol_set_trace");
-  acopf::CholTasks* tk[5] = {&chol->tg[0], &chol->tg[1], &chol->tg[2], &chol->tg[3], &chol->tg[4]};
+  acopf::CholTasks* tk[6] = {&chol->tg[0], &chol->tg[1], &chol->tg[2],
+                             &chol->tg[3], &chol->tg[4], &chol->tg[5]};
   if (chol->trace) {
     cudaFree(chol->trace);
     chol->trace = nullptr;
@@ -474,10 +491,10 @@ acopf_status acopf_chol_set_trace(acopf_chol* chol, int32_t enable) {
 
 acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out, int64_t capacity,
                                   int64_t* n_tasks) {
-  if (!chol || !n_tasks || which < 0 || which > 4 || capacity < 0 || (!out && capacity > 0))
+  if (!chol || !n_tasks || which < 0 || which > 5 || capacity < 0 || (!out && capacity > 0))
     return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: bad argument");
-  const acopf::CholTasks* tk[5] = {&chol->tg[0], &chol->tg[2], &chol->tg[3], &chol->tg[1],
-                                   &chol->tg[4]};
+  const acopf::CholTasks* tk[6] = {&chol->tg[0], &chol->tg[2], &chol->tg[3],
+                                   &chol->tg[1], &chol->tg[4], &chol->tg[5]};
   *n_tasks = tk[which]->n;
   if (!tk[which]->trace) return fail(ACOPF_E_INVALID_ARG, "acopf_chol_get_trace: trace is off");
   DeviceScope ds(chol->model->device);
