@@ -22,6 +22,11 @@ namespace {
 
 // Host threads of the parallel passes.
 constexpr int32_t kSymbolicThreads = 8;
+// Relaxed supernodes: a merge that stays within kRelaxSmallCols columns and
+// kRelaxSmallRows rows may carry up to kRelaxSmallZeros of its entries as
+// explicit zeros, any other up to kRelaxZeros.
+constexpr int32_t kRelaxSmallCols = 8, kRelaxSmallRows = 32;
+constexpr double kRelaxSmallZeros = 0.3, kRelaxZeros = 0.05;
 
 }  // namespace
 
@@ -212,6 +217,46 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
                         cnt[size_t(j) - 1] == cnt[size_t(j)] + 1 &&
                         j - sy.sn_first.back() < kMaxSupernodeWidth;
       if (!join) sy.sn_first.push_back(j);
+    }
+    // --- relaxed supernodes: a supernode absorbs the child whose columns end
+    // where its own begin when the merged supernode stays within
+    // kMaxSupernodeWidth columns and the explicit zeros it carries (rows of
+    // the parent's structure missing from the child's columns) are few
+    // enough for its size class.  The merged columns' rows are the child's
+    // columns then the parent's rows; the zeros stay exactly zero in the
+    // numeric factorization.
+    {
+      const int32_t nf = int32_t(sy.sn_first.size());
+      sy.sn_first.push_back(n);
+      std::vector<int32_t> mfirst(static_cast<size_t>(nf)), mw(static_cast<size_t>(nf)),
+          mh(static_cast<size_t>(nf));
+      std::vector<int64_t> mz(static_cast<size_t>(nf), 0);
+      std::vector<char> absorbed(static_cast<size_t>(nf), 0);
+      for (int32_t t = 0; t < nf; ++t) {
+        const int32_t f = sy.sn_first[size_t(t)], w = sy.sn_first[size_t(t) + 1] - f;
+        const int32_t h = int32_t(cnt[size_t(f)]) + 1;
+        mfirst[size_t(t)] = f;
+        mw[size_t(t)] = w;
+        mh[size_t(t)] = h;
+        if (t == 0 || parent[size_t(f) - 1] < f || parent[size_t(f) - 1] >= f + w) continue;
+        const int32_t c = t - 1;  // the child ending at column f
+        const int64_t W = mw[size_t(c)] + w, H = mw[size_t(c)] + h;
+        const int64_t z = mz[size_t(c)] + int64_t(mw[size_t(c)]) * (H - mh[size_t(c)]);
+        const double frac = double(z) / double(W * H - W * (W - 1) / 2);
+        const bool ok = W <= kMaxSupernodeWidth &&
+                        ((W <= kRelaxSmallCols && H <= kRelaxSmallRows && frac <= kRelaxSmallZeros) ||
+                         frac <= kRelaxZeros);
+        if (!ok) continue;
+        absorbed[size_t(c)] = 1;
+        mfirst[size_t(t)] = mfirst[size_t(c)];
+        mw[size_t(t)] = int32_t(W);
+        mh[size_t(t)] = int32_t(H);
+        mz[size_t(t)] = z;
+      }
+      std::vector<int32_t> first;
+      for (int32_t t = 0; t < nf; ++t)
+        if (!absorbed[size_t(t)]) first.push_back(mfirst[size_t(t)]);
+      sy.sn_first.swap(first);
     }
     sy.ns = int32_t(sy.sn_first.size());
     sy.sn_first.push_back(n);
