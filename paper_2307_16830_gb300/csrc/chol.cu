@@ -53,7 +53,6 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kStageDoubles =
     cmax(cmax(kWarps * kSmallStage, kCholBlockDoubles), cmax(3 * T * T + T, kCholMaxWidth * (kCholMaxWidth + 1)));
 constexpr int kRelInts = cmax(kWarps * kCholWarpRows, kCholBlockRows);
-constexpr int kSolveDoubles = kCholMaxWidth * (kCholMaxWidth + 1);
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------
@@ -930,8 +929,10 @@ __device__ void forward_small(const CholDev& d, int t, int lane, double* __restr
   __syncwarp();  // the slice is reused by the warp's next supernode
 }
 
-// The same by a whole block, the diagonal block and y_t staged in shared
-// memory and the triangular solve done by the first warp.
+// The same by a whole block for a supernode whose update vector exceeds the
+// staged solves' capacity (below): the diagonal block and y_t staged in
+// shared memory, the triangular solve done by the first warp, the update
+// vector accumulated in global memory.
 __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
                               double* __restrict__ sL, double* __restrict__ sy) {
   const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
@@ -1032,16 +1033,208 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
   for (int k = threadIdx.x; k < w; k += kThreads) __stcg(x + f + k, sx[k]);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_chol_forward_tasks(CholDev d, CholTasks g,
-                                                                     double* __restrict__ y) {
-  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
-  task_loop(g, d.abort, [&](int4 tk) { forward_large(d, tk.y, y, sL, sv); });
+// Staged block-task solves: a supernode whose update vector fits
+// kSolveZCap doubles keeps its whole front in shared memory (the diagonal
+// block, its reciprocal pivots, y_t or x_t, the update vector or the
+// gathered solution below), the diagonal block is solved by warp 0 in
+// registers (rows lane and lane + 32) with shuffles, and every vector is
+// read and written in global memory once.
+constexpr int kSolveZCap = 1024;
+struct SolveStage {
+  double* L;    // w x w diagonal block, column-major (leading dimension w)
+  double* v;    // w: y_t / x_t
+  double* di;   // w: 1 / L[j][j]
+  double* z;    // m <= kSolveZCap: update vector / gathered x below
+};
+
+// Global loads a thread of the staged solves keeps in flight.
+constexpr int kSolveBatch = 16;
+
+__device__ void stage_diag(const CholDev& d, const double* __restrict__ Lt, int f, int w, int h,
+                           const SolveStage& S) {
+  for (int base = threadIdx.x; base < w * w; base += kSolveBatch * kThreads) {
+    double v[kSolveBatch];
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u) {
+      const int idx = base + u * kThreads, k = idx / w, i = idx - k * w;
+      v[u] = idx < w * w && i >= k ? __ldcg(Lt + size_t(k) * h + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u)
+      if (base + u * kThreads < w * w) S.L[base + u * kThreads] = v[u];
+  }
+  for (int i = threadIdx.x; i < w; i += kThreads) S.di[i] = __ldcg(d.Dinv + f + i);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_chol_backward_tasks(CholDev d, CholTasks g,
+__device__ void forward_staged(const CholDev& d, int t, double* __restrict__ y, const SolveStage& S) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
+  const int tid = threadIdx.x;
+  stage_diag(d, Lt, f, w, h, S);
+  for (int i = tid; i < w; i += kThreads) S.v[i] = __ldcg(y + f + i);
+  for (int i = tid; i < m; i += kThreads) S.z[i] = 0.0;
+  __syncthreads();
+  // the children's update vectors, one child at a time (a child's rows are
+  // distinct; two children may share rows)
+  for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
+    const int c = __ldg(d.kid + q);
+    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
+                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
+    const double* __restrict__ zc = d.Zx + __ldg(d.z_off + c);
+    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+    for (int base = 0; base < mc; base += 4 * kThreads) {
+      double v[4];
+      int r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ii = base + u * kThreads + tid;
+        r[u] = ii < mc ? __ldg(rel + ii) : -1;
+        v[u] = ii < mc ? __ldcg(zc + ii) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (r[u] < 0) continue;
+        if (r[u] < w)
+          S.v[r[u]] += v[u];
+        else
+          S.z[r[u] - w] += v[u];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {  // y_t <- L_tt^-1 y_t
+    const int lane = tid;
+    double y0 = lane < w ? S.v[lane] : 0.0, y1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
+    const double d0 = lane < w ? S.di[lane] : 0.0, d1 = lane + 32 < w ? S.di[lane + 32] : 0.0;
+    for (int k = 0; k < w; ++k) {
+      const double* Lk = S.L + k * w;
+      if (k < 32) {
+        const double yk = __shfl_sync(0xffffffffu, y0 * d0, k);
+        if (lane == k) y0 = yk;
+        if (lane > k && lane < w) y0 = fma(-Lk[lane], yk, y0);
+        if (lane + 32 < w) y1 = fma(-Lk[lane + 32], yk, y1);
+      } else {
+        const double yk = __shfl_sync(0xffffffffu, y1 * d1, k - 32);
+        if (lane + 32 == k) y1 = yk;
+        if (lane + 32 > k && lane + 32 < w) y1 = fma(-Lk[lane + 32], yk, y1);
+      }
+    }
+    if (lane < w) S.v[lane] = y0;
+    if (lane + 32 < w) S.v[lane + 32] = y1;
+  }
+  __syncthreads();
+  for (int i = tid; i < w; i += kThreads) __stcg(y + f + i, S.v[i]);
+  // z_t = (gathered) - L21 y_t: each row's dot product split over P threads,
+  // a thread's kSolveBatch loads in flight together
+  const int P = w <= kSolveBatch ? 1 : (w <= 2 * kSolveBatch ? 2 : 4);
+  const int part = tid & (P - 1);
+  for (int i0 = 0; i0 < m; i0 += kThreads / P) {
+    const int i = i0 + tid / P;
+    double v[kSolveBatch];
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u) {
+      const int k = part + P * u;
+      v[u] = i < m && k < w ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u) {
+      const int k = part + P * u;
+      if (k < w) acc = fma(v[u], S.v[k], acc);
+    }
+    for (int o = P / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, P);
+    if (i < m && part == 0) __stcg(zt + i, S.z[i] - acc);
+  }
+}
+
+__device__ void backward_staged(const CholDev& d, int t, double* __restrict__ x, const SolveStage& S) {
+  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
+  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0, m = h - w;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  const int tid = threadIdx.x, lane = tid & 31;
+  stage_diag(d, Lt, f, w, h, S);
+  for (int i = tid; i < w; i += kThreads) S.v[i] = __ldcg(x + f + i);
+  for (int i = tid; i < m; i += kThreads) S.z[i] = __ldcg(x + __ldg(d.rowidx + r0 + w + i));
+  __syncthreads();
+  // x_t -= L21' x(below): column k's dot product by P threads per column
+  {
+    int P = 32;  // threads per column: the most (a power of two) that fit
+    while (P > 1 && w * P > kThreads) P >>= 1;
+    const int part = tid & (P - 1);
+    for (int k0 = 0; k0 < w; k0 += kThreads / P) {
+      const int k = k0 + tid / P;
+      double acc = 0.0;
+      for (int b = 0; b < m; b += P * kSolveBatch) {  // kSolveBatch loads in flight
+        double v[kSolveBatch];
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u) {
+          const int i = b + part + P * u;
+          v[u] = k < w && i < m ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u) {
+          const int i = b + part + P * u;
+          if (i < m) acc = fma(v[u], S.z[i], acc);
+        }
+      }
+      for (int o = P / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, P);
+      if (k < w && part == 0) S.v[k] -= acc;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {  // x_t <- L_tt^-T x_t
+    double x0 = lane < w ? S.v[lane] : 0.0, x1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
+    const double d0 = lane < w ? S.di[lane] : 0.0, d1 = lane + 32 < w ? S.di[lane + 32] : 0.0;
+    for (int k = w - 1; k >= 0; --k) {
+      // row k of L_tt below the diagonal, read by column: L[k][i] = L(i * w + k)
+      if (k >= 32) {
+        const double xk = __shfl_sync(0xffffffffu, x1 * d1, k - 32);
+        if (lane + 32 == k) x1 = xk;
+        if (lane + 32 < k) x1 = fma(-S.L[(lane + 32) * w + k], xk, x1);
+        x0 = fma(-S.L[lane * w + k], xk, x0);  // lane < 32 <= k
+      } else {
+        const double xk = __shfl_sync(0xffffffffu, x0 * d0, k);
+        if (lane == k) x0 = xk;
+        if (lane < k) x0 = fma(-S.L[lane * w + k], xk, x0);
+      }
+    }
+    if (lane < w) __stcg(x + f + lane, x0);
+    if (lane + 32 < w) __stcg(x + f + lane + 32, x1);
+  }
+}
+
+// Whether supernode t's update vector fits the staged solves.
+__device__ __forceinline__ bool solve_staged(const CholDev& d, int t) {
+  return (__ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t)) -
+             (__ldg(d.sn_first + t + 1) - __ldg(d.sn_first + t)) <= kSolveZCap;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_chol_forward_tasks(CholDev d, CholTasks g,
+                                                                     double* __restrict__ y) {
+  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth], sdi[kCholMaxWidth],
+      sz[kSolveZCap];
+  const SolveStage S{sL, sv, sdi, sz};
+  task_loop(g, d.abort, [&](int4 tk) {
+    if (solve_staged(d, tk.y))
+      forward_staged(d, tk.y, y, S);
+    else
+      forward_large(d, tk.y, y, sL, sv);
+  });
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_chol_backward_tasks(CholDev d, CholTasks g,
                                                                       double* __restrict__ x) {
-  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth];
-  task_loop(g, d.abort, [&](int4 tk) { backward_large(d, tk.y, x, sL, sv); });
+  __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth], sdi[kCholMaxWidth],
+      sz[kSolveZCap];
+  const SolveStage S{sL, sv, sdi, sz};
+  task_loop(g, d.abort, [&](int4 tk) {
+    if (solve_staged(d, tk.y))
+      backward_staged(d, tk.y, x, S);
+    else
+      backward_large(d, tk.y, x, sL, sv);
+  });
 }
 
 // Warp tasks: each warp takes the next task of the list, waits (bounded)

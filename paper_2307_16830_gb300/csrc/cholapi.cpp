@@ -58,7 +58,8 @@ struct acopf_chol {
   acopf::CholTasks tg[6] = {};
   int32_t* flags = nullptr;             // the graphs' done flags and counters
   size_t flag_ints = 0;
-  int blocks = 0, warp_blocks = 0, solve_blocks = 0;  // persistent blocks of the task kernels
+  // persistent blocks of the task kernels
+  int blocks = 0, warp_blocks = 0, solve_blocks = 0, solve_warp_blocks = 0;
   const int64_t* amap = nullptr;
   const int32_t* perm = nullptr;
   double* work = nullptr;       // n: the permuted right-hand side / solution
@@ -155,13 +156,14 @@ cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cud
   for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
     e = acopf::launch_chol_bottom_fwd(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->work, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_solve_warps(d, chol->tg[1], chol->work, true, chol->solve_blocks, s);
+    e = acopf::launch_chol_solve_warps(d, chol->tg[1], chol->work, true, chol->solve_warp_blocks, s);
   if (e == cudaSuccess)
     e = acopf::launch_chol_forward_tasks(d, chol->tg[2], chol->work, chol->solve_blocks, s);
   if (e == cudaSuccess)
     e = acopf::launch_chol_backward_tasks(d, chol->tg[3], chol->work, chol->solve_blocks, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_solve_warps(d, chol->tg[4], chol->work, false, chol->solve_blocks, s);
+    e = acopf::launch_chol_solve_warps(d, chol->tg[4], chol->work, false, chol->solve_warp_blocks,
+                                       s);
   for (size_t v = bp.size() - 1; e == cudaSuccess && v > 0; --v)
     e = acopf::launch_chol_bottom_bwd(d, chol->bot_sn + bp[v - 1], bp[v] - bp[v - 1], chol->work, s);
   if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
@@ -337,7 +339,8 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   }
   c->blocks = per_sm * sms;
   c->warp_blocks = warp_per_sm * sms;
-  c->solve_blocks = 4 * sms;
+  c->solve_blocks = 2 * sms;
+  c->solve_warp_blocks = 4 * sms;
   acopf::CholDev& d = c->dev;
   d.n = sy.n;
   d.sn_first = reinterpret_cast<const int32_t*>(base + o_first);
