@@ -159,7 +159,7 @@ def test_served_results_same_alone_and_in_mix(dev, acopf):
                 assert st["ticks"] < sum(j.n_calls for j in js)  # calls shared launches
             else:
                 assert st["ticks"] == 0
-                assert st["launches"] == 2 * sum(j.n_calls for j in js)
+                assert st["launches"] == acopf.launches_per_call(0) * sum(j.n_calls for j in js)
     for m in models:
         m.close()
 
