@@ -621,15 +621,22 @@ acopf_status acopf_batch_info(const acopf_batch* batch, int32_t* schedule, int64
  * thread admits queued requests in arrival order while the device bytes of
  * the admitted requests (inputs, outputs and scratch, allocated from the
  * server's stream-ordered pool) stay within the budget, and runs them:
+ * An admitted request's device region is allocated and its inputs are
+ * uploaded on the server's copy stream, apart from the compute stream that
+ * runs the calls, so a large upload overlaps the calls of the requests
+ * already running.
  *   ACOPF_SERVE_CONTINUOUS: continuous batching.  Each step ("tick") is one
- *     batched evaluation (the acopf_batch kernels) of every admitted request
- *     that has calls left, one call each; requests join at the next tick
- *     after admission and leave when their last call is done, so requests
- *     that arrive while others run share launches with them.  A bounded
- *     number of ticks is in flight (ACOPF_SERVE_OPT_INFLIGHT).
+ *     batched evaluation (the acopf_batch kernels) of admitted requests
+ *     whose inputs are on the device and that have calls left, one call
+ *     each, chosen within a work budget (ACOPF_SERVE_OPT_TICK_WORK: the
+ *     longest-admitted one, then least remaining work first); requests join
+ *     at the first tick after their upload completes and leave when their
+ *     last call is done, so requests that arrive while others run share
+ *     launches with them.  A bounded number of ticks is in flight
+ *     (ACOPF_SERVE_OPT_INFLIGHT).
  *   ACOPF_SERVE_FIFO: plain launches.  Each admitted request's calls are
  *     queued as single-instance launches (acopf_eval_assemble's kernels) in
- *     arrival order on the server's stream.
+ *     arrival order on the compute stream, each request's after its upload.
  * Results do not depend on the mode or on co-scheduled requests: each
  * request has its own scratch and runs the code its single-instance call
  * runs, so its outputs are bit-identical to those of acopf_eval_assemble.
@@ -682,7 +689,8 @@ typedef struct {
   int32_t peak_active;
 } acopf_server_stats;
 
-/* Starts a server on `device` with its own stream, memory pool and thread.
+/* Starts a server on `device` with its own two streams (compute, copy),
+ * memory pool and thread.
  * budget_bytes > 0 caps the device bytes of admitted requests; max_active
  * >= 1 caps the number of admitted requests.  Returns ACOPF_E_NO_DEVICE for
  * device < 0. */
@@ -724,8 +732,15 @@ acopf_status acopf_server_get_stats(acopf_server* server, acopf_server_stats* ou
 /* Server options (scheduling only; results never change).
  * ACOPF_SERVE_OPT_INFLIGHT (default 4, range 1..16): continuous-mode ticks
  * queued on the GPU ahead of completion.  More hides the host's per-tick
- * work behind the GPU's; fewer lets a new request join sooner. */
+ * work behind the GPU's; fewer lets a new request join sooner.
+ * ACOPF_SERVE_OPT_TICK_WORK (default 60,000, >= 1): the work budget of one
+ * continuous-mode tick, counted as buses + branches + generators of one
+ * call per request (an 80,000-bus call is about 200,000).  A tick takes the
+ * longest-admitted runnable request, then others in order of least
+ * remaining work (calls left x work per call) while the sum stays within
+ * the budget. */
 #define ACOPF_SERVE_OPT_INFLIGHT 1
+#define ACOPF_SERVE_OPT_TICK_WORK 2
 acopf_status acopf_server_set_option(acopf_server* server, int32_t option, int64_t value);
 
 #ifdef __cplusplus

@@ -150,6 +150,7 @@ _server_release = _sig("acopf_server_release", C.c_int32, _vp, C.c_uint64)
 _server_stats = _sig("acopf_server_get_stats", C.c_int32, _vp, C.POINTER(ServerStats))
 _server_set_option = _sig("acopf_server_set_option", C.c_int32, _vp, C.c_int32, C.c_int64)
 SERVE_OPT_INFLIGHT = 1
+SERVE_OPT_TICK_WORK = 2
 
 _pipeline_create = _sig("acopf_pipeline_create", C.c_int32, _vp, C.c_int32, C.POINTER(_vp))
 _pipeline_destroy = _sig("acopf_pipeline_destroy", C.c_int32, _vp)

@@ -5,6 +5,7 @@
 // slack projection, Gauss-Newton right-hand side, step bound and trials.  Reductions run over a fixed
 // grid (4 blocks per SM): per-block partials in a fixed order, then one
 // block combining them in block order, so every result is reproducible.
+#include "fp64_device.cuh"
 #include "ipm_internal.h"
 
 namespace acopf {
@@ -88,42 +89,48 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_rhs(DevStep st, IpmVec v, d
 
 // Step bounds and barrier terms at the iterate, per block:
 // [primal fraction-to-boundary alpha, dual alpha, grad phi' d, sum log gaps].
+// The FP64 unit bounds these passes, so each gap's reciprocal is the
+// three-operation one (within an ulp), the step bounds compare ratios
+// tau gap / |dv| through reciprocals of the step components, and the
+// logarithms are summed as one logarithm of their product per thread.
 __device__ __forceinline__ void primal_terms(double v, double dv, double lo, double hi, double tau,
-                                             double mu, double (&a)[4]) {
+                                             double mu, double (&a)[4], LogSum& lg) {
   if (finite_bound(lo)) {
     const double gap = v - lo;
-    if (dv < 0.0) a[0] = fmin(a[0], -tau * gap / dv);
-    a[2] -= mu * dv / gap;
-    a[3] += log(gap);
+    if (dv < 0.0) a[0] = fmin(a[0], -tau * gap * recip(dv));
+    a[2] = fma(-mu * dv, recip(gap), a[2]);
+    lg.add(gap);
   }
   if (finite_bound(hi)) {
     const double gap = hi - v;
-    if (dv > 0.0) a[0] = fmin(a[0], tau * gap / dv);
-    a[2] += mu * dv / gap;
-    a[3] += log(gap);
+    if (dv > 0.0) a[0] = fmin(a[0], tau * gap * recip(dv));
+    a[2] = fma(mu * dv, recip(gap), a[2]);
+    lg.add(gap);
   }
 }
 
 __device__ __forceinline__ void dual_term(double z, double dz, double tau, double (&a)[4]) {
-  if (dz < 0.0) a[1] = fmin(a[1], -tau * z / dz);
+  if (dz < 0.0) a[1] = fmin(a[1], -tau * z * recip(dz));
 }
 
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_dir(IpmVec v, int n, int m, double tau,
                                                           double mu, double* __restrict__ part) {
   double a[4] = {1.0, 1.0, 0.0, 0.0};
+  LogSum lg;
   const int stride = gridDim.x * kIpmThreads;
   for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
     const double dx = v.dx[j];
     a[2] = fma(v.grad[j], dx, a[2]);
-    primal_terms(v.x[j], dx, v.xl[j], v.xu[j], tau, mu, a);
+    primal_terms(v.x[j], dx, v.xl[j], v.xu[j], tau, mu, a, lg);
     dual_term(v.zl_x[j], v.dzl_x[j], tau, a);
     dual_term(v.zu_x[j], v.dzu_x[j], tau, a);
   }
   for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
-    primal_terms(v.s[r], v.ds[r], v.sl[r], v.su[r], tau, mu, a);
+    primal_terms(v.s[r], v.ds[r], v.sl[r], v.su[r], tau, mu, a, lg);
     dual_term(v.zl_s[r], v.dzl_s[r], tau, a);
     dual_term(v.zu_s[r], v.dzu_s[r], tau, a);
   }
+  a[3] = lg.value();
   block_reduce<4, 2>(a, part);
 }
 
@@ -143,18 +150,20 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_measure(IpmVec v, const dou
                                                               int n, int m,
                                                               double* __restrict__ part) {
   double a[2] = {0.0, 0.0};
+  LogSum lg;
   const int stride = gridDim.x * kIpmThreads;
   for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
     const double lo = v.xl[j], hi = v.xu[j], xj = x[j];
-    if (finite_bound(lo)) a[1] += log(xj - lo);
-    if (finite_bound(hi)) a[1] += log(hi - xj);
+    if (finite_bound(lo)) lg.add(xj - lo);
+    if (finite_bound(hi)) lg.add(hi - xj);
   }
   for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
     const double lo = v.sl[r], hi = v.su[r], sr = s[r];
     a[0] += fabs(cons[r] - sr);
-    if (finite_bound(lo)) a[1] += log(sr - lo);
-    if (finite_bound(hi)) a[1] += log(hi - sr);
+    if (finite_bound(lo)) lg.add(sr - lo);
+    if (finite_bound(hi)) lg.add(hi - sr);
   }
+  a[1] = lg.value();
   block_reduce<2, 0>(a, part);
 }
 

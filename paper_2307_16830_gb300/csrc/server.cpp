@@ -1,9 +1,13 @@
 // Serving entry points (acopf_server_*): a request loop over resident models
 // with admission by device-memory budget and continuous batching.
 //
-// One server thread owns the stream, the memory pool and every CUDA call of
+// One server thread owns the streams, the memory pool and every CUDA call of
 // the loop; client threads only queue requests and read their records
-// under the mutex.
+// under the mutex.  A request's device region is allocated and its inputs
+// uploaded on a copy stream, so that a large upload does not hold up the
+// calls of the requests already running on the compute stream; a request
+// takes part in ticks (or, in FIFO mode, the compute stream waits for it)
+// once its upload has completed.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -29,6 +33,10 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxInflightLimit = 16;  // upper bound of ACOPF_SERVE_OPT_INFLIGHT
 constexpr int kRing = kMaxInflightLimit + 1;
+// Default work of one tick (sum over its requests of buses + branches +
+// generators of one call): a 20,000-bus call, or many small ones; larger
+// requests run alone in their ticks.
+constexpr int64_t kDefaultTickWork = 60000;
 
 enum class St { Queued, Active, Draining, Done };
 
@@ -79,6 +87,8 @@ struct Req {
   int32_t issued = 0;
   int variant = 0;
   cudaEvent_t done_ev = nullptr;
+  cudaEvent_t ready_ev = nullptr;  // its inputs are on the device (copy stream)
+  bool ready = false;
   std::vector<int4> items1, items2;  // instance index 0; patched per tick
 
   double* dev(size_t off) const { return reinterpret_cast<double*>(mem + off); }
@@ -121,7 +131,9 @@ struct acopf_server {
   int32_t mode = ACOPF_SERVE_CONTINUOUS;
   int32_t max_active = 1;
   std::atomic<int> max_inflight{4};  // ticks in flight (continuous mode)
-  cudaStream_t stream = nullptr;
+  std::atomic<int64_t> tick_work{kDefaultTickWork};  // work of one tick (continuous mode)
+  cudaStream_t stream = nullptr;       // calls, tick tables, output copies
+  cudaStream_t copy_stream = nullptr;  // request regions: allocation, inputs, release
   cudaMemPool_t pool = nullptr;
   std::thread th;
   // guarded by mu
@@ -186,16 +198,17 @@ cudaError_t start_request(acopf_server* S, Req* q) {
   const acopf::Layout& L = q->L;
   const ReqPlan& p = q->plan;
   void* mem = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&mem, p.bytes, S->pool, S->stream);
+  cudaError_t e = cudaMallocFromPoolAsync(&mem, p.bytes, S->pool, S->copy_stream);
   if (e != cudaSuccess) return e;
   q->mem = static_cast<char*>(mem);
   e = cudaEventCreateWithFlags(&q->done_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->ready_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(q->mem + p.o_ws, 0, p.ws.bytes, S->stream);  // arrival counter = 0
+  e = cudaMemsetAsync(q->mem + p.o_ws, 0, p.ws.bytes, S->copy_stream);  // arrival counter = 0
   auto h2d = [&](size_t off, const double* src, size_t count) {
     if (e == cudaSuccess && count)
       e = cudaMemcpyAsync(q->dev(off), src, count * sizeof(double), cudaMemcpyHostToDevice,
-                          S->stream);
+                          S->copy_stream);
   };
   const size_t np = size_t(r.n_points);
   h2d(p.o_x, r.x, np * size_t(L.n));
@@ -206,6 +219,7 @@ cudaError_t start_request(acopf_server* S, Req* q) {
     h2d(p.o_pd, r.Pd, size_t(L.nb));
     h2d(p.o_qd, r.Qd, size_t(L.nb));
   }
+  if (e == cudaSuccess) e = cudaEventRecord(q->ready_ev, S->copy_stream);
   if (e != cudaSuccess) return e;
   q->dm = r.model->dm;
   acopf::bind_workspace(q->dm, q->mem + p.o_ws, p.ws);
@@ -215,7 +229,9 @@ cudaError_t start_request(acopf_server* S, Req* q) {
   }
   q->variant = (r.delta_w != 0.0 || r.delta_c != 0.0 ? 2 : 0) + (q->dm.has_shunt ? 1 : 0);
   acopf::append_items(L, 0, q->items1, q->items2);
-  if (S->mode == ACOPF_SERVE_FIFO) {
+  if (S->mode == ACOPF_SERVE_FIFO) {  // in arrival order: the compute stream waits for it
+    q->ready = true;
+    e = cudaStreamWaitEvent(S->stream, q->ready_ev, 0);
     for (int32_t c = 0; c < r.n_calls && e == cudaSuccess; ++c)
       e = acopf::launch_eval(q->dm, acopf::OUT_ALL, q->args(c), S->stream);
     q->issued = r.n_calls;
@@ -256,13 +272,38 @@ cudaError_t grow_slot(acopf_server* S, Slot& sl, size_t need) {
   return e;
 }
 
-// One continuous-batching step: one call of every admitted request that has
-// calls left, in one batched evaluation.
+// Work of one call of a request (the kernels' units: buses, branches,
+// generators).
+int64_t call_work(const Req* q) { return int64_t(q->L.nb) + q->L.nl + q->L.ng; }
+
+// One continuous-batching step: one call each of the runnable requests
+// (admitted, inputs on the device, calls left) chosen for this tick, in one
+// batched evaluation.  The longest-admitted runnable request always takes
+// part (so every request progresses); the others join in order of least
+// remaining work (calls left x work per call; ties: arrival) while the
+// tick's work stays within the budget.  A small request thus shares its
+// ticks with other small ones instead of waiting behind every large one.
 cudaError_t tick(acopf_server* S) {
-  std::vector<Req*> members;
+  std::vector<Req*> cand;
   for (Req* q : S->active)
-    if (q->st == St::Active && q->issued < q->r.n_calls) members.push_back(q);
-  if (members.empty()) return cudaSuccess;
+    if (q->st == St::Active && q->ready && q->issued < q->r.n_calls) cand.push_back(q);
+  if (cand.empty()) return cudaSuccess;
+  auto oldest = std::min_element(cand.begin(), cand.end(),
+                                 [](const Req* a, const Req* b) { return a->id < b->id; });
+  std::iter_swap(cand.begin(), oldest);
+  std::sort(cand.begin() + 1, cand.end(), [](const Req* a, const Req* b) {
+    const int64_t wa = call_work(a) * (a->r.n_calls - a->issued);
+    const int64_t wb = call_work(b) * (b->r.n_calls - b->issued);
+    return wa != wb ? wa < wb : a->id < b->id;
+  });
+  std::vector<Req*> members{cand.front()};
+  int64_t work = call_work(cand.front());
+  const int64_t budget = S->tick_work.load();
+  for (size_t j = 1; j < cand.size(); ++j)
+    if (work + call_work(cand[j]) <= budget) {
+      members.push_back(cand[j]);
+      work += call_work(cand[j]);
+    }
   const size_t A = members.size();
   size_t n1 = 0, n2 = 0;
   for (Req* q : members) {
@@ -347,7 +388,10 @@ int poll_done(acopf_server* S, cudaError_t& err) {
       continue;
     }
     if (e != cudaSuccess) err = e;
-    cudaFreeAsync(q->mem, S->stream);
+    // every use of the region is complete (the host saw its last event):
+    // it goes back to the pool in the copy stream's order, where the next
+    // regions are allocated
+    cudaFreeAsync(q->mem, S->copy_stream);
     q->mem = nullptr;
     complete(S, q, e == cudaSuccess ? ACOPF_OK : ACOPF_E_CUDA);
     S->active.erase(S->active.begin() + long(i));
@@ -359,8 +403,9 @@ int poll_done(acopf_server* S, cudaError_t& err) {
 // Ends every admitted request with `st` after a CUDA failure of the loop.
 void fail_all(acopf_server* S, acopf_status st) {
   cudaStreamSynchronize(S->stream);
+  cudaStreamSynchronize(S->copy_stream);
   for (Req* q : S->active) {
-    if (q->mem) cudaFreeAsync(q->mem, S->stream);
+    if (q->mem) cudaFreeAsync(q->mem, S->copy_stream);
     q->mem = nullptr;
     complete(S, q, st);
   }
@@ -411,7 +456,7 @@ void serve(acopf_server* S) {
       cudaError_t e = start_request(S, q);
       if (e == cudaErrorMemoryAllocation) {  // the pool could not serve it: this request fails
         cudaGetLastError();
-        if (q->mem) cudaFreeAsync(q->mem, S->stream);
+        if (q->mem) cudaFreeAsync(q->mem, S->copy_stream);
         q->mem = nullptr;
         acopf::set_last_error("server: device allocation failed for a request");
         complete(S, q, ACOPF_E_OOM);
@@ -421,9 +466,20 @@ void serve(acopf_server* S) {
       if (e != cudaSuccess && err == cudaSuccess) err = e;
     }
     bool progressed = !admitted.empty();
+    for (Req* q : S->active) {  // uploads that have completed
+      if (q->ready || q->st != St::Active || err != cudaSuccess) continue;
+      const cudaError_t e = cudaEventQuery(q->ready_ev);
+      if (e == cudaSuccess) {
+        q->ready = true;
+        progressed = true;
+      } else if (e != cudaErrorNotReady) {
+        err = e;
+      }
+    }
     if (err == cudaSuccess && S->mode == ACOPF_SERVE_CONTINUOUS) {
       bool calls_left = false;
-      for (Req* q : S->active) calls_left |= q->st == St::Active && q->issued < q->r.n_calls;
+      for (Req* q : S->active)
+        calls_left |= q->st == St::Active && q->ready && q->issued < q->r.n_calls;
       if (calls_left && int(S->inflight.size()) < S->max_inflight.load()) {
         err = tick(S);
         progressed = true;
@@ -464,9 +520,11 @@ void free_server(acopf_server* S) {
   }
   for (auto& kv : S->reqs) {
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+    if (kv.second->ready_ev) cudaEventDestroy(kv.second->ready_ev);
     delete kv.second;
   }
   if (S->pool) cudaMemPoolDestroy(S->pool);
+  if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
 }
@@ -493,6 +551,7 @@ acopf_status acopf_server_create(int device, int64_t budget_bytes, int32_t mode,
   DeviceScope ds(device);
   cudaError_t e = ds.error();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
@@ -531,6 +590,7 @@ acopf_status acopf_server_destroy(acopf_server* server) {
   if (server->th.joinable()) server->th.join();
   DeviceScope ds(server->device);
   cudaStreamSynchronize(server->stream);
+  cudaStreamSynchronize(server->copy_stream);
   free_server(server);
   return ACOPF_OK;
 }
@@ -622,9 +682,10 @@ acopf_status acopf_server_release(acopf_server* server, uint64_t ticket) {
   Req* q = find(server, ticket);
   if (!q) return fail(ACOPF_E_INVALID_ARG, "acopf_server_release: unknown ticket");
   if (!q->done) return fail(ACOPF_E_BUSY, "acopf_server_release: request not done");
-  if (q->done_ev) {
+  if (q->done_ev || q->ready_ev) {
     DeviceScope ds(server->device);
-    cudaEventDestroy(q->done_ev);
+    if (q->done_ev) cudaEventDestroy(q->done_ev);
+    if (q->ready_ev) cudaEventDestroy(q->ready_ev);
   }
   server->reqs.erase(ticket);
   delete q;
@@ -638,6 +699,12 @@ acopf_status acopf_server_set_option(acopf_server* server, int32_t option, int64
       return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: in-flight ticks must be in [1, 16]");
     server->max_inflight.store(int(value));
     server->cv_work.notify_all();
+    return ACOPF_OK;
+  }
+  if (option == ACOPF_SERVE_OPT_TICK_WORK) {
+    if (value < 1)
+      return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: the tick work must be >= 1");
+    server->tick_work.store(value);
     return ACOPF_OK;
   }
   return fail(ACOPF_E_INVALID_ARG, "acopf_server_set_option: unknown option");

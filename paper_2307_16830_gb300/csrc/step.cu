@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "acopf_internal.h"
+#include "fp64_device.cuh"
 
 namespace acopf {
 namespace {
@@ -36,13 +37,13 @@ __device__ __forceinline__ void inv_gaps(double v, double lo, double hi, double&
   const bool fl = is_finite_bits(lo), fh = is_finite_bits(hi);
   const double a = v - lo, b = hi - v;
   if (fl && fh && mid_range(a) && mid_range(b)) {
-    const double r = __drcp_rn(a * b);
+    const double r = recip_nr(a * b);
     il = b * r;
     iu = a * r;
     return;
   }
-  il = fl ? __drcp_rn(a) : 0.0;
-  iu = fh ? __drcp_rn(b) : 0.0;
+  il = fl ? recip(a) : 0.0;
+  iu = fh ? recip(b) : 0.0;
 }
 
 // Rows: Sigma_s, q_s and w = C q_s + D q_y, with C = (dc Sigma_s + 1 + dc dw)^-1
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(kStepThreads) k_condense_rows(DevStep st, Step
     const double py = ldg(it.p_y + r);
     double w;
     if constexpr (REG) {
-      const double C = __drcp_rn(fma(dc, sig, fma(dc, dw, 1.0)));
+      const double C = recip(fma(dc, sig, fma(dc, dw, 1.0)));
       w = C * fma(sig + dw, py, q);  // C q_s + D q_y with D = (Sigma_s + dw) C
     } else {
       w = fma(sig, py, q);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kStepThreads) k_recover(
     const double sig = ldg(sigma_s + r), q = ldg(q_s + r), py = ldg(it.p_y + r);
     double ds;
     if constexpr (REG) {
-      const double C = __drcp_rn(fma(dc, sig, fma(dc, dw, 1.0)));
+      const double C = recip(fma(dc, sig, fma(dc, dw, 1.0)));
       ds = C * (fma(dc, q, adx) - py);
     } else {
       ds = adx - py;

@@ -175,9 +175,19 @@ def test_inflight_option_keeps_results(dev, acopf):
                 assert s.wait(t, 120.0) == acopf.OK
             for k, j in enumerate(js):
                 assert_request_equal(j.result(), ref[k], f"inflight {depth} request {k}")
+    # a tick budget of 1 work unit: every tick takes only its longest-admitted
+    # request, so the requests run one after another, with the same results
+    with acopf.server_create(0, BIG, acopf.SERVE_CONTINUOUS) as s:
+        s.set_option(acopf.SERVE_OPT_TICK_WORK, 1)
+        tickets = [j.submit(s) for j in js]
+        for t in tickets:
+            assert s.wait(t, 120.0) == acopf.OK
+        for k, j in enumerate(js):
+            assert_request_equal(j.result(), ref[k], f"tick work 1 request {k}")
+        assert s.stats()["ticks"] == sum(j.n_calls for j in js)
     with acopf.server_create(0, BIG, acopf.SERVE_CONTINUOUS) as s:
         for bad_opt, bad_val in ((acopf.SERVE_OPT_INFLIGHT, 0), (acopf.SERVE_OPT_INFLIGHT, 17),
-                                 (99, 1)):
+                                 (acopf.SERVE_OPT_TICK_WORK, 0), (99, 1)):
             with pytest.raises(acopf.AcopfError) as e:
                 s.set_option(bad_opt, bad_val)
             assert e.value.status == acopf.E_INVALID_ARG
