@@ -26,6 +26,8 @@ struct Layout {
   // Hessian COO sections
   int32_t HBLK = 0, HTH = 0, HG = 0, HB = 0, nnzh = 0;
   int32_t nnzk = 0;
+  // lanes of the bus-row phase (row chunks, a multiple of 32)
+  int32_t nrc = 0;
 };
 
 // Branch pi-model coefficients, structure of arrays: coef[k * nl + l] with
@@ -92,6 +94,12 @@ struct DevModel {
   // from gen_ptr and the row starts).
   const int4* brow;            // nl
   const uint32_t* bcnt;        // nl
+  // Bus-row phase: lane c runs row chunk c, two int4 each: {bus i (-1: an
+  // idle lane), position p, first slot, end slot} and {the chunk's first
+  // positions in rows va_i, vm_i (va columns) and vm_i (vm columns), the
+  // lane of the bus's first chunk | chunk count << 5}.  A bus's chunks are
+  // consecutive lanes of one warp, split between runs of equal neighbours.
+  const int4* rchunk;          // 2 L.nrc
   // scratch
   SlotPart* part_slot;         // 2 nl
   BusDiag* bus_diag;           // nb
@@ -112,6 +120,7 @@ struct HostModel {
   std::vector<int32_t> porder, pslot_ptr, slot_nbr, slot_of_arc, pbal_ptr, bal_idx;
   std::vector<int32_t> brow;   // 4 per branch
   std::vector<uint32_t> bcnt;
+  std::vector<int32_t> rchunk;  // 8 per bus-row lane (DevModel::rchunk)
   std::vector<int32_t> jrows, jcols, hrows, hcols, krowptr, kcolind;
   std::vector<double> xl, xu, gl, gu;
 };
@@ -129,6 +138,9 @@ constexpr int kGenThreads = 128;
 // Balance-row terms a warp of bus threads stages in shared memory (P and Q
 // values, 16 bytes each); warps with more terms sum from global memory.
 constexpr int kBalCap = 192;
+// Slots of one bus-row chunk (one round of loads in flight); a bus with
+// more than 32 x kRowChunk slots takes larger chunks.
+constexpr int kRowChunk = 4;
 
 inline int32_t ceil_div(int64_t a, int64_t b) { return static_cast<int32_t>((a + b - 1) / b); }
 

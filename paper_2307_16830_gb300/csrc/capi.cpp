@@ -38,7 +38,8 @@ void append_items(const Layout& L, int32_t inst, std::vector<int4>& p1, std::vec
   for (int k = 0; k < nbb; ++k) p1.push_back(make_int4(inst, 0, k, nbb));
   for (int k = 0; k < nbi; ++k) p1.push_back(make_int4(inst, 1, k, nbi));
   for (int k = 0; k < ngb; ++k) p1.push_back(make_int4(inst, 2, k, ngb));
-  for (int k = 0; k < nbi; ++k) p2.push_back(make_int4(inst, 3, k, nbi));
+  const int nbr = ceil_div(L.nrc, kBusThreads);  // bus-row blocks (row chunks)
+  for (int k = 0; k < nbr; ++k) p2.push_back(make_int4(inst, 3, k, nbr));
 }
 
 }  // namespace acopf
@@ -161,6 +162,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   const size_t o_c2 = p.take<double>(ng), o_c1 = p.take<double>(ng), o_c0 = p.take<double>(ng);
   const size_t o_krp = p.take<int32_t>(n + 1);
   const size_t o_brow = p.take<int4>(nl), o_bcnt = p.take<uint32_t>(nl);
+  const size_t o_rch = p.take<int4>(2 * size_t(L.nrc));
   const acopf::WorkspacePlan wsp = acopf::workspace_plan(L);
   const size_t o_ws = p.take<char>(wsp.bytes);
   void* arena = nullptr;
@@ -198,6 +200,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   if (e == cudaSuccess) e = up(o_krp, hm.krowptr.data(), (n + 1) * 4);
   if (e == cudaSuccess) e = up(o_brow, hm.brow.data(), nl * 16);
   if (e == cudaSuccess) e = up(o_bcnt, hm.bcnt.data(), nl * 4);
+  if (e == cudaSuccess) e = up(o_rch, hm.rchunk.data(), hm.rchunk.size() * 4);
   if (e == cudaSuccess) e = up(o_bptr, hm.pbal_ptr.data(), (nb + 1) * 4);
   if (e == cudaSuccess) e = up(o_pord, hm.porder.data(), nb * 4);
   if (e == cudaSuccess) e = up(o_psp, hm.pslot_ptr.data(), (nb + 1) * 4);
@@ -231,6 +234,7 @@ acopf_status acopf_model_create(const acopf_buses* buses, const acopf_branches* 
   dm.krowptr = reinterpret_cast<const int32_t*>(base + o_krp);
   dm.brow = reinterpret_cast<const int4*>(base + o_brow);
   dm.bcnt = reinterpret_cast<const uint32_t*>(base + o_bcnt);
+  dm.rchunk = reinterpret_cast<const int4*>(base + o_rch);
   dm.pbal_ptr = reinterpret_cast<const int32_t*>(base + o_bptr);
   dm.bal_idx = reinterpret_cast<const int32_t*>(base + o_bidx);
   acopf::bind_workspace(dm, base + o_ws, wsp);

@@ -824,88 +824,116 @@ __global__ void __launch_bounds__(kBranchThreads) k_asm_phase1(DevModel dm, Eval
 // (nu + 1)][vm_j (j < i)][vm_i], or just [vm_i] for a bus without branches.
 // The bus's slots run over its arcs by (other end, arc id), so parallel
 // branches (equal other end) are adjacent and their entries are summed.
-// Bus block blk of nblk (bus_warp_base interleaving).
+// Each lane runs one row chunk (DevModel::rchunk): about kRowChunk slots of
+// one bus, all their loads in flight at once; it writes the chunk's
+// off-diagonal entries from the row positions the chunk records and keeps
+// its part of the three diagonal sums.  The bus's last chunk lane adds the
+// chunks' parts in chunk order (shuffles within the warp) and writes the
+// diagonal entries: a bus with many branches costs one round of loads.
+// Warp w of block blk (of nblk) runs chunk warp w nblk + (nblk - 1 - blk),
+// so every block gets one warp from each quarter of the degree order and
+// block 0, which starts first, the heaviest.
 __device__ __forceinline__ void bus_rows_block(const DevModel& dm, const EvalArgs& a, int blk,
                                                int nblk) {
   const Layout& L = dm.L;
-  const int p = bus_warp_base(blk, nblk) + (threadIdx.x & 31);
-  const bool active = p < L.nb;
-  int i = 0, bva = 0, eva = 0, bvm = 0, evm = 0, k0 = 0, k1 = 0;
-  if (active) {  // structure only: independent of phase 1
-    i = ld(dm.porder + p);
+  const int lane = threadIdx.x & 31;
+  const int g = (threadIdx.x >> 5) * nblk + (nblk - 1 - blk);
+  int4 A = make_int4(-1, 0, 0, 0), B = make_int4(0, 0, 0, 0);
+  if (32 * g < L.nrc) {  // structure only: independent of phase 1
+    A = ld(dm.rchunk + 2 * (32 * g + lane));
+    B = ld(dm.rchunk + 2 * (32 * g + lane) + 1);
+  }
+  const int i = A.x;
+  int bva = 0, eva = 0, bvm = 0, evm = 0;
+  if (i >= 0) {
     const int* __restrict__ rp = dm.krowptr;
     bva = ld(rp + L.VA + i);
     eva = ld(rp + L.VA + i + 1);
     bvm = ld(rp + L.VM + i);
     evm = ld(rp + L.VM + i + 1);
-    k0 = ld(dm.pslot_ptr + p);
-    k1 = ld(dm.pslot_ptr + p + 1);
   }
   pdl_wait();
-  if (!active) return;
+  if (__all_sync(0xffffffffu, i < 0)) return;
   double* __restrict__ K = a.kvals;
   const int nlo = eva - bva - 1;  // distinct neighbours below i
-  const int nu = evm - bvm - nlo - 2;
-  int pva = bva, pvmva = bvm, pvmvm = bvm + nu + 1;
   double aa = 0.0, ma = 0.0, mm = 0.0;
-  double gv = 0.0, gx = 0.0, gw = 0.0;
-  int cur = -1;
-  const double2 dd = __ldcg(reinterpret_cast<const double2*>(dm.bus_diag + p));
-  const BusDiag d{dd.x, dd.y};
-  constexpr int U = 4;  // slots fetched per round, all loads in flight together
-  for (int k = k0; k < k1; k += U) {
-    double2 q0[U], q1[U], q2[U];
-    int jj[U];
+  if (i >= 0) {
+    int pva = B.x, pvmva = B.y, pvmvm = B.z;
+    double gv = 0.0, gx = 0.0, gw = 0.0;
+    int cur = -1;
+    constexpr int U = kRowChunk;  // slots fetched per round, all loads in flight together
+    for (int k = A.z; k < A.w; k += U) {
+      double2 q0[U], q1[U], q2[U];
+      int jj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (k + u < k1) {
-        const double2* src = reinterpret_cast<const double2*>(dm.part_slot + k + u);
-        q0[u] = __ldcg(src);
-        q1[u] = __ldcg(src + 1);
-        q2[u] = __ldcg(src + 2);
-        jj[u] = ld(dm.slot_nbr + k + u);
+      for (int u = 0; u < U; ++u) {
+        if (k + u < A.w) {
+          const double2* src = reinterpret_cast<const double2*>(dm.part_slot + k + u);
+          q0[u] = __ldcg(src);
+          q1[u] = __ldcg(src + 1);
+          q2[u] = __ldcg(src + 2);
+          jj[u] = ld(dm.slot_nbr + k + u);
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (k + u < k1) {
-        // SlotPart {aa, ma | mm, mx | vv, ww}
-        aa += q0[u].x;
-        ma += q0[u].y;
-        mm += q1[u].x;
-        const int j = jj[u];
-        if (j != cur) {
-          if (cur >= 0) {
-            if (cur > i && pvmva == bvm + nlo) ++pvmva;  // skip the (vm_i, va_i) slot
-            K[pvmva++] = gx;
-            if (cur < i) {
-              K[pva++] = gv;
-              K[pvmvm++] = gw;
+      for (int u = 0; u < U; ++u) {
+        if (k + u < A.w) {
+          // SlotPart {aa, ma | mm, mx | vv, ww}
+          aa += q0[u].x;
+          ma += q0[u].y;
+          mm += q1[u].x;
+          const int j = jj[u];
+          if (j != cur) {
+            if (cur >= 0) {
+              if (cur > i && pvmva == bvm + nlo) ++pvmva;  // skip the (vm_i, va_i) slot
+              K[pvmva++] = gx;
+              if (cur < i) {
+                K[pva++] = gv;
+                K[pvmvm++] = gw;
+              }
             }
+            cur = j;
+            gv = q2[u].x;
+            gx = q1[u].y;
+            gw = q2[u].y;
+          } else {  // parallel branches between i and j
+            gv += q2[u].x;
+            gx += q1[u].y;
+            gw += q2[u].y;
           }
-          cur = j;
-          gv = q2[u].x;
-          gx = q1[u].y;
-          gw = q2[u].y;
-        } else {  // parallel branches between i and j
-          gv += q2[u].x;
-          gx += q1[u].y;
-          gw += q2[u].y;
         }
       }
     }
-  }
-  if (cur >= 0) {
-    if (cur > i && pvmva == bvm + nlo) ++pvmva;
-    K[pvmva++] = gx;
-    if (cur < i) {
-      K[pva++] = gv;
-      K[pvmvm++] = gw;
+    if (cur >= 0) {
+      if (cur > i && pvmva == bvm + nlo) ++pvmva;
+      K[pvmva++] = gx;
+      if (cur < i) {
+        K[pva++] = gv;
+        K[pvmvm++] = gw;
+      }
     }
   }
-  K[bva + nlo] = d.va + aa;
-  if (k1 > k0) K[bvm + nlo] = ma;  // (vm_i, va_i) exists only when bus i has a branch
-  K[evm - 1] = d.vm + mm;
+  // the bus's chunks' diagonal parts, added in chunk order by its last chunk
+  const int first = B.w & 31, nch = B.w >> 5;  // nch = 0 on an idle lane
+  double ta = __shfl_sync(0xffffffffu, aa, first), tm = __shfl_sync(0xffffffffu, ma, first),
+         tmm = __shfl_sync(0xffffffffu, mm, first);
+  const int maxn = __reduce_max_sync(0xffffffffu, static_cast<unsigned>(nch));
+  for (int q = 1; q < maxn; ++q) {
+    const int src = first + min(q, max(nch - 1, 0));
+    const double va = __shfl_sync(0xffffffffu, aa, src), vb = __shfl_sync(0xffffffffu, ma, src),
+                 vc = __shfl_sync(0xffffffffu, mm, src);
+    if (q < nch) {
+      ta += va;
+      tm += vb;
+      tmm += vc;
+    }
+  }
+  if (i >= 0 && lane == first + nch - 1) {
+    const double2 dd = __ldcg(reinterpret_cast<const double2*>(dm.bus_diag + A.y));
+    K[bva + nlo] = dd.x + ta;
+    if (A.w > A.z) K[bvm + nlo] = tm;  // (vm_i, va_i) exists only when bus i has a branch
+    K[evm - 1] = dd.y + tmm;
+  }
 }
 
 __global__ void __launch_bounds__(kBusThreads, 5) k_bus_rows(DevModel dm, EvalArgs a) {
@@ -1058,7 +1086,7 @@ cudaError_t launch_eval_t(const DevModel& dm, const EvalArgs& a, cudaStream_t s,
       cudaError_t e = cudaEventRecord(mid, s);
       if (e != cudaSuccess) return e;
     }
-    return launch_ex(k_bus_rows, dim3(ceil_div(L.nb, kBusThreads)), dim3(kBusThreads), 0, s,
+    return launch_ex(k_bus_rows, dim3(ceil_div(L.nrc, kBusThreads)), dim3(kBusThreads), 0, s,
                      blocks > 0 && !mid && dm.pdl, dm, a);
   }
 }
@@ -1120,7 +1148,8 @@ cudaError_t launch_assemble(const DevModel& dm, const EvalArgs& a, cudaStream_t 
     k_asm_phase1<false><<<blocks, kBranchThreads, 0, s>>>(dm, a, nbb, nbi, ngb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_ex(k_bus_rows, dim3(nbi), dim3(kBusThreads), 0, s, dm.pdl != 0, dm, a);
+  return launch_ex(k_bus_rows, dim3(ceil_div(L.nrc, kBusThreads)), dim3(kBusThreads), 0, s,
+                   dm.pdl != 0, dm, a);
 }
 
 cudaError_t launch_batch(const DevModel* models, const EvalArgs* ios, const int4* items1,

@@ -477,6 +477,70 @@ acopf_status build_host_model(const acopf_buses* B, const acopf_branches* Lb, co
     }
   }
 
+  // ---- bus-row chunks ---------------------------------------------------------
+  // The bus rows' gather (phase 2) in pieces of about kRowChunk slots, one
+  // lane each, so that a bus with many branches takes one round of loads on
+  // several lanes instead of many rounds on one.  A chunk starts at a run of
+  // equal neighbours (parallel branches are summed inside one chunk) and
+  // records where its entries start in the bus's rows: the positions the
+  // whole-bus walk (one entry per distinct neighbour, va_i's own column
+  // skipped in row vm_i) has reached there.  Buses in processing order; a
+  // bus's chunks never straddle a warp (the rest of the warp idles).
+  {
+    std::vector<int32_t>& rc = hm.rchunk;
+    rc.clear();
+    int32_t lane = 0;
+    auto idle = [&]() {
+      rc.insert(rc.end(), {-1, 0, 0, 0, 0, 0, 0, 0});
+      lane = (lane + 1) & 31;
+    };
+    struct Chunk {
+      int32_t ka, kb, pva, pvmva, pvmvm;
+    };
+    std::vector<Chunk> ch;
+    for (int64_t p = 0; p < nb; ++p) {
+      const int32_t i = hm.porder[p], k0 = hm.pslot_ptr[p], k1 = hm.pslot_ptr[p + 1];
+      const int32_t bva = hm.krowptr[L.VA + i], eva = hm.krowptr[L.VA + i + 1];
+      const int32_t bvm = hm.krowptr[L.VM + i], evm = hm.krowptr[L.VM + i + 1];
+      const int32_t nlo = eva - bva - 1, nu = evm - bvm - nlo - 2;
+      for (int32_t cap = kRowChunk;; cap *= 2) {
+        ch.clear();
+        int32_t pva = bva, pvmva = bvm, pvmvm = bvm + nu + 1;
+        Chunk cur{k0, k0, pva, pvmva, pvmvm};
+        for (int32_t k = k0; k < k1;) {
+          const int32_t j = hm.slot_nbr[k];
+          int32_t r = k;
+          while (r < k1 && hm.slot_nbr[r] == j) ++r;
+          if (k > cur.ka && (k - cur.ka) + (r - k) > cap) {
+            cur.kb = k;
+            ch.push_back(cur);
+            cur = Chunk{k, k, pva, pvmva, pvmvm};
+          }
+          if (j > i && pvmva == bvm + nlo) ++pvmva;
+          ++pvmva;
+          if (j < i) {
+            ++pva;
+            ++pvmvm;
+          }
+          k = r;
+        }
+        cur.kb = k1;
+        ch.push_back(cur);
+        if (ch.size() <= 32) break;
+      }
+      const int32_t nch = int32_t(ch.size());
+      if (lane + nch > 32)
+        while (lane != 0) idle();
+      const int32_t first = lane;
+      for (const Chunk& c : ch) {
+        rc.insert(rc.end(), {i, int32_t(p), c.ka, c.kb, c.pva, c.pvmva, c.pvmvm, first | (nch << 5)});
+        lane = (lane + 1) & 31;
+      }
+    }
+    while (lane != 0) idle();
+    L.nrc = int32_t(rc.size() / 8);
+  }
+
   // ---- bounds -----------------------------------------------------------------
   const double inf = std::numeric_limits<double>::infinity();
   hm.xl.assign(n, 0.0);
