@@ -632,7 +632,8 @@ acopf_status acopf_batch_info(const acopf_batch* batch, int32_t* schedule, int64
  *     longest-admitted one, then least remaining work first); requests join
  *     at the first tick after their upload completes and leave when their
  *     last call is done, so requests that arrive while others run share
- *     launches with them.  A bounded number of ticks is in flight
+ *     launches with them (a tick of one request runs that request's plain
+ *     acopf_eval_assemble launches).  A bounded number of ticks is in flight
  *     (ACOPF_SERVE_OPT_INFLIGHT).
  *   ACOPF_SERVE_FIFO: plain launches.  Each admitted request's calls are
  *     queued as single-instance launches (acopf_eval_assemble's kernels) in
@@ -730,7 +731,7 @@ acopf_status acopf_server_release(acopf_server* server, uint64_t ticket);
 acopf_status acopf_server_get_stats(acopf_server* server, acopf_server_stats* out);
 
 /* Server options (scheduling only; results never change).
- * ACOPF_SERVE_OPT_INFLIGHT (default 4, range 1..16): continuous-mode ticks
+ * ACOPF_SERVE_OPT_INFLIGHT (default 16, range 1..16): continuous-mode ticks
  * queued on the GPU ahead of completion.  More hides the host's per-tick
  * work behind the GPU's; fewer lets a new request join sooner.
  * ACOPF_SERVE_OPT_TICK_WORK (default 60,000, >= 1): the work budget of one

@@ -130,7 +130,7 @@ struct acopf_server {
   int64_t budget = 0;
   int32_t mode = ACOPF_SERVE_CONTINUOUS;
   int32_t max_active = 1;
-  std::atomic<int> max_inflight{4};  // ticks in flight (continuous mode)
+  std::atomic<int> max_inflight{16};  // ticks in flight (continuous mode)
   std::atomic<int64_t> tick_work{kDefaultTickWork};  // work of one tick (continuous mode)
   cudaStream_t stream = nullptr;       // calls, tick tables, output copies
   cudaStream_t copy_stream = nullptr;  // request regions: allocation, inputs, release
@@ -305,6 +305,27 @@ cudaError_t tick(acopf_server* S) {
       work += call_work(cand[j]);
     }
   const size_t A = members.size();
+  if (A == 1) {  // a lone request runs its plain single-instance launches (same results)
+    const int k = S->ring_next;
+    Slot& sl = S->ring[k];
+    cudaError_t e = retire_slot(S, k, true);
+    Req* q = members.front();
+    if (e == cudaSuccess) e = acopf::launch_eval(q->dm, acopf::OUT_ALL, q->args(q->issued), S->stream);
+    if (e != cudaSuccess) return e;
+    if (++q->issued == q->r.n_calls) {
+      e = finish_request(S, q);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(sl.ev, S->stream);
+    if (e != cudaSuccess) return e;
+    sl.busy = true;
+    S->inflight.push_back(k);
+    S->ring_next = (k + 1) % kRing;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stats.ticks++;
+    S->stats.launches += acopf::launches_for(acopf::OUT_ALL);
+    return cudaSuccess;
+  }
   size_t n1 = 0, n2 = 0;
   for (Req* q : members) {
     n1 += q->items1.size();
