@@ -117,6 +117,14 @@ __device__ bool wait_done(const int32_t* flag, int32_t* abort) {
   }
 }
 
+// A kernel launched as a programmatic dependent (see launch_early) may run
+// out of tasks while the kernel before it is still running: before its
+// blocks exit they wait for that kernel's completion, so that the stream's
+// next work sees both finished (a no-op for a kernel launched without it).
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned sm_id() {
   unsigned r;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
@@ -841,6 +849,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_factor_tasks(CholDev d, Ch
       default: break;  // fin: no work
     }
   });
+  wait_prior_grid();
 }
 
 // ---------------------------------------------------------------------------
@@ -1222,10 +1231,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_forward_tasks(CholDev d, C
     else
       forward_large(d, tk.y, y, sL, sv);
   });
+  wait_prior_grid();
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_chol_backward_tasks(CholDev d, CholTasks g,
                                                                       double* __restrict__ x) {
+  // the backward warp tasks may start now: they wait for this kernel's flags
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth], sdi[kCholMaxWidth],
       sz[kSolveZCap];
   const SolveStage S{sL, sv, sdi, sz};
@@ -1257,6 +1269,11 @@ __device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abor
       const int q1 = __ldg(g.dep_ptr + t + 1);
       for (int q = __ldg(g.dep_ptr + t) + lane; q < q1 && ok; q += 32)
         ok = wait_done(g.done + __ldg(g.dep + q), abort);
+      if (g.xdep_ptr) {  // tasks of the graph launched before this one
+        const int x1 = __ldg(g.xdep_ptr + t + 1);
+        for (int q = __ldg(g.xdep_ptr + t) + lane; q < x1 && ok; q += 32)
+          ok = wait_done(g.xdone + __ldg(g.xdep + q), abort);
+      }
       __threadfence();
     }
     ok = __all_sync(0xffffffffu, ok);
@@ -1285,6 +1302,8 @@ __device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abor
 template <bool kForward>
 __global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTasks g,
                                                                 double* __restrict__ v) {
+  // (forward) the block tasks may start now: they wait for this kernel's flags
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double ws_all[kWarps * (kSmallPanel + kCholWarpRows)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* ws = ws_all + warp * (kSmallPanel + kCholWarpRows);
@@ -1294,6 +1313,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTa
     else
       backward_small(d, tk.y, lane, v, ws);
   });
+  wait_prior_grid();
 }
 
 // The factorization's warp tasks: one warp-small supernode per warp, staged
@@ -1419,11 +1439,28 @@ cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, doubl
   return cudaLaunchKernelEx(&cfg, k_chol_factor_tasks, d, t, tol);
 }
 
+// Launches kern with programmatic dependent launch when `early`: it may start
+// once every block of the kernel before it has started (each triggers at its
+// first instruction), and it waits for that kernel's tasks through flags.
+template <typename Kern, typename... Args>
+cudaError_t launch_early(Kern kern, int grid, bool early, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = early ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,
-                                      cudaStream_t s) {
+                                      bool early, cudaStream_t s) {
   if (t.n <= 0) return cudaSuccess;
-  k_chol_forward_tasks<<<std::min(blocks, t.n), kThreads, 0, s>>>(d, t, y);
-  return cudaGetLastError();
+  return launch_early(k_chol_forward_tasks, std::min(blocks, t.n), early, s, d, t, y);
 }
 
 cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
@@ -1434,14 +1471,11 @@ cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, dou
 }
 
 cudaError_t launch_chol_solve_warps(const CholDev& d, const CholTasks& t, double* v, bool forward,
-                                    int blocks, cudaStream_t s) {
+                                    int blocks, bool early, cudaStream_t s) {
   if (t.n <= 0) return cudaSuccess;
   const int grid = std::min(blocks, (t.n + kWarps - 1) / kWarps);
-  if (forward)
-    k_chol_solve_warps<true><<<grid, kThreads, 0, s>>>(d, t, v);
-  else
-    k_chol_solve_warps<false><<<grid, kThreads, 0, s>>>(d, t, v);
-  return cudaGetLastError();
+  if (forward) return launch_early(k_chol_solve_warps<true>, grid, early, s, d, t, v);
+  return launch_early(k_chol_solve_warps<false>, grid, early, s, d, t, v);
 }
 
 }  // namespace acopf

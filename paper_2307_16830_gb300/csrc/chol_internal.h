@@ -96,21 +96,22 @@ size_t chol_task_smem_bytes();
 cudaError_t chol_task_setup(int* blocks_per_sm, int* warp_blocks_per_sm);
 // The factorization, forward and backward solve task kernels with `blocks`
 // persistent blocks (tasks, done flags and counter as described above).
-// `early`: the factorization's task kernel is launched as a programmatic
-// dependent of the warp-task kernel before it, whose flags its tasks wait
-// for (xdep).
+// `early`: the kernel is launched as a programmatic dependent of the
+// kernel before it (the factorization's and the forward solve's warp-task
+// kernels), whose flags its tasks wait for (xdep).
 cudaError_t launch_chol_factor_tasks(const CholDev& d, const CholTasks& t, double tol, int blocks,
                                      bool early, cudaStream_t s);
 cudaError_t launch_chol_forward_tasks(const CholDev& d, const CholTasks& t, double* y, int blocks,
-                                      cudaStream_t s);
+                                      bool early, cudaStream_t s);
 cudaError_t launch_chol_backward_tasks(const CholDev& d, const CholTasks& t, double* x, int blocks,
                                        cudaStream_t s);
 // The factorization's warp tasks (one warp-small supernode per warp, after
 // the bottom levels and before the block-task kernel) with `blocks` blocks.
 cudaError_t launch_chol_factor_warps(const CholDev& d, const CholTasks& t, double tol, int blocks,
                                      cudaStream_t s);
-// The solves' warp tasks (one small supernode per warp) with `blocks` blocks.
+// The solves' warp tasks (one small supernode per warp) with `blocks` blocks;
+// `early` as above (the backward one after the backward block-task kernel).
 cudaError_t launch_chol_solve_warps(const CholDev& d, const CholTasks& t, double* v, bool forward,
-                                    int blocks, cudaStream_t s);
+                                    int blocks, bool early, cudaStream_t s);
 
 }  // namespace acopf

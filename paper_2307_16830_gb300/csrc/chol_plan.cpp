@@ -566,16 +566,42 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
       if (plan.sn_class[size_t(s)] != kSnBottom && !wsmall[size_t(s)])
         fcomp[size_t(s)] = F.add(kTaskBlock, s, 0, 0,
                                  2.0 + double(H[size_t(s)]) * W[size_t(s)] / 2000.0);
-    std::vector<std::vector<int32_t>> fdeps(F.dur.size()), bdeps(F.dur.size());
+    std::vector<std::vector<int32_t>> fdeps(F.dur.size()), bdeps(F.dur.size()),
+        fxdeps(F.dur.size());
     for (int32_t s = 0; s < ns; ++s) {
+      if (fcomp[size_t(s)] >= 0) child_warps(s, fxdeps[size_t(fcomp[size_t(s)])]);
       const int32_t p = sy.sn_parent[size_t(s)];
       if (p < 0 || fcomp[size_t(s)] < 0) continue;
       // s's task needs s's children (forward); s's task needs its parent's (backward)
       fdeps[size_t(fcomp[size_t(p)])].push_back(fcomp[size_t(s)]);
       bdeps[size_t(fcomp[size_t(s)])].push_back(fcomp[size_t(p)]);
     }
-    schedule(F.task, fdeps, F.dur, prm.workers, plan.forward, nullptr, nullptr);
+    // the forward block tasks also wait for their warp-small children's warp
+    // tasks (forward_warp positions): the block kernel may start while the
+    // warp kernel runs
+    schedule(F.task, fdeps, F.dur, prm.workers, plan.forward, nullptr, nullptr, nullptr, &fxdeps);
     schedule(F.task, bdeps, F.dur, prm.workers, plan.backward, nullptr, nullptr);
+    // the backward warp tasks whose parent is a block task wait for it
+    // (backward positions): the warp kernel may start while the block kernel runs
+    {
+      std::vector<int32_t> bpos(static_cast<size_t>(ns), -1);
+      for (int32_t k = 0; k < plan.backward.n_tasks(); ++k)
+        bpos[size_t(plan.backward.task[4 * size_t(k) + 1])] = k;
+      CholGraph& bw = plan.backward_warp;
+      bw.xdep_ptr.assign(size_t(bw.n_tasks()) + 1, 0);
+      bw.xdep.clear();
+      for (int32_t k = 0; k < bw.n_tasks(); ++k) {
+        const int32_t p = sy.sn_parent[size_t(bw.task[4 * size_t(k) + 1])];
+        if (p >= 0 && !wsmall[size_t(p)]) {
+          if (bpos[size_t(p)] < 0) {
+            err = "task plan: a warp-small supernode's parent has no solve task";
+            return ACOPF_E_INVALID_ARG;
+          }
+          bw.xdep.push_back(bpos[size_t(p)]);
+        }
+        bw.xdep_ptr[size_t(k) + 1] = int32_t(bw.xdep.size());
+      }
+    }
   } catch (const std::bad_alloc&) {
     err = "host allocation failed";
     return ACOPF_E_OOM;

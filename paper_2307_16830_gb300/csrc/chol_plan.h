@@ -74,9 +74,12 @@ constexpr int32_t kCholBlockMaxRows = 512;
 // supernode, b = tile row, c = tile column; potrf: a = supernode, b = c =
 // k; upd: a = supernode, b = tile row, c = tile column, k the panel tile
 // column of the product), its dependencies dep[dep_ptr[t] .. dep_ptr[t+1])
-// (all earlier in the list) and, for the factorization's block tasks, the
-// warp tasks it needs xdep[xdep_ptr[t] .. xdep_ptr[t+1]) (positions in
-// forward_warp's list; empty otherwise).
+// (all earlier in the list) and the tasks of the graph launched before it
+// that it needs, xdep[xdep_ptr[t] .. xdep_ptr[t+1]): for the
+// factorization's and the forward solve's block tasks, their warp-small
+// children (positions in forward_warp's list); for the backward solve's
+// warp tasks, a parent solved by a block task (position in backward's
+// list); empty for the other graphs.
 struct CholGraph {
   std::vector<int32_t> task, dep_ptr, dep, xdep_ptr, xdep;
   int32_t n_tasks() const { return int32_t(task.size() / 4); }

@@ -59,7 +59,8 @@ struct acopf_chol {
   int32_t* flags = nullptr;             // the graphs' done flags and counters
   size_t flag_ints = 0;
   // persistent blocks of the task kernels
-  int blocks = 0, warp_blocks = 0, solve_blocks = 0, solve_warp_blocks = 0;
+  int blocks = 0, warp_blocks = 0;
+  int fwd_blocks = 0, fwd_warp_blocks = 0, bwd_blocks = 0, bwd_warp_blocks = 0;  // the solves
   const int64_t* amap = nullptr;
   const int32_t* perm = nullptr;
   double* work = nullptr;       // n: the permuted right-hand side / solution
@@ -76,6 +77,14 @@ struct acopf_chol {
 };
 
 namespace {
+
+// Blocks per SM of the solves' block-task and warp-task kernels.  Backward,
+// the warp kernel starts under the block kernel and they run side by side
+// (one block-task block and three warp-task blocks fit an SM's registers
+// together); forward, the warp kernel fills the GPU (the block tasks' first
+// inputs come late in the warp phase, so sharing SMs measured slower).
+constexpr int kFwdBlocksPerSm = 2, kFwdWarpBlocksPerSm = 4;
+constexpr int kBwdBlocksPerSm = 1, kBwdWarpBlocksPerSm = 3;
 
 void release(acopf_chol* c) {
   if (c->factor_exec) cudaGraphExecDestroy(c->factor_exec);
@@ -156,14 +165,16 @@ cudaError_t record_solve(const acopf_chol* chol, const double* b, double* x, cud
   for (size_t v = 0; e == cudaSuccess && v + 1 < bp.size(); ++v)
     e = acopf::launch_chol_bottom_fwd(d, chol->bot_sn + bp[v], bp[v + 1] - bp[v], chol->work, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_solve_warps(d, chol->tg[1], chol->work, true, chol->solve_warp_blocks, s);
+    e = acopf::launch_chol_solve_warps(d, chol->tg[1], chol->work, true, chol->fwd_warp_blocks,
+                                       false, s);
+  if (e == cudaSuccess)  // under the warp tasks, waiting for their flags
+    e = acopf::launch_chol_forward_tasks(d, chol->tg[2], chol->work, chol->fwd_blocks,
+                                         chol->tg[1].n > 0, s);
   if (e == cudaSuccess)
-    e = acopf::launch_chol_forward_tasks(d, chol->tg[2], chol->work, chol->solve_blocks, s);
-  if (e == cudaSuccess)
-    e = acopf::launch_chol_backward_tasks(d, chol->tg[3], chol->work, chol->solve_blocks, s);
-  if (e == cudaSuccess)
-    e = acopf::launch_chol_solve_warps(d, chol->tg[4], chol->work, false, chol->solve_warp_blocks,
-                                       s);
+    e = acopf::launch_chol_backward_tasks(d, chol->tg[3], chol->work, chol->bwd_blocks, s);
+  if (e == cudaSuccess)  // under the block tasks, waiting for their flags
+    e = acopf::launch_chol_solve_warps(d, chol->tg[4], chol->work, false, chol->bwd_warp_blocks,
+                                       chol->tg[3].n > 0, s);
   for (size_t v = bp.size() - 1; e == cudaSuccess && v > 0; --v)
     e = acopf::launch_chol_bottom_bwd(d, chol->bot_sn + bp[v - 1], bp[v] - bp[v - 1], chol->work, s);
   if (e == cudaSuccess) e = acopf::launch_scatter(x, chol->work, chol->perm, chol->n, s);
@@ -269,14 +280,14 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_glp = p.take<int32_t>(ng + 1), o_glev = p.take<int32_t>(plan.grp_lev.size());
   const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
   const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
-  size_t o_task[5], o_dptr[5], o_dep[5];
+  size_t o_task[5], o_dptr[5], o_dep[5], o_xptr[5], o_xdep[5];
   for (int k = 0; k < 5; ++k) {
     o_task[k] = p.take<int32_t>(graphs[k]->task.size());
     o_dptr[k] = p.take<int32_t>(graphs[k]->dep_ptr.size());
     o_dep[k] = p.take<int32_t>(graphs[k]->dep.size() + 1);
+    o_xptr[k] = p.take<int32_t>(graphs[k]->xdep_ptr.size());
+    o_xdep[k] = p.take<int32_t>(graphs[k]->xdep.size() + 1);
   }
-  const size_t o_xptr = p.take<int32_t>(plan.factor.xdep_ptr.size());
-  const size_t o_xdep = p.take<int32_t>(plan.factor.xdep.size() + 1);
   // done flags and counters: per graph [its n flags, its counter]
   c->flag_ints = size_t(plan.forward_warp.n_tasks()) + 1;  // graph 5
   for (int k = 0; k < 5; ++k) c->flag_ints += size_t(graphs[k]->n_tasks()) + 1;
@@ -323,9 +334,9 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
     up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
     up(o_dep[k], graphs[k]->dep.data(), graphs[k]->dep.size() * 4);
+    up(o_xptr[k], graphs[k]->xdep_ptr.data(), graphs[k]->xdep_ptr.size() * 4);
+    up(o_xdep[k], graphs[k]->xdep.data(), graphs[k]->xdep.size() * 4);
   }
-  up(o_xptr, plan.factor.xdep_ptr.data(), plan.factor.xdep_ptr.size() * 4);
-  up(o_xdep, plan.factor.xdep.data(), plan.factor.xdep.size() * 4);
   up(o_amap, sy.amap.data(), sy.amap.size() * 8);
   up(o_perm, sy.perm.data(), n * 4);
   if (e == cudaSuccess) e = cudaMemset(base + o_status, 0, 2 * sizeof(int32_t));
@@ -339,8 +350,10 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   }
   c->blocks = per_sm * sms;
   c->warp_blocks = warp_per_sm * sms;
-  c->solve_blocks = 2 * sms;
-  c->solve_warp_blocks = 4 * sms;
+  c->fwd_blocks = kFwdBlocksPerSm * sms;
+  c->fwd_warp_blocks = kFwdWarpBlocksPerSm * sms;
+  c->bwd_blocks = kBwdBlocksPerSm * sms;
+  c->bwd_warp_blocks = kBwdWarpBlocksPerSm * sms;
   acopf::CholDev& d = c->dev;
   d.n = sy.n;
   d.sn_first = reinterpret_cast<const int32_t*>(base + o_first);
@@ -378,10 +391,17 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
     t.next = fl + t.n;
     fl += t.n + 1;
   }
-  // the factorization's block tasks also wait for its warp tasks
-  c->tg[0].xdep_ptr = reinterpret_cast<const int32_t*>(base + o_xptr);
-  c->tg[0].xdep = reinterpret_cast<const int32_t*>(base + o_xdep);
-  c->tg[0].xdone = c->tg[5].done;
+  // tasks that wait for the graph launched before theirs: the
+  // factorization's block tasks for its warp tasks, the forward solve's
+  // block tasks for its warp tasks, the backward solve's warp tasks for its
+  // block tasks
+  const int xsrc[3][3] = {{0, 0, 5}, {2, 2, 1}, {4, 4, 3}};  // {tg, graph, tg waited for}
+  for (const auto& x : xsrc) {
+    if (graphs[x[1]]->xdep_ptr.empty()) continue;
+    c->tg[x[0]].xdep_ptr = reinterpret_cast<const int32_t*>(base + o_xptr[x[1]]);
+    c->tg[x[0]].xdep = reinterpret_cast<const int32_t*>(base + o_xdep[x[1]]);
+    c->tg[x[0]].xdone = c->tg[x[2]].done;
+  }
   c->bot_sn = reinterpret_cast<const int32_t*>(base + o_bot);
   c->amap = reinterpret_cast<const int64_t*>(base + o_amap);
   c->perm = reinterpret_cast<const int32_t*>(base + o_perm);

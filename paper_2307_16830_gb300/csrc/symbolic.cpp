@@ -28,6 +28,24 @@ constexpr int32_t kSymbolicThreads = 8;
 constexpr int32_t kRelaxSmallCols = 8, kRelaxSmallRows = 32;
 constexpr double kRelaxSmallZeros = 0.3, kRelaxZeros = 0.05;
 
+// Runs fn(t0, t1) over [0, n) in up to kSymbolicThreads slices (fewer for
+// small n; the calling thread takes the first slice and any a thread could
+// not be started for).
+template <typename Fn>
+void parallel_slices(int32_t n, int64_t work, Fn fn) {
+  const int32_t nth = int32_t(std::min<int64_t>(kSymbolicThreads, 1 + work / 262144));
+  auto lo = [&](int32_t t) { return int32_t(int64_t(n) * t / nth); };
+  std::vector<std::thread> pool;
+  int32_t t = 1;
+  try {
+    for (; t < nth; ++t) pool.emplace_back(fn, lo(t), lo(t + 1));
+  } catch (const std::system_error&) {  // no thread: the slice runs here
+  }
+  for (int32_t u = t; u < nth; ++u) fn(lo(u), lo(u + 1));
+  fn(lo(0), lo(1));
+  for (auto& th : pool) th.join();
+}
+
 }  // namespace
 
 acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
@@ -98,29 +116,41 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     // ipos its inverse), gathered row by row from the adjacency; with
     // `upper`, the entries above the diagonal by rows too (= the lower
     // triangle by columns)
+    // (rows counted, then filled, in parallel slices of the order)
     auto gather_rows = [&](const std::vector<int32_t>& ord, const std::vector<int32_t>& ipos,
                            std::vector<int32_t>& lrp, std::vector<int32_t>& lci,
                            std::vector<int32_t>* urp, std::vector<int32_t>* uci) {
       lrp.assign(size_t(n) + 1, 0);
-      lci.clear();
-      lci.reserve(gi.size() / 2);
-      if (urp) {
-        urp->assign(size_t(n) + 1, 0);
-        uci->clear();
-        uci->reserve(gi.size() / 2);
-      }
-      for (int32_t k = 0; k < n; ++k) {
-        const int32_t v = ord[size_t(k)];
-        for (int32_t q = gp[size_t(v)]; q < gp[size_t(v) + 1]; ++q) {
-          const int32_t a = ipos[size_t(gi[size_t(q)])];
-          if (a < k)
-            lci.push_back(a);
-          else if (urp)
-            uci->push_back(a);
+      if (urp) urp->assign(size_t(n) + 1, 0);
+      parallel_slices(n, int64_t(gi.size()), [&](int32_t k0, int32_t k1) {
+        for (int32_t k = k0; k < k1; ++k) {
+          const int32_t v = ord[size_t(k)];
+          int32_t nlow = 0;
+          for (int32_t q = gp[size_t(v)]; q < gp[size_t(v) + 1]; ++q)
+            nlow += ipos[size_t(gi[size_t(q)])] < k;
+          lrp[size_t(k) + 1] = nlow;
+          if (urp) (*urp)[size_t(k) + 1] = gp[size_t(v) + 1] - gp[size_t(v)] - nlow;
         }
-        lrp[size_t(k) + 1] = int32_t(lci.size());
-        if (urp) (*urp)[size_t(k) + 1] = int32_t(uci->size());
+      });
+      for (int32_t k = 0; k < n; ++k) lrp[size_t(k) + 1] += lrp[size_t(k)];
+      lci.resize(size_t(lrp[size_t(n)]));
+      if (urp) {
+        for (int32_t k = 0; k < n; ++k) (*urp)[size_t(k) + 1] += (*urp)[size_t(k)];
+        uci->resize(size_t((*urp)[size_t(n)]));
       }
+      parallel_slices(n, int64_t(gi.size()), [&](int32_t k0, int32_t k1) {
+        for (int32_t k = k0; k < k1; ++k) {
+          const int32_t v = ord[size_t(k)];
+          int32_t pl = lrp[size_t(k)], pu = urp ? (*urp)[size_t(k)] : 0;
+          for (int32_t q = gp[size_t(v)]; q < gp[size_t(v) + 1]; ++q) {
+            const int32_t a = ipos[size_t(gi[size_t(q)])];
+            if (a < k)
+              lci[size_t(pl++)] = a;
+            else if (urp)
+              (*uci)[size_t(pu++)] = a;
+          }
+        }
+      });
     };
 
     // --- elimination tree of the reordered matrix (Liu) ----------------
@@ -146,30 +176,32 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     }
 
     // --- postorder (children in ascending order, depth first) -----------
-    std::vector<int32_t> post;
+    // Without a search: a parent's number exceeds its children's, so one
+    // ascending pass sums the subtree sizes and places each child's subtree
+    // after its smaller siblings' inside its parent's range (roots one after
+    // another, ascending), one descending pass turns those offsets into
+    // ranges, and each node ends its own range.
+    std::vector<int32_t> post(static_cast<size_t>(n));
     {
-      std::vector<int32_t> head(static_cast<size_t>(n), -1), next(static_cast<size_t>(n), -1);
-      post.reserve(size_t(n));
-      for (int32_t v = n - 1; v >= 0; --v)
-        if (parent[size_t(v)] >= 0) {
-          next[size_t(v)] = head[size_t(parent[size_t(v)])];
-          head[size_t(parent[size_t(v)])] = v;
+      std::vector<int32_t> size(static_cast<size_t>(n), 1), off(static_cast<size_t>(n), 0),
+          acc(static_cast<size_t>(n), 0);
+      for (int32_t v = 0; v < n; ++v)
+        if (parent[size_t(v)] >= 0) size[size_t(parent[size_t(v)])] += size[size_t(v)];
+      int32_t roots = 0;
+      for (int32_t v = 0; v < n; ++v) {
+        const int32_t p = parent[size_t(v)];
+        if (p >= 0) {
+          off[size_t(v)] = acc[size_t(p)];
+          acc[size_t(p)] += size[size_t(v)];
+        } else {
+          off[size_t(v)] = roots;
+          roots += size[size_t(v)];
         }
-      std::vector<int32_t> stack;
-      for (int32_t root = 0; root < n; ++root) {
-        if (parent[size_t(root)] != -1) continue;
-        stack.push_back(root);
-        while (!stack.empty()) {
-          const int32_t v = stack.back();
-          const int32_t c = head[size_t(v)];
-          if (c == -1) {
-            post.push_back(v);
-            stack.pop_back();
-          } else {
-            head[size_t(v)] = next[size_t(c)];
-            stack.push_back(c);
-          }
-        }
+      }
+      for (int32_t v = n - 1; v >= 0; --v) {  // off becomes the first position of v's subtree
+        const int32_t p = parent[size_t(v)];
+        if (p >= 0) off[size_t(v)] += off[size_t(p)];
+        post[size_t(off[size_t(v)] + size[size_t(v)] - 1)] = v;
       }
     }
     // final order: position k holds the renumbered node ordf[k] = md[post[k]],
