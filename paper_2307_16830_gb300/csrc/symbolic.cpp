@@ -98,12 +98,15 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
         }
       }
       gi.resize(ai.size());
-      for (int32_t v = 0; v < n; ++v) {
-        const int32_t o = bfs[size_t(v)];
-        int32_t t = gp[size_t(v)];
-        for (int32_t k = ap[size_t(o)]; k < ap[size_t(o) + 1]; ++k) gi[size_t(t++)] = nid[size_t(ai[size_t(k)])];
-        gp[size_t(v) + 1] = t;
-      }
+      for (int32_t v = 0; v < n; ++v)
+        gp[size_t(v) + 1] = gp[size_t(v)] + ap[size_t(bfs[size_t(v)]) + 1] - ap[size_t(bfs[size_t(v)])];
+      parallel_slices(n, int64_t(ai.size()), [&](int32_t v0, int32_t v1) {
+        for (int32_t v = v0; v < v1; ++v) {
+          const int32_t o = bfs[size_t(v)];
+          int32_t t = gp[size_t(v)];
+          for (int32_t k = ap[size_t(o)]; k < ap[size_t(o) + 1]; ++k) gi[size_t(t++)] = nid[size_t(ai[size_t(k)])];
+        }
+      });
       sy.perm.swap(bfs);  // (for now: the renumbering)
     }
     // --- fill-reducing order: approximate minimum degree (amd.cpp) -------
@@ -227,17 +230,26 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     gather_rows(ordf, ipf, brp, bci, &crp, &cri);
     std::vector<int32_t>().swap(gi);
 
-    // --- column counts (row subtrees) -----------------------------------
+    // --- column counts (row subtrees; rows in parallel slices, each with
+    // its own marks, the counts added atomically) --------------------------
     std::vector<int64_t> cnt(static_cast<size_t>(n), 0);
     std::vector<int32_t> mark(static_cast<size_t>(n), -1), nchild(static_cast<size_t>(n), 0);
-    for (int32_t i = 0; i < n; ++i) {
-      mark[size_t(i)] = i;
-      for (int32_t k = brp[size_t(i)]; k < brp[size_t(i) + 1]; ++k)
-        for (int32_t j = bci[size_t(k)]; j != -1 && mark[size_t(j)] != i; j = parent[size_t(j)]) {
-          mark[size_t(j)] = i;
-          cnt[size_t(j)]++;
-        }
-    }
+    parallel_slices(n, int64_t(bci.size()) * 2, [&](int32_t i0, int32_t i1) {
+      std::vector<int32_t> own;
+      int32_t* mk = mark.data();
+      if (i0 != 0) {  // the first slice uses the shared marks, the others their own
+        own.assign(static_cast<size_t>(n), -1);
+        mk = own.data();
+      }
+      for (int32_t i = i0; i < i1; ++i) {
+        mk[i] = i;
+        for (int32_t k = brp[size_t(i)]; k < brp[size_t(i) + 1]; ++k)
+          for (int32_t j = bci[size_t(k)]; j != -1 && mk[j] != i; j = parent[size_t(j)]) {
+            mk[j] = i;
+            __atomic_fetch_add(&cnt[size_t(j)], int64_t(1), __ATOMIC_RELAXED);
+          }
+      }
+    });
     for (int32_t j = 0; j < n; ++j)
       if (parent[size_t(j)] >= 0) nchild[size_t(parent[size_t(j)])]++;
 
