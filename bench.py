@@ -930,12 +930,27 @@ def main():
         run_reference(args, rank, world)
         return
     r = run_ours(args, rank, world, local)
-    small = run_small_workloads(local) if args.small_workloads and world == 1 else None
-    step = run_step_bench(args, local) if args.step and world == 1 else None
-    chol = run_chol_bench(args, local) if args.chol and world == 1 else None
-    ipm = run_ipm_bench(args, local) if args.ipm and world == 1 else None
-    batch = run_batch_bench(args, local) if args.batch and world == 1 else None
-    serve = run_serve_bench(args, local) if args.serve and world == 1 else None
+    def leg(enabled, fn):
+        """One extra leg on a clean device: Python garbage and PyTorch's cached
+        device memory from the previous legs released first."""
+        if not (enabled and world == 1):
+            return None
+        import gc
+
+        import torch
+        gc.collect()
+        torch.cuda.synchronize(local)
+        torch.cuda.empty_cache()
+        return fn()
+
+    # the served form first: its latencies depend on the host and on device
+    # memory growth, which the other legs would disturb
+    serve = leg(args.serve, lambda: run_serve_bench(args, local))
+    small = leg(args.small_workloads, lambda: run_small_workloads(local))
+    step = leg(args.step, lambda: run_step_bench(args, local))
+    chol = leg(args.chol, lambda: run_chol_bench(args, local))
+    ipm = leg(args.ipm, lambda: run_ipm_bench(args, local))
+    batch = leg(args.batch, lambda: run_batch_bench(args, local))
     if rank != 0:
         return
     cpu = None
