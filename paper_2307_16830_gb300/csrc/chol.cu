@@ -228,9 +228,28 @@ __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int ti
     }
     for (int i = k + 1 + tid; i < h; i += NT) P[size_t(k) * h + i] *= rinv;
     group_sync<NT>();
-    for (int j = k + 1 + warp; j < w; j += NW) {
-      const double ljk = P[size_t(k) * h + j];
-      for (int i = j + lane; i < h; i += 32) P[size_t(j) * h + i] -= P[size_t(k) * h + i] * ljk;
+    if constexpr (NT == 32) {
+      // one warp: the trailing panel entries (j, i), j in (k, w), i in [j, h),
+      // column by column, 32 per round, so every lane has an entry (an FP64
+      // warp instruction costs the same however many lanes are active)
+      int j = k + 1, r = lane;  // entry r of column j (row j + r)
+      while (j < w && r >= h - j) {
+        r -= h - j;
+        ++j;
+      }
+      while (j < w) {
+        P[size_t(j) * h + j + r] -= P[size_t(k) * h + j + r] * P[size_t(k) * h + j];
+        r += 32;
+        while (j < w && r >= h - j) {
+          r -= h - j;
+          ++j;
+        }
+      }
+    } else {
+      for (int j = k + 1 + warp; j < w; j += NW) {
+        const double ljk = P[size_t(k) * h + j];
+        for (int i = j + lane; i < h; i += 32) P[size_t(j) * h + i] -= P[size_t(k) * h + i] * ljk;
+      }
     }
     group_sync<NT>();
   }
