@@ -170,26 +170,30 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_measure(IpmVec v, const dou
 // Accepted step: y <- y - alpha dy (the printed system's Delta y is minus
 // the Newton step of y), z <- z + alpha_z dz, then the safeguard
 // z in [mu/(kappa gap), kappa mu/gap] at the new point (already in x, s).
-__device__ __forceinline__ double reset_z(double z, double gap, double mu, double kappa) {
-  return fmax(fmin(z, kappa * mu / gap), mu / (kappa * gap));
+// (hi_c = kappa mu, lo_c = mu / kappa: one reciprocal of the gap for both limits,
+// within an ulp)
+__device__ __forceinline__ double reset_z(double z, double gap, double hi_c, double lo_c) {
+  const double ig = recip(gap);
+  return fmax(fmin(z, hi_c * ig), lo_c * ig);
 }
 
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_accept(IpmVec v, int n, int m, double alpha,
                                                              double alpha_z, double mu,
                                                              double kappa) {
+  const double hi_c = kappa * mu, lo_c = mu / kappa;
   const int stride = gridDim.x * kIpmThreads;
   for (int j = blockIdx.x * kIpmThreads + threadIdx.x; j < n; j += stride) {
     const double x = v.x[j], lo = v.xl[j], hi = v.xu[j];
-    if (finite_bound(lo)) v.zl_x[j] = reset_z(fma(alpha_z, v.dzl_x[j], v.zl_x[j]), x - lo, mu, kappa);
-    if (finite_bound(hi)) v.zu_x[j] = reset_z(fma(alpha_z, v.dzu_x[j], v.zu_x[j]), hi - x, mu, kappa);
+    if (finite_bound(lo)) v.zl_x[j] = reset_z(fma(alpha_z, v.dzl_x[j], v.zl_x[j]), x - lo, hi_c, lo_c);
+    if (finite_bound(hi)) v.zu_x[j] = reset_z(fma(alpha_z, v.dzu_x[j], v.zu_x[j]), hi - x, hi_c, lo_c);
   }
   for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
     const double s = v.s[r], lo = v.sl[r], hi = v.su[r];
     const double yr = fma(-alpha, v.dy[r], v.y[r]);
     v.y[r] = yr;
     v.ym[r] = -yr;
-    if (finite_bound(lo)) v.zl_s[r] = reset_z(fma(alpha_z, v.dzl_s[r], v.zl_s[r]), s - lo, mu, kappa);
-    if (finite_bound(hi)) v.zu_s[r] = reset_z(fma(alpha_z, v.dzu_s[r], v.zu_s[r]), hi - s, mu, kappa);
+    if (finite_bound(lo)) v.zl_s[r] = reset_z(fma(alpha_z, v.dzl_s[r], v.zl_s[r]), s - lo, hi_c, lo_c);
+    if (finite_bound(hi)) v.zu_s[r] = reset_z(fma(alpha_z, v.dzu_s[r], v.zu_s[r]), hi - s, hi_c, lo_c);
   }
 }
 
