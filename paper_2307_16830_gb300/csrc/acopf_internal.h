@@ -188,7 +188,7 @@ struct DevStep {
   const int32_t* jt_slot;  // nnzj
   const int32_t* jt_row;   // nnzj
   double* w;               // m
-  double* res_part;        // 6 per block of the residual kernel
+  double* res_part;        // kResPart per block of the residual kernel
   int32_t res_blocks;      // its grid (fixed per device, so its sums have a fixed order)
 };
 
@@ -203,11 +203,17 @@ cudaError_t launch_condense(const DevStep& st, const StepIterate& it, const doub
                             double delta_w, double delta_c, double* sigma_x, double* sigma_s,
                             double* q_s, double* rhs, bool pdl, cudaStream_t s);
 // Grid of the residual kernel on a device with `sms` SMs (its scratch holds
-// 6 doubles per block).
+// kResPart doubles per block).
+constexpr int kResPart = 7;
 int residual_blocks(int sms);
+// out[0..8]: E at mu and its parts.
 cudaError_t launch_kkt_residual(const DevStep& st, const StepIterate& it, const double* y,
                                 const double* grad, const double* cons, const double* jvals,
                                 double mu, double* out, cudaStream_t s);
+// The same, and, when mu2 >= 0, out[9] = E at mu2 from the same pass.
+cudaError_t launch_kkt_residual2(const DevStep& st, const StepIterate& it, const double* y,
+                                 const double* grad, const double* cons, const double* jvals,
+                                 double mu, double mu2, double* out, cudaStream_t s);
 cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const double* jvals,
                            double delta_w, double delta_c, const double* sigma_s,
                            const double* q_s, const double* dx, double* ds, double* dy,

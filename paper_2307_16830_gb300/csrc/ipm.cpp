@@ -211,6 +211,27 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
     out_e = hout[0];
     return ACOPF_OK;
   };
+  // E at 0 (the convergence test) and at mu (the barrier test) from one pass.
+  auto residual_pair = [&](double mu2, double& e0, double& e_mu) -> acopf_status {
+    acopf::StepIterate si{};
+    si.x = it.x;
+    si.s = it.s;
+    si.xl = it.xl;
+    si.xu = it.xu;
+    si.sl = it.sl;
+    si.su = it.su;
+    si.zl_x = it.zl_x;
+    si.zu_x = it.zu_x;
+    si.zl_s = it.zl_s;
+    si.zu_s = it.zu_s;
+    cudaError_t err = acopf::launch_kkt_residual2(model->step, si, v.y, v.grad, v.cons, v.jvals,
+                                                  0.0, mu2, B.out, s);
+    if (err == cudaSuccess) err = fetch(10);
+    if (err != cudaSuccess) return cuda_fail(err, "acopf_ipm_solve: residual");
+    e0 = hout[0];
+    e_mu = hout[9];
+    return ACOPF_OK;
+  };
   auto record = [&](int32_t k, int field, double value) {
     if (history && k <= max_iter) history[size_t(k) * ACOPF_IPM_HISTORY_FIELDS + size_t(field)] = value;
   };
@@ -363,7 +384,8 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
 
   for (k = 0; k <= max_iter; ++k) {
     set_iterate();
-    st = residual(0.0, res0);
+    double emu = 0.0;
+    st = residual_pair(mu, res0, emu);
     if (st != ACOPF_OK) return st;
     record(k, 0, f);
     record(k, 1, res0);
@@ -374,11 +396,13 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
       break;
     }
     if (k == max_iter) break;
-    // monotone barrier update, possibly several times
-    while (mu > tol / 10.0) {
-      double emu = 0.0;
-      st = residual(mu, emu);
-      if (st != ACOPF_OK) return st;
+    // monotone barrier update, possibly several times (the first test uses
+    // E at mu from the pass above)
+    for (bool first = true; mu > tol / 10.0; first = false) {
+      if (!first) {
+        st = residual(mu, emu);
+        if (st != ACOPF_OK) return st;
+      }
       if (emu > kKappaEps * mu) break;
       mu = std::max(tol / 10.0, std::min(kKappaMu * mu, std::pow(mu, kThetaMu)));
       filter.assign(1, {theta_max, -INFINITY});

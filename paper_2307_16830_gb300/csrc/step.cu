@@ -15,6 +15,7 @@ namespace acopf {
 namespace {
 
 constexpr int kStepThreads = 256;
+constexpr int kResMax = 4;  // maxima per residual block (kResPart values in all)
 
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 
@@ -145,10 +146,11 @@ int blocks_for(int count) { return (count + kStepThreads - 1) / kStepThreads; }
 // of blocks per device strides over the variables (dual residual grad f -
 // A'y - zl_x + zu_x, complementarity of the variable bounds), then over the
 // rows (y - zl_s + zu_s, g - s, complementarity of the slack bounds, |y|).
-// Each block leaves max |r_d|, max |r_p|, max |r_c|, sum |y|, sum |z| and the
-// count of finite bounds (sums in a fixed order for the fixed grid; maxima
-// are order-free) for k_residual_final, which writes
-// out = [E, max|r_d|, max|r_p|, max|r_c|, ||y||_1, ||z||_1, n_z, s_d, s_c].
+// Each block leaves max |r_d|, max |r_p|, max |r_c|, max |r_c| at a second
+// mu, sum |y|, sum |z| and the count of finite bounds (sums in a fixed order
+// for the fixed grid; maxima are order-free) for k_residual_final, which
+// writes out = [E, max|r_d|, max|r_p|, max|r_c|, ||y||_1, ||z||_1, n_z, s_d,
+// s_c] and, for the two-mu form, out[9] = E at the second mu.
 // Maxima of absolute values are taken on the bit patterns (a non-negative
 // double orders like its bits as an unsigned integer; NaN bits exceed every
 // number's, so a NaN propagates) and counts are integers: both off the FP64
@@ -157,10 +159,14 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffULL;
 }
 
+// DUAL: also max |r_c| at a second barrier parameter mu2 (the iteration's
+// test at mu = 0 and its barrier test at mu from one pass).
+template <bool DUAL>
 __global__ void __launch_bounds__(kStepThreads) k_kkt_residual(
     DevStep st, StepIterate it, const double* __restrict__ y, const double* __restrict__ grad,
-    const double* __restrict__ cons, const double* __restrict__ J, double mu) {
-  unsigned long long mx[3] = {0ull, 0ull, 0ull};  // max |r_d|, |r_p|, |r_c| (bits)
+    const double* __restrict__ cons, const double* __restrict__ J, double mu, double mu2) {
+  // max |r_d|, |r_p|, |r_c|, |r_c at mu2| (bits)
+  unsigned long long mx[kResMax] = {0ull, 0ull, 0ull, 0ull};
   double ysum = 0.0, zsum = 0.0;
   long long nz = 0;
   const int stride = gridDim.x * kStepThreads;
@@ -191,11 +197,13 @@ __global__ void __launch_bounds__(kStepThreads) k_kkt_residual(
     const double lo = ldg(it.xl + j), hi = ldg(it.xu + j);
     if (is_finite_bits(lo)) {
       mx[2] = max(mx[2], abs_bits(fma(zl, x - lo, -mu)));
+      if constexpr (DUAL) mx[3] = max(mx[3], abs_bits(fma(zl, x - lo, -mu2)));
       zsum += fabs(zl);
       ++nz;
     }
     if (is_finite_bits(hi)) {
       mx[2] = max(mx[2], abs_bits(fma(zu, hi - x, -mu)));
+      if constexpr (DUAL) mx[3] = max(mx[3], abs_bits(fma(zu, hi - x, -mu2)));
       zsum += fabs(zu);
       ++nz;
     }
@@ -209,51 +217,53 @@ __global__ void __launch_bounds__(kStepThreads) k_kkt_residual(
     const double lo = ldg(it.sl + r), hi = ldg(it.su + r);
     if (is_finite_bits(lo)) {
       mx[2] = max(mx[2], abs_bits(fma(zl, sr - lo, -mu)));
+      if constexpr (DUAL) mx[3] = max(mx[3], abs_bits(fma(zl, sr - lo, -mu2)));
       zsum += fabs(zl);
       ++nz;
     }
     if (is_finite_bits(hi)) {
       mx[2] = max(mx[2], abs_bits(fma(zu, hi - sr, -mu)));
+      if constexpr (DUAL) mx[3] = max(mx[3], abs_bits(fma(zu, hi - sr, -mu2)));
       zsum += fabs(zu);
       ++nz;
     }
   }
   // Block reduction: shuffle trees (fixed order), then the warps in order.
-  __shared__ unsigned long long shm[kStepThreads / 32][3];
+  __shared__ unsigned long long shm[kStepThreads / 32][kResMax];
   __shared__ double shs[kStepThreads / 32][2];
   __shared__ long long shn[kStepThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) mx[q] = max(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
+    for (int q = 0; q < kResMax; ++q) mx[q] = max(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
     ysum += __shfl_down_sync(0xffffffffu, ysum, o);
     zsum += __shfl_down_sync(0xffffffffu, zsum, o);
     nz += __shfl_down_sync(0xffffffffu, nz, o);
   }
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) shm[warp][q] = mx[q];
+    for (int q = 0; q < kResMax; ++q) shm[warp][q] = mx[q];
     shs[warp][0] = ysum;
     shs[warp][1] = zsum;
     shn[warp] = nz;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long bm[3] = {0ull, 0ull, 0ull};
+    unsigned long long bm[kResMax] = {0ull, 0ull, 0ull, 0ull};
     double bs[2] = {0.0, 0.0};
     long long bn = 0;
     for (int w = 0; w < kStepThreads / 32; ++w) {
-      for (int q = 0; q < 3; ++q) bm[q] = max(bm[q], shm[w][q]);
+      for (int q = 0; q < kResMax; ++q) bm[q] = max(bm[q], shm[w][q]);
       bs[0] += shs[w][0];
       bs[1] += shs[w][1];
       bn += shn[w];
     }
-    double* out = st.res_part + 6 * blockIdx.x;
-    for (int q = 0; q < 3; ++q) out[q] = __longlong_as_double(static_cast<long long>(bm[q]));
-    out[3] = bs[0];
-    out[4] = bs[1];
-    out[5] = static_cast<double>(bn);  // exact below 2^53
+    double* out = st.res_part + kResPart * blockIdx.x;
+    for (int q = 0; q < kResMax; ++q) out[q] = __longlong_as_double(static_cast<long long>(bm[q]));
+    out[4] = bs[0];
+    out[5] = bs[1];
+    out[6] = static_cast<double>(bn);  // exact below 2^53
   }
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -266,60 +276,61 @@ __device__ __forceinline__ double max_bits(double a, double b) {
 
 // One block: the blocks' parts in a fixed order (each thread a strided
 // subset in ascending order, then fixed trees), and the scaled residual.
-__global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int nb,
+__global__ void __launch_bounds__(kStepThreads) k_residual_final(DevStep st, int nb, int dual,
                                                                  double* __restrict__ out) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  double c[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double c[kResPart] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // kResMax maxima, then 3 sums
   constexpr int U = 4;  // blocks fetched per round, all loads in flight together
   for (int b0 = threadIdx.x; b0 < nb; b0 += U * kStepThreads) {
-    double t[U][6];
+    double t[U][kResPart];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int b = b0 + u * kStepThreads;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) t[u][q] = b < nb ? __ldcg(st.res_part + 6 * b + q) : 0.0;
+      for (int q = 0; q < kResPart; ++q) t[u][q] = b < nb ? __ldcg(st.res_part + kResPart * b + q) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], t[u][q]);
+      for (int q = 0; q < kResMax; ++q) c[q] = max_bits(c[q], t[u][q]);
 #pragma unroll
-      for (int q = 3; q < 6; ++q) c[q] += t[u][q];
+      for (int q = kResMax; q < kResPart; ++q) c[q] += t[u][q];
     }
   }
-  __shared__ double sh[kStepThreads / 32][6];
+  __shared__ double sh[kStepThreads / 32][kResPart];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], __shfl_down_sync(0xffffffffu, c[q], o));
+    for (int q = 0; q < kResMax; ++q) c[q] = max_bits(c[q], __shfl_down_sync(0xffffffffu, c[q], o));
 #pragma unroll
-    for (int q = 3; q < 6; ++q) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+    for (int q = kResMax; q < kResPart; ++q) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
   }
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sh[warp][q] = c[q];
+    for (int q = 0; q < kResPart; ++q) sh[warp][q] = c[q];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 0; q < 6; ++q) c[q] = sh[0][q];
+    for (int q = 0; q < kResPart; ++q) c[q] = sh[0][q];
     for (int w = 1; w < kStepThreads / 32; ++w) {
-      for (int q = 0; q < 3; ++q) c[q] = max_bits(c[q], sh[w][q]);
-      for (int q = 3; q < 6; ++q) c[q] += sh[w][q];
+      for (int q = 0; q < kResMax; ++q) c[q] = max_bits(c[q], sh[w][q]);
+      for (int q = kResMax; q < kResPart; ++q) c[q] += sh[w][q];
     }
     const double smax = 100.0;  // s_max of the scaling
-    const double nz = c[5];
-    const double s_d = fmax(smax, (c[3] + c[4]) / (static_cast<double>(st.m) + nz)) / smax;
-    const double s_c = nz > 0.0 ? fmax(smax, c[4] / nz) / smax : 1.0;
+    const double nz = c[6];
+    const double s_d = fmax(smax, (c[4] + c[5]) / (static_cast<double>(st.m) + nz)) / smax;
+    const double s_c = nz > 0.0 ? fmax(smax, c[5] / nz) / smax : 1.0;
     out[0] = fmax(fmax(c[0] / s_d, c[1]), c[2] / s_c);
     out[1] = c[0];
     out[2] = c[1];
     out[3] = c[2];
-    out[4] = c[3];
-    out[5] = c[4];
+    out[4] = c[4];
+    out[5] = c[5];
     out[6] = nz;
     out[7] = s_d;
     out[8] = s_c;
+    if (dual) out[9] = fmax(fmax(c[0] / s_d, c[1]), c[3] / s_c);  // E at the second mu
   }
 }
 
@@ -356,7 +367,19 @@ int residual_blocks(int sms) { return 4 * sms; }
 cudaError_t launch_kkt_residual(const DevStep& st, const StepIterate& it, const double* y,
                                 const double* grad, const double* cons, const double* jvals,
                                 double mu, double* out, cudaStream_t s) {
-  k_kkt_residual<<<st.res_blocks, kStepThreads, 0, s>>>(st, it, y, grad, cons, jvals, mu);
+  return launch_kkt_residual2(st, it, y, grad, cons, jvals, mu, -1.0, out, s);
+}
+
+cudaError_t launch_kkt_residual2(const DevStep& st, const StepIterate& it, const double* y,
+                                 const double* grad, const double* cons, const double* jvals,
+                                 double mu, double mu2, double* out, cudaStream_t s) {
+  const int dual = mu2 >= 0.0;
+  if (dual)
+    k_kkt_residual<true><<<st.res_blocks, kStepThreads, 0, s>>>(st, it, y, grad, cons, jvals, mu,
+                                                                 mu2);
+  else
+    k_kkt_residual<false><<<st.res_blocks, kStepThreads, 0, s>>>(st, it, y, grad, cons, jvals,
+                                                                  mu, 0.0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -368,7 +391,7 @@ cudaError_t launch_kkt_residual(const DevStep& st, const StepIterate& it, const 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_residual_final, st, st.res_blocks, out);
+  return cudaLaunchKernelEx(&cfg, k_residual_final, st, st.res_blocks, dual, out);
 }
 
 cudaError_t launch_recover(const DevStep& st, const StepIterate& it, const double* jvals,

@@ -46,7 +46,7 @@ acopf_status ensure_step(acopf_model* m) {
   cudaError_t ae = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
   if (ae != cudaSuccess) return cuda_fail(ae, "acopf_condense: device attribute");
   const int res_blocks = acopf::residual_blocks(sms > 0 ? sms : 1);
-  const size_t o_rp2 = p.take<double>(6 * size_t(res_blocks));
+  const size_t o_rp2 = p.take<double>(acopf::kResPart * size_t(res_blocks));
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, p.off);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_condense: cudaMalloc");
