@@ -131,13 +131,15 @@ __device__ __forceinline__ unsigned sm_id() {
   return r;
 }
 
-// The persistent loop: take the next task, wait for its dependencies and
-// those in the other graph (warp 0's lanes each watch some of them), run it
-// with the whole block, publish its flag (fence, then a release store);
-// with a trace buffer, record the task's times.
+// The persistent loop: take the next task, load what none of its
+// dependencies write (`pre`, whose result `run` receives), wait for its
+// dependencies and those in the other graph (warp 0's lanes each watch some
+// of them), run it with the whole block, publish its flag (fence, then a
+// release store); with a trace buffer, record the task's times (ready =
+// the dependencies seen done).
 
-template <typename Run>
-__device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Run run) {
+template <typename Pre, typename Run>
+__device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Pre pre, Run run) {
   __shared__ int s_task, s_ok;
   __shared__ unsigned long long s_t0;
   for (;;) {
@@ -148,6 +150,8 @@ __device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Ru
     __syncthreads();
     const int t = s_task;
     if (t >= g.n) return;
+    const int4 tk = __ldg(g.task + t);
+    const auto early = pre(tk);
     if (threadIdx.x < 32) {
       bool ok = true;
       const int q1 = __ldg(g.dep_ptr + t + 1);
@@ -164,9 +168,8 @@ __device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Ru
     }
     __syncthreads();
     if (!s_ok) return;
-    const int4 tk = __ldg(g.task + t);
     const unsigned long long t1 = g.trace && threadIdx.x == 0 ? gpu_clock_ns() : 0ull;
-    run(tk);
+    run(tk, early);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -856,7 +859,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_factor_tasks(CholDev d, Ch
                                                                     double tol) {
   extern __shared__ double smem[];
   int* srel = reinterpret_cast<int*>(smem + kStageDoubles);
-  task_loop(g, d.abort, [&](int4 tk) {
+  task_loop(g, d.abort, [](int4) { return 0; }, [&](int4 tk, int) {
     const int kind = tk.x & 0xff, k = tk.x >> 8;
     switch (kind) {
       case kTaskGroup: group_factor(d, tk.y, tol, smem, srel); break;
@@ -894,66 +897,78 @@ __device__ void add_children_z(const CholDev& d, int t, int tid, int f, int w,
   }
 }
 
-// Forward substitution of one supernode by one warp (small supernodes).
-// The front's right-hand side (y_t, then the update vector z_t, which no
-// one else writes and which starts at zero) is gathered in shared memory:
-// y_t, then the children's update vectors one child after the other (each
-// child's loads issued before the previous child is added).  Then the
-// diagonal block (y_t in the lanes, pivots as stored reciprocals) and
-// z_t = (gathered) - L21 y_t, each stored once.  The panel is staged in
-// the warp's slice `ws` with all its loads in flight.
-__device__ void forward_small(const CholDev& d, int t, int lane, double* __restrict__ y,
-                              double* __restrict__ ws) {
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+// Gather-list entries a row of a solve task keeps in registers from before
+// its dependencies are done (longer lists load the rest afterwards).
+constexpr int kGatherRegs = 4;
+
+// Forward substitution of one supernode by one warp (small supernodes), in
+// two parts.  Before the wait (forward_small_pre): everything no dependency
+// writes: the panel (the factorization's, a kernel before), staged in the
+// warp's slice `ws`; y at the supernode's own columns (no other task writes
+// it); the pivots' reciprocals; each row's gather list.  After it
+// (forward_small_run): the children's update-vector entries, summed per row
+// in child order onto y_t (rows below: onto zero); the diagonal block (y_t
+// in the lanes, row r in lane r); z_t = (gathered) - L21 y_t; each stored
+// once.
+struct FwdSmall {
+  int f, w, h, p0, cnt;
+  double* zt;
+  double y0, di;
+  int idx[kGatherRegs];
+};
+
+__device__ FwdSmall forward_small_pre(const CholDev& d, int t, int lane,
+                                      const double* __restrict__ y, double* __restrict__ ws) {
+  FwdSmall s;
+  s.f = __ldg(d.sn_first + t);
+  s.w = __ldg(d.sn_first + t + 1) - s.f;
+  const int r0 = __ldg(d.sn_rowptr + t);
+  s.h = __ldg(d.sn_rowptr + t + 1) - r0;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
-  double* __restrict__ acc = ws + kSmallPanel;  // h entries: y_t then z_t
-  {
-    double v[kSmallPanel / 32];
+  s.zt = d.Zx + __ldg(d.z_off + t);
+  double v[kSmallPanel / 32];
 #pragma unroll
-    for (int u = 0; u < kSmallPanel / 32; ++u) {
-      const int e = lane + 32 * u;
-      v[u] = e < h * w ? __ldcg(Lt + e) : 0.0;
-    }
-    const double y0 = lane < w ? __ldcg(y + f + lane) : 0.0;
-#pragma unroll
-    for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
-    if (lane < h) acc[lane] = y0;  // rows >= w: 0
+  for (int u = 0; u < kSmallPanel / 32; ++u) {
+    const int e = lane + 32 * u;
+    v[u] = e < s.h * s.w ? __ldcg(Lt + e) : 0.0;
   }
-  const int k0 = __ldg(d.kid_ptr + t), k1 = __ldg(d.kid_ptr + t + 1);
-  int r = 0;
-  double zv = 0.0;
-  auto fetch = [&](int k) {  // lane's entry of child k's update vector and its row
-    const int c = __ldg(d.kid + k);
-    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
-                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
-    r = lane < mc ? __ldg(d.relmap + __ldg(d.rel_off + c) + lane) : -1;
-    zv = lane < mc ? __ldcg(d.Zx + __ldg(d.z_off + c) + lane) : 0.0;
-  };
-  if (k0 < k1) fetch(k0);
+  s.y0 = lane < s.w ? __ldcg(y + s.f + lane) : 0.0;
+  s.di = lane < s.w ? __ldcg(d.Dinv + s.f + lane) : 0.0;
+  s.p0 = lane < s.h ? __ldg(d.fg_ptr + r0 + lane) : 0;
+  s.cnt = lane < s.h ? __ldg(d.fg_ptr + r0 + lane + 1) - s.p0 : 0;
+#pragma unroll
+  for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
+#pragma unroll
+  for (int u = 0; u < kGatherRegs; ++u) s.idx[u] = u < s.cnt ? __ldg(d.fg_idx + s.p0 + u) : 0;
   __syncwarp();
-  for (int k = k0; k < k1; ++k) {
-    const int rr = r;
-    const double vv = zv;
-    if (k + 1 < k1) fetch(k + 1);
-    if (rr >= 0) acc[rr] += vv;  // a child's rows are distinct
-    __syncwarp();
-  }
-  double yv = lane < w ? acc[lane] : 0.0;
-  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
+  return s;
+}
+
+__device__ void forward_small_run(const CholDev& d, const FwdSmall& s, int lane,
+                                  double* __restrict__ y, const double* __restrict__ ws) {
+  double zv[kGatherRegs];
+#pragma unroll
+  for (int u = 0; u < kGatherRegs; ++u) zv[u] = u < s.cnt ? __ldcg(d.Zx + s.idx[u]) : 0.0;
+  double acc = s.y0;  // rows >= w: 0
+#pragma unroll
+  for (int u = 0; u < kGatherRegs; ++u)
+    if (u < s.cnt) acc += zv[u];
+  for (int q = kGatherRegs; q < s.cnt; ++q) acc += __ldcg(d.Zx + __ldg(d.fg_idx + s.p0 + q));
+  const int w = s.w, h = s.h, m = h - w;
+  double yv = lane < w ? acc : 0.0;
   for (int k = 0; k < w; ++k) {
-    const double yk = __shfl_sync(0xffffffffu, yv * di, k);
+    const double yk = __shfl_sync(0xffffffffu, yv * s.di, k);
     if (lane == k) yv = yk;
     if (lane > k && lane < w) yv = fma(-ws[k * h + lane], yk, yv);
   }
-  if (lane < w) __stcg(y + f + lane, yv);
-  double z = lane < m ? acc[w + lane] : 0.0;
+  if (lane < w) __stcg(y + s.f + lane, yv);
+  double z = __shfl_sync(0xffffffffu, acc, (w + lane) & 31);  // row w + lane
+  if (lane >= m) z = 0.0;
   for (int k = 0; k < w; ++k) {
     const double yk = __shfl_sync(0xffffffffu, yv, k);
     if (lane < m) z = fma(-ws[k * h + w + lane], yk, z);
   }
-  if (lane < m) __stcg(zt + lane, z);
+  if (lane < m) __stcg(s.zt + lane, z);
   __syncwarp();  // the slice is reused by the warp's next supernode
 }
 
@@ -995,38 +1010,55 @@ __device__ void forward_large(const CholDev& d, int t, double* __restrict__ y,
 
 // Backward substitution of one supernode by one warp (small supernodes):
 // x_t -= L21' x(R_t below) (fixed reduction trees), then the transposed
-// diagonal block (x_t in the lanes).  Panel staged as in forward_small.
-__device__ void backward_small(const CholDev& d, int t, int lane, double* __restrict__ x,
-                               double* __restrict__ ws) {
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0, m = h - w;
+// diagonal block (x_t in the lanes).  Before the wait: the panel (staged
+// in `ws`), x_t (the forward solve's result: no backward task but this one
+// writes it), the pivots' reciprocals and the rows below; after it: x at
+// those rows (the ancestors' results).
+struct BwdSmall {
+  int f, w, h, ri;
+  double xv, di;
+};
+
+__device__ BwdSmall backward_small_pre(const CholDev& d, int t, int lane,
+                                       const double* __restrict__ x, double* __restrict__ ws) {
+  BwdSmall s;
+  s.f = __ldg(d.sn_first + t);
+  s.w = __ldg(d.sn_first + t + 1) - s.f;
+  const int r0 = __ldg(d.sn_rowptr + t);
+  s.h = __ldg(d.sn_rowptr + t + 1) - r0;
+  const int m = s.h - s.w;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  const int ri = lane < m ? __ldg(d.rowidx + r0 + w + lane) : 0;
-  double xv = lane < w ? __ldcg(x + f + lane) : 0.0;
-  const double di = lane < w ? __ldcg(d.Dinv + f + lane) : 0.0;
-  {
-    double v[kSmallPanel / 32];
+  s.ri = lane < m ? __ldg(d.rowidx + r0 + s.w + lane) : 0;
+  s.xv = lane < s.w ? __ldcg(x + s.f + lane) : 0.0;
+  s.di = lane < s.w ? __ldcg(d.Dinv + s.f + lane) : 0.0;
+  double v[kSmallPanel / 32];
 #pragma unroll
-    for (int u = 0; u < kSmallPanel / 32; ++u) {
-      const int e = lane + 32 * u;
-      v[u] = e < h * w ? __ldcg(Lt + e) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
+  for (int u = 0; u < kSmallPanel / 32; ++u) {
+    const int e = lane + 32 * u;
+    v[u] = e < s.h * s.w ? __ldcg(Lt + e) : 0.0;
   }
-  const double xb = lane < m ? __ldcg(x + ri) : 0.0;
+#pragma unroll
+  for (int u = 0; u < kSmallPanel / 32; ++u) ws[lane + 32 * u] = v[u];
   __syncwarp();
+  return s;
+}
+
+__device__ void backward_small_run(const BwdSmall& s, int lane, double* __restrict__ x,
+                                   const double* __restrict__ ws) {
+  const int w = s.w, h = s.h, m = h - w;
+  const double xb = lane < m ? __ldcg(x + s.ri) : 0.0;
+  double xv = s.xv;
   for (int k = 0; k < w; ++k) {
     double acc = lane < m ? ws[k * h + w + lane] * xb : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == k) xv -= acc;
   }
   for (int k = w - 1; k >= 0; --k) {
-    const double xk = __shfl_sync(0xffffffffu, xv * di, k);
+    const double xk = __shfl_sync(0xffffffffu, xv * s.di, k);
     if (lane == k) xv = xk;
     if (lane < k) xv = fma(-ws[lane * h + k], xk, xv);
   }
-  if (lane < w) __stcg(x + f + lane, xv);
+  if (lane < w) __stcg(x + s.f + lane, xv);
   __syncwarp();
 }
 
@@ -1094,44 +1126,90 @@ __device__ void stage_diag(const CholDev& d, const double* __restrict__ Lt, int 
   for (int i = threadIdx.x; i < w; i += kThreads) S.di[i] = __ldcg(d.Dinv + f + i);
 }
 
-__device__ void forward_staged(const CholDev& d, int t, double* __restrict__ y, const SolveStage& S) {
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int h = __ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t), m = h - w;
+// Threads per row of the forward step's z_t = (gathered) - L21 y_t and per
+// column of the backward step's x_t -= L21' x(below).
+__device__ __forceinline__ int fwd_row_threads(int w) {
+  return w <= kSolveBatch ? 1 : (w <= 2 * kSolveBatch ? 2 : 4);
+}
+__device__ __forceinline__ int bwd_col_threads(int w) {
+  int P = 32;  // the most (a power of two) that fit
+  while (P > 1 && w * P > kThreads) P >>= 1;
+  return P;
+}
+
+// A staged step in two parts, like the warp tasks': before the wait, the
+// diagonal block and pivots into shared memory, the supernode's own entries
+// of y (forward) or x (backward), the thread's row's gather list (forward)
+// or row index below (backward), and the thread's first batch of L21 in
+// registers; after it, the entries the dependencies wrote, then the solve.
+struct StagedPre {
+  bool staged;
+  int f, w, h, r0;
+  int p0, cnt, ri;
+  int idx[kGatherRegs];
+  double lv[kSolveBatch];
+};
+
+__device__ bool staged_shape(const CholDev& d, int t, StagedPre& s) {
+  s.f = __ldg(d.sn_first + t);
+  s.w = __ldg(d.sn_first + t + 1) - s.f;
+  s.r0 = __ldg(d.sn_rowptr + t);
+  s.h = __ldg(d.sn_rowptr + t + 1) - s.r0;
+  s.staged = s.h - s.w <= kSolveZCap;
+  return s.staged;
+}
+
+__device__ StagedPre forward_staged_pre(const CholDev& d, int t, const double* __restrict__ y,
+                                        const SolveStage& S) {
+  StagedPre s;
+  if (!staged_shape(d, t, s)) return s;
+  const int f = s.f, w = s.w, h = s.h, m = h - w, tid = threadIdx.x;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
-  const int tid = threadIdx.x;
+  s.p0 = tid < h ? __ldg(d.fg_ptr + s.r0 + tid) : 0;
+  s.cnt = tid < h ? __ldg(d.fg_ptr + s.r0 + tid + 1) - s.p0 : 0;
+  {
+    const int P = fwd_row_threads(w), part = tid & (P - 1), i = tid / P;
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u) {
+      const int k = part + P * u;
+      s.lv[u] = i < m && k < w ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+    }
+  }
   stage_diag(d, Lt, f, w, h, S);
   for (int i = tid; i < w; i += kThreads) S.v[i] = __ldcg(y + f + i);
-  for (int i = tid; i < m; i += kThreads) S.z[i] = 0.0;
-  __syncthreads();
-  // the children's update vectors, one child at a time (a child's rows are
-  // distinct; two children may share rows)
-  for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
-    const int c = __ldg(d.kid + q);
-    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
-                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
-    const double* __restrict__ zc = d.Zx + __ldg(d.z_off + c);
-    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
-    for (int base = 0; base < mc; base += 4 * kThreads) {
-      double v[4];
-      int r[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int ii = base + u * kThreads + tid;
-        r[u] = ii < mc ? __ldg(rel + ii) : -1;
-        v[u] = ii < mc ? __ldcg(zc + ii) : 0.0;
-      }
+  for (int u = 0; u < kGatherRegs; ++u) s.idx[u] = u < s.cnt ? __ldg(d.fg_idx + s.p0 + u) : 0;
+  return s;
+}
+
+__device__ void forward_staged_run(const CholDev& d, int t, double* __restrict__ y,
+                                   const SolveStage& S, const StagedPre& s) {
+  const int f = s.f, w = s.w, h = s.h, m = h - w, tid = threadIdx.x;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  double* __restrict__ zt = d.Zx + __ldg(d.z_off + t);
+  // the children's update vectors: each row sums its gather list in child
+  // order onto y_t (rows below: onto zero)
+  for (int r = tid; r < h; r += kThreads) {
+    double acc = r < w ? S.v[r] : 0.0;
+    if (r == tid) {
+      double zv[kGatherRegs];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (r[u] < 0) continue;
-        if (r[u] < w)
-          S.v[r[u]] += v[u];
-        else
-          S.z[r[u] - w] += v[u];
-      }
+      for (int u = 0; u < kGatherRegs; ++u) zv[u] = u < s.cnt ? __ldcg(d.Zx + s.idx[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kGatherRegs; ++u)
+        if (u < s.cnt) acc += zv[u];
+      for (int q = kGatherRegs; q < s.cnt; ++q) acc += __ldcg(d.Zx + __ldg(d.fg_idx + s.p0 + q));
+    } else {
+      const int q1 = __ldg(d.fg_ptr + s.r0 + r + 1);
+      for (int q = __ldg(d.fg_ptr + s.r0 + r); q < q1; ++q)
+        acc += __ldcg(d.Zx + __ldg(d.fg_idx + q));
     }
-    __syncthreads();
+    if (r < w)
+      S.v[r] = acc;
+    else
+      S.z[r - w] = acc;
   }
+  __syncthreads();
   if (tid < 32) {  // y_t <- L_tt^-1 y_t
     const int lane = tid;
     double y0 = lane < w ? S.v[lane] : 0.0, y1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
@@ -1155,16 +1233,22 @@ __device__ void forward_staged(const CholDev& d, int t, double* __restrict__ y, 
   __syncthreads();
   for (int i = tid; i < w; i += kThreads) __stcg(y + f + i, S.v[i]);
   // z_t = (gathered) - L21 y_t: each row's dot product split over P threads,
-  // a thread's kSolveBatch loads in flight together
-  const int P = w <= kSolveBatch ? 1 : (w <= 2 * kSolveBatch ? 2 : 4);
+  // a thread's kSolveBatch loads in flight together (the first batch loaded
+  // before the wait)
+  const int P = fwd_row_threads(w);
   const int part = tid & (P - 1);
   for (int i0 = 0; i0 < m; i0 += kThreads / P) {
     const int i = i0 + tid / P;
     double v[kSolveBatch];
+    if (i0 == 0) {
 #pragma unroll
-    for (int u = 0; u < kSolveBatch; ++u) {
-      const int k = part + P * u;
-      v[u] = i < m && k < w ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+      for (int u = 0; u < kSolveBatch; ++u) v[u] = s.lv[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kSolveBatch; ++u) {
+        const int k = part + P * u;
+        v[u] = i < m && k < w ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+      }
     }
     double acc = 0.0;
 #pragma unroll
@@ -1177,29 +1261,51 @@ __device__ void forward_staged(const CholDev& d, int t, double* __restrict__ y, 
   }
 }
 
-__device__ void backward_staged(const CholDev& d, int t, double* __restrict__ x, const SolveStage& S) {
-  const int f = __ldg(d.sn_first + t), w = __ldg(d.sn_first + t + 1) - f;
-  const int r0 = __ldg(d.sn_rowptr + t), h = __ldg(d.sn_rowptr + t + 1) - r0, m = h - w;
+__device__ StagedPre backward_staged_pre(const CholDev& d, int t, const double* __restrict__ x,
+                                         const SolveStage& S) {
+  StagedPre s;
+  if (!staged_shape(d, t, s)) return s;
+  const int f = s.f, w = s.w, h = s.h, m = h - w, tid = threadIdx.x;
   const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
-  const int tid = threadIdx.x, lane = tid & 31;
+  s.ri = tid < m ? __ldg(d.rowidx + s.r0 + w + tid) : 0;
+  {
+    const int P = bwd_col_threads(w), part = tid & (P - 1), k = tid / P;
+#pragma unroll
+    for (int u = 0; u < kSolveBatch; ++u) {
+      const int i = part + P * u;
+      s.lv[u] = k < w && i < m ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+    }
+  }
   stage_diag(d, Lt, f, w, h, S);
   for (int i = tid; i < w; i += kThreads) S.v[i] = __ldcg(x + f + i);
-  for (int i = tid; i < m; i += kThreads) S.z[i] = __ldcg(x + __ldg(d.rowidx + r0 + w + i));
+  return s;
+}
+
+__device__ void backward_staged_run(const CholDev& d, int t, double* __restrict__ x,
+                                    const SolveStage& S, const StagedPre& s) {
+  const int f = s.f, w = s.w, h = s.h, m = h - w, tid = threadIdx.x, lane = tid & 31;
+  const double* __restrict__ Lt = d.Lx + __ldg(d.sn_off + t);
+  for (int i = tid; i < m; i += kThreads)
+    S.z[i] = __ldcg(x + (i == tid ? s.ri : __ldg(d.rowidx + s.r0 + w + i)));
   __syncthreads();
   // x_t -= L21' x(below): column k's dot product by P threads per column
   {
-    int P = 32;  // threads per column: the most (a power of two) that fit
-    while (P > 1 && w * P > kThreads) P >>= 1;
+    const int P = bwd_col_threads(w);
     const int part = tid & (P - 1);
     for (int k0 = 0; k0 < w; k0 += kThreads / P) {
       const int k = k0 + tid / P;
       double acc = 0.0;
       for (int b = 0; b < m; b += P * kSolveBatch) {  // kSolveBatch loads in flight
         double v[kSolveBatch];
+        if (k0 == 0 && b == 0) {
 #pragma unroll
-        for (int u = 0; u < kSolveBatch; ++u) {
-          const int i = b + part + P * u;
-          v[u] = k < w && i < m ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+          for (int u = 0; u < kSolveBatch; ++u) v[u] = s.lv[u];
+        } else {
+#pragma unroll
+          for (int u = 0; u < kSolveBatch; ++u) {
+            const int i = b + part + P * u;
+            v[u] = k < w && i < m ? __ldcg(Lt + size_t(k) * h + w + i) : 0.0;
+          }
         }
 #pragma unroll
         for (int u = 0; u < kSolveBatch; ++u) {
@@ -1233,23 +1339,19 @@ __device__ void backward_staged(const CholDev& d, int t, double* __restrict__ x,
   }
 }
 
-// Whether supernode t's update vector fits the staged solves.
-__device__ __forceinline__ bool solve_staged(const CholDev& d, int t) {
-  return (__ldg(d.sn_rowptr + t + 1) - __ldg(d.sn_rowptr + t)) -
-             (__ldg(d.sn_first + t + 1) - __ldg(d.sn_first + t)) <= kSolveZCap;
-}
-
 __global__ void __launch_bounds__(kThreads, 2) k_chol_forward_tasks(CholDev d, CholTasks g,
                                                                      double* __restrict__ y) {
   __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth], sdi[kCholMaxWidth],
       sz[kSolveZCap];
   const SolveStage S{sL, sv, sdi, sz};
-  task_loop(g, d.abort, [&](int4 tk) {
-    if (solve_staged(d, tk.y))
-      forward_staged(d, tk.y, y, S);
-    else
-      forward_large(d, tk.y, y, sL, sv);
-  });
+  task_loop(
+      g, d.abort, [&](int4 tk) { return forward_staged_pre(d, tk.y, y, S); },
+      [&](int4 tk, const StagedPre& st) {
+        if (st.staged)
+          forward_staged_run(d, tk.y, y, S, st);
+        else
+          forward_large(d, tk.y, y, sL, sv);
+      });
   wait_prior_grid();
 }
 
@@ -1260,19 +1362,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_backward_tasks(CholDev d, 
   __shared__ double sL[kCholMaxWidth * kCholMaxWidth], sv[kCholMaxWidth], sdi[kCholMaxWidth],
       sz[kSolveZCap];
   const SolveStage S{sL, sv, sdi, sz};
-  task_loop(g, d.abort, [&](int4 tk) {
-    if (solve_staged(d, tk.y))
-      backward_staged(d, tk.y, x, S);
-    else
-      backward_large(d, tk.y, x, sL, sv);
-  });
+  task_loop(
+      g, d.abort, [&](int4 tk) { return backward_staged_pre(d, tk.y, x, S); },
+      [&](int4 tk, const StagedPre& st) {
+        if (st.staged)
+          backward_staged_run(d, tk.y, x, S, st);
+        else
+          backward_large(d, tk.y, x, sL, sv);
+      });
 }
 
 // Warp tasks: each warp takes the next task of the list, waits (bounded)
 // for the tasks it depends on, runs it and sets its flag; the same progress
 // argument as task_loop, with warps for blocks.
-template <typename Run>
-__device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abort, Run run) {
+template <typename Pre, typename Run>
+__device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abort, Pre pre,
+                                               Run run) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int t = 0;
@@ -1283,6 +1388,8 @@ __device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abor
     }
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= g.n) return;
+    const int4 tk = __ldg(g.task + t);
+    const auto early = pre(tk);
     bool ok = true;  // the lanes watch the dependencies together
     {
       const int q1 = __ldg(g.dep_ptr + t + 1);
@@ -1297,9 +1404,8 @@ __device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abor
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) return;
-    const int4 tk = __ldg(g.task + t);
     const unsigned long long t1 = g.trace && lane == 0 ? gpu_clock_ns() : 0ull;
-    run(tk);
+    run(tk, early);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
@@ -1326,12 +1432,14 @@ __global__ void __launch_bounds__(kThreads) k_chol_solve_warps(CholDev d, CholTa
   __shared__ double ws_all[kWarps * (kSmallPanel + kCholWarpRows)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* ws = ws_all + warp * (kSmallPanel + kCholWarpRows);
-  warp_task_loop(g, d.abort, [&](int4 tk) {
-    if constexpr (kForward)
-      forward_small(d, tk.y, lane, v, ws);
-    else
-      backward_small(d, tk.y, lane, v, ws);
-  });
+  if constexpr (kForward)
+    warp_task_loop(
+        g, d.abort, [&](int4 tk) { return forward_small_pre(d, tk.y, lane, v, ws); },
+        [&](int4, const FwdSmall& st) { forward_small_run(d, st, lane, v, ws); });
+  else
+    warp_task_loop(
+        g, d.abort, [&](int4 tk) { return backward_small_pre(d, tk.y, lane, v, ws); },
+        [&](int4, const BwdSmall& st) { backward_small_run(st, lane, v, ws); });
   wait_prior_grid();
 }
 
@@ -1347,8 +1455,8 @@ __global__ void __launch_bounds__(kThreads) k_chol_factor_warps(CholDev d, CholT
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* ws = smem + warp * kSmallStage;
   int* wr = reinterpret_cast<int*>(smem + kWarps * kSmallStage) + warp * kCholWarpRows;
-  warp_task_loop(g, d.abort,
-                 [&](int4 tk) { factor_staged<32>(d, tk.y, lane, tol, ws, wr); });
+  warp_task_loop(g, d.abort, [](int4) { return 0; },
+                 [&](int4 tk, int) { factor_staged<32>(d, tk.y, lane, tol, ws, wr); });
 }
 
 constexpr size_t kFactorWarpSmem =

@@ -602,6 +602,37 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
         bw.xdep_ptr[size_t(k) + 1] = int32_t(bw.xdep.size());
       }
     }
+    // --- forward-solve gather lists: counts per row slot, then the entries
+    // child by child (so each slot's list is in child order) --------------
+    if (sy.z_off[size_t(ns)] > int64_t(INT32_MAX)) {
+      err = "task plan: the update vectors exceed 2^31 entries";
+      return ACOPF_E_INVALID_ARG;
+    }
+    const size_t slots = sy.rowidx.size();
+    plan.fg_ptr.assign(slots + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int32_t> fill;
+      if (pass == 1) {
+        for (size_t j = 0; j < slots; ++j) plan.fg_ptr[j + 1] += plan.fg_ptr[j];
+        plan.fg_idx.assign(size_t(plan.fg_ptr[slots]), 0);
+        fill.assign(plan.fg_ptr.begin(), plan.fg_ptr.end() - 1);
+      }
+      for (int32_t t = 0; t < ns; ++t) {
+        const size_t r0 = size_t(sy.sn_rowptr[size_t(t)]);
+        for (int32_t q = sy.kid_ptr[size_t(t)]; q < sy.kid_ptr[size_t(t) + 1]; ++q) {
+          const int32_t c = sy.kid[size_t(q)];
+          const int32_t mc = H[size_t(c)] - W[size_t(c)];
+          const int32_t* rel = sy.relmap.data() + sy.rel_off[size_t(c)];
+          for (int32_t i = 0; i < mc; ++i) {
+            const size_t j = r0 + size_t(rel[i]);
+            if (pass == 0)
+              ++plan.fg_ptr[j + 1];
+            else
+              plan.fg_idx[size_t(fill[j]++)] = int32_t(sy.z_off[size_t(c)] + i);
+          }
+        }
+      }
+    }
   } catch (const std::bad_alloc&) {
     err = "host allocation failed";
     return ACOPF_E_OOM;

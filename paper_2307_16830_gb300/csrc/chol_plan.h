@@ -95,8 +95,15 @@ struct CholGraph {
 // + I] (I = 0 .. tiles of the parent's front) is the first of c's update
 // rows whose parent row lies in tile row I or later (brk_off[c] = 0 for
 // the other supernodes).
+// Forward-solve gather lists: the update-vector entries (offsets into the
+// update vectors, z_off[c] + i) of a supernode's children that add into
+// row position r of supernode t are fg_idx[fg_ptr[j] .. fg_ptr[j+1]),
+// j = sn_rowptr[t] + r, in the order of t's children (each child adds at
+// most once to a row).  A solve task sums them for its own rows, every row
+// in the same order, without a pass per child.
 struct CholPlan {
   std::vector<int8_t> sn_class;
+  std::vector<int32_t> fg_ptr, fg_idx;
   std::vector<int32_t> bot_ptr, bot_sn, bot_stage, brk_off, tile_brk;
   std::vector<int32_t> grp_ptr, grp_sn, grp_lptr, grp_lev;
   // factorization's task kernel; warp tasks (forward_warp, backward_warp:

@@ -280,6 +280,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_glp = p.take<int32_t>(ng + 1), o_glev = p.take<int32_t>(plan.grp_lev.size());
   const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
   const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
+  const size_t o_fgp = p.take<int32_t>(plan.fg_ptr.size()), o_fgi = p.take<int32_t>(plan.fg_idx.size());
   size_t o_task[5], o_dptr[5], o_dep[5], o_xptr[5], o_xdep[5];
   for (int k = 0; k < 5; ++k) {
     o_task[k] = p.take<int32_t>(graphs[k]->task.size());
@@ -330,6 +331,8 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_bot, plan.bot_sn.data(), plan.bot_sn.size() * 4);
   up(o_boff, plan.brk_off.data(), ns * 4);
   up(o_brk, plan.tile_brk.data(), plan.tile_brk.size() * 4);
+  up(o_fgp, plan.fg_ptr.data(), plan.fg_ptr.size() * 4);
+  up(o_fgi, plan.fg_idx.data(), plan.fg_idx.size() * 4);
   for (int k = 0; k < 5; ++k) {
     up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
     up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
@@ -372,6 +375,8 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.grp_lev = reinterpret_cast<const int32_t*>(base + o_glev);
   d.brk_off = reinterpret_cast<const int32_t*>(base + o_boff);
   d.tile_brk = reinterpret_cast<const int32_t*>(base + o_brk);
+  d.fg_ptr = reinterpret_cast<const int32_t*>(base + o_fgp);
+  d.fg_idx = reinterpret_cast<const int32_t*>(base + o_fgi);
   d.Lx = reinterpret_cast<double*>(base + o_lx);
   d.Ux = reinterpret_cast<double*>(base + o_ux);
   d.Zx = reinterpret_cast<double*>(base + o_zx);
