@@ -1048,10 +1048,20 @@ __device__ void backward_small_run(const BwdSmall& s, int lane, double* __restri
   const int w = s.w, h = s.h, m = h - w;
   const double xb = lane < m ? __ldcg(x + s.ri) : 0.0;
   double xv = s.xv;
-  for (int k = 0; k < w; ++k) {
-    double acc = lane < m ? ws[k * h + w + lane] * xb : 0.0;
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == k) xv -= acc;
+  {
+    // x_t[k] -= sum_i L21[i][k] x_b[i]: lane = g wp + k (wp = w rounded up
+    // to a power of two, G = 32 / wp row groups) sums rows g, g + G, ... in
+    // order, then the G partial sums of column k meet in a fixed tree: few
+    // FP64 instructions per column, which bound the warp-task phase
+    const int wp = w <= 1 ? 1 : (w <= 2 ? 2 : (w <= 4 ? 4 : 8)), G = 32 / wp;
+    const int k = lane & (wp - 1), g = lane / wp;
+    double acc = 0.0;
+    for (int i = g; i - g < m; i += G) {
+      const double xi = __shfl_sync(0xffffffffu, xb, i & 31);
+      if (k < w && i < m) acc = fma(ws[k * h + w + i], xi, acc);
+    }
+    for (int o = wp; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane < w) xv -= acc;
   }
   for (int k = w - 1; k >= 0; --k) {
     const double xk = __shfl_sync(0xffffffffu, xv * s.di, k);
@@ -1101,7 +1111,7 @@ __device__ void backward_large(const CholDev& d, int t, double* __restrict__ x,
 // read and written in global memory once.
 constexpr int kSolveZCap = 1024;
 struct SolveStage {
-  double* L;    // w x w diagonal block, column-major (leading dimension w)
+  double* L;    // w x w diagonal block, columns scaled by 1 / L[j][j] (stage_diag)
   double* v;    // w: y_t / x_t
   double* di;   // w: 1 / L[j][j]
   double* z;    // m <= kSolveZCap: update vector / gathered x below
@@ -1110,18 +1120,25 @@ struct SolveStage {
 // Global loads a thread of the staged solves keeps in flight.
 constexpr int kSolveBatch = 16;
 
+// The diagonal block with each column scaled by its pivot's reciprocal,
+// L_tt diag(L_tt)^-1 (unit diagonal, the diagonal itself not stored): the
+// substitutions then carry one FMA per step on their dependent chain, the
+// pivots applied once to the whole vector (forward: after, backward:
+// before).
 __device__ void stage_diag(const CholDev& d, const double* __restrict__ Lt, int f, int w, int h,
                            const SolveStage& S) {
   for (int base = threadIdx.x; base < w * w; base += kSolveBatch * kThreads) {
-    double v[kSolveBatch];
+    double v[kSolveBatch], dk[kSolveBatch];
 #pragma unroll
     for (int u = 0; u < kSolveBatch; ++u) {
       const int idx = base + u * kThreads, k = idx / w, i = idx - k * w;
-      v[u] = idx < w * w && i >= k ? __ldcg(Lt + size_t(k) * h + i) : 0.0;
+      const bool in = idx < w * w && i > k;
+      v[u] = in ? __ldcg(Lt + size_t(k) * h + i) : 0.0;
+      dk[u] = in ? __ldcg(d.Dinv + f + k) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kSolveBatch; ++u)
-      if (base + u * kThreads < w * w) S.L[base + u * kThreads] = v[u];
+      if (base + u * kThreads < w * w) S.L[base + u * kThreads] = v[u] * dk[u];
   }
   for (int i = threadIdx.x; i < w; i += kThreads) S.di[i] = __ldcg(d.Dinv + f + i);
 }
@@ -1210,25 +1227,22 @@ __device__ void forward_staged_run(const CholDev& d, int t, double* __restrict__
       S.z[r - w] = acc;
   }
   __syncthreads();
-  if (tid < 32) {  // y_t <- L_tt^-1 y_t
+  if (tid < 32) {  // y_t <- L_tt^-1 y_t: u = (unit block)^-1 y_t, y_t = u / pivots
     const int lane = tid;
-    double y0 = lane < w ? S.v[lane] : 0.0, y1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
-    const double d0 = lane < w ? S.di[lane] : 0.0, d1 = lane + 32 < w ? S.di[lane + 32] : 0.0;
+    double u0 = lane < w ? S.v[lane] : 0.0, u1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
     for (int k = 0; k < w; ++k) {
       const double* Lk = S.L + k * w;
       if (k < 32) {
-        const double yk = __shfl_sync(0xffffffffu, y0 * d0, k);
-        if (lane == k) y0 = yk;
-        if (lane > k && lane < w) y0 = fma(-Lk[lane], yk, y0);
-        if (lane + 32 < w) y1 = fma(-Lk[lane + 32], yk, y1);
+        const double uk = __shfl_sync(0xffffffffu, u0, k);
+        if (lane > k && lane < w) u0 = fma(-Lk[lane], uk, u0);
+        if (lane + 32 < w) u1 = fma(-Lk[lane + 32], uk, u1);
       } else {
-        const double yk = __shfl_sync(0xffffffffu, y1 * d1, k - 32);
-        if (lane + 32 == k) y1 = yk;
-        if (lane + 32 > k && lane + 32 < w) y1 = fma(-Lk[lane + 32], yk, y1);
+        const double uk = __shfl_sync(0xffffffffu, u1, k - 32);
+        if (lane + 32 > k && lane + 32 < w) u1 = fma(-Lk[lane + 32], uk, u1);
       }
     }
-    if (lane < w) S.v[lane] = y0;
-    if (lane + 32 < w) S.v[lane + 32] = y1;
+    if (lane < w) S.v[lane] = u0 * S.di[lane];
+    if (lane + 32 < w) S.v[lane + 32] = u1 * S.di[lane + 32];
   }
   __syncthreads();
   for (int i = tid; i < w; i += kThreads) __stcg(y + f + i, S.v[i]);
@@ -1318,19 +1332,17 @@ __device__ void backward_staged_run(const CholDev& d, int t, double* __restrict_
     }
   }
   __syncthreads();
-  if (tid < 32) {  // x_t <- L_tt^-T x_t
-    double x0 = lane < w ? S.v[lane] : 0.0, x1 = lane + 32 < w ? S.v[lane + 32] : 0.0;
-    const double d0 = lane < w ? S.di[lane] : 0.0, d1 = lane + 32 < w ? S.di[lane + 32] : 0.0;
+  if (tid < 32) {  // x_t <- L_tt^-T x_t: the pivots first, then the unit block's transpose
+    double x0 = lane < w ? S.v[lane] * S.di[lane] : 0.0;
+    double x1 = lane + 32 < w ? S.v[lane + 32] * S.di[lane + 32] : 0.0;
     for (int k = w - 1; k >= 0; --k) {
-      // row k of L_tt below the diagonal, read by column: L[k][i] = L(i * w + k)
+      // row k of the unit block below the diagonal, read by column: U[k][i] = S.L(i * w + k)
       if (k >= 32) {
-        const double xk = __shfl_sync(0xffffffffu, x1 * d1, k - 32);
-        if (lane + 32 == k) x1 = xk;
+        const double xk = __shfl_sync(0xffffffffu, x1, k - 32);
         if (lane + 32 < k) x1 = fma(-S.L[(lane + 32) * w + k], xk, x1);
         x0 = fma(-S.L[lane * w + k], xk, x0);  // lane < 32 <= k
       } else {
-        const double xk = __shfl_sync(0xffffffffu, x0 * d0, k);
-        if (lane == k) x0 = xk;
+        const double xk = __shfl_sync(0xffffffffu, x0, k);
         if (lane < k) x0 = fma(-S.L[lane * w + k], xk, x0);
       }
     }
