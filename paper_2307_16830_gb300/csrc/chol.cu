@@ -1267,6 +1267,7 @@ __device__ void forward_staged_run(const CholDev& d, int t, double* __restrict__
     double acc = 0.0;
 #pragma unroll
     for (int u = 0; u < kSolveBatch; ++u) {
+      if (P * u >= w) break;  // the same for the whole warp: no empty FP64 issues
       const int k = part + P * u;
       if (k < w) acc = fma(v[u], S.v[k], acc);
     }
@@ -1323,6 +1324,7 @@ __device__ void backward_staged_run(const CholDev& d, int t, double* __restrict_
         }
 #pragma unroll
         for (int u = 0; u < kSolveBatch; ++u) {
+          if (b + P * u >= m) break;  // the same for the whole warp
           const int i = b + part + P * u;
           if (i < m) acc = fma(v[u], S.z[i], acc);
         }
