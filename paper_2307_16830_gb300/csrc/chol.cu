@@ -105,7 +105,7 @@ __device__ bool wait_done(const int32_t* flag, int32_t* abort) {
   if (ld_acquire(flag)) return true;
   const unsigned long long t0 = gpu_clock_ns();
   for (unsigned it = 0;; ++it) {
-    __nanosleep(it < 32 ? 64 : 512);
+    __nanosleep(it < 32 ? 64 : 256);
     if (ld_acquire(flag)) return true;
     if ((it & 31) == 31) {
       if (ld_acquire(abort)) return false;
@@ -164,15 +164,13 @@ __device__ __forceinline__ void task_loop(const CholTasks& g, int32_t* abort, Pr
       }
       ok = __all_sync(0xffffffffu, ok);
       if (threadIdx.x == 0) s_ok = ok;
-      __threadfence();
     }
-    __syncthreads();
+    __syncthreads();  // orders the block's reads after warp 0's acquires
     if (!s_ok) return;
     const unsigned long long t1 = g.trace && threadIdx.x == 0 ? gpu_clock_ns() : 0ull;
     run(tk, early);
-    __syncthreads();
+    __syncthreads();  // the block's writes before thread 0's release
     if (threadIdx.x == 0) {
-      __threadfence();
       st_release(g.done + t, 1);
       if (g.trace) {
         long long* r = g.trace + 6 * size_t(t);
@@ -1414,15 +1412,14 @@ __device__ __forceinline__ void warp_task_loop(const CholTasks& g, int32_t* abor
         for (int q = __ldg(g.xdep_ptr + t) + lane; q < x1 && ok; q += 32)
           ok = wait_done(g.xdone + __ldg(g.xdep + q), abort);
       }
-      __threadfence();
+      __syncwarp();  // orders every lane's reads after the lanes' acquires
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) return;
     const unsigned long long t1 = g.trace && lane == 0 ? gpu_clock_ns() : 0ull;
     run(tk, early);
-    __syncwarp();
+    __syncwarp();  // the lanes' writes before lane 0's release
     if (lane == 0) {
-      __threadfence();
       st_release(g.done + t, 1);
       if (g.trace) {
         long long* r = g.trace + 6 * size_t(t);
