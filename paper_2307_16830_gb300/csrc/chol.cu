@@ -650,8 +650,12 @@ __device__ void tile_potrf(const CholDev& d, int s, int k, double tol, double* s
   }
 }
 
-// Tile (I, J) -= tile (I, k) tile (J, k)' (lower part of a diagonal tile):
-// rows over the lanes, a column per warp and round.
+// Tile (I, J) -= tile (I, k) tile (J, k)' (lower part of a diagonal tile).
+// Off the diagonal: rows over the lanes, a column per warp and round.  On
+// it: the lower triangle's entries (column by column) spread evenly over
+// all threads, so that no warp issues FMAs for the upper triangle (an FP64
+// warp instruction costs the same however few lanes are active; the
+// diagonal updates lie on the factorization's critical path).
 __device__ void tile_upd(const CholDev& d, int s, int I, int J, int k, double* smem) {
   const Front F(d, s);
   int rk, n, r0, nr, c0, nc;
@@ -663,12 +667,27 @@ __device__ void tile_upd(const CholDev& d, int s, int I, int J, int k, double* s
   tile_load(F, r0, nr, rk, n, As);
   tile_load(F, c0, nc, rk, n, Bs);
   __syncthreads();
+  const int ld = F.ld(c0);
+  if (I == J) {  // nr == nc
+    const int ne = nr * (nr + 1) / 2;
+    for (int e = threadIdx.x; e < ne; e += kThreads) {
+      int j = 0, st = 0;  // column j's entries start at st
+      while (st + (nr - j) <= e) {
+        st += nr - j;
+        ++j;
+      }
+      const int i = j + (e - st);
+      double acc = 0.0;
+      for (int q = 0; q < n; ++q) acc = fma(As[q * T + i], Bs[q * T + j], acc);
+      double* C = F.at(r0 + i, c0) + size_t(j) * ld;
+      __stcg(C, __ldcg(C) - acc);
+    }
+    return;
+  }
   const int i = int(threadIdx.x & 31);
   if (i >= nr) return;
   double* C = F.at(r0 + i, c0);
-  const int ld = F.ld(c0);
   for (int j = int(threadIdx.x >> 5); j < nc; j += kWarps) {
-    if (I == J && i < j) continue;
     double acc = 0.0;
     for (int q = 0; q < n; ++q) acc = fma(As[q * T + i], Bs[q * T + j], acc);
     __stcg(C + size_t(j) * ld, __ldcg(C + size_t(j) * ld) - acc);

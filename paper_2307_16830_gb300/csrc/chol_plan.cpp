@@ -455,6 +455,9 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
       return xdeps[size_t(t)];
     };
     std::vector<int32_t> comp(static_cast<size_t>(ns), -1);
+    // a tiled supernode's completion: the last writers of its update
+    // matrix's tiles (its parent's tasks wait for them directly: no join task)
+    std::vector<std::vector<int32_t>> comp_tiles(static_cast<size_t>(ns));
     std::vector<int32_t> grp_task(static_cast<size_t>(ng));
     for (int32_t g = 0; g < ng; ++g) {
       grp_task[size_t(g)] = B.add(kTaskGroup, g, 0, 0, grp_us[size_t(g)]);
@@ -463,8 +466,11 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
     for (int32_t s = 0; s < ns; ++s)
       if (grp[size_t(s)] >= 0) comp[size_t(s)] = grp_task[size_t(grp[size_t(s)])];
     auto child_comps = [&](int32_t s, std::vector<int32_t>& out) {  // bottom: done before
-      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q)
-        if (comp[size_t(sy.kid[size_t(q)])] >= 0) out.push_back(comp[size_t(sy.kid[size_t(q)])]);
+      for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q) {
+        const int32_t k = sy.kid[size_t(q)];
+        if (comp[size_t(k)] >= 0) out.push_back(comp[size_t(k)]);
+        out.insert(out.end(), comp_tiles[size_t(k)].begin(), comp_tiles[size_t(k)].end());
+      }
     };
     auto child_warps = [&](int32_t s, std::vector<int32_t>& out) {
       for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q)
@@ -531,15 +537,13 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
             L(i, j) = u;
           }
       }
-      const int32_t fin = B.add(kTaskFin, s, 0, 0, 0.5);
-      deps.emplace_back();
+      std::vector<int32_t>& ct = comp_tiles[size_t(s)];
       if (nb > nbp) {
         for (int32_t i = nbp; i < nb; ++i)
-          for (int32_t j = nbp; j <= i; ++j) deps.back().push_back(L(i, j));
+          for (int32_t j = nbp; j <= i; ++j) ct.push_back(L(i, j));
       } else {
-        deps.back().push_back(L(nbp - 1, nbp - 1));
+        ct.push_back(L(nbp - 1, nbp - 1));
       }
-      comp[size_t(s)] = fin;
     }
     for (int32_t g = 0; g < ng; ++g) {
       std::vector<int32_t>& d = deps[size_t(grp_task[size_t(g)])];
@@ -548,6 +552,7 @@ acopf_status chol_plan(const CholSymbolic& sy, const CholPlanParams& prm, CholPl
         for (int32_t q = sy.kid_ptr[size_t(s)]; q < sy.kid_ptr[size_t(s) + 1]; ++q) {
           const int32_t k = sy.kid[size_t(q)];
           if (grp[size_t(k)] != g && comp[size_t(k)] >= 0) d.push_back(comp[size_t(k)]);
+          d.insert(d.end(), comp_tiles[size_t(k)].begin(), comp_tiles[size_t(k)].end());
         }
         child_warps(s, xd(grp_task[size_t(g)]));
       }

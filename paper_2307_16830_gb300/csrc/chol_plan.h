@@ -14,8 +14,9 @@
 //           asm (children's update matrices added into one tile), potrf
 //           (Cholesky of a diagonal tile of the panel), trsm (a tile below
 //           it times the inverse transpose of that factor), upd (one tile
-//           minus the product of two trsm tiles) and fin (no work; done
-//           once the supernode's update matrix is complete).
+//           minus the product of two trsm tiles); the parent's tasks wait
+//           for the last writers of the update matrix's tiles (kTaskFin,
+//           a join task with no work, is no longer generated).
 // The small supernodes whose descendants are all small or bottom ones
 // (warp-small) are factored by a kernel of warp tasks, one supernode per
 // warp, in the forward solve's warp list (the same dependencies: children
