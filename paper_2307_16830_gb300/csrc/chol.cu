@@ -303,19 +303,25 @@ __device__ __forceinline__ void tri_advance(int& i, int& j, int m, int step) {
 
 // Extend-add of t's children's update matrices, one child at a time: the
 // entries in t's columns go to the panel P, the rest to the update matrix
-// U.  The child's row map is staged in `srel`; the lower triangle of its
-// update matrix is read NT entries per round, kBatch rounds in flight.
+// U.  A child's descriptor (kid_desc: its update rows, row map and update
+// matrix offsets) is read one child ahead, so each child costs one round of
+// dependent loads; its row map is staged in `srel`, and the lower triangle
+// of its update matrix is read NT entries per round, kBatch rounds in
+// flight.
 template <int NT>
 __device__ void extend_add(const CholDev& d, int t, int tid, double* __restrict__ P, int h,
                            int w, double* __restrict__ U, int* __restrict__ srel) {
   constexpr int kBatch = 8;
   const int m = h - w;
-  for (int q = __ldg(d.kid_ptr + t); q < __ldg(d.kid_ptr + t + 1); ++q) {
-    const int c = __ldg(d.kid + q);
-    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
-                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
-    const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
-    const int32_t* __restrict__ rel = d.relmap + __ldg(d.rel_off + c);
+  const int q0 = __ldg(d.kid_ptr + t), q1 = __ldg(d.kid_ptr + t + 1);
+  int4 next = q0 < q1 ? __ldg(d.kid_desc + q0) : make_int4(0, 0, 0, 0);
+  for (int q = q0; q < q1; ++q) {
+    const int4 kd = next;  // the child's descriptor, loaded one child ahead
+    if (q + 1 < q1) next = __ldg(d.kid_desc + q + 1);
+    const int mc = kd.x;
+    const double* __restrict__ Uc =
+        d.Ux + ((static_cast<int64_t>(kd.w) << 32) | static_cast<uint32_t>(kd.z));
+    const int32_t* __restrict__ rel = d.relmap + kd.y;
     const int nl = mc * (mc + 1) / 2;
     int i = 0, j = 0;
     tri_advance(i, j, mc, tid);

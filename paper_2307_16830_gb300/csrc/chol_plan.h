@@ -121,7 +121,7 @@ struct CholPlan {
 struct CholPlanParams {
   double group_fma = 20000.0;  // work of one group task at most
   int32_t group_members = 64;
-  double tile_fma = 60000.0;  // supernodes above this work are tiled
+  double tile_fma = 30000.0;  // supernodes above this work are tiled
   int32_t workers = 304;       // concurrent blocks the list schedule assumes
   int32_t warps = 4864;        // concurrent warps of the warp tasks
 };

@@ -281,6 +281,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
   const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
   const size_t o_fgp = p.take<int32_t>(plan.fg_ptr.size()), o_fgi = p.take<int32_t>(plan.fg_idx.size());
+  const size_t o_kd = p.take<int32_t>(4 * sy.kid.size());
   size_t o_task[5], o_dptr[5], o_dep[5], o_xptr[5], o_xdep[5];
   for (int k = 0; k < 5; ++k) {
     o_task[k] = p.take<int32_t>(graphs[k]->task.size());
@@ -333,6 +334,24 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   up(o_brk, plan.tile_brk.data(), plan.tile_brk.size() * 4);
   up(o_fgp, plan.fg_ptr.data(), plan.fg_ptr.size() * 4);
   up(o_fgi, plan.fg_idx.data(), plan.fg_idx.size() * 4);
+  {  // children's descriptors for the extend-add
+    std::vector<int32_t> kd;
+    try {
+      kd.resize(4 * sy.kid.size());
+    } catch (const std::bad_alloc&) {
+      release(c);
+      return fail(ACOPF_E_OOM, "host allocation failed");
+    }
+    for (size_t q = 0; q < sy.kid.size(); ++q) {
+      const size_t k = size_t(sy.kid[q]);
+      const int64_t uo = sy.u_off[k];
+      kd[4 * q] = (sy.sn_rowptr[k + 1] - sy.sn_rowptr[k]) - (sy.sn_first[k + 1] - sy.sn_first[k]);
+      kd[4 * q + 1] = sy.rel_off[k];
+      kd[4 * q + 2] = int32_t(uint32_t(uint64_t(uo) & 0xffffffffu));
+      kd[4 * q + 3] = int32_t(uint32_t(uint64_t(uo) >> 32));
+    }
+    up(o_kd, kd.data(), kd.size() * 4);
+  }
   for (int k = 0; k < 5; ++k) {
     up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
     up(o_dptr[k], graphs[k]->dep_ptr.data(), graphs[k]->dep_ptr.size() * 4);
@@ -375,6 +394,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.grp_lev = reinterpret_cast<const int32_t*>(base + o_glev);
   d.brk_off = reinterpret_cast<const int32_t*>(base + o_boff);
   d.tile_brk = reinterpret_cast<const int32_t*>(base + o_brk);
+  d.kid_desc = reinterpret_cast<const int4*>(base + o_kd);
   d.fg_ptr = reinterpret_cast<const int32_t*>(base + o_fgp);
   d.fg_idx = reinterpret_cast<const int32_t*>(base + o_fgi);
   d.Lx = reinterpret_cast<double*>(base + o_lx);
