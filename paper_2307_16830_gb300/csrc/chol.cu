@@ -198,15 +198,14 @@ __device__ __forceinline__ void group_sync() {
 // matrix U of leading dimension m = h - w, both in shared memory)
 // ---------------------------------------------------------------------------
 // Column by column: every thread takes the same pivot and its reciprocal;
-// the trailing columns go one per warp, rows over the lanes.
+// the trailing entries go NT per round across columns.
 // (FP64 is slow on this part: one warp instruction occupies a sub-partition
 // for 64 cycles however many lanes are active, so the pivot's reciprocal
 // square root, a 400-cycle chain, is computed by one warp and shared.)
 template <int NT>
 __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int tid, double tol,
                              int32_t* bad, double* __restrict__ dinv) {
-  constexpr int NW = NT / 32;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int warp = tid >> 5;
   __shared__ double s_rinv;
   for (int k = 0; k < w; ++k) {
     double rinv = 0.0;
@@ -229,65 +228,25 @@ __device__ void factor_panel(double* __restrict__ P, int h, int w, int f, int ti
     }
     for (int i = k + 1 + tid; i < h; i += NT) P[size_t(k) * h + i] *= rinv;
     group_sync<NT>();
-    if constexpr (NT == 32) {
-      // one warp: the trailing panel entries (j, i), j in (k, w), i in [j, h),
-      // column by column, 32 per round, so every lane has an entry (an FP64
-      // warp instruction costs the same however many lanes are active)
-      int j = k + 1, r = lane;  // entry r of column j (row j + r)
+    {
+      // the trailing panel entries (j, i), j in (k, w), i in [j, h), column
+      // by column, NT per round, so every lane has an entry (an FP64 warp
+      // instruction costs the same however many lanes are active)
+      int j = k + 1, r = tid;  // entry r of column j (row j + r)
       while (j < w && r >= h - j) {
         r -= h - j;
         ++j;
       }
       while (j < w) {
         P[size_t(j) * h + j + r] -= P[size_t(k) * h + j + r] * P[size_t(k) * h + j];
-        r += 32;
+        r += NT;
         while (j < w && r >= h - j) {
           r -= h - j;
           ++j;
         }
       }
-    } else {
-      for (int j = k + 1 + warp; j < w; j += NW) {
-        const double ljk = P[size_t(k) * h + j];
-        for (int i = j + lane; i < h; i += 32) P[size_t(j) * h + i] -= P[size_t(k) * h + i] * ljk;
-      }
     }
     group_sync<NT>();
-  }
-}
-
-// U -= L21 L21' on the lower triangle.  A block: a column per warp, rows
-// over the lanes.  A warp: the lower triangle's entries column by column,
-// 32 consecutive ones per round, so every lane has an entry.
-template <int NT>
-__device__ void form_update(const double* __restrict__ P, int h, int w, int tid,
-                            double* __restrict__ U) {
-  constexpr int NW = NT / 32;
-  const int lane = tid & 31, m = h - w;
-  if constexpr (NT == 32) {
-    const int total = m * (m + 1) / 2;
-    int i = lane, j = 0;  // entry `lane` of the triangle: column j, row i
-    while (j < m && i >= m) {
-      i -= m - j - 1;
-      ++j;
-    }
-    for (int e = lane; e < total; e += 32) {
-      double acc = 0.0;
-      for (int k = 0; k < w; ++k) acc = fma(P[size_t(k) * h + w + i], P[size_t(k) * h + w + j], acc);
-      U[size_t(j) * m + i] -= acc;
-      i += 32;  // the entry 32 further on
-      while (j < m && i >= m) {
-        i -= m - j - 1;
-        ++j;
-      }
-    }
-  } else {
-    for (int j = tid >> 5; j < m; j += NW)
-      for (int i = j + lane; i < m; i += 32) {
-        double acc = 0.0;
-        for (int k = 0; k < w; ++k) acc = fma(P[size_t(k) * h + w + i], P[size_t(k) * h + w + j], acc);
-        U[size_t(j) * m + i] -= acc;
-      }
   }
 }
 
@@ -298,6 +257,26 @@ __device__ __forceinline__ void tri_advance(int& i, int& j, int m, int step) {
   while (j < m && i >= m) {
     i -= m - j - 1;
     ++j;
+  }
+}
+
+// U -= L21 L21' on the lower triangle: its entries column by column, NT
+// consecutive ones per round (thread tid takes entries tid, tid + NT, ...),
+// so every lane has an entry (an FP64 warp instruction costs the same
+// however many lanes are active; a column per warp left most lanes of the
+// short columns idle).
+template <int NT>
+__device__ void form_update(const double* __restrict__ P, int h, int w, int tid,
+                            double* __restrict__ U) {
+  const int m = h - w;
+  const int total = m * (m + 1) / 2;
+  int i = 0, j = 0;  // entry tid of the triangle: column j, row i
+  tri_advance(i, j, m, tid);
+  for (int e = tid; e < total; e += NT) {
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(P[size_t(k) * h + w + i], P[size_t(k) * h + w + j], acc);
+    U[size_t(j) * m + i] -= acc;
+    tri_advance(i, j, m, NT);
   }
 }
 
