@@ -57,25 +57,63 @@ acopf_status chol_symbolic(int32_t n, const std::vector<int32_t>& rp,
     // --- the symmetric pattern without its diagonal (both triangles) ------
     std::vector<int32_t> gp(size_t(n) + 1, 0), gi;
     {
-      std::vector<int32_t> ap(size_t(n) + 1, 0), ai;
-      for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k)
-          if (ci[size_t(k)] != i) {
-            ap[size_t(i) + 1]++;
-            ap[size_t(ci[size_t(k)]) + 1]++;
-          }
-      for (int32_t i = 0; i < n; ++i) ap[size_t(i) + 1] += ap[size_t(i)];
-      ai.resize(size_t(ap[size_t(n)]));
-      {
-        std::vector<int32_t> nx(ap.begin(), ap.end() - 1);
-        for (int32_t i = 0; i < n; ++i)
+      // node v's list: its row's lower entries (input order), then the rows
+      // below it that hold v (ascending).  Slices of the rows in parallel:
+      // each slice counts the transposed entries it contributes per node,
+      // a prefix over (node, slice) gives every slice its own cursors, and
+      // the slices (ascending rows) fill in parallel without atomics: the
+      // same lists as a sequential pass.
+      constexpr int32_t S = kSymbolicThreads;
+      std::vector<int32_t> ap(size_t(n) + 1, 0), ai, nlow(static_cast<size_t>(n));
+      std::vector<int32_t> cur(size_t(S) * size_t(n), 0);  // slice q's count, then cursor, of node v
+      auto slice_lo = [&](int32_t q) { return int32_t(int64_t(n) * q / S); };
+      auto by_slice = [&](auto fn) {
+        std::vector<std::thread> pool;
+        int32_t q = 1;
+        try {
+          for (; q < S; ++q) pool.emplace_back(fn, q);
+        } catch (const std::system_error&) {
+        }
+        for (int32_t u = q; u < S; ++u) fn(u);
+        fn(0);
+        for (auto& th : pool) th.join();
+      };
+      by_slice([&](int32_t q) {
+        int32_t* c = cur.data() + size_t(q) * size_t(n);
+        for (int32_t i = slice_lo(q); i < slice_lo(q + 1); ++i) {
+          int32_t nl = 0;
           for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
             const int32_t j = ci[size_t(k)];
             if (j == i) continue;
-            ai[size_t(nx[size_t(i)]++)] = j;
-            ai[size_t(nx[size_t(j)]++)] = i;
+            ++nl;
+            ++c[j];
           }
+          nlow[size_t(i)] = nl;
+        }
+      });
+      for (int32_t v = 0; v < n; ++v) {
+        int32_t o = ap[size_t(v)] + nlow[size_t(v)];
+        for (int32_t q = 0; q < S; ++q) {
+          int32_t& c = cur[size_t(q) * size_t(n) + size_t(v)];
+          const int32_t cnt = c;
+          c = o;
+          o += cnt;
+        }
+        ap[size_t(v) + 1] = o;
       }
+      ai.resize(size_t(ap[size_t(n)]));
+      by_slice([&](int32_t q) {
+        int32_t* c = cur.data() + size_t(q) * size_t(n);
+        for (int32_t i = slice_lo(q); i < slice_lo(q + 1); ++i) {
+          int32_t o = ap[size_t(i)];
+          for (int32_t k = rp[size_t(i)]; k < rp[size_t(i) + 1]; ++k) {
+            const int32_t j = ci[size_t(k)];
+            if (j == i) continue;
+            ai[size_t(o++)] = j;
+            ai[size_t(c[j]++)] = i;
+          }
+        }
+      });
       // --- locality: the nodes renumbered breadth first (each component
       // from its lowest unvisited node), so that the order and the passes
       // after it, which walk the graph, find neighbours near each other in
