@@ -16,8 +16,12 @@ correction to the interior-point reference it cites (Waechter and Biegler
 description, with its default constants: the fraction-to-boundary rule with
 tau = max(tau_min, 1 - mu); the filter line search (switching condition,
 Armijo condition on the barrier objective, sufficient decrease in the
-constraint violation or the barrier objective, filter acceptance; no
-second-order correction); the monotone
+constraint violation or the barrier objective, filter acceptance) with its
+second-order correction (`second_order_correction`: when the first trial
+point is rejected and does not reduce the violation, the same matrix is
+solved again with the constraint residual replaced by
+c_soc = alpha c(x_k) + c(x_trial), at most soc_max times while the violation
+keeps falling by kappa_soc; reading d11); the monotone
 barrier update mu <- max(eps/10, min(kappa_mu mu, mu^theta_mu)) when the
 barrier problem's error is below kappa_eps mu; the inertia correction on
 delta_w (delta_c = 0); the safeguard of the bound multipliers
@@ -37,6 +41,12 @@ Readings:
   and flows at the middle of their bounds (0 when unbounded), pushed into
   the interior; slacks at g(x0) pushed into their bounds; y = 0; bound
   multipliers 1 at finite bounds.
+* (d11) second-order correction: c(x) = g(x) - s; the corrected step is the
+  whole primal-dual solution of the corrected system (x, s and y move by the
+  fraction-to-boundary step alpha_soc along it, the bound multipliers by
+  their own fraction-to-boundary step along its Delta z); the corrected
+  point's switching and Armijo tests use the first trial step alpha_{k,0},
+  as the reference states.
 """
 from __future__ import annotations
 
@@ -50,7 +60,8 @@ from .chol import is_positive_definite, solve_condensed
 from .step import Iterate, condense, kkt_residual, recover
 
 __all__ = ["IpmOptions", "IpmResult", "ipm_start", "ipm_solve", "relaxed_bounds",
-           "push_interior", "fraction_to_boundary", "barrier_objective", "restoration"]
+           "push_interior", "fraction_to_boundary", "barrier_objective", "restoration",
+           "second_order_correction"]
 
 
 @dataclasses.dataclass
@@ -79,6 +90,8 @@ class IpmOptions:
     kappa_w_plus: float = 8.0
     kappa_w_plus_bar: float = 100.0
     max_backtracks: int = 60
+    soc_max: int = 4              # second-order corrections per line search at most (p_max)
+    kappa_soc: float = 0.99       # ... each must cut the violation below this fraction of the last
     resto_max_iter: int = 200     # restoration iterations at most
     resto_stall: int = 10         # ... and without a 1 % decrease of the violation for this many
     resto_mu_min: float = 1e-9    # the restoration's barrier parameter at least
@@ -194,6 +207,23 @@ def _reset_z(z, gap, mu, kappa):
     with np.errstate(divide="ignore", invalid="ignore"):
         out = np.where(np.isfinite(gap) & (z > 0),
                        np.maximum(np.minimum(z, kappa * mu / gap), mu / (kappa * gap)), z)
+    return out
+
+
+def second_order_correction(grid, J, it, kv, dw, c_soc):
+    """One second-order-corrected direction of the filter line search (the
+    interior-point reference the paper cites, reading d11): the Newton system
+    of the iterate `it` (its matrix kv = M_cond with regularisation dw, its
+    right-hand side) with the constraint part -(g - s) replaced by -c_soc.
+    Returns dx, ds, dy (the step of y, reading d7) and the four
+    bound-multiplier steps."""
+    it_soc = dataclasses.replace(it, p_y=-c_soc)
+    c = condense(grid, J, it_soc, dw, 0.0)
+    dx = solve_condensed(grid, kv, c["rhs"][0])
+    r = recover(grid, J, it_soc, dx, dw, 0.0)
+    out = dict(dx=dx, ds=r["ds"][0], dy=-r["dy"][0])
+    for k in ("dzl_x", "dzu_x", "dzl_s", "dzu_s"):
+        out[k] = r[k][0]
     return out
 
 
@@ -383,22 +413,57 @@ def ipm_solve(grid, opts: IpmOptions | None = None, factor_check=None) -> IpmRes
             opts.gamma_theta,
             opts.gamma_phi * theta / (-gphi) if gphi < 0 else np.inf,
             opts.delta * theta ** opts.s_theta / (-gphi) ** opts.s_phi if gphi < 0 else np.inf)
+        def acceptable(tht, pht, a):
+            """"f" (Armijo step), "h" (filter-type step) or None for a trial
+            point of violation tht and barrier objective pht at step a."""
+            if any(tht >= fth and pht >= fph for fth, fph in filt):
+                return None
+            switching = gphi < 0 and a * (-gphi) ** opts.s_phi > opts.delta * theta ** opts.s_theta
+            if switching and theta <= theta_min:
+                return "f" if pht <= phi + opts.eta_phi * a * gphi else None
+            if tht <= (1 - opts.gamma_theta) * theta or pht <= phi - opts.gamma_phi * theta:
+                return "h"
+            return None
+
         alpha = a_max
         accepted = None
-        for _ in range(opts.max_backtracks):
+        n_soc = 0
+        for bt in range(opts.max_backtracks):
             xt, st_ = x + alpha * dx, s + alpha * ds
             ft, ct = objective(grid, xt)[0], constraints(grid, xt)[0]
             tht = theta_of(ct, st_)
             pht = barrier_objective(ft, xt, st_, b, mu)
-            in_filter = any(tht >= fth and pht >= fph for fth, fph in filt)
-            switching = gphi < 0 and alpha * (-gphi) ** opts.s_phi > opts.delta * theta ** opts.s_theta
-            if not in_filter:
-                if switching and theta <= theta_min:
-                    if pht <= phi + opts.eta_phi * alpha * gphi:
-                        accepted = ("f", xt, st_, ft, ct)
+            kind = acceptable(tht, pht, alpha)
+            if kind is not None:
+                accepted = (kind, xt, st_, ft, ct)
+                break
+            if bt == 0 and tht >= theta:
+                # second-order correction: c_soc = alpha c(x_k) + c(x_trial), then
+                # alpha_soc c_soc + c(x_soc) while the violation keeps falling
+                c_soc = alpha * (cons - s) + (ct - st_)
+                th_old = theta
+                for _ in range(opts.soc_max):
+                    n_soc += 1
+                    d = second_order_correction(grid, J, it, kv, dw, c_soc)
+                    a_soc = min(fraction_to_boundary(x, d["dx"], b["xl"], b["xu"], tau),
+                                fraction_to_boundary(s, d["ds"], b["sl"], b["su"], tau))
+                    xs, ss = x + a_soc * d["dx"], s + a_soc * d["ds"]
+                    fs, cs = objective(grid, xs)[0], constraints(grid, xs)[0]
+                    ths = theta_of(cs, ss)
+                    kind = acceptable(ths, barrier_objective(fs, xs, ss, b, mu), a_max)
+                    if kind is not None:
+                        accepted = (kind, xs, ss, fs, cs)
+                        alpha, dy = a_soc, d["dy"]
+                        dzl_x, dzu_x, dzl_s, dzu_s = (d[k] for k in ("dzl_x", "dzu_x", "dzl_s",
+                                                                     "dzu_s"))
+                        a_z = min(_dual_fraction(zl_x, dzl_x, tau), _dual_fraction(zu_x, dzu_x, tau),
+                                  _dual_fraction(zl_s, dzl_s, tau), _dual_fraction(zu_s, dzu_s, tau))
                         break
-                elif tht <= (1 - opts.gamma_theta) * theta or pht <= phi - opts.gamma_phi * theta:
-                    accepted = ("h", xt, st_, ft, ct)
+                    if ths > opts.kappa_soc * th_old:
+                        break
+                    c_soc = a_soc * c_soc + (cs - ss)
+                    th_old = ths
+                if accepted is not None:
                     break
             alpha *= 0.5
             if alpha < alpha_min:
@@ -448,7 +513,7 @@ def ipm_solve(grid, opts: IpmOptions | None = None, factor_check=None) -> IpmRes
             zl_s = _reset_z(zl_s, s - b["sl"], mu, opts.kappa_sigma)
             zu_s = _reset_z(zu_s, b["su"] - s, mu, opts.kappa_sigma)
         grad, J = gradient(grid, x)[0], jacobian(grid, x)[0]
-        history[-1].update(alpha=alpha, alpha_z=a_z, delta_w=dw)
+        history[-1].update(alpha=alpha, alpha_z=a_z, delta_w=dw, soc=n_soc)
     return IpmResult(status=status, iterations=it_count, objective=float(f),
                      residual=float(res0["residual"]) if res0 else np.inf, x=x, s=s, y=y,
                      zl_x=zl_x, zu_x=zu_x, zl_s=zl_s, zu_s=zu_s, mu=mu, history=history)

@@ -11,7 +11,7 @@
 // parameter, regularization) are taken on the host from a few reduced values
 // per step; every vector stays on the device.  The rules and constants are
 // those of the interior-point reference the paper cites for its line
-// search (no second-order correction); a failed line search enters a
+// search, with its second-order correction (reading d11); a failed line search enters a
 // feasibility restoration (reading d10) that returns to the iteration or
 // ends the solve as infeasible.
 #include <algorithm>
@@ -37,6 +37,8 @@ constexpr double kKappaEps = 10.0, kKappaMu = 0.2, kThetaMu = 1.5, kTauMin = 0.9
 constexpr double kBoundPush = 1e-2, kBoundFrac = 1e-2;
 constexpr double kGammaTheta = 1e-5, kGammaPhi = 1e-8, kDelta = 1.0, kSTheta = 1.1, kSPhi = 2.3;
 constexpr double kEtaPhi = 1e-4, kAlphaMinFrac = 0.05, kKappaSigma = 1e10;
+constexpr int kSocMax = 4;          // second-order corrections per line search at most
+constexpr double kKappaSoc = 0.99;  // ... each cutting the violation below this fraction
 constexpr double kDeltaW0 = 1e-4, kDeltaWMin = 1e-20, kDeltaWMax = 1e40;
 constexpr double kKappaWMinus = 1.0 / 3.0, kKappaWPlus = 8.0, kKappaWPlusBar = 100.0;
 constexpr int kMaxBacktracks = 60, kMaxInertiaTries = 200;
@@ -60,6 +62,9 @@ struct Buffers {
   acopf::IpmVec v{};
   double *xl, *xu, *sl, *su, *sigma_x, *sigma_s, *q_s, *rhs, *hvals, *kvals;
   double *xr, *lo_s, *hi_s, *r;  // restoration: proximal centre, pushed slack box, violation
+  // second-order correction: its direction (dx, ds, dy and the bound
+  // multipliers' steps; the rest of an IpmVec is the iterate's), c_soc, -c_soc
+  double *dx2, *ds2, *dy2, *dzl_x2, *dzu_x2, *dzl_s2, *dzu_s2, *c_soc, *py_soc;
   double *f, *ft, *out, *part;  // out: 16 reduced scalars, part: per-block partials
   ~Buffers() {
     if (arena) cudaFree(arena);
@@ -100,7 +105,7 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   Buffers B;
   acopf::ArenaPlan p;
   const size_t N = size_t(n), M = size_t(m);
-  enum { kVecN = 20, kVecM = 27 };
+  enum { kVecN = 20, kVecM = 29 };
   const size_t o_n = p.take<double>(kVecN * N), o_m = p.take<double>(kVecM * M);
   const size_t o_j = p.take<double>(size_t(L.nnzj)), o_h = p.take<double>(size_t(L.nnzh));
   const size_t o_k = p.take<double>(size_t(L.nnzk)), o_s = p.take<double>(32);
@@ -124,6 +129,9 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   v.p_zl_s = mv(12); v.p_zu_s = mv(13); B.sigma_s = mv(14); B.q_s = mv(15); v.ds = mv(16);
   v.dy = mv(17); v.dzl_s = mv(18); v.dzu_s = mv(19);
   B.xr = nv(15); B.lo_s = mv(20); B.hi_s = mv(21); B.r = mv(22);
+  B.dx2 = nv(16); B.dzl_x2 = nv(17); B.dzu_x2 = nv(18);
+  B.ds2 = mv(23); B.dy2 = mv(24); B.dzl_s2 = mv(25); B.dzu_s2 = mv(26); B.c_soc = mv(27);
+  B.py_soc = mv(28);
   v.xl = B.xl; v.xu = B.xu; v.sl = B.sl; v.su = B.su;
   v.jvals = reinterpret_cast<double*>(base + o_j);
   B.hvals = reinterpret_cast<double*>(base + o_h);
@@ -455,38 +463,87 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
       alpha_min = std::min({alpha_min, kGammaPhi * theta / (-gphi),
                             kDelta * std::pow(theta, kSTheta) / std::pow(-gphi, kSPhi)});
     alpha_min *= kAlphaMinFrac;
-    // filter line search
-    double alpha = a_max, ft = 0.0, tht = 0.0, pht = 0.0;
-    int accepted = 0;  // 1: f-type, 2: h-type
-    for (int b = 0; b < kMaxBacktracks; ++b) {
-      e = acopf::launch_ipm_trial(v, n, m, alpha, blocks, s);
-      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: trial point");
-      st = acopf_eval_obj(model, v.xt, B.ft, as);
-      if (st == ACOPF_OK) st = acopf_eval_cons(model, v.xt, v.cons_t, as);
-      if (st != ACOPF_OK) return st;
-      e = acopf::launch_ipm_measure(v, v.xt, v.st, v.cons_t, n, m, blocks, B.part, B.out + 2, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(B.out, B.ft, 8, cudaMemcpyDeviceToDevice, s);
-      if (e == cudaSuccess) e = fetch(4);
-      if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: trial measures");
+    // filter line search: 1 (f-type), 2 (h-type) or 0 for a trial point of
+    // violation tht_ and barrier objective pht_ at step a
+    auto acceptable = [&](double tht_, double pht_, double a) -> int {
+      for (const auto& fe : filter)
+        if (tht_ >= fe.first && pht_ >= fe.second) return 0;
+      const bool switching =
+          gphi < 0.0 && a * std::pow(-gphi, kSPhi) > kDelta * std::pow(theta, kSTheta);
+      if (switching && theta <= theta_min) return pht_ <= phi + kEtaPhi * a * gphi ? 1 : 0;
+      if (tht_ <= (1.0 - kGammaTheta) * theta || pht_ <= phi - kGammaPhi * theta) return 2;
+      return 0;
+    };
+    // the trial point x + a d, s + a d (direction of w): objective, constraints, measures
+    auto trial = [&](const acopf::IpmVec& w, double a) -> acopf_status {
+      cudaError_t err = acopf::launch_ipm_trial(w, n, m, a, blocks, s);
+      if (err != cudaSuccess) return cuda_fail(err, "acopf_ipm_solve: trial point");
+      acopf_status r = acopf_eval_obj(model, v.xt, B.ft, as);
+      if (r == ACOPF_OK) r = acopf_eval_cons(model, v.xt, v.cons_t, as);
+      if (r != ACOPF_OK) return r;
+      err = acopf::launch_ipm_measure(v, v.xt, v.st, v.cons_t, n, m, blocks, B.part, B.out + 2, s);
+      if (err == cudaSuccess) err = cudaMemcpyAsync(B.out, B.ft, 8, cudaMemcpyDeviceToDevice, s);
+      if (err == cudaSuccess) err = fetch(4);
+      if (err != cudaSuccess) return cuda_fail(err, "acopf_ipm_solve: trial measures");
       result->trial_points++;
+      return ACOPF_OK;
+    };
+    // the second-order correction's direction in w (the iterate's vectors,
+    // the correction's step buffers)
+    acopf::IpmVec w = v;
+    w.dx = B.dx2; w.ds = B.ds2; w.dy = B.dy2; w.dzl_x = B.dzl_x2; w.dzu_x = B.dzu_x2;
+    w.dzl_s = B.dzl_s2; w.dzu_s = B.dzu_s2;
+    acopf_iterate it_soc = it;
+    it_soc.p_y = B.py_soc;
+    double alpha = a_max, alpha_z = a_z, ft = 0.0, tht = 0.0, pht = 0.0;
+    int accepted = 0;  // 1: f-type, 2: h-type
+    bool soc_step = false;
+    for (int b = 0; b < kMaxBacktracks; ++b) {
+      st = trial(v, alpha);
+      if (st != ACOPF_OK) return st;
       ft = hout[0];
       tht = hout[2];
       pht = ft - mu * hout[3];
-      bool in_filter = false;
-      for (const auto& fe : filter)
-        if (tht >= fe.first && pht >= fe.second) in_filter = true;
-      const bool switching =
-          gphi < 0.0 && alpha * std::pow(-gphi, kSPhi) > kDelta * std::pow(theta, kSTheta);
-      if (!in_filter) {
-        if (switching && theta <= theta_min) {
-          if (pht <= phi + kEtaPhi * alpha * gphi) {
-            accepted = 1;
+      accepted = acceptable(tht, pht, alpha);
+      if (accepted) break;
+      if (b == 0 && tht >= theta) {
+        // second-order correction: c_soc = alpha c(x_k) + c(x_trial), then
+        // alpha_soc c_soc + c(x_soc) while the violation keeps falling; the
+        // corrected point's tests use the first trial step alpha_{k,0}
+        double th_old = theta, a_c = alpha;
+        const double *c0 = v.cons, *s0 = v.s;
+        for (int q = 0; q < kSocMax && !accepted; ++q) {
+          e = acopf::launch_soc_rhs(B.c_soc, B.py_soc, c0, s0, v.cons_t, v.st, a_c, m, blocks, s);
+          if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: second-order correction");
+          c0 = s0 = nullptr;
+          st = acopf_condense(model, &it_soc, v.jvals, dw, 0.0, B.sigma_x, B.sigma_s, B.q_s, B.rhs,
+                              as);
+          if (st == ACOPF_OK) st = acopf_chol_solve(chol, B.rhs, w.dx, as);
+          if (st == ACOPF_OK)
+            st = acopf_recover_step(model, &it_soc, v.jvals, dw, 0.0, B.sigma_s, B.q_s, w.dx,
+                                    w.ds, w.dy, w.dzl_x, w.dzu_x, w.dzl_s, w.dzu_s, as);
+          if (st != ACOPF_OK) return st;
+          e = acopf::launch_ipm_dir(w, n, m, tau, mu, blocks, B.part, B.out, s);
+          if (e == cudaSuccess) e = fetch(2);
+          if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: second-order correction");
+          const double a_soc = hout[0], az_soc = hout[1];
+          st = trial(w, a_soc);
+          if (st != ACOPF_OK) return st;
+          const double fs = hout[0], ths = hout[2], phs = fs - mu * hout[3];
+          accepted = acceptable(ths, phs, a_max);
+          if (accepted) {
+            soc_step = true;
+            alpha = a_soc;
+            alpha_z = az_soc;
+            ft = fs;
+            tht = ths;
             break;
           }
-        } else if (tht <= (1.0 - kGammaTheta) * theta || pht <= phi - kGammaPhi * theta) {
-          accepted = 2;
-          break;
+          if (ths > kKappaSoc * th_old) break;
+          th_old = ths;
+          a_c = a_soc;
         }
+        if (accepted) break;
       }
       alpha *= 0.5;
       if (alpha < alpha_min) break;
@@ -523,13 +580,20 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
     std::swap(v.cons, v.cons_t);
     f = ft;
     theta = tht;
-    e = acopf::launch_ipm_accept(v, n, m, alpha, a_z, mu, kKappaSigma, blocks, s);
+    {
+      acopf::IpmVec va = v;  // the step taken: the correction's when it was accepted
+      if (soc_step) {
+        va.dx = B.dx2; va.ds = B.ds2; va.dy = B.dy2; va.dzl_x = B.dzl_x2; va.dzu_x = B.dzu_x2;
+        va.dzl_s = B.dzl_s2; va.dzu_s = B.dzu_s2;
+      }
+      e = acopf::launch_ipm_accept(va, n, m, alpha, alpha_z, mu, kKappaSigma, blocks, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: update");
     st = acopf_eval_grad(model, v.x, v.grad, as);
     if (st == ACOPF_OK) st = acopf_eval_jac_coo(model, v.x, v.jvals, as);
     if (st != ACOPF_OK) return st;
     record(k, 4, alpha);
-    record(k, 5, a_z);
+    record(k, 5, alpha_z);
     record(k, 6, dw);
   }
   e = cudaStreamSynchronize(s);

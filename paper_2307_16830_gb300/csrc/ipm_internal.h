@@ -34,6 +34,11 @@ cudaError_t launch_ipm_measure(const IpmVec& v, const double* x, const double* s
                                double* out, cudaStream_t s);
 cudaError_t launch_ipm_accept(const IpmVec& v, int n, int m, double alpha, double alpha_z,
                               double mu, double kappa, int blocks, cudaStream_t s);
+// Second-order correction: c = a (cons - sv) + (ct - st) when cons is not
+// NULL (the first correction), else c = a c + (ct - st); py = -c.
+cudaError_t launch_soc_rhs(double* c, double* py, const double* cons, const double* sv,
+                           const double* ct, const double* st, double a, int m, int blocks,
+                           cudaStream_t s);
 
 // Feasibility restoration.  s = clip(cons, lo_s, hi_s), r = cons - s, w = 1
 // where r != 0 (r, w may be NULL); out[0..1] = sum |r|, sum r^2.

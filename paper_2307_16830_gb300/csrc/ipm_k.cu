@@ -143,6 +143,26 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_trial(IpmVec v, int n, int 
     v.st[r] = fma(alpha, v.ds[r], v.s[r]);
 }
 
+// Second-order correction's constraint residual: c = a (cons - s) + (ct - st)
+// for the first correction (cons, s: the current iterate), c = a c + (ct -
+// st) for the next ones; py = -c, the corrected Newton right-hand side's
+// constraint part.
+__global__ void __launch_bounds__(kIpmThreads) k_soc_rhs(double* __restrict__ c,
+                                                          double* __restrict__ py,
+                                                          const double* __restrict__ cons,
+                                                          const double* __restrict__ sv,
+                                                          const double* __restrict__ ct,
+                                                          const double* __restrict__ st,
+                                                          double a, int m) {
+  const int stride = gridDim.x * kIpmThreads;
+  for (int r = blockIdx.x * kIpmThreads + threadIdx.x; r < m; r += stride) {
+    const double prev = cons ? cons[r] - sv[r] : c[r];
+    const double cr = fma(a, prev, ct[r] - st[r]);
+    c[r] = cr;
+    py[r] = -cr;
+  }
+}
+
 // At a point (x, s) with its constraint values: [sum |g - s|, sum log gaps].
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_measure(IpmVec v, const double* __restrict__ x,
                                                               const double* __restrict__ s,
@@ -383,6 +403,14 @@ cudaError_t launch_ipm_measure(const IpmVec& v, const double* x, const double* s
                                double* out, cudaStream_t s) {
   k_ipm_measure<<<blocks, kIpmThreads, 0, s>>>(v, x, sv, cons, n, m, part);
   k_ipm_final<2, 0><<<1, kIpmThreads, 0, s>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_soc_rhs(double* c, double* py, const double* cons, const double* sv,
+                           const double* ct, const double* st, double a, int m, int blocks,
+                           cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  k_soc_rhs<<<blocks, kIpmThreads, 0, s>>>(c, py, cons, sv, ct, st, a, m);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,12 @@
 * The solution on the half-loaded 30-bus network matches an independent
   solver (scipy's SLSQP from the same start) and satisfies the bounds and
   the relaxed constraints.
+* The second-order correction (reading d11): its direction solves the same
+  linearization with the constraint residual replaced by c_soc, i.e. the
+  constraint row moves by -eps c_soc and the other rows of Eq. first by
+  -eps F, checked from the callbacks alone; the opposite sign of c_soc
+  fails; on the half-loaded 7-bus edge case the solve takes a corrected
+  step and converges to the point the solve without corrections reaches.
 * The initial-point and step-bound rules against hand values.
 * The feasibility restoration (reading d10): on the 30-bus network at 0.8
   and 1.0 times its loads, which have no feasible point, the solve stops as
@@ -66,6 +72,62 @@ def _newton_check(dy_sign):
                      z1, mu)
     return [np.max(np.abs(F1[i] - (1 - eps) * F0[i])) / (eps * np.max(np.abs(F0[i])))
             for i in range(7)]
+
+
+def _soc_check(c_sign):
+    """Relative errors of the corrected direction against the linearized
+    conditions: rows 0, 1, 3-6 of Eq. first scale by (1 - eps), the
+    constraint row moves by -eps c_soc (c_sign = -1 plants a sign mistake)."""
+    g = synth.workload_grid("30bus-opf")
+    L = oracle.layout(g)
+    st = ipm_start(g, IpmOptions())
+    b = {k: st[k] for k in ("xl", "xu", "sl", "su")}
+    rng = np.random.default_rng(1)
+    x, s = st["x"], st["s"]
+    y = rng.standard_normal(L.m) * 0.1
+    z = {k: st[k] * (1 + rng.random(st[k].size)) for k in ("zl_x", "zu_x", "zl_s", "zu_s")}
+    mu = 0.1
+    F0 = _conditions(g, b, x, s, y, z, mu)
+    J = oracle.jacobian(g, x)[0]
+    it = oracle.Iterate(x=x, s=s, **b, **z, p_x=-F0[0], p_s=-F0[1], p_y=-F0[2], p_zl_x=-F0[3],
+                        p_zu_x=-F0[4], p_zl_s=-F0[5], p_zu_s=-F0[6])
+    H = oracle.hessian(g, x, -y, 1.0)[0]
+    c = oracle.condense(g, J, it, 0.0, 0.0)
+    kv, _ = oracle.condensed_kkt(g, H, J, c["sigma_x"][0], c["sigma_s"][0], 0.0, 0.0)
+    c_soc = 0.7 * F0[2] + 0.05 * rng.standard_normal(L.m) * np.max(np.abs(F0[2]))
+    d = oracle.second_order_correction(g, J, it, kv, 0.0, c_sign * c_soc)
+    eps = 1e-7
+    z1 = {k: z[k] + eps * d["d" + k] for k in z}
+    F1 = _conditions(g, b, x + eps * d["dx"], s + eps * d["ds"], y + eps * d["dy"], z1, mu)
+    err = []
+    for i in range(7):
+        want = F0[i] - eps * (c_soc if i == 2 else F0[i])
+        scale = np.max(np.abs(c_soc if i == 2 else F0[i]))
+        err.append(np.max(np.abs(F1[i] - want)) / (eps * scale))
+    return err
+
+
+def test_second_order_correction_solves_the_corrected_linearization():
+    err = _soc_check(1.0)
+    assert max(err) < 1e-3, err
+
+
+def test_opposite_sign_of_the_correction_fails():
+    err = _soc_check(-1.0)
+    assert err[2] > 0.1, err
+
+
+def test_corrected_step_taken_and_solution_unchanged():
+    g = synth.make_edge_case_grid(7)
+    g = dataclasses.replace(g, Pd=g.Pd * 0.5, Qd=g.Qd * 0.5)
+    r = oracle.ipm_solve(g, IpmOptions(tol=1e-4))
+    assert r.status == "converged", r.status
+    assert sum(h.get("soc", 0) for h in r.history) >= 1
+    # the same point (to the tolerance) as without corrections
+    r0 = oracle.ipm_solve(g, IpmOptions(tol=1e-4, soc_max=0))
+    assert r0.status == "converged"
+    assert abs(r.objective - r0.objective) <= 1e-4 * abs(r0.objective)
+    assert np.max(np.abs(r.x - r0.x)) <= 1e-2
 
 
 def test_newton_step_solves_the_linearized_conditions():
