@@ -375,7 +375,12 @@ acopf_status acopf_chol_get_trace(acopf_chol* chol, int32_t which, int64_t* out,
  * correction on delta_w (delta_c = 0), solve and step recovery (the printed
  * Delta y is minus the Newton step of y), the fraction-to-boundary step
  * bounds and the filter line search of the interior-point reference the
- * paper cites (its default constants; no second-order correction).  A step
+ * paper cites (its default constants), with its second-order correction:
+ * when the first trial point is rejected without reducing the constraint
+ * violation, the factored system is solved again with the constraint
+ * residual replaced by alpha c(x) + c(x_trial) (up to 4 times while the
+ * violation keeps falling by 1 %), and an accepted corrected point moves
+ * the whole iterate along the corrected direction.  A step
  * below the line search's minimum enters a feasibility restoration: Gauss-
  * Newton steps on 1/2 ||g(x) - clip(g(x))||^2 (slacks following g, clipped
  * onto their box pushed inside) plus a log barrier on x's bounds and a
