@@ -847,7 +847,7 @@ def run_reference(args, rank, world):
     """The CPU oracle as the reference arm: each step is one full oracle
     evaluate-and-assemble call on the benchmark's own workload (the
     80,000-bus grid by default) at a fresh point, on one host core.  At most
-    REF_MAX_CALLS calls are timed (and at most 2 untimed ones run first), so
+    REF_MAX_CALLS calls are timed (and at most 3 untimed ones run first), so
     the run ends within a few minutes; the line reports the calls timed."""
     if rank != 0:
         return
@@ -856,7 +856,7 @@ def run_reference(args, rank, world):
     seed = synth.WORKLOADS[args.workload]["seed"]
     st_full = oracle.kkt_structure(full)
     steps = min(args.steps, REF_MAX_CALLS)
-    warm = min(args.warmup, 2)
+    warm = min(args.warmup, 3)
     pts = [synth.make_point(full, synth.point_seed(seed, 9000 + k)) for k in range(warm + steps)]
     for k in range(warm):
         oracle.eval_assemble(full, pts[k], structure=st_full)
