@@ -455,15 +455,23 @@ __device__ void tile_asm(const CholDev& d, int s, int I, int J, double* smem) {
   F.span(J, c0, nc);
   double* S = smem;
   tile_load(F, r0, nr, c0, nc, S);
-  for (int q = __ldg(d.kid_ptr + s); q < __ldg(d.kid_ptr + s + 1); ++q) {
-    const int c = __ldg(d.kid + q);
-    const int mc = (__ldg(d.sn_rowptr + c + 1) - __ldg(d.sn_rowptr + c)) -
-                   (__ldg(d.sn_first + c + 1) - __ldg(d.sn_first + c));
-    const int32_t* rel = d.relmap + __ldg(d.rel_off + c);
-    const int32_t* brk = d.tile_brk + __ldg(d.brk_off + c);
+  // children's descriptors and tile breakpoints, read one child ahead
+  const int q0 = __ldg(d.kid_ptr + s), q1 = __ldg(d.kid_ptr + s + 1);
+  int4 next = q0 < q1 ? __ldg(d.kid_desc + q0) : make_int4(0, 0, 0, 0);
+  int next_brk = q0 < q1 ? __ldg(d.kid_brk + q0) : 0;
+  for (int q = q0; q < q1; ++q) {
+    const int4 kd = next;
+    const int32_t* brk = d.tile_brk + next_brk;
+    if (q + 1 < q1) {
+      next = __ldg(d.kid_desc + q + 1);
+      next_brk = __ldg(d.kid_brk + q + 1);
+    }
+    const int mc = kd.x;
+    const int32_t* rel = d.relmap + kd.y;
     const int ia = __ldg(brk + I), ni = __ldg(brk + I + 1) - ia;
     const int ja = __ldg(brk + J), nj = __ldg(brk + J + 1) - ja;
-    const double* __restrict__ Uc = d.Ux + __ldg(d.u_off + c);
+    const double* __restrict__ Uc =
+        d.Ux + ((static_cast<int64_t>(kd.w) << 32) | static_cast<uint32_t>(kd.z));
     __syncthreads();  // the tile is loaded / the previous child's additions are done
     for (int idx = threadIdx.x; idx < ni * nj; idx += kThreads) {
       const int i = ia + idx % ni, j = ja + idx / ni;

@@ -63,6 +63,7 @@ struct CholDev {
   const int32_t* brk_off;    // ns: a tiled supernode's child's breakpoints in tile_brk
   const int32_t* tile_brk;
   const int4* kid_desc;      // per kid slot q: {m of kid[q], rel_off, u_off low, u_off high}
+  const int32_t* kid_brk;    // per kid slot q: brk_off of kid[q]
   const int32_t* fg_ptr;     // forward-solve gather lists (chol_plan.h)
   const int32_t* fg_idx;
   double* Lx;                // the supernodal blocks

@@ -281,7 +281,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   const size_t o_bot = p.take<int32_t>(plan.bot_sn.size() + 1);
   const size_t o_boff = p.take<int32_t>(ns), o_brk = p.take<int32_t>(plan.tile_brk.size());
   const size_t o_fgp = p.take<int32_t>(plan.fg_ptr.size()), o_fgi = p.take<int32_t>(plan.fg_idx.size());
-  const size_t o_kd = p.take<int32_t>(4 * sy.kid.size());
+  const size_t o_kd = p.take<int32_t>(4 * sy.kid.size()), o_kb = p.take<int32_t>(sy.kid.size());
   size_t o_task[5], o_dptr[5], o_dep[5], o_xptr[5], o_xdep[5];
   for (int k = 0; k < 5; ++k) {
     o_task[k] = p.take<int32_t>(graphs[k]->task.size());
@@ -351,6 +351,8 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
       kd[4 * q + 3] = int32_t(uint32_t(uint64_t(uo) >> 32));
     }
     up(o_kd, kd.data(), kd.size() * 4);
+    for (size_t q = 0; q < sy.kid.size(); ++q) kd[q] = plan.brk_off[size_t(sy.kid[q])];
+    up(o_kb, kd.data(), sy.kid.size() * 4);
   }
   for (int k = 0; k < 5; ++k) {
     up(o_task[k], graphs[k]->task.data(), graphs[k]->task.size() * 4);
@@ -395,6 +397,7 @@ acopf_status acopf_chol_create(acopf_model* model, acopf_chol** out) {
   d.brk_off = reinterpret_cast<const int32_t*>(base + o_boff);
   d.tile_brk = reinterpret_cast<const int32_t*>(base + o_brk);
   d.kid_desc = reinterpret_cast<const int4*>(base + o_kd);
+  d.kid_brk = reinterpret_cast<const int32_t*>(base + o_kb);
   d.fg_ptr = reinterpret_cast<const int32_t*>(base + o_fgp);
   d.fg_idx = reinterpret_cast<const int32_t*>(base + o_fgi);
   d.Lx = reinterpret_cast<double*>(base + o_lx);
