@@ -426,6 +426,18 @@ typedef struct {
 } acopf_ipm_result;
 acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* options, double* x_out,
                              double* history, acopf_ipm_result* result, acopf_stream stream);
+/* The same solve with a sparse Cholesky object the caller created for this
+ * model (acopf_chol_create) and keeps: the symbolic phase of the
+ * factorization, most of the setup, is then paid once per network instead
+ * of once per solve (repeated solves on one network: new loads, new set
+ * points).  The object's factor is overwritten; it must not be used by
+ * another call during the solve.  ACOPF_E_INVALID_ARG for a NULL object or
+ * one created for another model; otherwise as acopf_ipm_solve, whose
+ * results it reproduces bit for bit. */
+acopf_status acopf_ipm_solve_chol(acopf_model* model, acopf_chol* chol,
+                                  const acopf_ipm_options* options, double* x_out,
+                                  double* history, acopf_ipm_result* result,
+                                  acopf_stream stream);
 
 /* Pipelined host-buffer evaluation: consecutive acopf_eval_assemble calls of
  * one model with HOST inputs and outputs, whose host-to-device copies,

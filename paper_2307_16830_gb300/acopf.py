@@ -215,6 +215,8 @@ class IpmResult(C.Structure):
 IPM_CONVERGED, IPM_MAX_ITER, IPM_LINE_SEARCH_FAILED, IPM_INERTIA_FAILED = 0, 1, 2, 3
 IPM_INFEASIBLE = 4
 IPM_HISTORY_FIELDS = ("f", "residual", "mu", "theta", "alpha", "alpha_z", "delta_w")
+_ipm_solve_chol = _sig("acopf_ipm_solve_chol", C.c_int32, _vp, _vp, C.POINTER(IpmOptions), _vp,
+                       _vp, C.POINTER(IpmResult), _vp)
 _ipm_solve = _sig("acopf_ipm_solve", C.c_int32, _vp, C.POINTER(IpmOptions), _vp, _vp,
                   C.POINTER(IpmResult), _vp)
 
@@ -237,6 +239,7 @@ EXPORTED = [
     "acopf_pipeline_wait", "acopf_condense", "acopf_recover_step", "acopf_kkt_residual",
     "acopf_chol_create", "acopf_chol_destroy", "acopf_chol_factor", "acopf_chol_solve",
     "acopf_chol_info", "acopf_chol_permutation", "acopf_chol_analyze", "acopf_ipm_solve",
+    "acopf_ipm_solve_chol",
     "acopf_chol_set_trace", "acopf_chol_get_trace",
 ]
 
@@ -833,13 +836,19 @@ def chol_analyze(model: Model, with_perm: bool = False):
 
 
 def ipm_solve(model: Model, tol: float = 1e-4, max_iter: int = 200, mu_init: float = 0.1,
-              stream=None):
-    """Algorithm 1 on the model (acopf_ipm_solve).  Returns (result dict,
-    final x, history array of shape (max_iter + 1, 7))."""
+              stream=None, chol: "Chol | None" = None):
+    """Algorithm 1 on the model (acopf_ipm_solve; with ``chol``, a Cholesky
+    object of this model the caller keeps, acopf_ipm_solve_chol).  Returns
+    (result dict, final x, history array of shape (max_iter + 1, 7))."""
     opts = IpmOptions(float(tol), int(max_iter), float(mu_init))
     res = IpmResult()
     x = np.empty(model.n, dtype=np.float64)
     hist = np.empty((int(max_iter) + 1, len(IPM_HISTORY_FIELDS)), dtype=np.float64)
-    _check(_ipm_solve(model.handle, C.byref(opts), x.ctypes.data, hist.ctypes.data, C.byref(res),
-                      _stream(stream)), "acopf_ipm_solve")
+    if chol is None:
+        _check(_ipm_solve(model.handle, C.byref(opts), x.ctypes.data, hist.ctypes.data,
+                          C.byref(res), _stream(stream)), "acopf_ipm_solve")
+    else:
+        _check(_ipm_solve_chol(model.handle, chol._h, C.byref(opts), x.ctypes.data,
+                               hist.ctypes.data, C.byref(res), _stream(stream)),
+               "acopf_ipm_solve_chol")
     return {k: getattr(res, k) for k, _ in res._fields_}, x, hist

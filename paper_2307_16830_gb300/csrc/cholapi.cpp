@@ -215,6 +215,10 @@ cudaError_t run_recorded(cudaGraphExec_t& exec, bool reuse, cudaStream_t s, Reco
 
 }  // namespace
 
+namespace acopf {
+acopf_model* chol_model(const acopf_chol* c) { return c->model; }
+}  // namespace acopf
+
 extern "C" {
 
 acopf_status acopf_chol_analyze(acopf_model* model, acopf_chol_stats* stats,

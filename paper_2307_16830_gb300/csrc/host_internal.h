@@ -111,6 +111,8 @@ void free_step(acopf_model* m);
 // Builds the Jacobian's row and column lists and the row scratch of the
 // condensation (m->step), once (stepapi.cpp).
 acopf_status step_lists(acopf_model* m);
+// The model a Cholesky object was created for.
+acopf_model* chol_model(const acopf_chol* c);
 
 // Validates the scalar arguments of an evaluation.
 acopf_status check_eval_scalars(double obj_weight, double delta_w, double delta_c);

@@ -75,8 +75,12 @@ struct Buffers {
 
 extern "C" {
 
-acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* options, double* x_out,
-                             double* history, acopf_ipm_result* result, acopf_stream stream) {
+// The solve; `given`: a Cholesky object of this model to use (the caller's),
+// or NULL to create one for this solve.
+static acopf_status ipm_solve_impl(acopf_model* model, acopf_chol* given,
+                                   const acopf_ipm_options* options, double* x_out,
+                                   double* history, acopf_ipm_result* result,
+                                   acopf_stream stream) {
   if (!model || !options || !result)
     return fail(ACOPF_E_INVALID_ARG, "acopf_ipm_solve: null pointer");
   if (model->device < 0) return fail(ACOPF_E_NO_DEVICE, "acopf_ipm_solve: host-only model");
@@ -190,13 +194,17 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   up(v.s, hs);
   if (e != cudaSuccess) return cuda_fail(e, "acopf_ipm_solve: slacks");
 
-  acopf_chol* chol = nullptr;
-  st = acopf_chol_create(model, &chol);
-  if (st != ACOPF_OK) return st;
+  acopf_chol* chol = given;
+  if (!chol) {
+    st = acopf_chol_create(model, &chol);
+    if (st != ACOPF_OK) return st;
+  }
   struct CholGuard {
     acopf_chol* c;
-    ~CholGuard() { acopf_chol_destroy(c); }
-  } guard{chol};
+    ~CholGuard() {
+      if (c) acopf_chol_destroy(c);
+    }
+  } guard{given ? nullptr : chol};
 
   // ---- helpers ---------------------------------------------------------------
   acopf_iterate it{};
@@ -607,6 +615,22 @@ acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* option
   result->seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   return ACOPF_OK;
+}
+
+acopf_status acopf_ipm_solve(acopf_model* model, const acopf_ipm_options* options, double* x_out,
+                             double* history, acopf_ipm_result* result, acopf_stream stream) {
+  return ipm_solve_impl(model, nullptr, options, x_out, history, result, stream);
+}
+
+acopf_status acopf_ipm_solve_chol(acopf_model* model, acopf_chol* chol,
+                                  const acopf_ipm_options* options, double* x_out,
+                                  double* history, acopf_ipm_result* result,
+                                  acopf_stream stream) {
+  if (!model || !chol) return fail(ACOPF_E_INVALID_ARG, "acopf_ipm_solve_chol: null pointer");
+  if (acopf::chol_model(chol) != model)
+    return fail(ACOPF_E_INVALID_ARG,
+                "acopf_ipm_solve_chol: the Cholesky object was made for another model");
+  return ipm_solve_impl(model, chol, options, x_out, history, result, stream);
 }
 
 }  // extern "C"

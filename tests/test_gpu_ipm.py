@@ -109,6 +109,36 @@ def test_ipm_rejects_bad_arguments(acopf):
             assert e.value.status == acopf.E_INVALID_ARG
 
 
+def test_ipm_with_a_kept_cholesky_object_reproduces_the_solve(acopf):
+    """acopf_ipm_solve_chol: the caller's Cholesky object, kept over two
+    solves, gives the plain solve's iterates bit for bit, without the
+    symbolic phase in the setup; another model's object is refused."""
+    g = synth.workload_grid("10kbus-geo-opf")
+    with acopf.model_create(g, 0) as m:
+        r0, x0, h0 = acopf.ipm_solve(m, tol=1e-4, max_iter=200)
+        ch = acopf.chol_create(m)
+        try:
+            runs = [acopf.ipm_solve(m, tol=1e-4, max_iter=200, chol=ch) for _ in range(2)]
+        finally:
+            ch.close()
+    assert r0["status"] == acopf.IPM_CONVERGED
+    for r, x, h in runs:
+        assert (r["status"], r["iterations"]) == (r0["status"], r0["iterations"])
+        assert np.array_equal(x, x0)
+        assert np.array_equal(np.nan_to_num(h, nan=-1.0), np.nan_to_num(h0, nan=-1.0))
+        assert r["objective"] == r0["objective"]
+    assert runs[1][0]["setup_seconds"] < r0["setup_seconds"], (runs[1][0], r0)
+    g30 = synth.workload_grid("30bus-opf")
+    with acopf.model_create(g30, 0) as a, acopf.model_create(g30, 0) as b:
+        ch = acopf.chol_create(a)
+        try:
+            with pytest.raises(acopf.AcopfError) as e:
+                acopf.ipm_solve(b, chol=ch)
+            assert e.value.status == acopf.E_INVALID_ARG
+        finally:
+            ch.close()
+
+
 def test_ipm_10k_near_planar_matches_oracle(acopf):
     """The 10,000-bus near-planar short-line network: both converge to the
     same point (objective within 1e-7 relative, x within 1e-4) in iteration
